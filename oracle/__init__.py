@@ -1,0 +1,147 @@
+"""Oracle for the EVIS event-synthesis path — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  The product (``paper_2607_08098_b300``) never imports it and fails
+loudly when its CUDA library is missing.
+
+The arithmetic lives in ``evis_oracle.cpp`` (single-threaded C++17, ``-O2 -ffp-contract=off``);
+this file only compiles it and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "evis_oracle.cpp")
+_SO = os.path.join(_HERE, "libevis_oracle.so")
+_lib = None
+
+IN_LOG, IN_LUM, IN_RGB = 0, 1, 2
+MODE_B_PRIMARY = 0x10
+TIE_INDEX = 0x20
+
+EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2"), ("p", "<i2")])
+
+
+class _Env(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("c_on", ctypes.c_float), ("c_off", ctypes.c_float),
+                ("c_on_map", ctypes.c_void_p), ("c_off_map", ctypes.c_void_p),
+                ("refractory_ns", ctypes.c_int64), ("t0_ns", ctypes.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (g++, host only, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", _SRC, "-o", _SO])
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        lib.orc_create.restype = ctypes.c_void_p
+        lib.orc_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_uint32]
+        lib.orc_destroy.argtypes = [ctypes.c_void_p]
+        lib.orc_step.restype = ctypes.c_int32
+        lib.orc_step.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64] + [ctypes.c_void_p] * 2
+        lib.orc_num_events.restype = ctypes.c_int64
+        lib.orc_num_events.argtypes = [ctypes.c_void_p]
+        lib.orc_take_events.restype = ctypes.c_int64
+        lib.orc_take_events.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+        lib.orc_get_state.restype = ctypes.c_int32
+        lib.orc_get_state.argtypes = [ctypes.c_void_p] * 4
+        lib.orc_log_intensity.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_float, ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class Oracle:
+    """One oracle context over a list of ``scenes.EnvScene``-like environments."""
+
+    def __init__(self, envs, eps: float = 1e-4, flags: int = 0):
+        lib = _load()
+        self._keep = []
+        arr = (_Env * len(envs))()
+        for i, e in enumerate(envs):
+            con = coff = None
+            if getattr(e, "c_on_map", None) is not None:
+                con = np.ascontiguousarray(e.c_on_map, dtype=np.float32)
+                coff = np.ascontiguousarray(e.c_off_map, dtype=np.float32)
+                self._keep += [con, coff]
+            arr[i] = _Env(e.W, e.H, e.K, e.c_on, e.c_off, _ptr(con), _ptr(coff),
+                          int(e.refractory_ns), int(e.t0_ns))
+        self._h = lib.orc_create(ctypes.addressof(arr), len(envs), float(eps), int(flags))
+        if not self._h:
+            raise ValueError("oracle rejected the environment table")
+        self.envs = list(envs)
+        self.total = 0
+        self.offsets = []
+        for e in envs:
+            self.offsets.append(self.total)
+            self.total += (e.H * e.W + 3) // 4 * 4
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.orc_destroy(self._h)
+            self._h = None
+
+    def trace_sizes(self):
+        nk = sum(e.K * 2 * e.H * e.W for e in self.envs)
+        nl = sum(e.K * e.H * e.W for e in self.envs)
+        return nk, nl
+
+    def step(self, frames, mv, depth, dt_ns: int, trace: bool = False):
+        frames = np.ascontiguousarray(frames, dtype=np.float32)
+        mv = np.ascontiguousarray(mv, dtype=np.float32)
+        depth = np.ascontiguousarray(depth, dtype=np.float32)
+        keys = lint = None
+        if trace:
+            nk, nl = self.trace_sizes()
+            keys = np.empty(nk, dtype=np.uint64)
+            lint = np.empty(nl, dtype=np.float32)
+        rc = _lib.orc_step(self._h, _ptr(frames), _ptr(mv), _ptr(depth), int(dt_ns), _ptr(keys),
+                           _ptr(lint))
+        if rc != 0:
+            raise ValueError("oracle step rejected its arguments")
+        return (keys, lint) if trace else None
+
+    def events(self) -> np.ndarray:
+        n = _lib.orc_num_events(self._h)
+        out = np.empty(n, dtype=EVENT_DTYPE)
+        got = _lib.orc_take_events(self._h, _ptr(out), n)
+        return out[:got]
+
+    def state(self):
+        Lref = np.empty(self.total, dtype=np.float32)
+        tl = np.empty(self.total, dtype=np.int64)
+        clk = np.empty(len(self.envs), dtype=np.int64)
+        _lib.orc_get_state(self._h, _ptr(Lref), _ptr(tl), _ptr(clk))
+        return Lref, tl, clk
+
+
+def log_intensity(x, mode: int = IN_LUM, eps: float = 1e-4) -> np.ndarray:
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n = x.size // 3 if mode == IN_RGB else x.size
+    out = np.empty(n, dtype=np.float32)
+    lib.orc_log_intensity(_ptr(x), n, mode, float(eps), _ptr(out))
+    return out
+
+
+def sort_events(ev: np.ndarray) -> np.ndarray:
+    """Canonical order used by every parity comparison: (env, t, y, x, p)."""
+    idx = np.lexsort((ev["p"], ev["x"], ev["y"], ev["t"], ev["env"]))
+    return ev[idx]

@@ -1,0 +1,397 @@
+// EVIS event-synthesis ORACLE — test infrastructure, not the product.
+//
+// A plain, slow, single-threaded C++17 restatement of the data-parallel path of EVIS
+// ("bidirectional motion-vector warping with depth splatting" followed by the "HDR event
+// formation model").  Only the tests, the smoke check and the benchmark's CPU-baseline leg
+// load it; the CUDA library never does, and this file shares no code, header or constant
+// table with it.  Compiled with -O2 -ffp-contract=off so every float operation below is one
+// IEEE-754 binary32 operation rounded to nearest (no fused multiply-add), which is the
+// operation order the CUDA kernels must reproduce bit for bit.
+//
+// Precision: the decisions the method takes (z-buffer argmin, event count floor) are taken
+// in binary32 on both sides; timestamps use one binary64 multiply and llrint.  The paper
+// fixes no precision.
+//
+// Parity status: every function below is pinned by a test under tests/ (brute force,
+// closed forms or invariants) except the full event stream of a textured scene, which has
+// nothing but this oracle to compare against (parity unpinned beyond these pins).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+// Flag bits of the oracle's configuration word (same numeric meaning as the library's).
+constexpr uint32_t IN_MASK = 0x3u, IN_LOG = 0u, IN_LUM = 1u, IN_RGB = 2u;
+constexpr uint32_t MODE_B_PRIMARY = 0x10u;  // Sec. 3.3: B primary, A only fills B's holes
+constexpr uint32_t TIE_INDEX = 0x20u;       // key = (depth, source index), no weight field
+
+constexpr uint64_t EMPTY = ~0ull;
+constexpr int MAX_CROSSINGS = 4096;          // per pixel per substep
+constexpr int64_t NO_EVENT = std::numeric_limits<int64_t>::min();
+
+struct Env {
+  int W, H, K;
+  float c_on, c_off;
+  int64_t refractory_ns, t0_ns;
+  bool has_map;
+};
+
+struct Event {  // 16 bytes: t, x, y, env, polarity
+  int64_t t_ns;
+  uint16_t x, y, env;
+  int16_t p;
+};
+
+struct Ctx {
+  std::vector<Env> envs;
+  std::vector<int64_t> off;   // packed pixel offsets (H*W rounded up to 4)
+  int64_t total = 0;
+  float eps = 1e-4f;
+  uint32_t flags = 0;
+  bool have_A = false;
+  std::vector<float> LA, mvA, ZA;          // retained keyframe A (Sec. 3.3 needs A and B)
+  std::vector<float> Lref;                 // per-pixel reference level (Sec. 3.2)
+  std::vector<int64_t> t_last;             // last emitted event time (refractory, Sec. 3.4)
+  std::vector<float> con, coff;            // per-pixel thresholds (Eq. 8), if any env has them
+  std::vector<int64_t> clock;              // time of keyframe A per env
+  std::vector<Event> events;
+};
+
+inline bool valid_depth(float z) { return z > 0.0f && z < INFINITY; }
+
+inline uint32_t float_bits(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  return u;
+}
+
+// Eq. 3 (Rec. 709 luminance) and L = log(I + eps) (Sec. 3.2).  The log is taken in binary64
+// and rounded once; non-positive or NaN arguments are clamped to the smallest normal float.
+float log_intensity(float I, float eps) {
+  float s = I + eps;
+  if (!(s > 0.0f)) s = std::numeric_limits<float>::min();
+  return static_cast<float>(std::log(static_cast<double>(s)));
+}
+
+float rec709(float R, float G, float B) {
+  float a = 0.2126f * R;
+  float b = 0.7152f * G;
+  float c = 0.0722f * B;
+  return (a + b) + c;
+}
+
+// Bilinear footprint z-test splat of one source (Sec. 3.3, Eq. 6).  The target q is spread
+// over the integer pixels around it; a pixel belongs to the footprint iff its bilinear weight
+// is > 0 and it lies inside the image.  The z-buffer keeps the smallest 64-bit key
+// [depth bits | quantised (1 - weight) | source index]: nearest surface first, then the larger
+// bilinear weight, then the lower source index.
+void splat_source(uint64_t* zbuf, int W, int H, float qx, float qy, float Zt, uint32_t src,
+                  bool tie_index) {
+  // No footprint pixel can be inside unless -1 < q < size; this also rejects NaN.
+  if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H)))
+    return;
+  float fx0 = std::floor(qx), fy0 = std::floor(qy);
+  float ax = qx - fx0, ay = qy - fy0;
+  int x0 = static_cast<int>(fx0), y0 = static_cast<int>(fy0);
+  float wx[2] = {1.0f - ax, ax};
+  float wy[2] = {1.0f - ay, ay};
+  uint64_t hi = static_cast<uint64_t>(float_bits(Zt)) << 32;
+  for (int dy = 0; dy < 2; ++dy) {
+    for (int dx = 0; dx < 2; ++dx) {
+      float w = wx[dx] * wy[dy];
+      int cx = x0 + dx, cy = y0 + dy;
+      if (!(w > 0.0f) || cx < 0 || cx >= W || cy < 0 || cy >= H) continue;
+      uint32_t wq = 0;
+      if (!tie_index) {
+        uint32_t v = static_cast<uint32_t>((1.0f - w) * 256.0f);
+        wq = v < 255u ? v : 255u;
+      }
+      uint64_t key = hi | (static_cast<uint64_t>(wq) << 24) | src;
+      uint64_t& slot = zbuf[static_cast<size_t>(cy) * W + cx];
+      if (key < slot) slot = key;
+    }
+  }
+}
+
+// Depth of the other keyframe at the correspondence endpoint (Eq. 7 needs Z_A(p_A) and
+// Z_B(p_B)): nearest pixel, rounding half up; the source's own depth when the endpoint
+// falls outside the image or has no valid depth.
+float other_depth(const float* Zother, int W, int H, float ux, float uy, float own) {
+  float nx = std::floor(ux + 0.5f), ny = std::floor(uy + 0.5f);
+  if (!(nx >= 0.0f && nx <= static_cast<float>(W - 1) && ny >= 0.0f &&
+        ny <= static_cast<float>(H - 1)))
+    return own;
+  float z = Zother[static_cast<size_t>(ny) * W + static_cast<size_t>(nx)];
+  return valid_depth(z) ? z : own;
+}
+
+// Splat every source of keyframe A forward (q_A = p - f m_A, Eq. 5) with
+// Z~ = (1-f) Z_A(p) + f Z_B(p - m_A(p)) (Eq. 7; m_A reused as the forward velocity).
+void splat_A(uint64_t* zbuf, int W, int H, const float* mvA, const float* ZA, const float* ZB,
+             float f, float g, bool tie_index) {
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      size_t p = static_cast<size_t>(y) * W + x;
+      float zs = ZA[p];
+      if (!valid_depth(zs)) continue;
+      float mx = mvA[2 * p], my = mvA[2 * p + 1];
+      float qx = static_cast<float>(x) - f * mx;
+      float qy = static_cast<float>(y) - f * my;
+      float zo = other_depth(ZB, W, H, static_cast<float>(x) - mx, static_cast<float>(y) - my, zs);
+      float zt = g * zs + f * zo;
+      splat_source(zbuf, W, H, qx, qy, zt, static_cast<uint32_t>(p), tie_index);
+    }
+  }
+}
+
+// Splat every source of keyframe B backward (q_B = p + (1-f) m_B, Eq. 5) with
+// Z~ = (1-f) Z_A(p + m_B(p)) + f Z_B(p) (Eq. 7; m_B is the exact B->A correspondence).
+void splat_B(uint64_t* zbuf, int W, int H, const float* mvB, const float* ZA, const float* ZB,
+             float f, float g, bool tie_index) {
+  for (int y = 0; y < H; ++y) {
+    for (int x = 0; x < W; ++x) {
+      size_t p = static_cast<size_t>(y) * W + x;
+      float zs = ZB[p];
+      if (!valid_depth(zs)) continue;
+      float mx = mvB[2 * p], my = mvB[2 * p + 1];
+      float qx = static_cast<float>(x) + g * mx;
+      float qy = static_cast<float>(y) + g * my;
+      float zo = other_depth(ZA, W, H, static_cast<float>(x) + mx, static_cast<float>(y) + my, zs);
+      float zt = g * zo + f * zs;
+      splat_source(zbuf, W, H, qx, qy, zt, static_cast<uint32_t>(p), tie_index);
+    }
+  }
+}
+
+// Threshold crossings of one pixel at one substep (Eq. 4 and the reference update of
+// Sec. 3.2, with the per-pixel thresholds of Eq. 8 and the refractory period of Sec. 3.4).
+// Each crossed level Lref + p k theta is timestamped by linear interpolation between the
+// previous defined sample (t_prev, L_prev) and this one (t_i, L).
+void cross_pixel(Ctx& c, int env, int x, int y, float L, float& Lref, float& Lprev,
+                 int64_t& tprev, int64_t ti, int64_t& tlast, float th_on, float th_off,
+                 int64_t refr) {
+  float d = L - Lref;
+  int pol = d > 0.0f ? 1 : -1;
+  float th = pol > 0 ? th_on : th_off;
+  float q = std::fabs(d) / th;
+  int n = 0;
+  if (q >= 1.0f) n = q >= static_cast<float>(MAX_CROSSINGS) ? MAX_CROSSINGS
+                                                            : static_cast<int>(std::floor(q));
+  float lev = Lref;
+  for (int k = 1; k <= n; ++k) {
+    lev = Lref + static_cast<float>(pol * k) * th;
+    float num = lev - Lprev;
+    float den = L - Lprev;
+    float fr = den == 0.0f ? 1.0f : num / den;
+    if (!(fr > 0.0f)) fr = 0.0f;
+    else if (fr > 1.0f) fr = 1.0f;
+    int64_t t = tprev + std::llrint(static_cast<double>(fr) * static_cast<double>(ti - tprev));
+    if (refr <= 0 || tlast == NO_EVENT || t - tlast >= refr) {
+      c.events.push_back(Event{t, static_cast<uint16_t>(x), static_cast<uint16_t>(y),
+                               static_cast<uint16_t>(env), static_cast<int16_t>(pol)});
+      tlast = t;
+    }
+  }
+  if (n > 0) Lref = lev;  // keeps the sub-threshold residual (Sec. 3.2)
+  Lprev = L;
+  tprev = ti;
+}
+
+// One keyframe gap of one environment: K substeps f = i/K (Sec. 3.3), each a bidirectional
+// splat, a time blend with hole filling, and the event model.  Optional trace outputs:
+// keys[(i-1)*2 + dir][p] and Lint[(i-1)][p] (NaN where the pixel got no sample).
+void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB, int64_t dt,
+              uint64_t* keys, float* Lint) {
+  const Env& en = c.envs[e];
+  const int W = en.W, H = en.H, K = en.K;
+  const size_t HW = static_cast<size_t>(W) * H;
+  const size_t o = static_cast<size_t>(c.off[e]);
+  const float* LA = c.LA.data() + o;
+  const float* mvA = c.mvA.data() + 2 * o;
+  const float* ZA = c.ZA.data() + o;
+  float* Lref = c.Lref.data() + o;
+  int64_t* tlast = c.t_last.data() + o;
+  const int64_t T0 = c.clock[e];
+  const bool tie_index = (c.flags & TIE_INDEX) != 0;
+  const bool b_primary = (c.flags & MODE_B_PRIMARY) != 0;
+
+  std::vector<float> Lprev(LA, LA + HW);
+  std::vector<int64_t> tprev(HW, T0);
+  std::vector<uint64_t> zA(HW), zB(HW);
+  for (int i = 1; i <= K; ++i) {
+    float f = static_cast<float>(i) / static_cast<float>(K);
+    float g = 1.0f - f;
+    int64_t ti = T0 + (static_cast<int64_t>(i) * dt) / K;
+    std::fill(zA.begin(), zA.end(), EMPTY);
+    std::fill(zB.begin(), zB.end(), EMPTY);
+    splat_A(zA.data(), W, H, mvA, ZA, ZB, f, g, tie_index);
+    splat_B(zB.data(), W, H, mvB, ZA, ZB, f, g, tie_index);
+    if (keys) {
+      std::memcpy(keys + (static_cast<size_t>(i - 1) * 2) * HW, zA.data(), HW * 8);
+      std::memcpy(keys + (static_cast<size_t>(i - 1) * 2 + 1) * HW, zB.data(), HW * 8);
+    }
+    for (int y = 0; y < H; ++y) {
+      for (int x = 0; x < W; ++x) {
+        size_t t = static_cast<size_t>(y) * W + x;
+        bool hasA = zA[t] != EMPTY, hasB = zB[t] != EMPTY;
+        float la = hasA ? LA[zA[t] & 0xFFFFFFu] : 0.0f;
+        float lb = hasB ? LB[zB[t] & 0xFFFFFFu] : 0.0f;
+        float L;
+        if (b_primary) {  // Sec. 3.3: backward-warped B is primary, A fills B's holes
+          if (hasB) L = lb;
+          else if (hasA) L = la;
+          else L = NAN;
+        } else {          // time blend of both directions, hole filled from the other one
+          if (hasA && hasB) L = g * la + f * lb;
+          else if (hasA) L = la;
+          else if (hasB) L = lb;
+          else L = NAN;
+        }
+        if (Lint) Lint[static_cast<size_t>(i - 1) * HW + t] = L;
+        if (!hasA && !hasB) continue;  // no sample this substep: the pixel holds its state
+        float th_on = en.c_on, th_off = en.c_off;
+        if (en.has_map) {
+          th_on = c.con[o + t];
+          th_off = c.coff[o + t];
+        }
+        cross_pixel(c, e, x, y, L, Lref[t], Lprev[t], tprev[t], ti, tlast[t], th_on, th_off,
+                    en.refractory_ns);
+      }
+    }
+  }
+}
+
+void to_log(const Ctx& c, const float* frames, std::vector<float>& L) {
+  L.assign(c.total, 0.0f);
+  uint32_t mode = c.flags & IN_MASK;
+  for (size_t e = 0; e < c.envs.size(); ++e) {
+    size_t o = static_cast<size_t>(c.off[e]);
+    size_t n = static_cast<size_t>(c.envs[e].W) * c.envs[e].H;
+    for (size_t p = o; p < o + n; ++p) {
+      if (mode == IN_LOG) L[p] = frames[p];
+      else if (mode == IN_LUM) L[p] = log_intensity(frames[p], c.eps);
+      else L[p] = log_intensity(rec709(frames[3 * p], frames[3 * p + 1], frames[3 * p + 2]), c.eps);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+typedef struct {
+  int32_t width, height, K;
+  float c_on, c_off;
+  const float* c_on_map;   // optional host [H*W]
+  const float* c_off_map;
+  int64_t refractory_ns;
+  int64_t t0_ns;
+} orc_env;
+
+// Returns a new oracle context or null on invalid arguments.
+void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags) {
+  if (!envs || n_envs <= 0 || n_envs > 65536 || !(eps >= 0.0f)) return nullptr;
+  if ((flags & IN_MASK) == 3u) return nullptr;
+  Ctx* c = new Ctx();
+  c->eps = eps;
+  c->flags = flags;
+  bool any_map = false;
+  for (int i = 0; i < n_envs; ++i) {
+    const orc_env& d = envs[i];
+    if (d.width <= 0 || d.height <= 0 || d.width > 65535 || d.height > 65535 ||
+        static_cast<int64_t>(d.width) * d.height > (1 << 24) || d.K < 1 ||
+        !(d.c_on > 0.0f) || !(d.c_off > 0.0f) || d.refractory_ns < 0 ||
+        ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))) {
+      delete c;
+      return nullptr;
+    }
+    c->envs.push_back(Env{d.width, d.height, d.K, d.c_on, d.c_off, d.refractory_ns, d.t0_ns,
+                          d.c_on_map != nullptr});
+    c->off.push_back(c->total);
+    c->total += (static_cast<int64_t>(d.width) * d.height + 3) / 4 * 4;
+    any_map |= d.c_on_map != nullptr;
+  }
+  if (any_map) {
+    c->con.assign(c->total, 0.0f);
+    c->coff.assign(c->total, 0.0f);
+    for (int i = 0; i < n_envs; ++i) {
+      if (!envs[i].c_on_map) continue;
+      size_t n = static_cast<size_t>(envs[i].width) * envs[i].height;
+      std::memcpy(c->con.data() + c->off[i], envs[i].c_on_map, n * 4);
+      std::memcpy(c->coff.data() + c->off[i], envs[i].c_off_map, n * 4);
+    }
+  }
+  c->Lref.assign(c->total, 0.0f);
+  c->t_last.assign(c->total, NO_EVENT);
+  for (int i = 0; i < n_envs; ++i) c->clock.push_back(envs[i].t0_ns);
+  return c;
+}
+
+void orc_destroy(void* h) { delete static_cast<Ctx*>(h); }
+
+// One keyframe (host arrays in the packed layout).  The first call only sets the reference
+// level to the keyframe's log-intensity; each later call synthesises the K substeps between
+// the retained keyframe and this one and appends the events.  Trace pointers (optional)
+// receive, per env in order, K*2*H*W keys and K*H*W interpolated values.
+int32_t orc_step(void* h, const float* frames, const float* mv, const float* depth,
+                 int64_t dt_ns, uint64_t* trace_keys, float* trace_L) {
+  Ctx& c = *static_cast<Ctx*>(h);
+  if (!frames || !mv || !depth || dt_ns <= 0) return 1;
+  std::vector<float> LB;
+  to_log(c, frames, LB);
+  if (!c.have_A) {
+    c.Lref = LB;
+    c.LA = LB;
+    c.mvA.assign(mv, mv + 2 * c.total);
+    c.ZA.assign(depth, depth + c.total);
+    c.have_A = true;
+    return 0;
+  }
+  size_t tk = 0, tl = 0;
+  for (size_t e = 0; e < c.envs.size(); ++e) {
+    size_t o = static_cast<size_t>(c.off[e]);
+    size_t HW = static_cast<size_t>(c.envs[e].W) * c.envs[e].H;
+    run_pair(c, static_cast<int>(e), LB.data() + o, mv + 2 * o, depth + o, dt_ns,
+             trace_keys ? trace_keys + tk : nullptr, trace_L ? trace_L + tl : nullptr);
+    tk += static_cast<size_t>(c.envs[e].K) * 2 * HW;
+    tl += static_cast<size_t>(c.envs[e].K) * HW;
+    c.clock[e] += dt_ns;
+  }
+  c.LA = LB;
+  c.mvA.assign(mv, mv + 2 * c.total);
+  c.ZA.assign(depth, depth + c.total);
+  return 0;
+}
+
+int64_t orc_num_events(void* h) { return static_cast<int64_t>(static_cast<Ctx*>(h)->events.size()); }
+
+// Moves up to cap events (16 bytes each) into dst in emission order; returns the count.
+int64_t orc_take_events(void* h, void* dst, int64_t cap) {
+  Ctx& c = *static_cast<Ctx*>(h);
+  int64_t n = static_cast<int64_t>(c.events.size());
+  if (n > cap) n = cap;
+  std::memcpy(dst, c.events.data(), static_cast<size_t>(n) * sizeof(Event));
+  c.events.erase(c.events.begin(), c.events.begin() + n);
+  return n;
+}
+
+// Copies the per-pixel state out (any pointer may be null).
+int32_t orc_get_state(void* h, float* Lref, int64_t* t_last, int64_t* clocks) {
+  Ctx& c = *static_cast<Ctx*>(h);
+  if (Lref) std::memcpy(Lref, c.Lref.data(), c.Lref.size() * 4);
+  if (t_last) std::memcpy(t_last, c.t_last.data(), c.t_last.size() * 8);
+  if (clocks) std::memcpy(clocks, c.clock.data(), c.clock.size() * 8);
+  return 0;
+}
+
+// a1 alone: log-intensity of n linear (mode 1) or RGB (mode 2) samples.
+void orc_log_intensity(const float* in, int64_t n, int32_t mode, float eps, float* out) {
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = mode == 2 ? log_intensity(rec709(in[3 * i], in[3 * i + 1], in[3 * i + 2]), eps)
+                       : log_intensity(in[i], eps);
+}
+
+}  // extern "C"
