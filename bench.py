@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the EVIS event-synthesis hot path on B300.
+
+Workload (default): 64 environments at 346x260, K = 16 sub-frames per keyframe gap,
+C = 0.25, refractory period 100 us, fp32, three depth layers per environment with seeded
+random rigid motions (synthetic scenes; no dataset).  Inputs are linear radiance, motion
+vectors and depth, resident in HBM, so the log conversion is part of the timed path.
+
+One step = one keyframe gap of every environment: the input-preparation kernel (log,
+motion bound) and the synthesis kernel (bidirectional splat, z-buffer, blend, threshold
+crossings, event compaction).  Metric: Mpixel-substeps/s (sum over environments of
+H * W * K per step / time); events/s is reported beside it.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl evis|reference]
+
+Under torchrun each rank runs its own 64 environments (disjoint seeds, no data exchange:
+weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel-substeps/s"
+UNIT = "Mpx-substeps/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["evis", "reference"], default="evis")
+    ap.add_argument("--envs", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-envs", type=int, default=6, help="oracle sample size (environments)")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(n_envs, rank):
+    import scenes
+    return scenes.config2(n_envs=n_envs, first_env=rank * n_envs)
+
+
+def config_block(w, n_envs):
+    return {"workload": f"{n_envs} envs at 346x260, K=16, C=0.25, refractory 100us, "
+                        "3 depth layers, linear-radiance inputs",
+            "envs": n_envs, "width": 346, "height": 260, "K": 16, "C": 0.25,
+            "refractory_ns": 100_000, "dt_ns": w.dt_ns, "input": "linear luminance (log on path)",
+            "pixel_substeps_per_step": w.pixel_substeps,
+            "l2": "flushed between timed steps (256 MB write); each step also reads a fresh keyframe"}
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(device_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline and reference arm: the oracle on a bounded sample
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample_rate(n_envs, n_steps, rank=0):
+    """Times the oracle (single thread) on n_envs environments for n_steps keyframe gaps.
+    Returns (Mpx-substeps/s, events/s, seconds, description)."""
+    import oracle
+    import scenes
+    w = scenes.config2(n_envs=n_envs, first_env=rank * n_envs)
+    kfs = [scenes.render(w.envs, k) for k in range(n_steps + 1)]
+    o = oracle.Oracle(w.envs, eps=1e-4, flags=oracle.IN_LUM)
+    o.step(kfs[0].I, kfs[0].mv, kfs[0].Z, w.dt_ns)
+    t0 = time.perf_counter()
+    for kf in kfs[1:]:
+        o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
+    sec = time.perf_counter() - t0
+    nev = len(o.events())
+    return (w.pixel_substeps * n_steps / sec / 1e6, nev / sec, sec,
+            f"{n_envs} of the environments x {n_steps} keyframe gaps (same scenes, same K, C, "
+            f"refractory), single-threaded C++ oracle")
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    per_step_envs = 2
+    import oracle
+    import scenes
+    w = scenes.config2(n_envs=per_step_envs)
+    n_kf = args.warmup + args.steps + 1
+    kfs = [scenes.render(w.envs, k) for k in range(n_kf)]
+    o = oracle.Oracle(w.envs, eps=1e-4, flags=oracle.IN_LUM)
+    o.step(kfs[0].I, kfs[0].mv, kfs[0].Z, w.dt_ns)
+    for kf in kfs[1:1 + args.warmup]:
+        o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
+    o.events()
+    t0 = time.perf_counter()
+    for kf in kfs[1 + args.warmup:]:
+        o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
+    sec = time.perf_counter() - t0
+    nev = len(o.events())
+    value = w.pixel_substeps * args.steps / sec / 1e6
+    sample = (f"each step: {per_step_envs} of the 64 environments (346x260, K=16) for one "
+              f"keyframe gap, single-threaded C++ oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_block(scenes.config2(), 64),
+            "events_per_s": nev / sec,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# the CUDA path
+# ------------------------------------------------------------------------------------------
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def traffic_record():
+    """ncu DRAM bytes per launch of the synthesis kernel, if a capture of the current kernel
+    source was committed (profiles/step_kernel_traffic.json), else None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2607_08098_b300", "csrc", "evis_kernels.cu")
+    try:
+        rec = json.load(open(p))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("kernel_sha256") == h:
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def evis_arm(args, world, rank, local):
+    import torch
+    import paper_2607_08098_b300 as ev
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args.envs, rank)
+    n_kf = args.warmup + args.steps + 1
+    kfs = [None] * n_kf
+
+    import scenes
+    dev = []
+    for k in range(n_kf):
+        kf = scenes.render(w.envs, k, want=("I", "mv", "Z"))
+        dev.append(tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)))
+        kfs[k] = kf if k < 2 else None
+    flags = ev.IN_LUM | ev.KEEP_INPUTS
+    # size the event buffer from one keyframe gap
+    probe = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=1 << 27)
+    probe.step(*dev[0], w.dt_ns)
+    probe.step(*dev[1], w.dt_ns)
+    per_step = probe.event_count()
+    probe.close()
+    capacity = int(per_step * 1.5 * (args.steps + 1)) + (1 << 20)
+    ctx = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=capacity)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    ctx.step(*dev[0], w.dt_ns)                      # first keyframe: reference levels only
+    for k in range(1, 1 + args.warmup):
+        flush.zero_()
+        ctx.step(*dev[k], w.dt_ns)
+    ctx.clear_events()
+    ctx.profile(args.steps)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()                               # L2 flush between timed steps
+        starts[s].record(stream)
+        ctx.step(*dev[1 + args.warmup + s], w.dt_ns)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    n_events = ctx.event_count()
+    if n_events > capacity:
+        raise RuntimeError("event buffer overflow in the timed region")
+    prof = ctx.profile_read()
+    syn_ms = float(prof[:, 1].mean())
+    prep_ms = float(prof[:, 0].mean())
+    ctx.close()
+
+    total_units = w.pixel_substeps * args.steps
+    if dist:
+        t = torch.tensor([total_ms, float(total_units), float(n_events)], device="cuda",
+                         dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_ms, total_units, n_events = float(mx[0]), float(sm[1]), float(sm[2])
+    value = total_units / (total_ms / 1e3) / 1e6
+    events_per_s = n_events / (total_ms / 1e3)
+
+    # roofline of the synthesis kernel: algorithmic bytes per launch / its mean duration
+    px = w.pixels
+    ev_per_step = n_events / args.steps / max(world, 1)
+    alg_bytes = px * (32 + 8 + 16) + ev_per_step * 16
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / (syn_ms / 1e3) / 1e9
+    tr = traffic_record()
+    roofline = {"kernel": "step_kernel (splat + z-buffer + blend + crossings + compaction)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "traffic": None if tr is None else tr["dram_bytes_per_launch_scaled"],
+                "kernel_ms": syn_ms, "prep_ms": prep_ms}
+
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = e2e_leg(ev, w, dev, args, capacity=int(per_step * 1.5) + (1 << 20))
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        r, evs, sec, desc = oracle_sample_rate(args.cpu_envs, 2)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": sec, "events_per_s": evs}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded layered scenes; the paper's scenes are not available)",
+            "config": config_block(w, args.envs), "events_per_s": events_per_s,
+            "events_per_step": n_events / args.steps, "step_ms": step_ms,
+            "wall_s": wall, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "parallelism": f"env shards x{world}, no collective on the data path"}
+    print(json.dumps(line), flush=True)
+
+
+def e2e_leg(ev, w, dev, args, capacity):
+    """Host buffers in, events out: pinned host keyframes copied by evis_step_host, the
+    step's events read back to pinned host memory, all inside the timed region."""
+    import torch
+    n = args.e2e_steps
+    host = []
+    for k in range(n + 1):
+        host.append(tuple(t.cpu().pin_memory() for t in dev[k]))
+    out = torch.empty(capacity * 16, dtype=torch.uint8).pin_memory()
+    ctx = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM, capacity=capacity)
+    ctx.step_host(*host[0], w.dt_ns)
+    import ctypes
+    cnt = ctypes.c_int64()
+    h2d = sum(t.numel() * 4 for t in host[0])
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(1, n + 1):
+        ctx.step_host(*host[k], w.dt_ns)
+        st = ev.lib().evis_read_events(ctx.handle, out.data_ptr(), capacity, ctypes.byref(cnt))
+        if st != ev.OK:
+            raise RuntimeError(f"evis_read_events: {ev.status_string(st)}")
+        d2h += cnt.value * 16 + 8
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ctx.close()
+    return {"value": w.pixel_substeps * n / sec / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h // n, "steps": n,
+            "path": "evis_step_host (pinned host keyframe -> device) + evis_read_events "
+                    "(all events -> pinned host)"}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_info()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        evis_arm(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

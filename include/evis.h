@@ -1,0 +1,187 @@
+/*
+ * evis.h -- C ABI of libevis.so, the CUDA (sm_103a) event-synthesis path of EVIS.
+ *
+ * The library turns a sequence of rendered keyframes (linear-HDR radiance or log-intensity,
+ * the renderer's backward motion vectors and depth) into an event stream.  For every
+ * keyframe gap it synthesises K sub-frames by splatting keyframe A forward and keyframe B
+ * backward (Sec. 3.3, Eq. 5), resolves collisions with a per-pixel depth z-buffer
+ * (Eqs. 6-7), blends the two directions in time with hole filling, and runs the event
+ * model on each sub-frame: log-intensity against a per-pixel reference level, contrast
+ * threshold, polarity, reference update keeping the residual (Sec. 3.2, Eq. 4), per-pixel
+ * ON/OFF thresholds (Eq. 8) and a refractory period (Sec. 3.4).  Each crossing is emitted
+ * as (env, x, y, t, polarity) with a timestamp interpolated linearly between sub-frames.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named "device" must be CUDA device (or managed) memory of the current device;
+ *    pointers named "host" must be host memory (pinned for asynchronous copies).
+ *  - Packed layout: the environments of a context are stored back to back.  Environment e
+ *    owns pixels [pix_off(e), pix_off(e) + H_e * W_e), pix_off being the prefix sum of
+ *    H * W rounded up to a multiple of 4 (16-byte aligned starts).  Pixel (x, y) of an
+ *    environment has index y * W + x.  Per-pixel arrays hold one float per pixel;
+ *    motion vectors hold two (dx, dy interleaved); RGB frames hold three (R, G, B).
+ *  - Motion vectors follow the renderer's convention (Sec. 3.3): mv(p) of a keyframe is the
+ *    displacement, in pixels (+x right, +y down), from p to the position of the same surface
+ *    point in the previous keyframe.
+ *  - Depth: a source pixel takes part in the splat iff its depth is finite and > 0.
+ *  - All work is enqueued on the context's stream; nothing blocks unless stated.
+ *  - Errors detected on the host return immediately and change nothing.  Errors detected
+ *    on the device (event buffer overflow) are latched and returned by the next call that
+ *    synchronises (evis_read_events, evis_event_count).
+ *  - One context must not be used by two host threads at the same time.
+ */
+#ifndef EVIS_H
+#define EVIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; 0 means the legacy default stream. */
+typedef struct CUstream_st *evis_stream_t;
+typedef struct evis_ctx evis_ctx;
+
+typedef enum {
+  EVIS_OK = 0,
+  EVIS_ERR_INVALID_ARG = 1, /* bad size, pointer, flag or threshold; nothing was done */
+  EVIS_ERR_CUDA = 2,        /* a CUDA call failed; see evis_last_error */
+  EVIS_ERR_OOM = 3,         /* device allocation failed */
+  EVIS_ERR_OVERFLOW = 4,    /* more events than the buffer (or the caller's array) holds */
+  EVIS_ERR_STATE = 5,       /* call not valid in the context's current state */
+  EVIS_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} evis_status;
+
+/* One event (16 bytes): time in ns, pixel, environment index, polarity +1 / -1. */
+typedef struct {
+  int64_t t_ns;
+  uint16_t x, y, env;
+  int16_t p;
+} evis_event;
+
+/* Input modes (Sec. 3.2): frames are log-intensity L, linear luminance I (L = log(I + eps)),
+ * or linear RGB radiance (I = 0.2126 R + 0.7152 G + 0.0722 B, Eq. 3, then the log). */
+#define EVIS_IN_LOG 0x0u
+#define EVIS_IN_LUM 0x1u
+#define EVIS_IN_RGB 0x2u
+/* Blend of the two warp directions: time blend (1-f) A + f B with hole filling (default),
+ * or B primary with A filling only B's holes (Sec. 3.3). */
+#define EVIS_MODE_BLEND 0x0u
+#define EVIS_MODE_B_PRIMARY 0x10u
+/* z-buffer tie-break among equal depths: larger bilinear weight then lower source index
+ * (default), or lower source index only. */
+#define EVIS_TIE_WEIGHT 0x0u
+#define EVIS_TIE_INDEX 0x20u
+/* The caller keeps the previous keyframe's mv and depth (and, in EVIS_IN_LOG mode, its
+ * frames) alive and unmodified until the next evis_step has completed on the stream, so the
+ * library reads them in place instead of keeping its own copy. */
+#define EVIS_KEEP_INPUTS 0x100u
+
+typedef struct {
+  int32_t width, height; /* 1..65535 each, width * height <= 2^24 */
+  int32_t K;             /* sub-frames per keyframe gap, 1..4096 (f = i/K, i = 1..K) */
+  float c_on, c_off;     /* contrast thresholds (log units), finite and > 0 */
+  const float *c_on_map; /* optional device [H*W] per-pixel thresholds (Eq. 8); both or */
+  const float *c_off_map;/* neither; caller-owned, read at every step, must outlive ctx */
+  int64_t refractory_ns; /* 0 = off (Sec. 3.4) */
+  int64_t t0_ns;         /* time of the first keyframe */
+} evis_env_desc;
+
+typedef struct {
+  float eps;              /* added before the log (Sec. 3.2), finite and >= 0 */
+  uint32_t flags;         /* EVIS_IN_* | EVIS_MODE_* | EVIS_TIE_* | EVIS_KEEP_INPUTS */
+  int64_t event_capacity; /* events the device buffer holds between two reads, >= 1 */
+} evis_config;
+
+/* Creates a context for n_envs environments (1..65535) on the current CUDA device and
+ * allocates all device memory it will use (keyframe copies, reference levels, refractory
+ * times, event buffer).  The descriptor array is copied; threshold maps are referenced.
+ * Returns EVIS_ERR_INVALID_ARG for a bad descriptor or config (checked before any CUDA
+ * call), EVIS_ERR_OOM when the device memory does not fit.  *out is set only on success. */
+evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_config *cfg,
+                        evis_stream_t stream, evis_ctx **out);
+
+/* Feeds the next keyframe (device pointers, packed layout; frames per the input mode).
+ * The first call on a context sets the reference level of every pixel to the keyframe's
+ * log-intensity and emits nothing (Sec. 3.2).  Each later call synthesises the K_e
+ * sub-frames between the previous keyframe and this one (Sec. 3.3, Eqs. 5-7) and appends
+ * their events (Sec. 3.2 Eq. 4, Sec. 3.4) to the device buffer; sub-frame i of environment
+ * e is at t = T_e + (i * dt_ns) / K_e, T_e being the previous keyframe's time.
+ * Asynchronous; inputs may be reused once the stream has passed this call, except under
+ * EVIS_KEEP_INPUTS.  0 < dt_ns <= 2^40. */
+evis_status evis_step(evis_ctx *ctx, const float *frames, const float *mv, const float *depth,
+                      int64_t dt_ns);
+
+/* Same as evis_step with HOST inputs: the library copies them into its own device buffers
+ * on the context's stream (host memory should be pinned) and then steps.  The first call
+ * allocates those buffers. */
+evis_status evis_step_host(evis_ctx *ctx, const float *frames, const float *mv,
+                           const float *depth, int64_t dt_ns);
+
+/* Synchronises the stream, copies the buffered events (in no particular order) to dst
+ * (host or device, up to cap events), empties the buffer and clears latched errors.
+ * *n_out = number of events produced since the last read.  Returns EVIS_ERR_OVERFLOW when
+ * that number exceeds the buffer capacity or cap: the first min(capacity, cap) stored
+ * events are delivered and the per-pixel state has advanced as if none were lost. */
+evis_status evis_read_events(evis_ctx *ctx, evis_event *dst, int64_t cap, int64_t *n_out);
+
+/* Synchronises and reports the number of events produced since the last read. */
+evis_status evis_event_count(evis_ctx *ctx, int64_t *n_out);
+
+/* Device-side view of the event buffer for consumers on the GPU: *events points to the
+ * capacity-sized array, *count to the 64-bit produced-event counter.  Valid until destroy. */
+evis_status evis_events_device(evis_ctx *ctx, evis_event **events, uint64_t **count);
+
+/* Asynchronously empties the event buffer (stream-ordered, no synchronisation). */
+evis_status evis_clear_events(evis_ctx *ctx);
+
+/* Synchronises and copies the per-pixel reference levels [total px] and last emitted event
+ * times [total px] (INT64_MIN = none) and the per-environment keyframe times [n_envs] to
+ * host memory (any pointer may be null). */
+evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t *clocks);
+
+/* Debug form of evis_step: also writes, for every environment in order and every
+ * sub-frame i = 1..K_e, the two z-buffers (keys[((i-1)*2 + dir) * H*W + p], dir 0 = A
+ * forward, dir 1 = B backward; key = depth bits << 32 | quantised (1 - weight) << 24 |
+ * source index, all ones = no source) and the blended log-intensity (Lint[(i-1) * H*W + p],
+ * NaN where the pixel got no sample).  keys / Lint are device arrays of
+ * sum_e K_e * 2 * H_e * W_e uint64 and sum_e K_e * H_e * W_e floats. */
+evis_status evis_step_trace(evis_ctx *ctx, const float *frames, const float *mv,
+                            const float *depth, int64_t dt_ns, uint64_t *keys, float *Lint);
+
+/* Log-intensity of n samples (Sec. 3.2, Eq. 3): mode EVIS_IN_LUM reads n floats, EVIS_IN_RGB
+ * n RGB triplets; out[i] = log(I + eps) (non-positive arguments clamp to the smallest
+ * normal float).  Device pointers, enqueued on stream. */
+evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float eps, float *out,
+                               evis_stream_t stream);
+
+/* Per-kernel timing for profiling.  With max_steps > 0, each following evis_step (or
+ * evis_step_host / evis_step_trace) records CUDA events on the context's stream around its
+ * two phases, for at most max_steps steps; max_steps = 0 disables and forgets the records.
+ * The events cost nothing on the device.  The keyframe that only sets the reference level
+ * records no synthesis phase (its duration reads 0). */
+evis_status evis_profile_enable(evis_ctx *ctx, int32_t max_steps);
+
+/* Synchronises and writes, for each recorded step s (at most cap), ms[2*s] = duration of
+ * the input preparation (log-intensity, copies, motion bound) and ms[2*s+1] = duration of
+ * the synthesis kernel (splat, blend, events), in milliseconds; *n_steps = steps written. */
+evis_status evis_profile_read(evis_ctx *ctx, float *ms, int32_t cap, int32_t *n_steps);
+
+/* Total packed pixels of the context (the length of its per-pixel arrays). */
+evis_status evis_total_pixels(evis_ctx *ctx, int64_t *n_out);
+
+/* Releases the context and all its device memory (synchronises the stream first). */
+evis_status evis_destroy(evis_ctx *ctx);
+
+/* Static description of a status code. */
+const char *evis_status_string(evis_status s);
+
+/* Text of the last CUDA or validation error seen by ctx (empty if none); with ctx = NULL,
+ * why the calling thread's last failed evis_create failed. */
+const char *evis_last_error(evis_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVIS_H */

@@ -1,0 +1,274 @@
+"""EVIS event synthesis on B300: a thin ctypes binding of libevis.so.
+
+Every step of the path runs in the library's CUDA kernels; this module only marshals
+arguments (torch CUDA tensors -> device pointers, the current torch stream -> the context's
+stream).  There is no CPU fallback: importing the binding without the built library raises.
+The C entry points are documented in ``include/evis.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libevis.so")
+
+IN_LOG, IN_LUM, IN_RGB = 0x0, 0x1, 0x2
+MODE_BLEND, MODE_B_PRIMARY = 0x0, 0x10
+TIE_WEIGHT, TIE_INDEX = 0x0, 0x20
+KEEP_INPUTS = 0x100
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_STATE, ERR_TIMEOUT = range(7)
+
+EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2"), ("p", "<i2")])
+
+
+class EnvDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("c_on", ctypes.c_float), ("c_off", ctypes.c_float),
+                ("c_on_map", ctypes.c_void_p), ("c_off_map", ctypes.c_void_p),
+                ("refractory_ns", ctypes.c_int64), ("t0_ns", ctypes.c_int64)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("event_capacity", ctypes.c_int64)]
+
+
+class EvisError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{status_string(status)} ({status}){': ' + msg if msg else ''}")
+
+
+_lib = None
+
+_SIGS = {
+    "evis_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_step": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64]),
+    "evis_step_host": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64]),
+    "evis_step_trace": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64] +
+                        [ctypes.c_void_p] * 2),
+    "evis_read_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p]),
+    "evis_event_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_events_device": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "evis_clear_events": (ctypes.c_int, [ctypes.c_void_p]),
+    "evis_get_state": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
+                                          ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "evis_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_void_p]),
+    "evis_total_pixels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "evis_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "evis_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+}
+
+
+def lib():
+    """The loaded libevis.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2607_08098_b300.build` "
+                "(the event-synthesis path has no CPU fallback)")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().evis_status_string(int(status)).decode()
+
+
+def _check(status: int, handle=None):
+    if status != OK:
+        msg = lib().evis_last_error(handle).decode() if handle is not None else ""
+        raise EvisError(status, msg)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Context:
+    """An event-synthesis context over a list of environments.
+
+    ``envs`` items need ``W, H, K, c_on, c_off`` and may have ``refractory_ns``, ``t0_ns``
+    and per-pixel ``c_on_map`` / ``c_off_map`` (CUDA float32 tensors of H*W, kept alive by
+    this object).  Inputs to :meth:`step` are CUDA float32 tensors in the packed layout.
+    """
+
+    def __init__(self, envs, eps: float = 1e-4, flags: int = 0, capacity: int = 1 << 22,
+                 stream=None):
+        import torch
+        L = lib()
+        self.envs = list(envs)
+        self.flags = int(flags)
+        self.capacity = int(capacity)
+        self._keep = []
+        arr = (EnvDesc * len(self.envs))()
+        for i, e in enumerate(self.envs):
+            con = getattr(e, "c_on_map", None)
+            coff = getattr(e, "c_off_map", None)
+            if con is not None:
+                con = torch.as_tensor(con, dtype=torch.float32).cuda().contiguous()
+                coff = torch.as_tensor(coff, dtype=torch.float32).cuda().contiguous()
+                self._keep += [con, coff]
+            arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), float(e.c_on), float(e.c_off),
+                             _ptr(con), _ptr(coff), int(getattr(e, "refractory_ns", 0)),
+                             int(getattr(e, "t0_ns", 0)))
+        cfg = Config(float(eps), self.flags, self.capacity)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = L.evis_create(ctypes.addressof(arr), len(self.envs), ctypes.addressof(cfg),
+                           _stream_handle(self._stream), ctypes.byref(h))
+        if st != OK:
+            raise EvisError(st, L.evis_last_error(None).decode())
+        self._h = h
+        n = ctypes.c_int64()
+        _check(L.evis_total_pixels(self._h, ctypes.byref(n)), self._h)
+        self.total = n.value
+        self.n_frame = self.total * (3 if (self.flags & 0x3) == IN_RGB else 1)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().evis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_inputs(self, frames, mv, depth):
+        for name, t, n in (("frames", frames, self.n_frame), ("mv", mv, 2 * self.total),
+                           ("depth", depth, self.total)):
+            if not t.is_cuda or t.dtype.itemsize != 4 or t.numel() != n:
+                raise ValueError(f"{name}: expected a CUDA float32 tensor of {n} elements")
+
+    def step(self, frames, mv, depth, dt_ns: int):
+        self._check_inputs(frames, mv, depth)
+        _check(lib().evis_step(self._h, _ptr(frames), _ptr(mv), _ptr(depth), int(dt_ns)), self._h)
+
+    def step_trace(self, frames, mv, depth, dt_ns: int):
+        """Step and return (keys [sum K*2*H*W] uint64 as int64, Lint [sum K*H*W]) tensors."""
+        import torch
+        self._check_inputs(frames, mv, depth)
+        nk = sum(e.K * 2 * e.H * e.W for e in self.envs)
+        nl = sum(e.K * e.H * e.W for e in self.envs)
+        keys = torch.empty(nk, dtype=torch.int64, device=frames.device)
+        lint = torch.empty(nl, dtype=torch.float32, device=frames.device)
+        _check(lib().evis_step_trace(self._h, _ptr(frames), _ptr(mv), _ptr(depth), int(dt_ns),
+                                     _ptr(keys), _ptr(lint)), self._h)
+        return keys, lint
+
+    def step_host(self, frames: np.ndarray, mv: np.ndarray, depth: np.ndarray, dt_ns: int):
+        """Step from host arrays (numpy or pinned torch CPU tensors)."""
+        def hp(a, n):
+            if hasattr(a, "data_ptr"):
+                if a.numel() != n:
+                    raise ValueError("host input has the wrong size")
+                return a.data_ptr()
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            if a.size != n:
+                raise ValueError("host input has the wrong size")
+            return a.ctypes.data
+        _check(lib().evis_step_host(self._h, hp(frames, self.n_frame), hp(mv, 2 * self.total),
+                                    hp(depth, self.total), int(dt_ns)), self._h)
+
+    def read_events(self, cap: int | None = None, allow_overflow: bool = False):
+        """Drain the event buffer to a numpy structured array (EVENT_DTYPE)."""
+        n = ctypes.c_int64()
+        cnt = self.event_count()
+        if cap is None:
+            cap = min(cnt, self.capacity)
+        out = np.empty(max(cap, 0), dtype=EVENT_DTYPE)
+        st = lib().evis_read_events(self._h, out.ctypes.data if cap else None, int(cap),
+                                    ctypes.byref(n))
+        if st == ERR_OVERFLOW and allow_overflow:
+            return out[:min(n.value, cap)], n.value
+        _check(st, self._h)
+        return (out[:n.value], n.value) if allow_overflow else out[:n.value]
+
+    def event_count(self) -> int:
+        n = ctypes.c_int64()
+        st = lib().evis_event_count(self._h, ctypes.byref(n))
+        if st not in (OK, ERR_OVERFLOW):
+            _check(st, self._h)
+        return n.value
+
+    def clear_events(self):
+        _check(lib().evis_clear_events(self._h), self._h)
+
+    def events_device(self):
+        ev = ctypes.c_void_p()
+        cnt = ctypes.c_void_p()
+        _check(lib().evis_events_device(self._h, ctypes.byref(ev), ctypes.byref(cnt)), self._h)
+        return ev.value, cnt.value
+
+    def profile(self, max_steps: int):
+        """Record per-phase CUDA events for the next ``max_steps`` steps (0 disables)."""
+        _check(lib().evis_profile_enable(self._h, int(max_steps)), self._h)
+
+    def profile_read(self) -> np.ndarray:
+        """[steps, 2] milliseconds: (input preparation, synthesis kernel) per profiled step."""
+        buf = np.zeros(2 * 4096, dtype=np.float32)
+        n = ctypes.c_int32()
+        _check(lib().evis_profile_read(self._h, buf.ctypes.data, 4096, ctypes.byref(n)), self._h)
+        return buf[:2 * n.value].reshape(-1, 2)
+
+    def state(self):
+        Lref = np.empty(self.total, dtype=np.float32)
+        tl = np.empty(self.total, dtype=np.int64)
+        clk = np.empty(len(self.envs), dtype=np.int64)
+        _check(lib().evis_get_state(self._h, Lref.ctypes.data, tl.ctypes.data, clk.ctypes.data),
+               self._h)
+        return Lref, tl, clk
+
+
+def log_intensity(x, mode: int = IN_LUM, eps: float = 1e-4):
+    """log(I + eps) of a CUDA tensor (I, or Rec. 709 luminance of [..., 3] RGB) on the GPU."""
+    import torch
+    x = x.contiguous()
+    n = x.numel() // 3 if mode == IN_RGB else x.numel()
+    out = torch.empty(n, dtype=torch.float32, device=x.device)
+    _check(lib().evis_log_intensity(_ptr(x), n, int(mode), float(eps), _ptr(out),
+                                    torch.cuda.current_stream().cuda_stream))
+    return out
+
+
+def sort_events(ev: np.ndarray) -> np.ndarray:
+    """Order (env, t, y, x, p): the buffer order is arbitrary, this one is canonical."""
+    return ev[np.lexsort((ev["p"], ev["x"], ev["y"], ev["t"], ev["env"]))]

@@ -1,0 +1,473 @@
+// Host side of libevis: argument validation, device memory, stream ordering and the C ABI
+// declared in include/evis.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "evis_internal.h"
+
+using evis::DevEnv;
+using evis::Tile;
+
+struct evis_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  evis_config cfg{};
+  uint32_t mode = 0;
+  bool keep = false;
+  bool need_L = false;     // library holds converted / copied log-intensity slots
+  int n = 0;
+  std::vector<evis_env_desc> envs;
+  std::vector<int64_t> off;
+  int64_t total = 0;
+  int max_px = 0;
+  int tile_h = 16;
+  int n_tiles = 0;
+  bool any_refr = false;
+
+  DevEnv *d_envs = nullptr;
+  Tile *d_tiles = nullptr;
+  float *d_L[2] = {nullptr, nullptr};
+  float *d_mv[2] = {nullptr, nullptr};
+  float *d_Z[2] = {nullptr, nullptr};
+  float *d_Lref = nullptr;
+  int64_t *d_tlast = nullptr;
+  float *d_flow = nullptr;     // [2][n]
+  int64_t *d_clock = nullptr;  // [2][n]
+  ulonglong2 *d_events = nullptr;
+  unsigned long long *d_count = nullptr;
+  int64_t *d_tr_off = nullptr; // [2][n]: key offsets, then L offsets
+  float *d_in[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int in_slot = 0;
+
+  int slot = 0;       // keyframe slot currently holding A
+  int clk = 0;        // clock buffer holding the time of A
+  bool have_A = false;
+  const float *A_L = nullptr, *A_mv = nullptr, *A_Z = nullptr;
+
+  std::vector<cudaEvent_t> prof;   // 3 events per profiled step
+  int prof_max = 0, prof_n = 0;
+
+  std::vector<void *> allocs;
+  std::string err;
+};
+
+namespace {
+
+constexpr int64_t kMaxDt = int64_t(1) << 40;
+thread_local std::string g_create_error;  // why the last evis_create on this thread failed
+
+evis_status fail(evis_ctx *c, evis_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+evis_status cuda_fail(evis_ctx *c, cudaError_t e, const char *where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? EVIS_ERR_OOM : EVIS_ERR_CUDA;
+}
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+std::string validate(const evis_env_desc *envs, int32_t n, const evis_config *cfg) {
+  if (!envs) return "envs is null";
+  if (!cfg) return "cfg is null";
+  if (n < 1 || n > 65535) return "n_envs must be in 1..65535";
+  if (!std::isfinite(cfg->eps) || cfg->eps < 0.0f) return "eps must be finite and >= 0";
+  const uint32_t known = 0x3u | EVIS_MODE_B_PRIMARY | EVIS_TIE_INDEX | EVIS_KEEP_INPUTS;
+  if (cfg->flags & ~known) return "unknown flag bits";
+  if ((cfg->flags & 0x3u) == 0x3u) return "invalid input mode";
+  if (cfg->event_capacity < 1 || cfg->event_capacity > (int64_t(1) << 40))
+    return "event_capacity must be in 1..2^40";
+  for (int i = 0; i < n; ++i) {
+    const evis_env_desc &d = envs[i];
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "env %d: ", i);
+    std::string p(buf);
+    if (d.width < 1 || d.width > 65535 || d.height < 1 || d.height > 65535)
+      return p + "width and height must be in 1..65535";
+    if (int64_t(d.width) * d.height > (int64_t(1) << 24)) return p + "width*height must be <= 2^24";
+    if (d.K < 1 || d.K > 4096) return p + "K must be in 1..4096";
+    if (!finite_pos(d.c_on) || !finite_pos(d.c_off)) return p + "thresholds must be finite and > 0";
+    if ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))
+      return p + "give both threshold maps or neither";
+    if (d.refractory_ns < 0) return p + "refractory_ns must be >= 0";
+  }
+  return "";
+}
+
+template <class T>
+cudaError_t dalloc(evis_ctx *c, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return cudaSuccess;
+}
+
+void release(evis_ctx *c) {
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  for (cudaEvent_t ev : c->prof) cudaEventDestroy(ev);
+  c->prof.clear();
+  c->prof_max = c->prof_n = 0;
+}
+
+__global__ void fill_i64(int64_t *p, int64_t v, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = v;
+}
+
+evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
+                    int64_t dt, uint64_t *tr_keys, float *tr_L) {
+  if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
+  if (dt <= 0 || dt > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const int b = c->slot ^ 1;
+  const bool prof = c->prof_n < c->prof_max;
+  cudaEvent_t *pev = prof ? &c->prof[3 * c->prof_n] : nullptr;
+  if (prof && (e = cudaEventRecord(pev[0], c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "profile event");
+  float *flowB = c->d_flow + b * c->n;
+  e = cudaMemsetAsync(flowB, 0, sizeof(float) * c->n, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset flow");
+  evis::PrepArgs pa{};
+  pa.envs = c->d_envs;
+  pa.frames = frames;
+  pa.mv = mv;
+  pa.Z = depth;
+  pa.L_out = c->need_L ? c->d_L[b] : nullptr;
+  pa.mv_out = c->keep ? nullptr : c->d_mv[b];
+  pa.Z_out = c->keep ? nullptr : c->d_Z[b];
+  pa.flow = flowB;
+  pa.eps = c->cfg.eps;
+  pa.mode = c->mode;
+  pa.max_px = c->max_px;
+  e = evis::launch_prep(pa, c->n, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "prep kernel");
+  const float *LB = c->need_L ? c->d_L[b] : frames;
+  const float *mvB = c->keep ? mv : c->d_mv[b];
+  const float *ZB = c->keep ? depth : c->d_Z[b];
+  if (prof && (e = cudaEventRecord(pev[1], c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "profile event");
+  if (c->have_A) {
+    evis::StepArgs s{};
+    s.envs = c->d_envs;
+    s.tiles = c->d_tiles;
+    s.LA = c->A_L;
+    s.mvA = c->A_mv;
+    s.ZA = c->A_Z;
+    s.LB = LB;
+    s.mvB = mvB;
+    s.ZB = ZB;
+    s.Lref = c->d_Lref;
+    s.tlast = c->d_tlast;
+    s.clock_in = c->d_clock + c->clk * c->n;
+    s.clock_out = c->d_clock + (c->clk ^ 1) * c->n;
+    s.flowA = c->d_flow + c->slot * c->n;
+    s.flowB = flowB;
+    s.events = c->d_events;
+    s.ev_count = c->d_count;
+    s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
+    s.dt = dt;
+    s.flags = c->cfg.flags;
+    s.tr_keys = tr_keys;
+    s.tr_L = tr_L;
+    s.tr_koff = c->d_tr_off;
+    s.tr_loff = c->d_tr_off + c->n;
+    e = evis::launch_step(s, c->n_tiles, c->tile_h, tr_keys != nullptr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    c->clk ^= 1;
+  } else {
+    e = evis::launch_init_ref(LB, c->d_Lref, c->total, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    c->have_A = true;
+  }
+  if (prof) {
+    if ((e = cudaEventRecord(pev[2], c->stream)) != cudaSuccess) return cuda_fail(c, e, "profile event");
+    ++c->prof_n;
+  }
+  c->slot = b;
+  c->A_L = LB;
+  c->A_mv = mvB;
+  c->A_Z = ZB;
+  return EVIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_config *cfg,
+                        evis_stream_t stream, evis_ctx **out) {
+  if (!out) return EVIS_ERR_INVALID_ARG;
+  g_create_error = validate(envs, n_envs, cfg);
+  if (!g_create_error.empty()) return EVIS_ERR_INVALID_ARG;
+  evis_ctx *c = new evis_ctx();
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->cfg = *cfg;
+  c->mode = cfg->flags & 0x3u;
+  c->keep = (cfg->flags & EVIS_KEEP_INPUTS) != 0;
+  c->need_L = c->mode != EVIS_IN_LOG || !c->keep;
+  c->n = n_envs;
+  c->envs.assign(envs, envs + n_envs);
+  std::vector<DevEnv> denv(n_envs);
+  std::vector<int64_t> troff(2 * n_envs);
+  int64_t ko = 0, lo = 0;
+  for (int i = 0; i < n_envs; ++i) {
+    const evis_env_desc &d = envs[i];
+    c->off.push_back(c->total);
+    const int64_t px = int64_t(d.width) * d.height;
+    DevEnv &v = denv[i];
+    v.W = d.width;
+    v.H = d.height;
+    v.K = d.K;
+    v.tile_h = c->tile_h;
+    v.pix_off = c->total;
+    v.c_on = d.c_on;
+    v.c_off = d.c_off;
+    v.con_map = d.c_on_map;
+    v.coff_map = d.c_off_map;
+    v.refractory_ns = d.refractory_ns;
+    c->total += (px + 3) / 4 * 4;
+    c->max_px = std::max<int>(c->max_px, static_cast<int>(px));
+    c->any_refr |= d.refractory_ns > 0;
+    troff[i] = ko;
+    troff[n_envs + i] = lo;
+    ko += int64_t(d.K) * 2 * px;
+    lo += int64_t(d.K) * px;
+  }
+  // target tiles, longest-running (largest K) first
+  std::vector<Tile> tiles;
+  for (int i = 0; i < n_envs; ++i) {
+    const evis_env_desc &d = envs[i];
+    for (int y = 0; y < d.height; y += c->tile_h)
+      for (int x = 0; x < d.width; x += evis::kTileW) tiles.push_back(Tile{i, x, y, 0});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [&](const Tile &a, const Tile &b) { return envs[a.env].K > envs[b.env].K; });
+  c->n_tiles = static_cast<int>(tiles.size());
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  auto bail = [&](cudaError_t err, const char *where) {
+    evis_status s = cuda_fail(c, err, where);
+    g_create_error = c->err;
+    release(c);
+    delete c;
+    return s;
+  };
+  if (e != cudaSuccess) return bail(e, "cudaGetDevice");
+  if ((e = dalloc(c, &c->d_envs, n_envs)) != cudaSuccess) return bail(e, "alloc envs");
+  if ((e = dalloc(c, &c->d_tiles, tiles.size())) != cudaSuccess) return bail(e, "alloc tiles");
+  if ((e = dalloc(c, &c->d_Lref, c->total)) != cudaSuccess) return bail(e, "alloc Lref");
+  if (c->any_refr && (e = dalloc(c, &c->d_tlast, c->total)) != cudaSuccess)
+    return bail(e, "alloc t_last");
+  if ((e = dalloc(c, &c->d_flow, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc flow");
+  if ((e = dalloc(c, &c->d_clock, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc clock");
+  if ((e = dalloc(c, &c->d_events, cfg->event_capacity)) != cudaSuccess) return bail(e, "alloc events");
+  if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");
+  if ((e = dalloc(c, &c->d_tr_off, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc trace offsets");
+  for (int s = 0; s < 2; ++s) {
+    if (c->need_L && (e = dalloc(c, &c->d_L[s], c->total)) != cudaSuccess) return bail(e, "alloc L");
+    if (!c->keep) {
+      if ((e = dalloc(c, &c->d_mv[s], 2 * c->total)) != cudaSuccess) return bail(e, "alloc mv");
+      if ((e = dalloc(c, &c->d_Z[s], c->total)) != cudaSuccess) return bail(e, "alloc Z");
+    }
+  }
+  std::vector<int64_t> clocks(2 * n_envs);
+  for (int i = 0; i < n_envs; ++i) clocks[i] = clocks[n_envs + i] = envs[i].t0_ns;
+  cudaStream_t s = c->stream;
+  if ((e = cudaMemcpyAsync(c->d_envs, denv.data(), sizeof(DevEnv) * n_envs, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(c->d_clock, clocks.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemcpyAsync(c->d_tr_off, troff.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
+      (e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s)) ||
+      (e = cudaMemsetAsync(c->d_flow, 0, sizeof(float) * 2 * n_envs, s)))
+    return bail(e, "upload tables");
+  if (c->d_tlast) {
+    fill_i64<<<1024, 256, 0, s>>>(c->d_tlast, evis::kNoEvent, c->total);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "fill t_last");
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "create sync");
+  *out = c;
+  return EVIS_OK;
+}
+
+evis_status evis_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
+                      int64_t dt_ns) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  return do_step(c, frames, mv, depth, dt_ns, nullptr, nullptr);
+}
+
+evis_status evis_step_trace(evis_ctx *c, const float *frames, const float *mv,
+                            const float *depth, int64_t dt_ns, uint64_t *keys, float *Lint) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (!keys || !Lint) return fail(c, EVIS_ERR_INVALID_ARG, "null trace buffer");
+  return do_step(c, frames, mv, depth, dt_ns, keys, Lint);
+}
+
+evis_status evis_step_host(evis_ctx *c, const float *frames, const float *mv,
+                           const float *depth, int64_t dt_ns) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
+  if (dt_ns <= 0 || dt_ns > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
+  const size_t fw = c->mode == EVIS_IN_RGB ? 3 : 1;
+  cudaError_t e;
+  if (!c->d_in[0][0]) {
+    for (int s = 0; s < 2; ++s) {
+      if ((e = dalloc(c, &c->d_in[s][0], fw * c->total)) != cudaSuccess ||
+          (e = dalloc(c, &c->d_in[s][1], 2 * c->total)) != cudaSuccess ||
+          (e = dalloc(c, &c->d_in[s][2], c->total)) != cudaSuccess)
+        return cuda_fail(c, e, "alloc host-step buffers");
+    }
+  }
+  float **in = c->d_in[c->in_slot];
+  if ((e = cudaMemcpyAsync(in[0], frames, sizeof(float) * fw * c->total, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(in[1], mv, sizeof(float) * 2 * c->total, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(in[2], depth, sizeof(float) * c->total, cudaMemcpyHostToDevice, c->stream)))
+    return cuda_fail(c, e, "host to device copy");
+  evis_status st = do_step(c, in[0], in[1], in[2], dt_ns, nullptr, nullptr);
+  if (st == EVIS_OK) c->in_slot ^= 1;  // keep the previous keyframe's buffers intact
+  return st;
+}
+
+evis_status evis_read_events(evis_ctx *c, evis_event *dst, int64_t cap, int64_t *n_out) {
+  if (!c || !n_out || cap < 0 || (cap > 0 && !dst)) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "read sync");
+  unsigned long long cnt = 0;
+  if ((e = cudaMemcpy(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "read count");
+  const int64_t produced = static_cast<int64_t>(cnt);
+  const int64_t n = std::min<int64_t>(produced, std::min<int64_t>(c->cfg.event_capacity, cap));
+  if (n > 0 && (e = cudaMemcpy(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault)) != cudaSuccess)
+    return cuda_fail(c, e, "copy events");
+  if ((e = cudaMemset(c->d_count, 0, sizeof(unsigned long long))) != cudaSuccess)
+    return cuda_fail(c, e, "reset count");
+  *n_out = produced;
+  return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+}
+
+evis_status evis_event_count(evis_ctx *c, int64_t *n_out) {
+  if (!c || !n_out) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "count sync");
+  unsigned long long cnt = 0;
+  if ((e = cudaMemcpy(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "read count");
+  *n_out = static_cast<int64_t>(cnt);
+  return cnt > static_cast<unsigned long long>(c->cfg.event_capacity) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+}
+
+evis_status evis_events_device(evis_ctx *c, evis_event **events, uint64_t **count) {
+  if (!c || !events || !count) return EVIS_ERR_INVALID_ARG;
+  *events = reinterpret_cast<evis_event *>(c->d_events);
+  *count = reinterpret_cast<uint64_t *>(c->d_count);
+  return EVIS_OK;
+}
+
+evis_status evis_clear_events(evis_ctx *c) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream);
+  return e == cudaSuccess ? EVIS_OK : cuda_fail(c, e, "clear events");
+}
+
+evis_status evis_get_state(evis_ctx *c, float *Lref, int64_t *t_last, int64_t *clocks) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state sync");
+  if (Lref && (e = cudaMemcpy(Lref, c->d_Lref, sizeof(float) * c->total, cudaMemcpyDefault)))
+    return cuda_fail(c, e, "copy Lref");
+  if (t_last) {
+    if (c->d_tlast) {
+      if ((e = cudaMemcpy(t_last, c->d_tlast, sizeof(int64_t) * c->total, cudaMemcpyDefault)))
+        return cuda_fail(c, e, "copy t_last");
+    } else {
+      std::fill(t_last, t_last + c->total, evis::kNoEvent);
+    }
+  }
+  if (clocks && (e = cudaMemcpy(clocks, c->d_clock + c->clk * c->n, sizeof(int64_t) * c->n,
+                                cudaMemcpyDefault)))
+    return cuda_fail(c, e, "copy clocks");
+  return EVIS_OK;
+}
+
+evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float eps, float *out,
+                               evis_stream_t stream) {
+  if (n < 0 || (n > 0 && (!in || !out)) || (mode != EVIS_IN_LUM && mode != EVIS_IN_RGB) ||
+      !std::isfinite(eps) || eps < 0.0f)
+    return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = evis::launch_log(in, n, mode, eps, out, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
+}
+
+evis_status evis_profile_enable(evis_ctx *c, int32_t max_steps) {
+  if (!c || max_steps < 0 || max_steps > (1 << 20)) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  for (cudaEvent_t ev : c->prof) cudaEventDestroy(ev);
+  c->prof.clear();
+  c->prof_max = c->prof_n = 0;
+  for (int i = 0; i < 3 * max_steps; ++i) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(c, e, "profile events");
+    c->prof.push_back(ev);
+  }
+  c->prof_max = max_steps;
+  return EVIS_OK;
+}
+
+evis_status evis_profile_read(evis_ctx *c, float *ms, int32_t cap, int32_t *n_steps) {
+  if (!c || !n_steps || cap < 0 || (cap > 0 && !ms)) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  const int n = std::min(cap, c->prof_n);
+  for (int s = 0; s < n; ++s) {
+    float a = 0.f, b = 0.f;
+    if ((e = cudaEventElapsedTime(&a, c->prof[3 * s], c->prof[3 * s + 1])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&b, c->prof[3 * s + 1], c->prof[3 * s + 2])) != cudaSuccess)
+      return cuda_fail(c, e, "profile elapsed");
+    ms[2 * s] = a;
+    ms[2 * s + 1] = b;
+  }
+  *n_steps = n;
+  return EVIS_OK;
+}
+
+evis_status evis_total_pixels(evis_ctx *c, int64_t *n_out) {
+  if (!c || !n_out) return EVIS_ERR_INVALID_ARG;
+  *n_out = c->total;
+  return EVIS_OK;
+}
+
+evis_status evis_destroy(evis_ctx *c) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  release(c);
+  delete c;
+  return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
+}
+
+const char *evis_status_string(evis_status s) {
+  switch (s) {
+    case EVIS_OK: return "ok";
+    case EVIS_ERR_INVALID_ARG: return "invalid argument";
+    case EVIS_ERR_CUDA: return "CUDA error";
+    case EVIS_ERR_OOM: return "out of device memory";
+    case EVIS_ERR_OVERFLOW: return "event buffer overflow";
+    case EVIS_ERR_STATE: return "invalid state";
+    case EVIS_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char *evis_last_error(evis_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

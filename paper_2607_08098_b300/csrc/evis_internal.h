@@ -1,0 +1,71 @@
+// Internal declarations of libevis: device-side tables and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "evis.h"
+
+namespace evis {
+
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kMaxCrossings = 4096;         // crossings per pixel per sub-frame
+constexpr int64_t kNoEvent = INT64_MIN;     // t_last of a pixel that never fired
+constexpr int kTileW = 32;                  // tile width = one warp of targets
+constexpr int kThreads = 256;               // threads per step CTA (8 warps)
+constexpr int kEventStage = 1024;           // events staged in shared memory per CTA
+
+// Per-environment constants, resident in device memory.
+struct DevEnv {
+  int32_t W, H, K, tile_h;
+  int64_t pix_off;
+  float c_on, c_off;
+  const float *con_map, *coff_map;   // this environment's maps (device) or null
+  int64_t refractory_ns;
+};
+
+// One target tile: environment and top-left pixel.
+struct Tile {
+  int32_t env, x0, y0, pad;
+};
+
+// Arguments of one step launch (packed base pointers; environment offsets are applied
+// inside the kernel).
+struct StepArgs {
+  const DevEnv *envs;
+  const Tile *tiles;
+  const float *LA, *mvA, *ZA;
+  const float *LB, *mvB, *ZB;
+  float *Lref;
+  int64_t *tlast;            // null when no environment has a refractory period
+  const int64_t *clock_in;
+  int64_t *clock_out;
+  const float *flowA, *flowB;
+  ulonglong2 *events;
+  unsigned long long *ev_count;
+  unsigned long long capacity;
+  int64_t dt;
+  uint32_t flags;
+  uint64_t *tr_keys;         // debug trace (null in the production path)
+  float *tr_L;
+  const int64_t *tr_koff, *tr_loff;
+};
+
+struct PrepArgs {
+  const DevEnv *envs;
+  const float *frames, *mv, *Z;  // caller's keyframe
+  float *L_out;                  // log-intensity destination (null: frames are used as L)
+  float *mv_out, *Z_out;         // copies (null under EVIS_KEEP_INPUTS)
+  float *flow;                   // per-environment max |mv| (inf-norm), pre-zeroed
+  float eps;
+  uint32_t mode;
+  int max_px;                    // largest environment (pixels)
+};
+
+cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);
+cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
+cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_h, bool trace, cudaStream_t s);
+cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, float *out,
+                       cudaStream_t s);
+
+}  // namespace evis

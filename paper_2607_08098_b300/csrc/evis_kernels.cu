@@ -1,0 +1,445 @@
+// CUDA kernels of the EVIS event-synthesis path (sm_103a).
+//
+// Compiled with -fmad=false and written with explicit round-to-nearest intrinsics so that
+// every floating-point step that decides a z-buffer winner or an event count is the same
+// single IEEE-754 binary32 operation, in the same order, as in the method's definition:
+// splat winners, event counts, pixels and polarities are then reproducible bit for bit on
+// any IEEE host.
+//
+// Kernels
+//   prep_kernel  per keyframe: log-intensity (Sec. 3.2, Eq. 3), optional copies of the
+//                motion/depth maps, per-environment max |mv| (the splat halo).
+//   step_kernel  per keyframe gap: one CTA owns a 32 x TY target tile of one environment
+//                and keeps, for all K sub-frames, its pixels' event state in registers.
+//                Per sub-frame it splats every source of A (forward) and B (backward) whose
+//                footprint can reach the tile into two shared-memory z-buffers with 64-bit
+//                atomicMin on (depth, weight, source) keys (Eqs. 5-7), resolves the winners,
+//                blends in time with hole filling, runs the event model (Eq. 4, Eq. 8,
+//                refractory period) and compacts the events: warp-aggregated reservation in
+//                a shared staging buffer, one global atomic per CTA per sub-frame and a
+//                coalesced 16-byte-per-thread flush.
+#include <cfloat>
+
+#include "evis_internal.h"
+
+namespace evis {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool valid_depth(float z) { return z > 0.0f && z < INFINITY; }
+
+// L = log(I + eps), Sec. 3.2; non-positive or NaN arguments clamp to the smallest normal.
+__device__ __forceinline__ float log_intensity(float I, float eps) {
+  float s = __fadd_rn(I, eps);
+  if (!(s > 0.0f)) s = FLT_MIN;
+  return logf(s);
+}
+
+// Rec. 709 luminance, Eq. 3: ((0.2126 R + 0.7152 G) + 0.0722 B), each product rounded.
+__device__ __forceinline__ float rec709(float R, float G, float B) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, R), __fmul_rn(0.7152f, G)),
+                   __fmul_rn(0.0722f, B));
+}
+
+// Depth of the other keyframe at the correspondence endpoint (Eq. 7): nearest pixel with
+// halves rounded up, else the source's own depth (outside the image or invalid there).
+__device__ __forceinline__ float other_depth(const float *__restrict__ Zo, int W, int H,
+                                             float ux, float uy, float own) {
+  const float nx = floorf(__fadd_rn(ux, 0.5f)), ny = floorf(__fadd_rn(uy, 0.5f));
+  if (!(nx >= 0.0f && nx <= static_cast<float>(W - 1) && ny >= 0.0f &&
+        ny <= static_cast<float>(H - 1)))
+    return own;
+  const float z = __ldg(Zo + static_cast<int>(ny) * W + static_cast<int>(nx));
+  return valid_depth(z) ? z : own;
+}
+
+// Bilinear-footprint z-test splat of one source into the tile's z-buffer (Eq. 6): every
+// integer pixel around q with weight > 0, inside the image and inside the tile, keeps the
+// minimum key [depth bits | quantised (1 - w) | source index].
+template <int TY>
+__device__ __forceinline__ void splat_tile(unsigned long long *zb, int x0, int y0, int W, int H,
+                                           float qx, float qy, float zt, uint32_t src,
+                                           bool tie_index) {
+  if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H)))
+    return;
+  const float fx0 = floorf(qx), fy0 = floorf(qy);
+  const int lx0 = static_cast<int>(fx0) - x0, ly0 = static_cast<int>(fy0) - y0;
+  if (lx0 < -1 || lx0 >= kTileW || ly0 < -1 || ly0 >= TY) return;
+  const float ax = __fsub_rn(qx, fx0), ay = __fsub_rn(qy, fy0);
+  const float wx[2] = {__fsub_rn(1.0f, ax), ax};
+  const float wy[2] = {__fsub_rn(1.0f, ay), ay};
+  const unsigned long long hi = static_cast<unsigned long long>(__float_as_uint(zt)) << 32;
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy) {
+    const int ly = ly0 + dy;
+    if (ly < 0 || ly >= TY || y0 + ly >= H) continue;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const int lx = lx0 + dx;
+      if (lx < 0 || lx >= kTileW || x0 + lx >= W) continue;
+      const float w = __fmul_rn(wx[dx], wy[dy]);
+      if (!(w > 0.0f)) continue;
+      unsigned wq = 0;
+      if (!tie_index) wq = min(__float2uint_rz(__fmul_rn(__fsub_rn(1.0f, w), 256.0f)), 255u);
+      atomicMin(&zb[ly * kTileW + lx], hi | (static_cast<unsigned long long>(wq) << 24) | src);
+    }
+  }
+}
+
+// Time of the k-th crossing of a pixel in this sub-frame: the level Lref + p k theta,
+// interpolated linearly between the previous sample (tprev, Lprev) and this one (ti, L).
+__device__ __forceinline__ int64_t crossing_time(float Lref, int pk, float th, float Lprev,
+                                                 float L, int64_t tprev, int64_t ti) {
+  const float lev = __fadd_rn(Lref, __fmul_rn(static_cast<float>(pk), th));
+  const float num = __fsub_rn(lev, Lprev);
+  const float den = __fsub_rn(L, Lprev);
+  float fr = den == 0.0f ? 1.0f : __fdiv_rn(num, den);
+  if (!(fr > 0.0f)) fr = 0.0f;
+  else if (fr > 1.0f) fr = 1.0f;
+  return tprev + __double2ll_rn(__dmul_rn(static_cast<double>(fr),
+                                          static_cast<double>(ti - tprev)));
+}
+
+__device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int env, int p) {
+  ulonglong2 r;
+  r.x = static_cast<unsigned long long>(t);
+  r.y = static_cast<unsigned long long>(x & 0xFFFF) |
+        (static_cast<unsigned long long>(y & 0xFFFF) << 16) |
+        (static_cast<unsigned long long>(env & 0xFFFF) << 32) |
+        (static_cast<unsigned long long>(static_cast<uint16_t>(static_cast<int16_t>(p))) << 48);
+  return r;
+}
+
+template <int TY, bool TRACE>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
+  constexpr int NT = TY * kTileW / kThreads;  // targets per thread (rows warp + 8 j)
+  static_assert(NT >= 1 && NT * kThreads == TY * kTileW, "tile height must be 8, 16 or 32");
+  __shared__ unsigned long long zb[2][TY * kTileW];
+  __shared__ ulonglong2 stage[kEventStage];
+  __shared__ unsigned s_n, s_flush;
+  __shared__ unsigned long long s_base;
+
+  const Tile tl = a.tiles[blockIdx.x];
+  const DevEnv E = a.envs[tl.env];
+  const int W = E.W, H = E.H, K = E.K;
+  const int64_t o = E.pix_off;
+  const float *__restrict__ LA = a.LA + o;
+  const float *__restrict__ LB = a.LB + o;
+  const float2 *__restrict__ mvA = reinterpret_cast<const float2 *>(a.mvA) + o;
+  const float2 *__restrict__ mvB = reinterpret_cast<const float2 *>(a.mvB) + o;
+  const float *__restrict__ ZA = a.ZA + o;
+  const float *__restrict__ ZB = a.ZB + o;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
+  const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
+  const int64_t T0 = a.clock_in[tl.env];
+  const int64_t refr = E.refractory_ns;
+  const int tx = tl.x0 + lane;
+  const int64_t HW = static_cast<int64_t>(W) * H;
+
+  float Lref[NT], Lprev[NT], thon[NT], thoff[NT];
+  int64_t tprev[NT], tlast[NT];
+  int pix[NT];
+  bool act[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int ty = tl.y0 + warp + 8 * j;
+    act[j] = tx < W && ty < H;
+    pix[j] = ty * W + tx;
+    tprev[j] = T0;
+    tlast[j] = kNoEvent;
+    Lref[j] = 0.0f;
+    Lprev[j] = 0.0f;
+    thon[j] = E.c_on;
+    thoff[j] = E.c_off;
+    if (act[j]) {
+      Lref[j] = a.Lref[o + pix[j]];
+      Lprev[j] = LA[pix[j]];
+      if (a.tlast) tlast[j] = a.tlast[o + pix[j]];
+      if (E.con_map) {
+        thon[j] = E.con_map[pix[j]];
+        thoff[j] = E.coff_map[pix[j]];
+      }
+    }
+  }
+
+  // Sources that can reach the tile lie within the largest |mv| (+ footprint) of it.
+  const float mf = fmaxf(a.flowA[tl.env], a.flowB[tl.env]);
+  const int h = mf < 65536.0f ? static_cast<int>(ceilf(mf)) + 2 : 65536;
+  const int sx0 = max(0, tl.x0 - h), sx1 = min(W, tl.x0 + kTileW + h);
+  const int sy0 = max(0, tl.y0 - h), sy1 = min(H, tl.y0 + TY + h);
+  if (tid == 0) s_n = 0;
+
+  for (int i = 1; i <= K; ++i) {
+    const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
+    const float g = __fsub_rn(1.0f, f);
+    const int64_t ti = T0 + (static_cast<int64_t>(i) * a.dt) / K;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int s = (warp + 8 * j) * kTileW + lane;
+      zb[0][s] = kEmptyKey;
+      zb[1][s] = kEmptyKey;
+    }
+    __syncthreads();
+
+    // ---- splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
+    for (int sy = sy0 + warp; sy < sy1; sy += 8) {
+      const float fy = static_cast<float>(sy);
+      for (int sx = sx0 + lane; sx < sx1; sx += kTileW) {
+        const int p = sy * W + sx;
+        const float fx = static_cast<float>(sx);
+        const float za = __ldg(ZA + p);
+        if (valid_depth(za)) {  // A forward: q = p - f m_A, p_B = p - m_A
+          const float2 m = __ldg(mvA + p);
+          const float qx = __fsub_rn(fx, __fmul_rn(f, m.x));
+          const float qy = __fsub_rn(fy, __fmul_rn(f, m.y));
+          const float zo = other_depth(ZB, W, H, __fsub_rn(fx, m.x), __fsub_rn(fy, m.y), za);
+          const float zt = __fadd_rn(__fmul_rn(g, za), __fmul_rn(f, zo));
+          splat_tile<TY>(zb[0], tl.x0, tl.y0, W, H, qx, qy, zt, static_cast<uint32_t>(p),
+                         tie_index);
+        }
+        const float zbv = __ldg(ZB + p);
+        if (valid_depth(zbv)) {  // B backward: q = p + (1-f) m_B, p_A = p + m_B
+          const float2 m = __ldg(mvB + p);
+          const float qx = __fadd_rn(fx, __fmul_rn(g, m.x));
+          const float qy = __fadd_rn(fy, __fmul_rn(g, m.y));
+          const float zo = other_depth(ZA, W, H, __fadd_rn(fx, m.x), __fadd_rn(fy, m.y), zbv);
+          const float zt = __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zbv));
+          splat_tile<TY>(zb[1], tl.x0, tl.y0, W, H, qx, qy, zt, static_cast<uint32_t>(p),
+                         tie_index);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- resolve, blend, threshold crossings (count pass) ----
+    float Lnew[NT], th[NT];
+    int nc[NT], pol[NT];
+    bool has[NT];
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      nc[j] = 0;
+      pol[j] = 1;
+      th[j] = thon[j];
+      has[j] = false;
+      Lnew[j] = 0.0f;
+      if (!act[j]) continue;
+      const int s = (warp + 8 * j) * kTileW + lane;
+      const unsigned long long kA = zb[0][s], kB = zb[1][s];
+      const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
+      const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
+      const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
+      float L;
+      if (b_primary) {
+        L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
+      } else {
+        L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))
+                           : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+      }
+      if (TRACE) {
+        const int64_t kb = a.tr_koff[tl.env] + static_cast<int64_t>(i - 1) * 2 * HW + pix[j];
+        a.tr_keys[kb] = kA;
+        a.tr_keys[kb + HW] = kB;
+        a.tr_L[a.tr_loff[tl.env] + static_cast<int64_t>(i - 1) * HW + pix[j]] = L;
+      }
+      if (!hasA && !hasB) continue;  // no sample: the pixel holds its state this sub-frame
+      has[j] = true;
+      Lnew[j] = L;
+      const float d = __fsub_rn(L, Lref[j]);
+      pol[j] = d > 0.0f ? 1 : -1;
+      th[j] = pol[j] > 0 ? thon[j] : thoff[j];
+      const float q = __fdiv_rn(fabsf(d), th[j]);
+      int n = 0;
+      if (q >= 1.0f) n = q >= static_cast<float>(kMaxCrossings) ? kMaxCrossings
+                                                                : static_cast<int>(floorf(q));
+      nc[j] = n;
+      if (refr <= 0) {
+        cnt += n;
+      } else {
+        int64_t tl_ = tlast[j];
+        for (int k = 1; k <= n; ++k) {
+          const int64_t t = crossing_time(Lref[j], pol[j] * k, th[j], Lprev[j], L, tprev[j], ti);
+          if (tl_ == kNoEvent || t - tl_ >= refr) {
+            ++cnt;
+            tl_ = t;
+          }
+        }
+      }
+    }
+
+    // ---- warp-aggregated reservation: staging buffer first, global overflow path ----
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    unsigned base = 0;
+    unsigned long long gbase = 0;
+    if (total > 0) {
+      if (lane == 31) {
+        base = atomicAdd(&s_n, static_cast<unsigned>(total));
+        const unsigned room = base < kEventStage ? kEventStage - base : 0u;
+        if (room < static_cast<unsigned>(total))
+          gbase = atomicAdd(a.ev_count, static_cast<unsigned long long>(total - room));
+      }
+      base = __shfl_sync(kFull, base, 31);
+      gbase = __shfl_sync(kFull, gbase, 31);
+    }
+    const unsigned room = base < kEventStage ? kEventStage - base : 0u;
+
+    // ---- write pass: regenerate the crossings, emit, update the state ----
+    unsigned e = static_cast<unsigned>(incl - cnt);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      if (!has[j]) continue;
+      const int n = nc[j];
+      const int ty = tl.y0 + warp + 8 * j;
+      for (int k = 1; k <= n; ++k) {
+        const int64_t t = crossing_time(Lref[j], pol[j] * k, th[j], Lprev[j], Lnew[j], tprev[j], ti);
+        if (refr <= 0 || tlast[j] == kNoEvent || t - tlast[j] >= refr) {
+          const ulonglong2 rec = make_event(t, tx, ty, tl.env, pol[j]);
+          if (e < room) {
+            stage[base + e] = rec;
+          } else {
+            const unsigned long long gi = gbase + (e - room);
+            if (gi < a.capacity) a.events[gi] = rec;
+          }
+          ++e;
+          tlast[j] = t;
+        }
+      }
+      if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(static_cast<float>(pol[j] * n), th[j]));
+      Lprev[j] = Lnew[j];
+      tprev[j] = ti;
+    }
+    __syncthreads();
+
+    // ---- flush the staging buffer: one global reservation, coalesced 16 B stores ----
+    if (tid == 0) {
+      const unsigned n = min(s_n, static_cast<unsigned>(kEventStage));
+      s_flush = n;
+      s_base = n ? atomicAdd(a.ev_count, static_cast<unsigned long long>(n)) : 0ull;
+      s_n = 0;
+    }
+    __syncthreads();
+    const unsigned nf = s_flush;
+    const unsigned long long gb = s_base;
+    for (unsigned r = tid; r < nf; r += kThreads) {
+      const unsigned long long gi = gb + r;
+      if (gi < a.capacity) a.events[gi] = stage[r];
+    }
+  }
+
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (!act[j]) continue;
+    a.Lref[o + pix[j]] = Lref[j];
+    if (a.tlast) a.tlast[o + pix[j]] = tlast[j];
+  }
+  if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) a.clock_out[tl.env] = T0 + a.dt;
+}
+
+__global__ void prep_kernel(const PrepArgs a) {
+  const int e = blockIdx.y;
+  const DevEnv E = a.envs[e];
+  const int n = E.W * E.H;
+  const int64_t o = E.pix_off;
+  float mx = 0.0f;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const float2 m = reinterpret_cast<const float2 *>(a.mv)[o + p];
+    mx = fmaxf(mx, fmaxf(fabsf(m.x), fabsf(m.y)));
+    if (a.mv_out) reinterpret_cast<float2 *>(a.mv_out)[o + p] = m;
+    if (a.Z_out) a.Z_out[o + p] = a.Z[o + p];
+    if (a.L_out) {
+      float L;
+      if (a.mode == EVIS_IN_LOG) {
+        L = a.frames[o + p];
+      } else if (a.mode == EVIS_IN_LUM) {
+        L = log_intensity(a.frames[o + p], a.eps);
+      } else {
+        const float *c = a.frames + 3 * (o + p);
+        L = log_intensity(rec709(c[0], c[1], c[2]), a.eps);
+      }
+      a.L_out[o + p] = L;
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, d));
+  __shared__ float sm[32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, d));
+    // non-negative floats order like their bit patterns
+    if (threadIdx.x == 0 && mx > 0.0f) atomicMax(reinterpret_cast<int *>(a.flow + e), __float_as_int(mx));
+  }
+}
+
+__global__ void init_ref_kernel(const float *__restrict__ L, float *__restrict__ Lref, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    Lref[i] = L[i];
+}
+
+__global__ void log_kernel(const float *__restrict__ in, int64_t n, uint32_t mode, float eps,
+                           float *__restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    out[i] = mode == EVIS_IN_RGB ? log_intensity(rec709(in[3 * i], in[3 * i + 1], in[3 * i + 2]), eps)
+                                 : log_intensity(in[i], eps);
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 148 * 64) b = 148 * 64;
+  return static_cast<int>(b);
+}
+
+}  // namespace
+
+cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s) {
+  const int threads = 256;
+  int bx = (a.max_px + threads * 4 - 1) / (threads * 4);
+  if (bx < 1) bx = 1;
+  prep_kernel<<<dim3(bx, n_envs), threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s) {
+  init_ref_kernel<<<grid_for(n, 256), 256, 0, s>>>(L, Lref, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, float *out,
+                       cudaStream_t s) {
+  if (n > 0) log_kernel<<<grid_for(n, 256), 256, 0, s>>>(in, n, mode, eps, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_h, bool trace, cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+#define EVIS_STEP_CASE(TY)                                                     \
+  case TY:                                                                     \
+    if (trace) step_kernel<TY, true><<<n_tiles, kThreads, 0, s>>>(a);          \
+    else step_kernel<TY, false><<<n_tiles, kThreads, 0, s>>>(a);               \
+    break;
+  switch (tile_h) {
+    EVIS_STEP_CASE(8)
+    EVIS_STEP_CASE(16)
+    EVIS_STEP_CASE(32)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef EVIS_STEP_CASE
+  return cudaGetLastError();
+}
+
+}  // namespace evis

@@ -242,10 +242,11 @@ def config1() -> Workload:
                     33_333_333, 10)
 
 
-def config2(n_envs: int = 64, W: int = 346, H: int = 260) -> Workload:
-    """64 envs at 346x260, 32 pairs, K=16, C=0.25, refractory 100 us, three depth layers."""
+def config2(n_envs: int = 64, W: int = 346, H: int = 260, first_env: int = 0) -> Workload:
+    """64 envs at 346x260, 32 pairs, K=16, C=0.25, refractory 100 us, three depth layers.
+    ``first_env`` shifts the seeds (environment e uses seed index first_env + e)."""
     envs = []
-    for e in range(n_envs):
+    for e in range(first_env, first_env + n_envs):
         rng = _rng(2, e)
         envs.append(EnvScene(W=W, H=H, K=16, c_on=0.25, c_off=0.25, refractory_ns=100_000,
                              layers=_random_layers(rng, W, H, 3, vmax=10.0, wmax=0.1)))

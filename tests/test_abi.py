@@ -1,0 +1,109 @@
+"""The C-ABI library builds, loads and exports every symbol include/evis.h declares, and its
+host-side validation rejects bad arguments before touching CUDA (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def evis():
+    from paper_2607_08098_b300 import build
+    build.build()
+    import paper_2607_08098_b300 as ev
+    return ev
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(evis_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(evis):
+    names = _declared()
+    assert {"evis_create", "evis_step", "evis_read_events", "evis_destroy"} <= names
+    out = subprocess.check_output(["nm", "-D", "--defined-only", evis.LIB_PATH], text=True)
+    exported = set(re.findall(r"\bT (evis_\w+)", out))
+    missing = names - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+    h = ctypes.CDLL(evis.LIB_PATH)
+    for n in names:
+        getattr(h, n)
+
+
+def test_binding_covers_the_abi(evis):
+    names = _declared()
+    bound = set(evis._SIGS)
+    assert names <= bound, names - bound
+
+
+def _desc(ev, **kw):
+    d = dict(width=64, height=32, K=8, c_on=0.2, c_off=0.2, c_on_map=None, c_off_map=None,
+             refractory_ns=0, t0_ns=0)
+    d.update(kw)
+    return ev.EnvDesc(**d)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(width=0), dict(height=70000), dict(width=8192, height=4096), dict(K=0), dict(K=5000),
+    dict(c_on=0.0), dict(c_off=-1.0), dict(c_on=float("nan")), dict(c_off=float("inf")),
+    dict(refractory_ns=-1), dict(c_on_map=1234),
+])
+def test_create_rejects_bad_descriptors_before_cuda(evis, bad):
+    L = evis.lib()
+    arr = (evis.EnvDesc * 1)(_desc(evis, **bad))
+    cfg = evis.Config(1e-4, 0, 1024)
+    h = ctypes.c_void_p()
+    st = L.evis_create(ctypes.addressof(arr), 1, ctypes.addressof(cfg), None, ctypes.byref(h))
+    assert st == evis.ERR_INVALID_ARG
+    assert h.value is None
+    assert L.evis_last_error(None).decode() != ""
+
+
+@pytest.mark.parametrize("cfg", [(-1.0, 0, 10), (float("nan"), 0, 10), (1e-4, 0x3, 10),
+                                 (1e-4, 0x8000, 10), (1e-4, 0, 0), (1e-4, 0, 1 << 41)])
+def test_create_rejects_bad_config(evis, cfg):
+    L = evis.lib()
+    arr = (evis.EnvDesc * 1)(_desc(evis))
+    c = evis.Config(*cfg)
+    h = ctypes.c_void_p()
+    st = L.evis_create(ctypes.addressof(arr), 1, ctypes.addressof(c), None, ctypes.byref(h))
+    assert st == evis.ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_counts_and_nulls(evis):
+    L = evis.lib()
+    arr = (evis.EnvDesc * 1)(_desc(evis))
+    c = evis.Config(1e-4, 0, 16)
+    h = ctypes.c_void_p()
+    assert L.evis_create(ctypes.addressof(arr), 0, ctypes.addressof(c), None, ctypes.byref(h)) == 1
+    assert L.evis_create(None, 1, ctypes.addressof(c), None, ctypes.byref(h)) == 1
+    assert L.evis_create(ctypes.addressof(arr), 1, None, None, ctypes.byref(h)) == 1
+    assert L.evis_create(ctypes.addressof(arr), 1, ctypes.addressof(c), None, None) == 1
+
+
+def test_null_context_calls_are_rejected(evis):
+    L = evis.lib()
+    n = ctypes.c_int64()
+    assert L.evis_step(None, None, None, None, 1) == evis.ERR_INVALID_ARG
+    assert L.evis_read_events(None, None, 0, ctypes.byref(n)) == evis.ERR_INVALID_ARG
+    assert L.evis_destroy(None) == evis.ERR_INVALID_ARG
+    assert L.evis_log_intensity(None, 4, 0, 1e-4, None, None) == evis.ERR_INVALID_ARG
+    assert L.evis_log_intensity(None, 4, 7, 1e-4, None, None) == evis.ERR_INVALID_ARG
+    assert evis.status_string(evis.ERR_OVERFLOW) == "event buffer overflow"
+
+
+def test_binding_fails_loudly_without_library(evis, monkeypatch):
+    monkeypatch.setattr(evis, "_lib", None)
+    monkeypatch.setattr(evis, "LIB_PATH", "/nonexistent/libevis.so")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        evis.lib()

@@ -1,0 +1,299 @@
+"""Parity of the CUDA path with the oracle, through the C ABI (needs a B300).
+
+Bar (bit-exact unless stated): splat winners (z-buffer keys), interpolated log-intensity,
+event streams in canonical order (env, t, y, x, p), reference levels, refractory times and
+keyframe clocks.  The log conversion of linear inputs is the one step outside the exact
+contract (CUDA logf vs the host log): it is checked within 2 ulp on its own.
+"""
+import numpy as np
+import pytest
+
+from evis_testutil import TinyEnv, packed_total
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_08098_b300 import build
+    build.build()
+    import paper_2607_08098_b300 as m
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).cuda()
+
+
+def _frames(kf, mode):
+    return {0: kf.L, 1: kf.I, 2: None if kf.rgb is None else kf.rgb.reshape(-1)}[mode]
+
+
+def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), capacity=1 << 22,
+             check_state=True):
+    """Feed the same keyframes to the oracle and the library; compare everything."""
+    mode = flags & 0x3
+    o = oracle_mod.Oracle(envs, eps=eps, flags=flags & 0xFF)
+    ctx = ev.Context(envs, eps=eps, flags=flags, capacity=capacity)
+    alive = []  # keeps inputs alive for EVIS_KEEP_INPUTS
+    for s, kf in enumerate(kfs):
+        fr = _frames(kf, mode)
+        g_in = (_dev(fr), _dev(kf.mv), _dev(kf.Z))
+        alive.append(g_in)
+        if s in trace_steps and s > 0:
+            ok, ol = o.step(fr, kf.mv, kf.Z, dt, trace=True)
+            gk, gl = ctx.step_trace(*g_in, dt)
+            torch.cuda.synchronize()
+            gk = gk.cpu().numpy().view(np.uint64)
+            gl = gl.cpu().numpy()
+            bad = np.nonzero(gk != ok)[0]
+            assert bad.size == 0, f"step {s}: {bad.size} splat keys differ, first at {bad[:5]}"
+            np.testing.assert_array_equal(gl, ol, err_msg=f"step {s}: interpolated L")
+        else:
+            o.step(fr, kf.mv, kf.Z, dt)
+            ctx.step(*g_in, dt)
+        alive = alive[-2:]
+    eo = oracle_mod.sort_events(o.events())
+    eg = ev.sort_events(ctx.read_events())
+    assert len(eg) == len(eo), (len(eg), len(eo))
+    np.testing.assert_array_equal(eg.view(np.uint8), eo.view(np.uint8))
+    if check_state:
+        so, sg = o.state(), ctx.state()
+        valid = np.zeros(so[0].size, dtype=bool)
+        for e, off in zip(envs, o.offsets):
+            valid[off:off + e.H * e.W] = True
+        np.testing.assert_array_equal(sg[0][valid], so[0][valid])
+        np.testing.assert_array_equal(sg[1][valid], so[1][valid])
+        np.testing.assert_array_equal(sg[2], so[2])
+    ctx.close()
+    return eo
+
+
+def test_config1_plain_single_env(ev, oracle_mod, scenes_mod):
+    """Plain single env 128x128, 10 frame pairs, K=8, C=0.2 -- the whole workload."""
+    w = scenes_mod.config1()
+    kfs = [scenes_mod.render(w.envs, k) for k in range(w.n_pairs + 1)]
+    evs = run_both(ev, oracle_mod, w.envs, kfs, w.dt_ns, trace_steps=(1, 5, 10))
+    assert len(evs) > 100_000
+
+
+def _ragged_envs(scenes_mod):
+    rng = np.random.default_rng(99)
+    sizes = [(37, 23, 3, 0), (70, 41, 5, 300_000), (1, 1, 2, 0), (33, 1, 4, 0), (5, 40, 1, 0),
+             (96, 64, 7, 50_000)]
+    envs = []
+    for i, (W, H, K, r) in enumerate(sizes):
+        lay = scenes_mod._random_layers(rng, W, H, 3, vmax=6.0, wmax=0.1)
+        e = scenes_mod.EnvScene(W=W, H=H, K=K, c_on=0.15 + 0.01 * i, c_off=0.2, refractory_ns=r,
+                                t0_ns=1000 * i, layers=lay)
+        if i == 5:
+            e.c_on_map = np.maximum(rng.normal(0.2, 0.03, W * H), 0.01).astype(np.float32)
+            e.c_off_map = np.maximum(rng.normal(0.2, 0.03, W * H), 0.01).astype(np.float32)
+        envs.append(e)
+    return envs
+
+
+def test_ragged_multi_env(ev, oracle_mod, scenes_mod):
+    """Uneven sizes (1x1, single rows/columns, ragged tiles), per-env K, refractory, maps."""
+    envs = _ragged_envs(scenes_mod)
+    kfs = [scenes_mod.render(envs, k) for k in range(4)]
+    run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(1, 2, 3))
+
+
+@pytest.mark.parametrize("flags", [0x10, 0x20, 0x30, 0x100, 0x110])
+def test_modes(ev, oracle_mod, scenes_mod, flags):
+    """B-primary blend, index-only tie-break and in-place (kept) inputs."""
+    envs = _ragged_envs(scenes_mod)[:2] + _ragged_envs(scenes_mod)[5:]
+    kfs = [scenes_mod.render(envs, k) for k in range(3)]
+    run_both(ev, oracle_mod, envs, kfs, 16_666_667, flags=flags, trace_steps=(1, 2))
+
+
+def test_adversarial_motion_and_depth(ev, oracle_mod):
+    """NaN / inf / non-positive depths, NaN and huge motion vectors, exact half-pixel
+    offsets and depth ties: winners, values and events still agree bit for bit."""
+    rng = np.random.default_rng(5)
+    envs = [TinyEnv(W=45, H=37, K=4, c_on=0.1, c_off=0.12, refractory_ns=10_000),
+            TinyEnv(W=64, H=16, K=3, c_on=0.2, c_off=0.2)]
+    n = packed_total(envs)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(3):
+        k = KF()
+        mvc = np.array([0, 0.5, -0.5, 1, -1, 1.5, 2, -2.25, 0.25, 3, -7, 40, np.nan, 1e9],
+                       dtype=np.float32)
+        mv = rng.choice(mvc, size=(n, 2)).astype(np.float32)
+        m = rng.random((n, 2)) < 0.5
+        mv[m] = rng.uniform(-9, 9, size=m.sum()).astype(np.float32)
+        zc = np.array([1, 2, 2, 3, 3, 3, 2.5, np.inf, np.nan, -1, 0], dtype=np.float32)
+        z = rng.choice(zc, size=n).astype(np.float32)
+        mz = rng.random(n) < 0.4
+        z[mz] = rng.uniform(0.5, 4, size=mz.sum()).astype(np.float32)
+        k.L = rng.normal(0, 1.5, size=n).astype(np.float32)
+        k.mv, k.Z, k.I, k.rgb = mv, z, None, None
+        kfs.append(k)
+    run_both(ev, oracle_mod, envs, kfs, 5_000_000, trace_steps=(1, 2))
+
+
+def test_static_scene_is_per_pixel_linear_esim(ev, oracle_mod):
+    envs = [TinyEnv(W=50, H=30, K=8, c_on=0.2, c_off=0.2)]
+    n = packed_total(envs)
+    rng = np.random.default_rng(3)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(4):
+        k = KF()
+        k.L = rng.normal(0, 1, size=n).astype(np.float32)
+        k.mv = np.zeros((n, 2), dtype=np.float32)
+        k.Z = np.ones(n, dtype=np.float32)
+        kfs.append(k)
+    run_both(ev, oracle_mod, envs, kfs, 10_000_000, trace_steps=(1, 3))
+
+
+def test_constant_image_emits_nothing(ev, scenes_mod):
+    w = scenes_mod.config2(n_envs=4)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    ctx = ev.Context(w.envs, flags=ev.IN_LOG)
+    for kf in kfs:
+        ctx.step(_dev(np.full_like(kf.L, 0.3)), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+    assert ctx.event_count() == 0
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_log_intensity_within_two_ulp(ev, oracle_mod, mode):
+    rng = np.random.default_rng(8)
+    n = 200_000
+    x = (10.0 ** rng.uniform(-6, 6, size=n * (3 if mode == 2 else 1))).astype(np.float32)
+    x[:8] = [0, -1, np.nan, np.inf, 1e-30, 1, 1e-4, 3.4e38]
+    got = ev.log_intensity(_dev(x), mode=mode, eps=1e-4).cpu().numpy()
+    want = oracle_mod.log_intensity(x, mode=mode, eps=1e-4)
+    fin = np.isfinite(want)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ulp = np.spacing(np.abs(want[fin]).astype(np.float32))
+    assert np.all(np.abs(got[fin] - want[fin]) <= 2 * ulp)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_linear_inputs_end_to_end(ev, oracle_mod, scenes_mod, mode):
+    """Linear / RGB radiance inputs: the GPU log may differ from the host one by an ulp, so the
+    streams are compared statistically (counts within 0.2 %, 99 % identical events)."""
+    w = scenes_mod.config1()
+    for lay in w.envs[0].layers:
+        lay.tint_r, lay.tint_g, lay.tint_b = 0.9, 1.1, 0.7
+    kfs = [scenes_mod.render(w.envs, k, want=("L", "I", "rgb", "mv", "Z")) for k in range(4)]
+    o = oracle_mod.Oracle(w.envs, eps=1e-4, flags=mode)
+    ctx = ev.Context(w.envs, eps=1e-4, flags=mode)
+    for kf in kfs:
+        fr = _frames(kf, mode)
+        o.step(fr, kf.mv, kf.Z, w.dt_ns)
+        ctx.step(_dev(fr), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+    eo, eg = o.events(), ctx.read_events()
+    assert abs(len(eg) - len(eo)) <= 0.002 * len(eo)
+    so = set(map(bytes, eo.view(np.dtype((np.void, 16)))))
+    sg = set(map(bytes, eg.view(np.dtype((np.void, 16)))))
+    assert len(so & sg) >= 0.99 * len(eo)
+
+
+def test_step_host_matches_device_step(ev, scenes_mod):
+    w = scenes_mod.config2(n_envs=3)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    a = ev.Context(w.envs, flags=ev.IN_LUM)
+    b = ev.Context(w.envs, flags=ev.IN_LUM | ev.KEEP_INPUTS)
+    alive = []
+    for kf in kfs:
+        g = (_dev(kf.I), _dev(kf.mv), _dev(kf.Z))
+        alive = (alive + [g])[-2:]
+        a.step(*g, w.dt_ns)
+        b.step_host(kf.I, kf.mv, kf.Z, w.dt_ns)
+    ea, eb = ev.sort_events(a.read_events()), ev.sort_events(b.read_events())
+    assert len(ea) > 0
+    np.testing.assert_array_equal(ea.view(np.uint8), eb.view(np.uint8))
+
+
+def test_overflow_reports_total_and_keeps_state(ev, oracle_mod, scenes_mod):
+    w = scenes_mod.config1()
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    o = oracle_mod.Oracle(w.envs)
+    ctx = ev.Context(w.envs, capacity=5000)
+    for kf in kfs:
+        o.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+        ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+    eo = o.events()
+    got, produced = ctx.read_events(allow_overflow=True)
+    assert produced == len(eo) > 5000 and len(got) == 5000
+    so = set(map(bytes, eo.view(np.dtype((np.void, 16)))))
+    assert all(bytes(r) in so for r in got.view(np.dtype((np.void, 16))))
+    np.testing.assert_array_equal(ctx.state()[0], o.state()[0])
+    assert ctx.event_count() == 0        # the read emptied the buffer
+    kf = scenes_mod.render(w.envs, 3)
+    ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+    o.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+    assert ctx.event_count() == len(o.events())
+
+
+def _subset(ev, oracle_mod, envs, kfs, dt, sample, flags=0):
+    """Oracle on a sample of environments (re-packed), for comparison with a full-size run."""
+    import scenes
+    sub = [envs[i] for i in sample]
+    off, _ = scenes.pixel_offsets(envs)
+    soff, stotal = scenes.pixel_offsets(sub)
+    o = oracle_mod.Oracle(sub, flags=flags)
+    for kf in kfs:
+        L = np.zeros(stotal, np.float32)
+        mv = np.zeros((stotal, 2), np.float32)
+        Z = np.ones(stotal, np.float32)
+        for j, i in enumerate(sample):
+            n = envs[i].H * envs[i].W
+            L[soff[j]:soff[j] + n] = kf.L[off[i]:off[i] + n]
+            mv[soff[j]:soff[j] + n] = kf.mv[off[i]:off[i] + n]
+            Z[soff[j]:soff[j] + n] = kf.Z[off[i]:off[i] + n]
+        o.step(L, mv, Z, dt)
+    return o, off, soff
+
+
+def test_config2_full_size_sampled(ev, oracle_mod, scenes_mod):
+    """64 envs at 346x260, K=16, C=0.25, refractory 100 us -- the benchmarked launch -- with
+    the oracle on three sampled environments."""
+    w = scenes_mod.config2()
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    ctx = ev.Context(w.envs, flags=ev.IN_LOG, capacity=1 << 27)
+    for kf in kfs:
+        ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+    eg = ctx.read_events()
+    Lref, tl, clk = ctx.state()
+    sample = [0, 31, 63]
+    o, off, soff = _subset(ev, oracle_mod, w.envs, kfs, w.dt_ns, sample)
+    eo = oracle_mod.sort_events(o.events())
+    so = o.state()
+    for j, i in enumerate(sample):
+        mine = eg[eg["env"] == i].copy()
+        mine["env"] = j
+        theirs = eo[eo["env"] == j]
+        mine = ev.sort_events(mine)
+        assert len(mine) == len(theirs) > 1000
+        np.testing.assert_array_equal(mine.view(np.uint8), theirs.view(np.uint8))
+        n = w.envs[i].H * w.envs[i].W
+        np.testing.assert_array_equal(Lref[off[i]:off[i] + n], so[0][soff[j]:soff[j] + n])
+        np.testing.assert_array_equal(tl[off[i]:off[i] + n], so[1][soff[j]:soff[j] + n])
+        assert clk[i] == so[2][j]
+
+
+def test_determinism(ev, scenes_mod):
+    w = scenes_mod.config2(n_envs=8)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    outs = []
+    for _ in range(2):
+        ctx = ev.Context(w.envs, capacity=1 << 24)
+        for kf in kfs:
+            ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+        outs.append(ev.sort_events(ctx.read_events()))
+    np.testing.assert_array_equal(outs[0].view(np.uint8), outs[1].view(np.uint8))
