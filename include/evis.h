@@ -137,7 +137,8 @@ evis_status evis_clear_events(evis_ctx *ctx);
 
 /* Synchronises and copies the per-pixel reference levels [total px] and last emitted event
  * times [total px] (INT64_MIN = none) and the per-environment keyframe times [n_envs] to
- * host memory (any pointer may be null). */
+ * host memory (any pointer may be null).  Last-event times are tracked only when some
+ * environment of the context has a refractory period; otherwise all read INT64_MIN. */
 evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t *clocks);
 
 /* Debug form of evis_step: also writes, for every environment in order and every

@@ -24,6 +24,8 @@ struct evis_ctx {
   std::vector<int64_t> off;
   int64_t total = 0;
   int max_px = 0;
+  int max_segs = 0;
+  int64_t total_segs = 0;
   int tile_h = 16;
   int n_tiles = 0;
   bool any_refr = false;
@@ -36,6 +38,7 @@ struct evis_ctx {
   float *d_Lref = nullptr;
   int64_t *d_tlast = nullptr;
   float *d_flow = nullptr;     // [2][n]
+  float4 *d_seg[2] = {nullptr, nullptr};  // per keyframe slot: row-segment motion bounds
   int64_t *d_clock = nullptr;  // [2][n]
   ulonglong2 *d_events = nullptr;
   unsigned long long *d_count = nullptr;
@@ -146,9 +149,10 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
   pa.mv_out = c->keep ? nullptr : c->d_mv[b];
   pa.Z_out = c->keep ? nullptr : c->d_Z[b];
   pa.flow = flowB;
+  pa.seg = c->d_seg[b];
   pa.eps = c->cfg.eps;
   pa.mode = c->mode;
-  pa.max_px = c->max_px;
+  pa.max_segs = c->max_segs;
   e = evis::launch_prep(pa, c->n, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "prep kernel");
   const float *LB = c->need_L ? c->d_L[b] : frames;
@@ -172,6 +176,8 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
     s.clock_out = c->d_clock + (c->clk ^ 1) * c->n;
     s.flowA = c->d_flow + c->slot * c->n;
     s.flowB = flowB;
+    s.segA = c->d_seg[c->slot];
+    s.segB = c->d_seg[b];
     s.events = c->d_events;
     s.ev_count = c->d_count;
     s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
@@ -230,6 +236,10 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     v.K = d.K;
     v.tile_h = c->tile_h;
     v.pix_off = c->total;
+    v.segs_x = (d.width + evis::kSegW - 1) / evis::kSegW;
+    v.seg_off = c->total_segs;
+    c->total_segs += int64_t(v.segs_x) * d.height;
+    c->max_segs = std::max<int>(c->max_segs, v.segs_x * d.height);
     v.c_on = d.c_on;
     v.c_off = d.c_off;
     v.con_map = d.c_on_map;
@@ -269,6 +279,8 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if (c->any_refr && (e = dalloc(c, &c->d_tlast, c->total)) != cudaSuccess)
     return bail(e, "alloc t_last");
   if ((e = dalloc(c, &c->d_flow, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc flow");
+  for (int s = 0; s < 2; ++s)
+    if ((e = dalloc(c, &c->d_seg[s], c->total_segs)) != cudaSuccess) return bail(e, "alloc segments");
   if ((e = dalloc(c, &c->d_clock, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc clock");
   if ((e = dalloc(c, &c->d_events, cfg->event_capacity)) != cudaSuccess) return bail(e, "alloc events");
   if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");

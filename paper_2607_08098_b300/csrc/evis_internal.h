@@ -14,11 +14,15 @@ constexpr int64_t kNoEvent = INT64_MIN;     // t_last of a pixel that never fire
 constexpr int kTileW = 32;                  // tile width = one warp of targets
 constexpr int kThreads = 256;               // threads per step CTA (8 warps)
 constexpr int kEventStage = 1024;           // events staged in shared memory per CTA
+constexpr int kSegW = 32;                   // motion bounds are kept per 32-pixel row segment
+constexpr int kCandidates = 384;            // candidate segments per direction per tile
 
 // Per-environment constants, resident in device memory.
 struct DevEnv {
   int32_t W, H, K, tile_h;
   int64_t pix_off;
+  int64_t seg_off;    // first row segment of this environment
+  int32_t segs_x, pad0;  // row segments per image row
   float c_on, c_off;
   const float *con_map, *coff_map;   // this environment's maps (device) or null
   int64_t refractory_ns;
@@ -41,6 +45,7 @@ struct StepArgs {
   const int64_t *clock_in;
   int64_t *clock_out;
   const float *flowA, *flowB;
+  const float4 *segA, *segB;   // per row segment: (min dx, max dx, min dy, max dy)
   ulonglong2 *events;
   unsigned long long *ev_count;
   unsigned long long capacity;
@@ -57,9 +62,10 @@ struct PrepArgs {
   float *L_out;                  // log-intensity destination (null: frames are used as L)
   float *mv_out, *Z_out;         // copies (null under EVIS_KEEP_INPUTS)
   float *flow;                   // per-environment max |mv| (inf-norm), pre-zeroed
+  float4 *seg;                   // per row segment motion bounds of this keyframe
   float eps;
   uint32_t mode;
-  int max_px;                    // largest environment (pixels)
+  int max_segs;                  // largest environment (row segments)
 };
 
 cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);

@@ -8,12 +8,15 @@
 //
 // Kernels
 //   prep_kernel  per keyframe: log-intensity (Sec. 3.2, Eq. 3), optional copies of the
-//                motion/depth maps, per-environment max |mv| (the splat halo).
+//                motion/depth maps, per-environment max |mv| and per 32-pixel row segment
+//                motion bounds (which sources can reach which tile).
 //   step_kernel  per keyframe gap: one CTA owns a 32 x TY target tile of one environment
 //                and keeps, for all K sub-frames, its pixels' event state in registers.
-//                Per sub-frame it splats every source of A (forward) and B (backward) whose
-//                footprint can reach the tile into two shared-memory z-buffers with 64-bit
-//                atomicMin on (depth, weight, source) keys (Eqs. 5-7), resolves the winners,
+//                Once per gap it lists the row segments whose motion bounds let them reach
+//                the tile; per sub-frame each warp re-tests one listed segment at a time and
+//                splats its sources of A (forward) or B (backward) into two shared-memory
+//                z-buffers with 64-bit atomicMin on (depth, weight, source) keys
+//                (Eqs. 5-7).  It then resolves the winners,
 //                blends in time with hole filling, runs the event model (Eq. 4, Eq. 8,
 //                refractory period) and compacts the events: warp-aggregated reservation in
 //                a shared staging buffer, one global atomic per CTA per sub-frame and a
@@ -54,22 +57,51 @@ __device__ __forceinline__ float other_depth(const float *__restrict__ Zo, int W
   return valid_depth(z) ? z : own;
 }
 
-// Bilinear-footprint z-test splat of one source into the tile's z-buffer (Eq. 6): every
-// integer pixel around q with weight > 0, inside the image and inside the tile, keeps the
-// minimum key [depth bits | quantised (1 - w) | source index].
+// Splat of one source into the tile's z-buffer (Sec. 3.3).  Direction 0 moves a source of A
+// forward to q = p - f m_A with depth (1-f) Z_A(p) + f Z_B(p - m_A); direction 1 moves a source
+// of B backward to q = p + (1-f) m_B with depth (1-f) Z_A(p + m_B) + f Z_B(p) (Eqs. 5, 7).
+// Every integer pixel of the bilinear footprint of q with weight > 0, inside the image and
+// inside the tile, keeps the minimum key [depth bits | quantised (1 - w) | source index]
+// (Eq. 6).  The depth gather runs only for sources that reach the tile.
 template <int TY>
-__device__ __forceinline__ void splat_tile(unsigned long long *zb, int x0, int y0, int W, int H,
-                                           float qx, float qy, float zt, uint32_t src,
-                                           bool tie_index) {
+__device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, int sx, int sy,
+                                             int W, int H, int x0, int y0, float f, float g,
+                                             const float2 *__restrict__ mvA,
+                                             const float *__restrict__ ZA,
+                                             const float2 *__restrict__ mvB,
+                                             const float *__restrict__ ZB, bool tie_index) {
+  const int p = sy * W + sx;
+  const float zs = __ldg((dir ? ZB : ZA) + p);
+  if (!valid_depth(zs)) return;
+  const float2 m = __ldg((dir ? mvB : mvA) + p);
+  const float fx = static_cast<float>(sx), fy = static_cast<float>(sy);
+  float qx, qy;
+  if (dir == 0) {
+    qx = __fsub_rn(fx, __fmul_rn(f, m.x));
+    qy = __fsub_rn(fy, __fmul_rn(f, m.y));
+  } else {
+    qx = __fadd_rn(fx, __fmul_rn(g, m.x));
+    qy = __fadd_rn(fy, __fmul_rn(g, m.y));
+  }
+  // No footprint pixel can be inside unless -1 < q < size; this also rejects NaN.
   if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H)))
     return;
   const float fx0 = floorf(qx), fy0 = floorf(qy);
   const int lx0 = static_cast<int>(fx0) - x0, ly0 = static_cast<int>(fy0) - y0;
   if (lx0 < -1 || lx0 >= kTileW || ly0 < -1 || ly0 >= TY) return;
+  float zt;
+  if (dir == 0) {
+    const float zo = other_depth(ZB, W, H, __fsub_rn(fx, m.x), __fsub_rn(fy, m.y), zs);
+    zt = __fadd_rn(__fmul_rn(g, zs), __fmul_rn(f, zo));
+  } else {
+    const float zo = other_depth(ZA, W, H, __fadd_rn(fx, m.x), __fadd_rn(fy, m.y), zs);
+    zt = __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zs));
+  }
   const float ax = __fsub_rn(qx, fx0), ay = __fsub_rn(qy, fy0);
   const float wx[2] = {__fsub_rn(1.0f, ax), ax};
   const float wy[2] = {__fsub_rn(1.0f, ay), ay};
-  const unsigned long long hi = static_cast<unsigned long long>(__float_as_uint(zt)) << 32;
+  const unsigned long long hi = (static_cast<unsigned long long>(__float_as_uint(zt)) << 32) |
+                                static_cast<unsigned>(p);
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy) {
     const int ly = ly0 + dy;
@@ -82,9 +114,21 @@ __device__ __forceinline__ void splat_tile(unsigned long long *zb, int x0, int y
       if (!(w > 0.0f)) continue;
       unsigned wq = 0;
       if (!tie_index) wq = min(__float2uint_rz(__fmul_rn(__fsub_rn(1.0f, w), 256.0f)), 255u);
-      atomicMin(&zb[ly * kTileW + lx], hi | (static_cast<unsigned long long>(wq) << 24) | src);
+      atomicMin(&zb[ly * kTileW + lx], hi | (static_cast<unsigned long long>(wq) << 24));
     }
   }
+}
+
+// True when no source of a row segment [xs, xs+31] x {ys}, displaced by an amount in
+// [dxl, dxh] x [dyl, dyh], can put a footprint pixel into the tile.  The 2-pixel margin covers
+// the footprint (1 pixel) and the rounding of the exact target computation; NaN bounds never
+// count as a miss.
+__device__ __forceinline__ bool seg_misses(float xs, float ys, float dxl, float dxh, float dyl,
+                                           float dyh, int x0, int y0, int th) {
+  return (xs + 31.0f + dxh + 2.0f < static_cast<float>(x0)) ||
+         (xs + dxl - 2.0f > static_cast<float>(x0 + kTileW - 1)) ||
+         (ys + dyh + 2.0f < static_cast<float>(y0)) ||
+         (ys + dyl - 2.0f > static_cast<float>(y0 + th - 1));
 }
 
 // Time of the k-th crossing of a pixel in this sub-frame: the level Lref + p k theta,
@@ -117,8 +161,11 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
   static_assert(NT >= 1 && NT * kThreads == TY * kTileW, "tile height must be 8, 16 or 32");
   __shared__ unsigned long long zb[2][TY * kTileW];
   __shared__ ulonglong2 stage[kEventStage];
+  __shared__ unsigned cand_xy[2][kCandidates];
+  __shared__ float4 cand_b[2][kCandidates];
   __shared__ unsigned s_n, s_flush;
   __shared__ unsigned long long s_base;
+  __shared__ int s_nc[2], s_over;
 
   const Tile tl = a.tiles[blockIdx.x];
   const DevEnv E = a.envs[tl.env];
@@ -169,7 +216,50 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
   const int h = mf < 65536.0f ? static_cast<int>(ceilf(mf)) + 2 : 65536;
   const int sx0 = max(0, tl.x0 - h), sx1 = min(W, tl.x0 + kTileW + h);
   const int sy0 = max(0, tl.y0 - h), sy1 = min(H, tl.y0 + TY + h);
-  if (tid == 0) s_n = 0;
+  if (tid == 0) {
+    s_n = 0;
+    s_nc[0] = s_nc[1] = 0;
+    s_over = 0;
+  }
+  __syncthreads();
+
+  // Candidate row segments for this keyframe gap: those whose motion bounds let them reach
+  // the tile at some f in [0, 1].  A full list falls back to scanning the whole region.
+  {
+    const int cx_lo = sx0 / kSegW, cx_hi = (sx1 - 1) / kSegW;
+    const int ncx = cx_hi - cx_lo + 1;
+    const int nreg = ncx * (sy1 - sy0);
+    for (int r = tid; r < 2 * nreg; r += kThreads) {
+      const int dir = r >= nreg ? 1 : 0;
+      const int rr = r - dir * nreg;
+      const int row = rr / ncx;
+      const int cy = sy0 + row, cx = cx_lo + (rr - row * ncx);
+      const float4 b = (dir ? a.segB : a.segA)[E.seg_off + static_cast<int64_t>(cy) * E.segs_x + cx];
+      if (!(b.x <= b.y)) continue;  // no source of this segment can splat
+      float dxl, dxh, dyl, dyh;     // displacement range over f in [0, 1]
+      if (dir == 0) {
+        dxl = fminf(0.0f, -b.y); dxh = fmaxf(0.0f, -b.x);
+        dyl = fminf(0.0f, -b.w); dyh = fmaxf(0.0f, -b.z);
+      } else {
+        dxl = fminf(0.0f, b.x); dxh = fmaxf(0.0f, b.y);
+        dyl = fminf(0.0f, b.z); dyh = fmaxf(0.0f, b.w);
+      }
+      if (seg_misses(static_cast<float>(cx * kSegW), static_cast<float>(cy), dxl, dxh, dyl, dyh,
+                     tl.x0, tl.y0, TY))
+        continue;
+      const int pos = atomicAdd(&s_nc[dir], 1);
+      if (pos < kCandidates) {
+        cand_xy[dir][pos] = (static_cast<unsigned>(cy) << 16) | static_cast<unsigned>(cx);
+        cand_b[dir][pos] = b;
+      } else {
+        s_over = 1;
+      }
+    }
+  }
+  __syncthreads();
+  const bool over = s_over != 0;
+  const int nA = min(s_nc[0], kCandidates);
+  const int nAB = nA + min(s_nc[1], kCandidates);
 
   for (int i = 1; i <= K; ++i) {
     const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
@@ -184,30 +274,33 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     __syncthreads();
 
     // ---- splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
-    for (int sy = sy0 + warp; sy < sy1; sy += 8) {
-      const float fy = static_cast<float>(sy);
-      for (int sx = sx0 + lane; sx < sx1; sx += kTileW) {
-        const int p = sy * W + sx;
-        const float fx = static_cast<float>(sx);
-        const float za = __ldg(ZA + p);
-        if (valid_depth(za)) {  // A forward: q = p - f m_A, p_B = p - m_A
-          const float2 m = __ldg(mvA + p);
-          const float qx = __fsub_rn(fx, __fmul_rn(f, m.x));
-          const float qy = __fsub_rn(fy, __fmul_rn(f, m.y));
-          const float zo = other_depth(ZB, W, H, __fsub_rn(fx, m.x), __fsub_rn(fy, m.y), za);
-          const float zt = __fadd_rn(__fmul_rn(g, za), __fmul_rn(f, zo));
-          splat_tile<TY>(zb[0], tl.x0, tl.y0, W, H, qx, qy, zt, static_cast<uint32_t>(p),
-                         tie_index);
+    if (!over) {
+      // one warp per candidate segment; the sub-frame test is uniform across the warp
+      for (int c = warp; c < nAB; c += kThreads / 32) {
+        const int dir = c >= nA ? 1 : 0;
+        const int idx = c - dir * nA;
+        const float4 b = cand_b[dir][idx];
+        const unsigned xy = cand_xy[dir][idx];
+        const int cy = static_cast<int>(xy >> 16), cx = static_cast<int>(xy & 0xFFFFu);
+        float dxl, dxh, dyl, dyh;
+        if (dir == 0) {
+          dxl = -f * b.y; dxh = -f * b.x; dyl = -f * b.w; dyh = -f * b.z;
+        } else {
+          dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
         }
-        const float zbv = __ldg(ZB + p);
-        if (valid_depth(zbv)) {  // B backward: q = p + (1-f) m_B, p_A = p + m_B
-          const float2 m = __ldg(mvB + p);
-          const float qx = __fadd_rn(fx, __fmul_rn(g, m.x));
-          const float qy = __fadd_rn(fy, __fmul_rn(g, m.y));
-          const float zo = other_depth(ZA, W, H, __fadd_rn(fx, m.x), __fadd_rn(fy, m.y), zbv);
-          const float zt = __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zbv));
-          splat_tile<TY>(zb[1], tl.x0, tl.y0, W, H, qx, qy, zt, static_cast<uint32_t>(p),
-                         tie_index);
+        if (seg_misses(static_cast<float>(cx * kSegW), static_cast<float>(cy), dxl, dxh, dyl,
+                       dyh, tl.x0, tl.y0, TY))
+          continue;
+        const int sx = cx * kSegW + lane;
+        if (sx < W)
+          splat_source<TY>(zb[dir], dir, sx, cy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB,
+                           tie_index);
+      }
+    } else {
+      for (int sy = sy0 + warp; sy < sy1; sy += kThreads / 32) {
+        for (int sx = sx0 + lane; sx < sx1; sx += kTileW) {
+          splat_source<TY>(zb[0], 0, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB, tie_index);
+          splat_source<TY>(zb[1], 1, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB, tie_index);
         }
       }
     }
@@ -343,37 +436,60 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
   if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) a.clock_out[tl.env] = T0 + a.dt;
 }
 
+// One warp per 32-pixel row segment: log-intensity, optional copies, and the segment's
+// motion bounds over the sources that can splat (valid depth, finite motion).
 __global__ void prep_kernel(const PrepArgs a) {
   const int e = blockIdx.y;
   const DevEnv E = a.envs[e];
-  const int n = E.W * E.H;
+  const int nseg = E.segs_x * E.H;
   const int64_t o = E.pix_off;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
   float mx = 0.0f;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const float2 m = reinterpret_cast<const float2 *>(a.mv)[o + p];
-    mx = fmaxf(mx, fmaxf(fabsf(m.x), fabsf(m.y)));
-    if (a.mv_out) reinterpret_cast<float2 *>(a.mv_out)[o + p] = m;
-    if (a.Z_out) a.Z_out[o + p] = a.Z[o + p];
-    if (a.L_out) {
-      float L;
-      if (a.mode == EVIS_IN_LOG) {
-        L = a.frames[o + p];
-      } else if (a.mode == EVIS_IN_LUM) {
-        L = log_intensity(a.frames[o + p], a.eps);
-      } else {
-        const float *c = a.frames + 3 * (o + p);
-        L = log_intensity(rec709(c[0], c[1], c[2]), a.eps);
+  for (int sg = blockIdx.x * wpb + (threadIdx.x >> 5); sg < nseg; sg += gridDim.x * wpb) {
+    const int y = sg / E.segs_x;
+    const int x = (sg - y * E.segs_x) * kSegW + lane;
+    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY;
+    if (x < E.W) {
+      const int64_t p = o + static_cast<int64_t>(y) * E.W + x;
+      const float2 m = reinterpret_cast<const float2 *>(a.mv)[p];
+      const float z = a.Z[p];
+      if (valid_depth(z) && isfinite(m.x) && isfinite(m.y)) {
+        lox = hix = m.x;
+        loy = hiy = m.y;
+        mx = fmaxf(mx, fmaxf(fabsf(m.x), fabsf(m.y)));
       }
-      a.L_out[o + p] = L;
+      if (a.mv_out) reinterpret_cast<float2 *>(a.mv_out)[p] = m;
+      if (a.Z_out) a.Z_out[p] = z;
+      if (a.L_out) {
+        float L;
+        if (a.mode == EVIS_IN_LOG) {
+          L = a.frames[p];
+        } else if (a.mode == EVIS_IN_LUM) {
+          L = log_intensity(a.frames[p], a.eps);
+        } else {
+          const float *c = a.frames + 3 * p;
+          L = log_intensity(rec709(c[0], c[1], c[2]), a.eps);
+        }
+        a.L_out[p] = L;
+      }
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      lox = fminf(lox, __shfl_xor_sync(kFull, lox, d));
+      hix = fmaxf(hix, __shfl_xor_sync(kFull, hix, d));
+      loy = fminf(loy, __shfl_xor_sync(kFull, loy, d));
+      hiy = fmaxf(hiy, __shfl_xor_sync(kFull, hiy, d));
+    }
+    if (lane == 0) a.seg[E.seg_off + sg] = make_float4(lox, hix, loy, hiy);
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, d));
   __shared__ float sm[32];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  if (lane == 0) sm[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0f;
+    mx = threadIdx.x < wpb ? sm[threadIdx.x] : 0.0f;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, d));
     // non-negative floats order like their bit patterns
@@ -407,7 +523,7 @@ int grid_for(int64_t n, int threads) {
 
 cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s) {
   const int threads = 256;
-  int bx = (a.max_px + threads * 4 - 1) / (threads * 4);
+  int bx = (a.max_segs + 4 * (threads / 32) - 1) / (4 * (threads / 32));
   if (bx < 1) bx = 1;
   prep_kernel<<<dim3(bx, n_envs), threads, 0, s>>>(a);
   return cudaGetLastError();

@@ -30,7 +30,11 @@ def _dev(a):
 
 
 def _frames(kf, mode):
-    return {0: kf.L, 1: kf.I, 2: None if kf.rgb is None else kf.rgb.reshape(-1)}[mode]
+    if mode == 0:
+        return kf.L
+    if mode == 1:
+        return kf.I
+    return kf.rgb.reshape(-1)
 
 
 def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), capacity=1 << 22,
@@ -67,7 +71,10 @@ def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), c
         for e, off in zip(envs, o.offsets):
             valid[off:off + e.H * e.W] = True
         np.testing.assert_array_equal(sg[0][valid], so[0][valid])
-        np.testing.assert_array_equal(sg[1][valid], so[1][valid])
+        if any(e.refractory_ns > 0 for e in envs):   # t_last is tracked only then
+            np.testing.assert_array_equal(sg[1][valid], so[1][valid])
+        else:
+            assert np.all(sg[1] == np.iinfo(np.int64).min)
         np.testing.assert_array_equal(sg[2], so[2])
     ctx.close()
     return eo
@@ -141,6 +148,26 @@ def test_adversarial_motion_and_depth(ev, oracle_mod):
     run_both(ev, oracle_mod, envs, kfs, 5_000_000, trace_steps=(1, 2))
 
 
+def test_wild_motion_overflows_candidate_lists(ev, oracle_mod):
+    """Motion of up to +-300 px in every row segment: each tile's list of candidate source
+    segments overflows and the kernel scans its whole source region instead."""
+    rng = np.random.default_rng(11)
+    envs = [TinyEnv(W=256, H=200, K=2, c_on=0.2, c_off=0.2)]
+    n = packed_total(envs)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(2):
+        k = KF()
+        k.mv = rng.uniform(-300, 300, size=(n, 2)).astype(np.float32)
+        k.Z = rng.uniform(1, 5, size=n).astype(np.float32)
+        k.L = rng.normal(0, 1, size=n).astype(np.float32)
+        kfs.append(k)
+    run_both(ev, oracle_mod, envs, kfs, 1_000_000, trace_steps=(1,))
+
+
 def test_static_scene_is_per_pixel_linear_esim(ev, oracle_mod):
     envs = [TinyEnv(W=50, H=30, K=8, c_on=0.2, c_off=0.2)]
     n = packed_total(envs)
@@ -184,8 +211,11 @@ def test_log_intensity_within_two_ulp(ev, oracle_mod, mode):
 
 @pytest.mark.parametrize("mode", [1, 2])
 def test_linear_inputs_end_to_end(ev, oracle_mod, scenes_mod, mode):
-    """Linear / RGB radiance inputs: the GPU log may differ from the host one by an ulp, so the
-    streams are compared statistically (counts within 0.2 %, 99 % identical events)."""
+    """Linear / RGB radiance inputs.  The GPU log may differ from the host one by an ulp, which
+    can move an interpolated timestamp by a few ns or, rarely, a crossing across a sub-frame
+    boundary, so the streams are compared per pixel: >= 99.5 % of pixels with the same event
+    count and polarities, and their timestamps within 1 ns at the median and 100 ns at the
+    99th percentile."""
     w = scenes_mod.config1()
     for lay in w.envs[0].layers:
         lay.tint_r, lay.tint_g, lay.tint_b = 0.9, 1.1, 0.7
@@ -198,9 +228,22 @@ def test_linear_inputs_end_to_end(ev, oracle_mod, scenes_mod, mode):
         ctx.step(_dev(fr), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
     eo, eg = o.events(), ctx.read_events()
     assert abs(len(eg) - len(eo)) <= 0.002 * len(eo)
-    so = set(map(bytes, eo.view(np.dtype((np.void, 16)))))
-    sg = set(map(bytes, eg.view(np.dtype((np.void, 16)))))
-    assert len(so & sg) >= 0.99 * len(eo)
+    W = w.envs[0].W
+    npx = W * w.envs[0].H
+
+    def by_pixel(e):
+        pix = e["y"].astype(np.int64) * W + e["x"]
+        order = np.lexsort((e["t"], pix))
+        return pix[order], e[order], np.bincount(pix, minlength=npx)
+
+    po, so, co = by_pixel(eo)
+    pg, sg, cg = by_pixel(eg)
+    same = co == cg
+    assert same.mean() >= 0.995
+    ko, kg = same[po], same[pg]
+    assert np.array_equal(so["p"][ko], sg["p"][kg])
+    dt = np.abs(so["t"][ko] - sg["t"][kg])
+    assert np.median(dt) <= 1 and np.percentile(dt, 99) <= 100
 
 
 def test_step_host_matches_device_step(ev, scenes_mod):
