@@ -249,8 +249,8 @@ def test_linear_inputs_end_to_end(ev, oracle_mod, scenes_mod, mode):
 def test_step_host_matches_device_step(ev, scenes_mod):
     w = scenes_mod.config2(n_envs=3)
     kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
-    a = ev.Context(w.envs, flags=ev.IN_LUM)
-    b = ev.Context(w.envs, flags=ev.IN_LUM | ev.KEEP_INPUTS)
+    a = ev.Context(w.envs, flags=ev.IN_LUM, capacity=1 << 24)
+    b = ev.Context(w.envs, flags=ev.IN_LUM | ev.KEEP_INPUTS, capacity=1 << 24)
     alive = []
     for kf in kfs:
         g = (_dev(kf.I), _dev(kf.mv), _dev(kf.Z))
