@@ -156,6 +156,11 @@ evis_status evis_step_trace(evis_ctx *ctx, const float *frames, const float *mv,
 evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float eps, float *out,
                                evis_stream_t stream);
 
+/* Selects the target tile of the synthesis kernel: tile_w x tile_h pixels per CTA, one of
+ * 32x16, 32x32, 64x16 (default), 64x32, 128x16.  Results do not depend on the shape, only
+ * speed does.  Synchronises the stream; EVIS_ERR_INVALID_ARG for another shape. */
+evis_status evis_set_tile_shape(evis_ctx *ctx, int32_t tile_w, int32_t tile_h);
+
 /* Per-kernel timing for profiling.  With max_steps > 0, each following evis_step (or
  * evis_step_host / evis_step_trace) records CUDA events on the context's stream around its
  * two phases, for at most max_steps steps; max_steps = 0 disables and forgets the records.

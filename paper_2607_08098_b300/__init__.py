@@ -60,6 +60,7 @@ _SIGS = {
     "evis_get_state": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "evis_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "evis_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p]),
@@ -237,6 +238,12 @@ class Context:
         cnt = ctypes.c_void_p()
         _check(lib().evis_events_device(self._h, ctypes.byref(ev), ctypes.byref(cnt)), self._h)
         return ev.value, cnt.value
+
+    TILE_SHAPES = ((32, 16), (32, 32), (64, 16), (64, 32), (128, 16))
+
+    def set_tile_shape(self, tile_w: int, tile_h: int):
+        """Target tile of the synthesis kernel (speed only; results are identical)."""
+        _check(lib().evis_set_tile_shape(self._h, int(tile_w), int(tile_h)), self._h)
 
     def profile(self, max_steps: int):
         """Record per-phase CUDA events for the next ``max_steps`` steps (0 disables)."""

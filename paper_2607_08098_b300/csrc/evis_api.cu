@@ -26,6 +26,7 @@ struct evis_ctx {
   int max_px = 0;
   int max_segs = 0;
   int64_t total_segs = 0;
+  int tile_w = 64;
   int tile_h = 16;
   int n_tiles = 0;
   bool any_refr = false;
@@ -126,6 +127,28 @@ __global__ void fill_i64(int64_t *p, int64_t v, int64_t n) {
     p[i] = v;
 }
 
+// Tiles of every environment for the context's tile shape, longest-running (largest K)
+// first so that the tail of the launch holds the short ones.
+std::vector<Tile> build_tiles(const evis_ctx *c) {
+  std::vector<Tile> tiles;
+  for (int i = 0; i < c->n; ++i) {
+    const evis_env_desc &d = c->envs[i];
+    for (int y = 0; y < d.height; y += c->tile_h)
+      for (int x = 0; x < d.width; x += c->tile_w) tiles.push_back(Tile{i, x, y, 0});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const Tile &a, const Tile &b) {
+    return c->envs[a.env].K > c->envs[b.env].K;
+  });
+  return tiles;
+}
+
+// Tile count of the smallest supported tile (the capacity of the device tile table).
+int64_t max_tiles(const evis_ctx *c) {
+  int64_t n = 0;
+  for (const evis_env_desc &d : c->envs) n += int64_t((d.width + 31) / 32) * ((d.height + 15) / 16);
+  return n;
+}
+
 evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
                     int64_t dt, uint64_t *tr_keys, float *tr_L) {
   if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
@@ -187,7 +210,7 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
     s.tr_L = tr_L;
     s.tr_koff = c->d_tr_off;
     s.tr_loff = c->d_tr_off + c->n;
-    e = evis::launch_step(s, c->n_tiles, c->tile_h, tr_keys != nullptr, c->stream);
+    e = evis::launch_step(s, c->n_tiles, c->tile_w, c->tile_h, tr_keys != nullptr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     c->clk ^= 1;
   } else {
@@ -253,15 +276,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     ko += int64_t(d.K) * 2 * px;
     lo += int64_t(d.K) * px;
   }
-  // target tiles, longest-running (largest K) first
-  std::vector<Tile> tiles;
-  for (int i = 0; i < n_envs; ++i) {
-    const evis_env_desc &d = envs[i];
-    for (int y = 0; y < d.height; y += c->tile_h)
-      for (int x = 0; x < d.width; x += evis::kTileW) tiles.push_back(Tile{i, x, y, 0});
-  }
-  std::stable_sort(tiles.begin(), tiles.end(),
-                   [&](const Tile &a, const Tile &b) { return envs[a.env].K > envs[b.env].K; });
+  std::vector<Tile> tiles = build_tiles(c);
   c->n_tiles = static_cast<int>(tiles.size());
 
   cudaError_t e = cudaGetDevice(&c->device);
@@ -274,7 +289,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   };
   if (e != cudaSuccess) return bail(e, "cudaGetDevice");
   if ((e = dalloc(c, &c->d_envs, n_envs)) != cudaSuccess) return bail(e, "alloc envs");
-  if ((e = dalloc(c, &c->d_tiles, tiles.size())) != cudaSuccess) return bail(e, "alloc tiles");
+  if ((e = dalloc(c, &c->d_tiles, max_tiles(c))) != cudaSuccess) return bail(e, "alloc tiles");
   if ((e = dalloc(c, &c->d_Lref, c->total)) != cudaSuccess) return bail(e, "alloc Lref");
   if (c->any_refr && (e = dalloc(c, &c->d_tlast, c->total)) != cudaSuccess)
     return bail(e, "alloc t_last");
@@ -417,6 +432,22 @@ evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float 
     return EVIS_ERR_INVALID_ARG;
   cudaError_t e = evis::launch_log(in, n, mode, eps, out, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
+}
+
+evis_status evis_set_tile_shape(evis_ctx *c, int32_t tile_w, int32_t tile_h) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (!evis::tile_shape_supported(tile_w, tile_h))
+    return fail(c, EVIS_ERR_INVALID_ARG, "unsupported tile shape");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "tile shape sync");
+  c->tile_w = tile_w;
+  c->tile_h = tile_h;
+  std::vector<Tile> tiles = build_tiles(c);
+  c->n_tiles = static_cast<int>(tiles.size());
+  if ((e = cudaMemcpy(c->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "upload tiles");
+  return EVIS_OK;
 }
 
 evis_status evis_profile_enable(evis_ctx *c, int32_t max_steps) {

@@ -11,11 +11,10 @@ namespace evis {
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxCrossings = 4096;         // crossings per pixel per sub-frame
 constexpr int64_t kNoEvent = INT64_MIN;     // t_last of a pixel that never fired
-constexpr int kTileW = 32;                  // tile width = one warp of targets
 constexpr int kThreads = 256;               // threads per step CTA (8 warps)
 constexpr int kEventStage = 1024;           // events staged in shared memory per CTA
 constexpr int kSegW = 32;                   // motion bounds are kept per 32-pixel row segment
-constexpr int kCandidates = 384;            // candidate segments per direction per tile
+constexpr int kCandidates = 512;            // candidate segments per direction per tile
 
 // Per-environment constants, resident in device memory.
 struct DevEnv {
@@ -70,7 +69,9 @@ struct PrepArgs {
 
 cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
-cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_h, bool trace, cudaStream_t s);
+cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_w, int tile_h, bool trace,
+                        cudaStream_t s);
+bool tile_shape_supported(int tile_w, int tile_h);
 cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, float *out,
                        cudaStream_t s);
 

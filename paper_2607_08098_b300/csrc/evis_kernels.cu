@@ -10,17 +10,18 @@
 //   prep_kernel  per keyframe: log-intensity (Sec. 3.2, Eq. 3), optional copies of the
 //                motion/depth maps, per-environment max |mv| and per 32-pixel row segment
 //                motion bounds (which sources can reach which tile).
-//   step_kernel  per keyframe gap: one CTA owns a 32 x TY target tile of one environment
+//   step_kernel  per keyframe gap: one CTA owns a TX x TY target tile of one environment
 //                and keeps, for all K sub-frames, its pixels' event state in registers.
 //                Once per gap it lists the row segments whose motion bounds let them reach
-//                the tile; per sub-frame each warp re-tests one listed segment at a time and
-//                splats its sources of A (forward) or B (backward) into two shared-memory
+//                the tile; per sub-frame all threads re-test the listed segments at once,
+//                and each warp splats the sources of one reaching segment of A (forward)
+//                or B (backward) into two shared-memory
 //                z-buffers with 64-bit atomicMin on (depth, weight, source) keys
 //                (Eqs. 5-7).  It then resolves the winners,
 //                blends in time with hole filling, runs the event model (Eq. 4, Eq. 8,
-//                refractory period) and compacts the events: warp-aggregated reservation in
-//                a shared staging buffer, one global atomic per CTA per sub-frame and a
-//                coalesced 16-byte-per-thread flush.
+//                refractory period) and compacts the events: a warp-wide reservation per
+//                crossing index in a shared staging buffer, one global atomic per CTA per
+//                sub-frame and a coalesced 16-byte-per-thread flush.
 #include <cfloat>
 
 #include "evis_internal.h"
@@ -63,7 +64,7 @@ __device__ __forceinline__ float other_depth(const float *__restrict__ Zo, int W
 // Every integer pixel of the bilinear footprint of q with weight > 0, inside the image and
 // inside the tile, keeps the minimum key [depth bits | quantised (1 - w) | source index]
 // (Eq. 6).  The depth gather runs only for sources that reach the tile.
-template <int TY>
+template <int TX, int TY>
 __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, int sx, int sy,
                                              int W, int H, int x0, int y0, float f, float g,
                                              const float2 *__restrict__ mvA,
@@ -88,7 +89,7 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
     return;
   const float fx0 = floorf(qx), fy0 = floorf(qy);
   const int lx0 = static_cast<int>(fx0) - x0, ly0 = static_cast<int>(fy0) - y0;
-  if (lx0 < -1 || lx0 >= kTileW || ly0 < -1 || ly0 >= TY) return;
+  if (lx0 < -1 || lx0 >= TX || ly0 < -1 || ly0 >= TY) return;
   float zt;
   if (dir == 0) {
     const float zo = other_depth(ZB, W, H, __fsub_rn(fx, m.x), __fsub_rn(fy, m.y), zs);
@@ -109,26 +110,49 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
       const int lx = lx0 + dx;
-      if (lx < 0 || lx >= kTileW || x0 + lx >= W) continue;
+      if (lx < 0 || lx >= TX || x0 + lx >= W) continue;
       const float w = __fmul_rn(wx[dx], wy[dy]);
       if (!(w > 0.0f)) continue;
       unsigned wq = 0;
       if (!tie_index) wq = min(__float2uint_rz(__fmul_rn(__fsub_rn(1.0f, w), 256.0f)), 255u);
-      atomicMin(&zb[ly * kTileW + lx], hi | (static_cast<unsigned long long>(wq) << 24));
+      atomicMin(&zb[ly * TX + lx], hi | (static_cast<unsigned long long>(wq) << 24));
     }
   }
 }
 
 // True when no source of a row segment [xs, xs+31] x {ys}, displaced by an amount in
-// [dxl, dxh] x [dyl, dyh], can put a footprint pixel into the tile.  The 2-pixel margin covers
-// the footprint (1 pixel) and the rounding of the exact target computation; NaN bounds never
-// count as a miss.
+// [dxl, dxh] x [dyl, dyh], can put a footprint pixel into the TX x TY tile at (x0, y0).  The
+// 2-pixel margin covers the footprint (1 pixel) and the rounding of the exact target
+// computation; NaN bounds never count as a miss.
+template <int TX, int TY>
 __device__ __forceinline__ bool seg_misses(float xs, float ys, float dxl, float dxh, float dyl,
-                                           float dyh, int x0, int y0, int th) {
+                                           float dyh, int x0, int y0) {
   return (xs + 31.0f + dxh + 2.0f < static_cast<float>(x0)) ||
-         (xs + dxl - 2.0f > static_cast<float>(x0 + kTileW - 1)) ||
+         (xs + dxl - 2.0f > static_cast<float>(x0 + TX - 1)) ||
          (ys + dyh + 2.0f < static_cast<float>(y0)) ||
-         (ys + dyl - 2.0f > static_cast<float>(y0 + th - 1));
+         (ys + dyl - 2.0f > static_cast<float>(y0 + TY - 1));
+}
+
+// t_prev + llrint(fr * (t_i - t_prev)) with the product taken in binary64 and rounded half to
+// even.  When t_i - t_prev < 2^29 the binary64 product of the binary32 fraction (24-bit
+// significand) and the interval is exact, so the same integer is obtained with a 64-bit
+// integer multiply, a shift and a round-half-even on the discarded bits.  Longer intervals
+// take the binary64 route.
+__device__ __forceinline__ int64_t interp_time(float fr, int64_t tprev, int64_t ti) {
+  const int64_t d = ti - tprev;
+  if (d < (int64_t(1) << 29)) {
+    const unsigned b = __float_as_uint(fr);          // fr in [0, 1]
+    const unsigned ex = b >> 23;
+    const unsigned long long m = ex ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+    const int sh = ex ? 150 - static_cast<int>(ex) : 149;   // fr = m * 2^-sh, sh >= 23
+    const unsigned long long P = m * static_cast<unsigned long long>(d);  // < 2^53
+    if (sh >= 64) return tprev;                      // fr * d < 2^-11
+    unsigned long long q = P >> sh;
+    const unsigned long long r = P & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (r > half || (r == half && (q & 1ull))) ++q;
+    return tprev + static_cast<int64_t>(q);
+  }
+  return tprev + __double2ll_rn(__dmul_rn(static_cast<double>(fr), static_cast<double>(d)));
 }
 
 // Time of the k-th crossing of a pixel in this sub-frame: the level Lref + p k theta,
@@ -141,8 +165,7 @@ __device__ __forceinline__ int64_t crossing_time(float Lref, int pk, float th, f
   float fr = den == 0.0f ? 1.0f : __fdiv_rn(num, den);
   if (!(fr > 0.0f)) fr = 0.0f;
   else if (fr > 1.0f) fr = 1.0f;
-  return tprev + __double2ll_rn(__dmul_rn(static_cast<double>(fr),
-                                          static_cast<double>(ti - tprev)));
+  return interp_time(fr, tprev, ti);
 }
 
 __device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int env, int p) {
@@ -155,15 +178,32 @@ __device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int en
   return r;
 }
 
-template <int TY, bool TRACE>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
-  constexpr int NT = TY * kTileW / kThreads;  // targets per thread (rows warp + 8 j)
-  static_assert(NT >= 1 && NT * kThreads == TY * kTileW, "tile height must be 8, 16 or 32");
-  __shared__ unsigned long long zb[2][TY * kTileW];
-  __shared__ ulonglong2 stage[kEventStage];
-  __shared__ unsigned cand_xy[2][kCandidates];
-  __shared__ float4 cand_b[2][kCandidates];
-  __shared__ unsigned s_n, s_flush;
+// Dynamic shared memory of one step CTA.
+template <int TX, int TY>
+struct StepSmem {
+  unsigned long long zb[2][TX * TY];       // z-buffers, A forward and B backward
+  ulonglong2 stage[kEventStage];           // events of this sub-frame before the flush
+  float4 cand_b[2][kCandidates];           // candidate segments' motion bounds
+  unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
+  unsigned hit[2 * kCandidates];           // candidates that can reach the tile this sub-frame
+};
+
+// Resident CTAs per SM each tile shape is compiled for (bounded by its shared memory); it
+// sets the register budget.
+template <int TX, int TY>
+constexpr int step_min_blocks() {
+  return TX * TY <= 512 ? 4 : (TX * TY <= 1024 ? 3 : 2);
+}
+
+template <int TX, int TY, bool TRACE>
+__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
+  constexpr int NT = TX * TY / kThreads;   // targets per thread
+  constexpr int NW = kThreads / 32;
+  constexpr int ROWS = kThreads / TX;      // tile rows covered by one pass of the block
+  static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
+  __shared__ unsigned s_n, s_flush, s_nhit;
   __shared__ unsigned long long s_base;
   __shared__ int s_nc[2], s_over;
 
@@ -178,22 +218,25 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
   const float *__restrict__ ZA = a.ZA + o;
   const float *__restrict__ ZB = a.ZB + o;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lanes_below = (1u << lane) - 1u;
   const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
   const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
   const int64_t T0 = a.clock_in[tl.env];
   const int64_t refr = E.refractory_ns;
-  const int tx = tl.x0 + lane;
+  const int tx = tl.x0 + tid % TX;
+  const int ty0 = tl.y0 + tid / TX;
   const int64_t HW = static_cast<int64_t>(W) * H;
 
+  // per-pixel event state of this thread's targets (rows ty0 + ROWS j), in registers for
+  // the whole keyframe gap
   float Lref[NT], Lprev[NT], thon[NT], thoff[NT];
   int64_t tprev[NT], tlast[NT];
-  int pix[NT];
   bool act[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
-    const int ty = tl.y0 + warp + 8 * j;
+    const int ty = ty0 + ROWS * j;
+    const int pix = ty * W + tx;
     act[j] = tx < W && ty < H;
-    pix[j] = ty * W + tx;
     tprev[j] = T0;
     tlast[j] = kNoEvent;
     Lref[j] = 0.0f;
@@ -201,12 +244,12 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     thon[j] = E.c_on;
     thoff[j] = E.c_off;
     if (act[j]) {
-      Lref[j] = a.Lref[o + pix[j]];
-      Lprev[j] = LA[pix[j]];
-      if (a.tlast) tlast[j] = a.tlast[o + pix[j]];
+      Lref[j] = a.Lref[o + pix];
+      Lprev[j] = LA[pix];
+      if (a.tlast) tlast[j] = a.tlast[o + pix];
       if (E.con_map) {
-        thon[j] = E.con_map[pix[j]];
-        thoff[j] = E.coff_map[pix[j]];
+        thon[j] = E.con_map[pix];
+        thoff[j] = E.coff_map[pix];
       }
     }
   }
@@ -214,10 +257,11 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
   // Sources that can reach the tile lie within the largest |mv| (+ footprint) of it.
   const float mf = fmaxf(a.flowA[tl.env], a.flowB[tl.env]);
   const int h = mf < 65536.0f ? static_cast<int>(ceilf(mf)) + 2 : 65536;
-  const int sx0 = max(0, tl.x0 - h), sx1 = min(W, tl.x0 + kTileW + h);
+  const int sx0 = max(0, tl.x0 - h), sx1 = min(W, tl.x0 + TX + h);
   const int sy0 = max(0, tl.y0 - h), sy1 = min(H, tl.y0 + TY + h);
   if (tid == 0) {
     s_n = 0;
+    s_nhit = 0;
     s_nc[0] = s_nc[1] = 0;
     s_over = 0;
   }
@@ -244,13 +288,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
         dxl = fminf(0.0f, b.x); dxh = fmaxf(0.0f, b.y);
         dyl = fminf(0.0f, b.z); dyh = fmaxf(0.0f, b.w);
       }
-      if (seg_misses(static_cast<float>(cx * kSegW), static_cast<float>(cy), dxl, dxh, dyl, dyh,
-                     tl.x0, tl.y0, TY))
+      if (seg_misses<TX, TY>(static_cast<float>(cx * kSegW), static_cast<float>(cy), dxl, dxh,
+                             dyl, dyh, tl.x0, tl.y0))
         continue;
       const int pos = atomicAdd(&s_nc[dir], 1);
       if (pos < kCandidates) {
-        cand_xy[dir][pos] = (static_cast<unsigned>(cy) << 16) | static_cast<unsigned>(cx);
-        cand_b[dir][pos] = b;
+        S.cand_xy[dir][pos] = (static_cast<unsigned>(cy) << 16) | static_cast<unsigned>(cx);
+        S.cand_b[dir][pos] = b;
       } else {
         s_over = 1;
       }
@@ -265,173 +309,169 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a) {
     const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
     const float g = __fsub_rn(1.0f, f);
     const int64_t ti = T0 + (static_cast<int64_t>(i) * a.dt) / K;
+
+    // ---- phase 1: clear the z-buffers; list the candidates that reach the tile now ----
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      const int s = (warp + 8 * j) * kTileW + lane;
-      zb[0][s] = kEmptyKey;
-      zb[1][s] = kEmptyKey;
+      S.zb[0][tid + kThreads * j] = kEmptyKey;
+      S.zb[1][tid + kThreads * j] = kEmptyKey;
+    }
+    if (!over) {
+      for (int c0 = 0; c0 < nAB; c0 += kThreads) {
+        const int c = c0 + tid;
+        bool hit = false;
+        if (c < nAB) {
+          const int dir = c >= nA ? 1 : 0;
+          const int idx = c - dir * nA;
+          const float4 b = S.cand_b[dir][idx];
+          const unsigned xy = S.cand_xy[dir][idx];
+          float dxl, dxh, dyl, dyh;
+          if (dir == 0) {
+            dxl = -f * b.y; dxh = -f * b.x; dyl = -f * b.w; dyh = -f * b.z;
+          } else {
+            dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
+          }
+          hit = !seg_misses<TX, TY>(static_cast<float>((xy & 0xFFFFu) * kSegW),
+                                    static_cast<float>(xy >> 16), dxl, dxh, dyl, dyh, tl.x0,
+                                    tl.y0);
+        }
+        const unsigned m = __ballot_sync(kFull, hit);
+        if (m) {
+          unsigned base = 0;
+          if (lane == 0) base = atomicAdd(&s_nhit, static_cast<unsigned>(__popc(m)));
+          base = __shfl_sync(kFull, base, 0);
+          if (hit) S.hit[base + __popc(m & lanes_below)] = static_cast<unsigned>(c);
+        }
+      }
     }
     __syncthreads();
 
-    // ---- splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
+    // ---- phase 2: splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
     if (!over) {
-      // one warp per candidate segment; the sub-frame test is uniform across the warp
-      for (int c = warp; c < nAB; c += kThreads / 32) {
+      const unsigned nh = s_nhit;
+      for (unsigned hh = warp; hh < nh; hh += NW) {  // one warp per segment, one lane per source
+        const int c = static_cast<int>(S.hit[hh]);
         const int dir = c >= nA ? 1 : 0;
-        const int idx = c - dir * nA;
-        const float4 b = cand_b[dir][idx];
-        const unsigned xy = cand_xy[dir][idx];
-        const int cy = static_cast<int>(xy >> 16), cx = static_cast<int>(xy & 0xFFFFu);
-        float dxl, dxh, dyl, dyh;
-        if (dir == 0) {
-          dxl = -f * b.y; dxh = -f * b.x; dyl = -f * b.w; dyh = -f * b.z;
-        } else {
-          dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
-        }
-        if (seg_misses(static_cast<float>(cx * kSegW), static_cast<float>(cy), dxl, dxh, dyl,
-                       dyh, tl.x0, tl.y0, TY))
-          continue;
-        const int sx = cx * kSegW + lane;
+        const unsigned xy = S.cand_xy[dir][c - dir * nA];
+        const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + lane;
         if (sx < W)
-          splat_source<TY>(zb[dir], dir, sx, cy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB,
-                           tie_index);
+          splat_source<TX, TY>(S.zb[dir], dir, sx, static_cast<int>(xy >> 16), W, H, tl.x0,
+                               tl.y0, f, g, mvA, ZA, mvB, ZB, tie_index);
       }
     } else {
-      for (int sy = sy0 + warp; sy < sy1; sy += kThreads / 32) {
-        for (int sx = sx0 + lane; sx < sx1; sx += kTileW) {
-          splat_source<TY>(zb[0], 0, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB, tie_index);
-          splat_source<TY>(zb[1], 1, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB, tie_index);
+      for (int sy = sy0 + warp; sy < sy1; sy += NW) {
+        for (int sx = sx0 + lane; sx < sx1; sx += 32) {
+          splat_source<TX, TY>(S.zb[0], 0, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB,
+                               tie_index);
+          splat_source<TX, TY>(S.zb[1], 1, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB,
+                               tie_index);
         }
       }
     }
     __syncthreads();
 
-    // ---- resolve, blend, threshold crossings (count pass) ----
-    float Lnew[NT], th[NT];
-    int nc[NT], pol[NT];
-    bool has[NT];
-    int cnt = 0;
+    // ---- phase 3: resolve, blend, threshold crossings, emission ----
+    if (tid == 0) s_nhit = 0;
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      nc[j] = 0;
-      pol[j] = 1;
-      th[j] = thon[j];
-      has[j] = false;
-      Lnew[j] = 0.0f;
-      if (!act[j]) continue;
-      const int s = (warp + 8 * j) * kTileW + lane;
-      const unsigned long long kA = zb[0][s], kB = zb[1][s];
-      const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
-      const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
-      const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
-      float L;
-      if (b_primary) {
-        L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
-      } else {
-        L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))
-                           : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
-      }
-      if (TRACE) {
-        const int64_t kb = a.tr_koff[tl.env] + static_cast<int64_t>(i - 1) * 2 * HW + pix[j];
-        a.tr_keys[kb] = kA;
-        a.tr_keys[kb + HW] = kB;
-        a.tr_L[a.tr_loff[tl.env] + static_cast<int64_t>(i - 1) * HW + pix[j]] = L;
-      }
-      if (!hasA && !hasB) continue;  // no sample: the pixel holds its state this sub-frame
-      has[j] = true;
-      Lnew[j] = L;
-      const float d = __fsub_rn(L, Lref[j]);
-      pol[j] = d > 0.0f ? 1 : -1;
-      th[j] = pol[j] > 0 ? thon[j] : thoff[j];
-      const float q = __fdiv_rn(fabsf(d), th[j]);
-      int n = 0;
-      if (q >= 1.0f) n = q >= static_cast<float>(kMaxCrossings) ? kMaxCrossings
-                                                                : static_cast<int>(floorf(q));
-      nc[j] = n;
-      if (refr <= 0) {
-        cnt += n;
-      } else {
-        int64_t tl_ = tlast[j];
-        for (int k = 1; k <= n; ++k) {
-          const int64_t t = crossing_time(Lref[j], pol[j] * k, th[j], Lprev[j], L, tprev[j], ti);
-          if (tl_ == kNoEvent || t - tl_ >= refr) {
-            ++cnt;
-            tl_ = t;
-          }
+      const int ty = ty0 + ROWS * j;
+      const int pix = ty * W + tx;
+      bool has = false;
+      float L = 0.0f, th = thon[j];
+      int n = 0, pol = 1;
+      if (act[j]) {
+        const unsigned long long kA = S.zb[0][tid + kThreads * j];
+        const unsigned long long kB = S.zb[1][tid + kThreads * j];
+        const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
+        const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
+        const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
+        if (b_primary) {
+          L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
+        } else {
+          L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))
+                             : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+        }
+        if (TRACE) {
+          const int64_t kb = a.tr_koff[tl.env] + static_cast<int64_t>(i - 1) * 2 * HW + pix;
+          a.tr_keys[kb] = kA;
+          a.tr_keys[kb + HW] = kB;
+          a.tr_L[a.tr_loff[tl.env] + static_cast<int64_t>(i - 1) * HW + pix] = L;
+        }
+        has = hasA || hasB;  // no sample: the pixel holds its state this sub-frame
+        if (has) {
+          const float d = __fsub_rn(L, Lref[j]);
+          pol = d > 0.0f ? 1 : -1;
+          th = pol > 0 ? thon[j] : thoff[j];
+          const float q = __fdiv_rn(fabsf(d), th);
+          if (q >= 1.0f) n = q >= static_cast<float>(kMaxCrossings) ? kMaxCrossings
+                                                                  : static_cast<int>(floorf(q));
         }
       }
-    }
-
-    // ---- warp-aggregated reservation: staging buffer first, global overflow path ----
-    int incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int v = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl += v;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    unsigned base = 0;
-    unsigned long long gbase = 0;
-    if (total > 0) {
-      if (lane == 31) {
-        base = atomicAdd(&s_n, static_cast<unsigned>(total));
-        const unsigned room = base < kEventStage ? kEventStage - base : 0u;
-        if (room < static_cast<unsigned>(total))
-          gbase = atomicAdd(a.ev_count, static_cast<unsigned long long>(total - room));
-      }
-      base = __shfl_sync(kFull, base, 31);
-      gbase = __shfl_sync(kFull, gbase, 31);
-    }
-    const unsigned room = base < kEventStage ? kEventStage - base : 0u;
-
-    // ---- write pass: regenerate the crossings, emit, update the state ----
-    unsigned e = static_cast<unsigned>(incl - cnt);
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      if (!has[j]) continue;
-      const int n = nc[j];
-      const int ty = tl.y0 + warp + 8 * j;
-      for (int k = 1; k <= n; ++k) {
-        const int64_t t = crossing_time(Lref[j], pol[j] * k, th[j], Lprev[j], Lnew[j], tprev[j], ti);
-        if (refr <= 0 || tlast[j] == kNoEvent || t - tlast[j] >= refr) {
-          const ulonglong2 rec = make_event(t, tx, ty, tl.env, pol[j]);
-          if (e < room) {
-            stage[base + e] = rec;
+      // crossings k = 1..n, one warp-wide reservation per k
+      const int nmax = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(n)));
+      for (int k = 1; k <= nmax; ++k) {
+        bool emit = false;
+        int64_t t = 0;
+        if (k <= n) {
+          t = crossing_time(Lref[j], pol * k, th, Lprev[j], L, tprev[j], ti);
+          emit = refr <= 0 || tlast[j] == kNoEvent || t - tlast[j] >= refr;
+          if (emit) tlast[j] = t;
+        }
+        const unsigned m = __ballot_sync(kFull, emit);
+        if (m == 0) continue;
+        const unsigned cnt = static_cast<unsigned>(__popc(m));
+        unsigned base = 0;
+        unsigned long long gb = 0;
+        if (lane == 0) {
+          base = atomicAdd(&s_n, cnt);
+          if (base + cnt > static_cast<unsigned>(kEventStage))  // staging full: go global
+            gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
+                                           base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+        }
+        base = __shfl_sync(kFull, base, 0);
+        gb = __shfl_sync(kFull, gb, 0);
+        if (emit) {
+          const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
+          const ulonglong2 rec = make_event(t, tx, ty, tl.env, pol);
+          if (idx < static_cast<unsigned>(kEventStage)) {
+            S.stage[idx] = rec;
           } else {
-            const unsigned long long gi = gbase + (e - room);
+            const unsigned long long gi =
+                gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
             if (gi < a.capacity) a.events[gi] = rec;
           }
-          ++e;
-          tlast[j] = t;
         }
       }
-      if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(static_cast<float>(pol[j] * n), th[j]));
-      Lprev[j] = Lnew[j];
-      tprev[j] = ti;
+      if (has) {
+        if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(static_cast<float>(pol * n), th));
+        Lprev[j] = L;
+        tprev[j] = ti;
+      }
     }
     __syncthreads();
 
-    // ---- flush the staging buffer: one global reservation, coalesced 16 B stores ----
+    // ---- phase 4: flush the staging buffer: one global reservation, 16 B per thread ----
     if (tid == 0) {
-      const unsigned n = min(s_n, static_cast<unsigned>(kEventStage));
-      s_flush = n;
-      s_base = n ? atomicAdd(a.ev_count, static_cast<unsigned long long>(n)) : 0ull;
+      const unsigned nn = min(s_n, static_cast<unsigned>(kEventStage));
+      s_flush = nn;
+      s_base = nn ? atomicAdd(a.ev_count, static_cast<unsigned long long>(nn)) : 0ull;
       s_n = 0;
     }
     __syncthreads();
     const unsigned nf = s_flush;
-    const unsigned long long gb = s_base;
+    const unsigned long long gbs = s_base;
     for (unsigned r = tid; r < nf; r += kThreads) {
-      const unsigned long long gi = gb + r;
-      if (gi < a.capacity) a.events[gi] = stage[r];
+      const unsigned long long gi = gbs + r;
+      if (gi < a.capacity) a.events[gi] = S.stage[r];
     }
   }
 
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     if (!act[j]) continue;
-    a.Lref[o + pix[j]] = Lref[j];
-    if (a.tlast) a.tlast[o + pix[j]] = tlast[j];
+    const int pix = (ty0 + ROWS * j) * W + tx;
+    a.Lref[o + pix] = Lref[j];
+    if (a.tlast) a.tlast[o + pix] = tlast[j];
   }
   if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) a.clock_out[tl.env] = T0 + a.dt;
 }
@@ -540,22 +580,38 @@ cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, flo
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_h, bool trace, cudaStream_t s) {
-  if (n_tiles <= 0) return cudaSuccess;
-#define EVIS_STEP_CASE(TY)                                                     \
-  case TY:                                                                     \
-    if (trace) step_kernel<TY, true><<<n_tiles, kThreads, 0, s>>>(a);          \
-    else step_kernel<TY, false><<<n_tiles, kThreads, 0, s>>>(a);               \
-    break;
-  switch (tile_h) {
-    EVIS_STEP_CASE(8)
-    EVIS_STEP_CASE(16)
-    EVIS_STEP_CASE(32)
-    default:
-      return cudaErrorInvalidValue;
+template <int TX, int TY, bool TRACE>
+cudaError_t launch_shape(const StepArgs &a, int n_tiles, cudaStream_t s) {
+  static bool configured = false;  // one attribute call per instantiation and process
+  const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
   }
-#undef EVIS_STEP_CASE
+  step_kernel<TX, TY, TRACE><<<n_tiles, kThreads, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+bool tile_shape_supported(int tw, int th) {
+  return (tw == 32 && (th == 16 || th == 32)) || (tw == 64 && (th == 16 || th == 32)) ||
+         (tw == 128 && th == 16);
+}
+
+cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_w, int tile_h, bool trace,
+                        cudaStream_t s) {
+  if (n_tiles <= 0) return cudaSuccess;
+#define EVIS_SHAPE(TX, TY)                                                               \
+  if (tile_w == TX && tile_h == TY)                                                      \
+    return trace ? launch_shape<TX, TY, true>(a, n_tiles, s) : launch_shape<TX, TY, false>(a, n_tiles, s);
+  EVIS_SHAPE(32, 16)
+  EVIS_SHAPE(32, 32)
+  EVIS_SHAPE(64, 16)
+  EVIS_SHAPE(64, 32)
+  EVIS_SHAPE(128, 16)
+#undef EVIS_SHAPE
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace evis

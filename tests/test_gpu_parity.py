@@ -38,11 +38,13 @@ def _frames(kf, mode):
 
 
 def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), capacity=1 << 22,
-             check_state=True):
+             check_state=True, tile=None):
     """Feed the same keyframes to the oracle and the library; compare everything."""
     mode = flags & 0x3
     o = oracle_mod.Oracle(envs, eps=eps, flags=flags & 0xFF)
     ctx = ev.Context(envs, eps=eps, flags=flags, capacity=capacity)
+    if tile is not None:
+        ctx.set_tile_shape(*tile)
     alive = []  # keeps inputs alive for EVIS_KEEP_INPUTS
     for s, kf in enumerate(kfs):
         fr = _frames(kf, mode)
@@ -104,11 +106,23 @@ def _ragged_envs(scenes_mod):
     return envs
 
 
-def test_ragged_multi_env(ev, oracle_mod, scenes_mod):
-    """Uneven sizes (1x1, single rows/columns, ragged tiles), per-env K, refractory, maps."""
+@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
+def test_ragged_multi_env(ev, oracle_mod, scenes_mod, tile):
+    """Uneven sizes (1x1, single rows/columns, ragged tiles), per-env K, refractory, maps,
+    for every tile shape of the synthesis kernel."""
     envs = _ragged_envs(scenes_mod)
     kfs = [scenes_mod.render(envs, k) for k in range(4)]
-    run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(1, 2, 3))
+    run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(1, 2, 3), tile=tile)
+
+
+def test_long_keyframe_gap_timestamps(ev, oracle_mod, scenes_mod):
+    """Sub-frame intervals of 2^29 ns and more take the binary64 timestamp route, shorter ones
+    the exact integer route; both must match the oracle's binary64 llrint."""
+    w = scenes_mod.config1()
+    envs = [scenes_mod.EnvScene(W=64, H=48, K=2, c_on=0.2, c_off=0.2, layers=w.envs[0].layers),
+            scenes_mod.EnvScene(W=64, H=48, K=7, c_on=0.2, c_off=0.2, layers=w.envs[0].layers)]
+    kfs = [scenes_mod.render(envs, k) for k in range(3)]
+    run_both(ev, oracle_mod, envs, kfs, 3_000_000_001, trace_steps=(1,))
 
 
 @pytest.mark.parametrize("flags", [0x10, 0x20, 0x30, 0x100, 0x110])
@@ -165,7 +179,8 @@ def test_wild_motion_overflows_candidate_lists(ev, oracle_mod):
         k.Z = rng.uniform(1, 5, size=n).astype(np.float32)
         k.L = rng.normal(0, 1, size=n).astype(np.float32)
         kfs.append(k)
-    run_both(ev, oracle_mod, envs, kfs, 1_000_000, trace_steps=(1,))
+    for tile in ((32, 16), (128, 16)):
+        run_both(ev, oracle_mod, envs, kfs, 1_000_000, trace_steps=(1,), tile=tile)
 
 
 def test_static_scene_is_per_pixel_linear_esim(ev, oracle_mod):
