@@ -173,6 +173,34 @@ evis_status evis_profile_enable(evis_ctx *ctx, int32_t max_steps);
  * the synthesis kernel (splat, blend, events), in milliseconds; *n_steps = steps written. */
 evis_status evis_profile_read(evis_ctx *ctx, float *ms, int32_t cap, int32_t *n_steps);
 
+/* One keyframe gap of ONE environment with no device allocation at all.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc when they need events, such
+ * as a simulator or engine that owns the whole GPU memory pool and hands out buffers, or a
+ * latency-critical loop that must not meet the allocator.  The caller passes every buffer
+ * (device pointers): keyframes A (previous) and B (new) as log-intensity, motion vectors
+ * and depth in the single-environment layout; the reference levels Lref [H*W] (set them to
+ * the first keyframe's log-intensity before the first call) and, when refractory_ns > 0,
+ * the last-event times t_last [H*W] (INT64_MIN = none), both updated in place; the event
+ * array (capacity entries) and its 64-bit event counter *count, to which the events of this
+ * gap are added exactly as evis_step adds them to a context's buffer (the caller resets it).
+ * Sub-frame i is at t_a_ns + (i * dt_ns) / K.  The results equal those of evis_step.
+ * flags may hold EVIS_MODE_B_PRIMARY and EVIS_TIE_INDEX only.
+ *
+ * Limits: width, height <= 4096 and width * height <= 1048576, set by a static scratch
+ * array of about 1.3 MB that every GPU loading the library holds until the process exits
+ * (it keeps the environment descriptor, tile list, clocks and motion bounds).  Larger
+ * sizes return EVIS_ERR_INVALID_ARG with the reason in evis_last_error(NULL).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls share the
+ * array, so calls whose work overlaps on the GPU (other streams, other host threads) race;
+ * serialise them on one stream.  Asynchronous on stream. */
+evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flags, const float *L_A,
+                              const float *mv_A, const float *Z_A, const float *L_B,
+                              const float *mv_B, const float *Z_B, float *Lref,
+                              int64_t *t_last, int64_t t_a_ns, int64_t dt_ns,
+                              evis_event *events, uint64_t *count, int64_t capacity,
+                              evis_stream_t stream);
+
 /* Total packed pixels of the context (the length of its per-pixel arrays). */
 evis_status evis_total_pixels(evis_ctx *ctx, int64_t *n_out);
 
@@ -183,7 +211,7 @@ evis_status evis_destroy(evis_ctx *ctx);
 const char *evis_status_string(evis_status s);
 
 /* Text of the last CUDA or validation error seen by ctx (empty if none); with ctx = NULL,
- * why the calling thread's last failed evis_create failed. */
+ * why the calling thread's last failed evis_create or evis_step_noalloc failed. */
 const char *evis_last_error(evis_ctx *ctx);
 
 #ifdef __cplusplus

@@ -64,6 +64,9 @@ _SIGS = {
     "evis_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "evis_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p]),
+    "evis_step_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32] + [ctypes.c_void_p] * 8 +
+                          [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_int64, ctypes.c_void_p]),
     "evis_total_pixels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "evis_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "evis_status_string": (ctypes.c_char_p, [ctypes.c_int]),

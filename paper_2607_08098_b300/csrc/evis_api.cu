@@ -231,6 +231,10 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
 
 }  // namespace
 
+namespace evis {
+void set_detached_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace evis
+
 extern "C" {
 
 evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_config *cfg,

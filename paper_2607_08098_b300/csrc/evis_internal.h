@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "evis.h"
 
 namespace evis {
@@ -72,6 +74,8 @@ cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t
 cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_w, int tile_h, bool trace,
                         cudaStream_t s);
 bool tile_shape_supported(int tile_w, int tile_h);
+// Error text reported by evis_last_error(NULL) for calls made without a context.
+void set_detached_error(const std::string &msg);
 cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, float *out,
                        cudaStream_t s);
 

@@ -1,0 +1,96 @@
+"""evis_step_noalloc, the entry point for callers that cannot allocate device memory (for
+example a host engine that owns the whole GPU memory pool and only hands out buffers): it must
+give exactly what the context-based evis_step gives, on two keyframe gaps in a row, while
+reusing the library's static scratch array between the calls.  Kept in a file of its own that
+pytest collects last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_08098_b300 import build
+    build.build()
+    import paper_2607_08098_b300 as m
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).cuda()
+
+
+def _env_scene(scenes_mod, refractory_ns):
+    layers = scenes_mod.config1().envs[0].layers
+    return scenes_mod.EnvScene(W=160, H=100, K=6, c_on=0.2, c_off=0.25,
+                               refractory_ns=refractory_ns, t0_ns=5_000, layers=layers)
+
+
+@pytest.mark.parametrize("refractory_ns", [0, 150_000])
+def test_noalloc_matches_evis_step_on_two_gaps(ev, scenes_mod, refractory_ns):
+    es = _env_scene(scenes_mod, refractory_ns)
+    n = es.W * es.H
+    dt = 16_666_667
+    kfs = [scenes_mod.render([es], k) for k in range(3)]
+    dev = [tuple(_dev(a[:n] if a.ndim == 1 else a[:n]) for a in (kf.L, kf.mv, kf.Z)) for kf in kfs]
+
+    # reference: the context-based path, events read after each gap
+    ctx = ev.Context([es], flags=ev.IN_LOG, capacity=1 << 22)
+    ref_events, ref_state = [], []
+    ctx.step(*(_dev(a) for a in (kfs[0].L, kfs[0].mv, kfs[0].Z)), dt)
+    for kf in kfs[1:]:
+        ctx.step(*(_dev(a) for a in (kf.L, kf.mv, kf.Z)), dt)
+        ref_events.append(ev.sort_events(ctx.read_events()))
+        Lref, tl, _ = ctx.state()
+        ref_state.append((Lref[:n].copy(), tl[:n].copy()))
+    ctx.close()
+
+    # the same two gaps through the allocation-free entry point
+    desc = ev.EnvDesc(es.W, es.H, es.K, es.c_on, es.c_off, None, None, refractory_ns, es.t0_ns)
+    Lref = dev[0][0].clone()
+    t_last = torch.full((n,), np.iinfo(np.int64).min, dtype=torch.int64, device="cuda")
+    cap = 1 << 21
+    events = torch.empty(cap * 2, dtype=torch.int64, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    L = ev.lib()
+    for gap in range(2):
+        A, B = dev[gap], dev[gap + 1]
+        count.zero_()
+        st = L.evis_step_noalloc(ctypes.byref(desc), 0, A[0].data_ptr(), A[1].data_ptr(),
+                                 A[2].data_ptr(), B[0].data_ptr(), B[1].data_ptr(),
+                                 B[2].data_ptr(), Lref.data_ptr(),
+                                 t_last.data_ptr() if refractory_ns else None,
+                                 es.t0_ns + gap * dt, dt, events.data_ptr(), count.data_ptr(),
+                                 cap, stream)
+        assert st == ev.OK, L.evis_last_error(None).decode()
+        torch.cuda.synchronize()
+        got_n = int(count.item())
+        assert got_n <= cap
+        got = events[:2 * got_n].cpu().numpy().view(ev.EVENT_DTYPE)
+        want = ref_events[gap]
+        assert len(want) > 1000
+        np.testing.assert_array_equal(ev.sort_events(got).view(np.uint8), want.view(np.uint8))
+        np.testing.assert_array_equal(Lref.cpu().numpy(), ref_state[gap][0])
+        if refractory_ns:
+            np.testing.assert_array_equal(t_last.cpu().numpy(), ref_state[gap][1])
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(ev):
+    L = ev.lib()
+    buf = torch.zeros(16, dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for W, H in ((4097, 8), (8, 4097), (2048, 1024)):
+        desc = ev.EnvDesc(W, H, 4, 0.2, 0.2, None, None, 0, 0)
+        p = buf.data_ptr()
+        st = L.evis_step_noalloc(ctypes.byref(desc), 0, p, p, p, p, p, p, p, None, 0, 1000,
+                                 p, cnt.data_ptr(), 1, torch.cuda.current_stream().cuda_stream)
+        assert st == ev.ERR_INVALID_ARG
+        assert "4096" in L.evis_last_error(None).decode()
