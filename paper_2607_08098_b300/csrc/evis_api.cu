@@ -40,6 +40,7 @@ struct evis_ctx {
   int64_t *d_tlast = nullptr;
   float *d_flow = nullptr;     // [2][n]
   float4 *d_seg[2] = {nullptr, nullptr};  // per keyframe slot: row-segment motion bounds
+  float4 *d_pack[2] = {nullptr, nullptr}; // per-source packs of A and B for the current gap
   int64_t *d_clock = nullptr;  // [2][n]
   ulonglong2 *d_events = nullptr;
   unsigned long long *d_count = nullptr;
@@ -173,6 +174,10 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
   pa.Z_out = c->keep ? nullptr : c->d_Z[b];
   pa.flow = flowB;
   pa.seg = c->d_seg[b];
+  pa.mvA = c->have_A ? c->A_mv : nullptr;
+  pa.ZA = c->have_A ? c->A_Z : nullptr;
+  pa.packA = c->d_pack[0];
+  pa.packB = c->d_pack[1];
   pa.eps = c->cfg.eps;
   pa.mode = c->mode;
   pa.max_segs = c->max_segs;
@@ -201,6 +206,8 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
     s.flowB = flowB;
     s.segA = c->d_seg[c->slot];
     s.segB = c->d_seg[b];
+    s.packA = c->d_pack[0];
+    s.packB = c->d_pack[1];
     s.events = c->d_events;
     s.ev_count = c->d_count;
     s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
@@ -300,6 +307,8 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if ((e = dalloc(c, &c->d_flow, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc flow");
   for (int s = 0; s < 2; ++s)
     if ((e = dalloc(c, &c->d_seg[s], c->total_segs)) != cudaSuccess) return bail(e, "alloc segments");
+  for (int s = 0; s < 2; ++s)
+    if ((e = dalloc(c, &c->d_pack[s], c->total)) != cudaSuccess) return bail(e, "alloc source packs");
   if ((e = dalloc(c, &c->d_clock, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc clock");
   if ((e = dalloc(c, &c->d_events, cfg->event_capacity)) != cudaSuccess) return bail(e, "alloc events");
   if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");

@@ -47,6 +47,7 @@ struct StepArgs {
   int64_t *clock_out;
   const float *flowA, *flowB;
   const float4 *segA, *segB;   // per row segment: (min dx, max dx, min dy, max dy)
+  const float4 *packA, *packB; // per source: (mx, my, Z, Z at the other endpoint), or null
   ulonglong2 *events;
   unsigned long long *ev_count;
   unsigned long long capacity;
@@ -64,6 +65,8 @@ struct PrepArgs {
   float *mv_out, *Z_out;         // copies (null under EVIS_KEEP_INPUTS)
   float *flow;                   // per-environment max |mv| (inf-norm), pre-zeroed
   float4 *seg;                   // per row segment motion bounds of this keyframe
+  const float *mvA, *ZA;         // previous keyframe (null for the first one)
+  float4 *packA, *packB;         // per-source packs of A and B for the gap (null: none)
   float eps;
   uint32_t mode;
   int max_segs;                  // largest environment (row segments)

@@ -58,51 +58,74 @@ __device__ __forceinline__ float other_depth(const float *__restrict__ Zo, int W
   return valid_depth(z) ? z : own;
 }
 
+// floor(v) of |v| < 2^22 without a conversion instruction: adding 1.5 * 2^23 with rounding
+// toward -infinity lands on the integer grid (ulp 1), whose low significand bits hold the
+// integer.  *fv receives floor(v) as a float (exact).
+__device__ __forceinline__ int floor_small(float v, float *fv) {
+  const float t = __fadd_rd(v, 12582912.0f);
+  *fv = __fsub_rn(t, 12582912.0f);
+  return __float_as_int(t) - 0x4B400000;
+}
+
+// (float)i for 0 <= i < 2^23 without a conversion instruction.
+__device__ __forceinline__ float small_int_to_float(int i) {
+  return __fsub_rn(__int_as_float(0x4B000000 + i), 8388608.0f);
+}
+
 // Splat of one source into the tile's z-buffer (Sec. 3.3).  Direction 0 moves a source of A
 // forward to q = p - f m_A with depth (1-f) Z_A(p) + f Z_B(p - m_A); direction 1 moves a source
 // of B backward to q = p + (1-f) m_B with depth (1-f) Z_A(p + m_B) + f Z_B(p) (Eqs. 5, 7).
 // Every integer pixel of the bilinear footprint of q with weight > 0, inside the image and
 // inside the tile, keeps the minimum key [depth bits | quantised (1 - w) | source index]
-// (Eq. 6).  The depth gather runs only for sources that reach the tile.
-template <int TX, int TY>
+// (Eq. 6).  PACKED reads (mx, my, Z, Z at the other endpoint) prepared once per keyframe gap;
+// otherwise the motion and depth maps are read and the other endpoint's depth is gathered
+// for sources that reach the tile.
+template <int TX, int TY, bool PACKED>
 __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, int sx, int sy,
-                                             int W, int H, int x0, int y0, float f, float g,
-                                             const float2 *__restrict__ mvA,
-                                             const float *__restrict__ ZA,
-                                             const float2 *__restrict__ mvB,
-                                             const float *__restrict__ ZB, bool tie_index) {
+                                             float fx, float fy, int W, int H, int x0, int y0,
+                                             float f, float g, const StepArgs &a, int64_t o) {
   const int p = sy * W + sx;
-  const float zs = __ldg((dir ? ZB : ZA) + p);
-  if (!valid_depth(zs)) return;
-  const float2 m = __ldg((dir ? mvB : mvA) + p);
-  const float fx = static_cast<float>(sx), fy = static_cast<float>(sy);
+  float mx, my, zs, zo = 0.0f;
+  if (PACKED) {
+    const float4 v = __ldg((dir ? a.packB : a.packA) + o + p);
+    mx = v.x;
+    my = v.y;
+    zs = v.z;
+    zo = v.w;
+    if (!valid_depth(zs)) return;
+  } else {
+    zs = __ldg((dir ? a.ZB : a.ZA) + o + p);
+    if (!valid_depth(zs)) return;
+    const float2 m = __ldg(reinterpret_cast<const float2 *>(dir ? a.mvB : a.mvA) + o + p);
+    mx = m.x;
+    my = m.y;
+  }
   float qx, qy;
   if (dir == 0) {
-    qx = __fsub_rn(fx, __fmul_rn(f, m.x));
-    qy = __fsub_rn(fy, __fmul_rn(f, m.y));
+    qx = __fsub_rn(fx, __fmul_rn(f, mx));
+    qy = __fsub_rn(fy, __fmul_rn(f, my));
   } else {
-    qx = __fadd_rn(fx, __fmul_rn(g, m.x));
-    qy = __fadd_rn(fy, __fmul_rn(g, m.y));
+    qx = __fadd_rn(fx, __fmul_rn(g, mx));
+    qy = __fadd_rn(fy, __fmul_rn(g, my));
   }
   // No footprint pixel can be inside unless -1 < q < size; this also rejects NaN.
   if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H)))
     return;
-  const float fx0 = floorf(qx), fy0 = floorf(qy);
-  const int lx0 = static_cast<int>(fx0) - x0, ly0 = static_cast<int>(fy0) - y0;
+  float fx0, fy0;
+  const int lx0 = floor_small(qx, &fx0) - x0, ly0 = floor_small(qy, &fy0) - y0;
   if (lx0 < -1 || lx0 >= TX || ly0 < -1 || ly0 >= TY) return;
-  float zt;
-  if (dir == 0) {
-    const float zo = other_depth(ZB, W, H, __fsub_rn(fx, m.x), __fsub_rn(fy, m.y), zs);
-    zt = __fadd_rn(__fmul_rn(g, zs), __fmul_rn(f, zo));
-  } else {
-    const float zo = other_depth(ZA, W, H, __fadd_rn(fx, m.x), __fadd_rn(fy, m.y), zs);
-    zt = __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zs));
+  if (!PACKED) {
+    zo = dir == 0 ? other_depth(a.ZB + o, W, H, __fsub_rn(fx, mx), __fsub_rn(fy, my), zs)
+                  : other_depth(a.ZA + o, W, H, __fadd_rn(fx, mx), __fadd_rn(fy, my), zs);
   }
+  const float zt = dir == 0 ? __fadd_rn(__fmul_rn(g, zs), __fmul_rn(f, zo))
+                            : __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zs));
   const float ax = __fsub_rn(qx, fx0), ay = __fsub_rn(qy, fy0);
   const float wx[2] = {__fsub_rn(1.0f, ax), ax};
   const float wy[2] = {__fsub_rn(1.0f, ay), ay};
   const unsigned long long hi = (static_cast<unsigned long long>(__float_as_uint(zt)) << 32) |
                                 static_cast<unsigned>(p);
+  const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy) {
     const int ly = ly0 + dy;
@@ -114,7 +137,10 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
       const float w = __fmul_rn(wx[dx], wy[dy]);
       if (!(w > 0.0f)) continue;
       unsigned wq = 0;
-      if (!tie_index) wq = min(__float2uint_rz(__fmul_rn(__fsub_rn(1.0f, w), 256.0f)), 255u);
+      if (!tie_index) {
+        float unused;  // truncation of (1 - w) * 256 in [0, 256]
+        wq = min(static_cast<unsigned>(floor_small(__fmul_rn(__fsub_rn(1.0f, w), 256.0f), &unused)), 255u);
+      }
       atomicMin(&zb[ly * TX + lx], hi | (static_cast<unsigned long long>(wq) << 24));
     }
   }
@@ -143,9 +169,10 @@ __device__ __forceinline__ int64_t interp_time(float fr, int64_t tprev, int64_t 
   if (d < (int64_t(1) << 29)) {
     const unsigned b = __float_as_uint(fr);          // fr in [0, 1]
     const unsigned ex = b >> 23;
-    const unsigned long long m = ex ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+    const unsigned m = ex ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
     const int sh = ex ? 150 - static_cast<int>(ex) : 149;   // fr = m * 2^-sh, sh >= 23
-    const unsigned long long P = m * static_cast<unsigned long long>(d);  // < 2^53
+    const unsigned long long P = static_cast<unsigned long long>(m) *
+                                 static_cast<unsigned>(d);   // 24 x 29 bits: < 2^53
     if (sh >= 64) return tprev;                      // fr * d < 2^-11
     unsigned long long q = P >> sh;
     const unsigned long long r = P & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
@@ -157,9 +184,9 @@ __device__ __forceinline__ int64_t interp_time(float fr, int64_t tprev, int64_t 
 
 // Time of the k-th crossing of a pixel in this sub-frame: the level Lref + p k theta,
 // interpolated linearly between the previous sample (tprev, Lprev) and this one (ti, L).
-__device__ __forceinline__ int64_t crossing_time(float Lref, int pk, float th, float Lprev,
+__device__ __forceinline__ int64_t crossing_time(float Lref, float pk, float th, float Lprev,
                                                  float L, int64_t tprev, int64_t ti) {
-  const float lev = __fadd_rn(Lref, __fmul_rn(static_cast<float>(pk), th));
+  const float lev = __fadd_rn(Lref, __fmul_rn(pk, th));
   const float num = __fsub_rn(lev, Lprev);
   const float den = __fsub_rn(L, Lprev);
   float fr = den == 0.0f ? 1.0f : __fdiv_rn(num, den);
@@ -186,6 +213,8 @@ struct StepSmem {
   float4 cand_b[2][kCandidates];           // candidate segments' motion bounds
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
   unsigned hit[2 * kCandidates];           // candidates that can reach the tile this sub-frame
+  int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
+  unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
 };
 
 // Resident CTAs per SM each tile shape is compiled for (bounded by its shared memory); it
@@ -195,7 +224,7 @@ constexpr int step_min_blocks() {
   return TX * TY <= 512 ? 4 : (TX * TY <= 1024 ? 3 : 2);
 }
 
-template <int TX, int TY, bool TRACE>
+template <int TX, int TY, bool TRACE, bool PACKED>
 __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
   constexpr int NT = TX * TY / kThreads;   // targets per thread
   constexpr int NW = kThreads / 32;
@@ -213,13 +242,9 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
   const int64_t o = E.pix_off;
   const float *__restrict__ LA = a.LA + o;
   const float *__restrict__ LB = a.LB + o;
-  const float2 *__restrict__ mvA = reinterpret_cast<const float2 *>(a.mvA) + o;
-  const float2 *__restrict__ mvB = reinterpret_cast<const float2 *>(a.mvB) + o;
-  const float *__restrict__ ZA = a.ZA + o;
-  const float *__restrict__ ZB = a.ZB + o;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lanes_below = (1u << lane) - 1u;
-  const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
+  const float lane_f = small_int_to_float(lane);
   const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
   const int64_t T0 = a.clock_in[tl.env];
   const int64_t refr = E.refractory_ns;
@@ -304,11 +329,20 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
   const bool over = s_over != 0;
   const int nA = min(s_nc[0], kCandidates);
   const int nAB = nA + min(s_nc[1], kCandidates);
+  // t_i = T0 + floor(i dt / K), stepped with a quotient and a remainder
+  const int64_t dq = a.dt / K, dr = a.dt % K;
+  int64_t tq = 0, trem = 0;
 
   for (int i = 1; i <= K; ++i) {
     const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
     const float g = __fsub_rn(1.0f, f);
-    const int64_t ti = T0 + (static_cast<int64_t>(i) * a.dt) / K;
+    tq += dq;
+    trem += dr;
+    if (trem >= K) {
+      trem -= K;
+      ++tq;
+    }
+    const int64_t ti = T0 + tq;
 
     // ---- phase 1: clear the z-buffers; list the candidates that reach the tile now ----
 #pragma unroll
@@ -331,9 +365,9 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
           } else {
             dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
           }
-          hit = !seg_misses<TX, TY>(static_cast<float>((xy & 0xFFFFu) * kSegW),
-                                    static_cast<float>(xy >> 16), dxl, dxh, dyl, dyh, tl.x0,
-                                    tl.y0);
+          hit = !seg_misses<TX, TY>(small_int_to_float(static_cast<int>(xy & 0xFFFFu) * kSegW),
+                                    small_int_to_float(static_cast<int>(xy >> 16)), dxl, dxh,
+                                    dyl, dyh, tl.x0, tl.y0);
         }
         const unsigned m = __ballot_sync(kFull, hit);
         if (m) {
@@ -353,18 +387,20 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
         const int c = static_cast<int>(S.hit[hh]);
         const int dir = c >= nA ? 1 : 0;
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
-        const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + lane;
+        const int xs = static_cast<int>(xy & 0xFFFFu) * kSegW, sy = static_cast<int>(xy >> 16);
+        const int sx = xs + lane;
         if (sx < W)
-          splat_source<TX, TY>(S.zb[dir], dir, sx, static_cast<int>(xy >> 16), W, H, tl.x0,
-                               tl.y0, f, g, mvA, ZA, mvB, ZB, tie_index);
+          splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy,
+                                       __fadd_rn(small_int_to_float(xs), lane_f),
+                                       small_int_to_float(sy), W, H, tl.x0, tl.y0, f, g, a, o);
       }
     } else {
       for (int sy = sy0 + warp; sy < sy1; sy += NW) {
+        const float fy = small_int_to_float(sy);
         for (int sx = sx0 + lane; sx < sx1; sx += 32) {
-          splat_source<TX, TY>(S.zb[0], 0, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB,
-                               tie_index);
-          splat_source<TX, TY>(S.zb[1], 1, sx, sy, W, H, tl.x0, tl.y0, f, g, mvA, ZA, mvB, ZB,
-                               tie_index);
+          const float fx = small_int_to_float(sx);
+          splat_source<TX, TY, PACKED>(S.zb[0], 0, sx, sy, fx, fy, W, H, tl.x0, tl.y0, f, g, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[1], 1, sx, sy, fx, fy, W, H, tl.x0, tl.y0, f, g, a, o);
         }
       }
     }
@@ -377,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
       const int ty = ty0 + ROWS * j;
       const int pix = ty * W + tx;
       bool has = false;
-      float L = 0.0f, th = thon[j];
+      float L = 0.0f, th = thon[j], nf = 0.0f;
       int n = 0, pol = 1;
       if (act[j]) {
         const unsigned long long kA = S.zb[0][tid + kThreads * j];
@@ -403,19 +439,63 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
           pol = d > 0.0f ? 1 : -1;
           th = pol > 0 ? thon[j] : thoff[j];
           const float q = __fdiv_rn(fabsf(d), th);
-          if (q >= 1.0f) n = q >= static_cast<float>(kMaxCrossings) ? kMaxCrossings
-                                                                  : static_cast<int>(floorf(q));
+          if (q >= 1.0f) {
+            if (q >= static_cast<float>(kMaxCrossings)) {
+              n = kMaxCrossings;
+              nf = static_cast<float>(kMaxCrossings);
+            } else {
+              n = floor_small(q, &nf);
+            }
+          }
         }
       }
-      // crossings k = 1..n, one warp-wide reservation per k
-      const int nmax = static_cast<int>(__reduce_max_sync(kFull, static_cast<unsigned>(n)));
-      for (int k = 1; k <= nmax; ++k) {
-        bool emit = false;
+      // ---- crossings k = 1..n of the warp's 32 pixels, spread over its lanes ----
+      // Item c of the warp (pixels in lane order, k ascending) is computed by lane c % 32.
+      int incl = n;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      const int excl = incl - n;
+      for (int c0 = 0; c0 < total; c0 += 32) {
+        const int c = c0 + lane;
+        // owner = number of lanes whose items all lie before c
+        int own = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+          const int v = __shfl_sync(kFull, incl, own + st - 1);
+          if (v <= c) own += st;
+        }
+        own = min(own, 31);
+        const int k = c - __shfl_sync(kFull, excl, own) + 1;
+        const float oL = __shfl_sync(kFull, L, own);
+        const float oLref = __shfl_sync(kFull, Lref[j], own);
+        const float oLprev = __shfl_sync(kFull, Lprev[j], own);
+        const float oth = __shfl_sync(kFull, th, own);
+        const int opol = __shfl_sync(kFull, pol, own);
+        const int64_t otprev = __shfl_sync(kFull, tprev[j], own);
         int64_t t = 0;
-        if (k <= n) {
-          t = crossing_time(Lref[j], pol * k, th, Lprev[j], L, tprev[j], ti);
-          emit = refr <= 0 || tlast[j] == kNoEvent || t - tlast[j] >= refr;
-          if (emit) tlast[j] = t;
+        if (c < total) {
+          const float kf = small_int_to_float(k);
+          t = crossing_time(oLref, opol > 0 ? kf : -kf, oth, oLprev, oL, otprev, ti);
+        }
+        bool emit = c < total;
+        if (a.tlast) {
+          // refractory filter (Sec. 3.4) in order along each pixel's crossings: each owner
+          // walks its items of this chunk; t_last carries over to the next chunk
+          S.rt[warp][lane] = t;
+          __syncwarp();
+          const int lo = max(excl, c0), hi = min(incl, c0 + 32);
+          for (int cc = lo; cc < hi; ++cc) {
+            const int64_t tt = S.rt[warp][cc - c0];
+            const bool keep = refr <= 0 || tlast[j] == kNoEvent || tt - tlast[j] >= refr;
+            if (keep) tlast[j] = tt;
+            S.rkeep[warp][cc - c0] = keep ? 1 : 0;
+          }
+          __syncwarp();
+          emit = emit && S.rkeep[warp][lane] != 0;
         }
         const unsigned m = __ballot_sync(kFull, emit);
         if (m == 0) continue;
@@ -431,8 +511,10 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
         base = __shfl_sync(kFull, base, 0);
         gb = __shfl_sync(kFull, gb, 0);
         if (emit) {
+          const int otid = warp * 32 + own;
           const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
-          const ulonglong2 rec = make_event(t, tx, ty, tl.env, pol);
+          const ulonglong2 rec = make_event(t, tl.x0 + otid % TX, tl.y0 + otid / TX + ROWS * j,
+                                            tl.env, opol);
           if (idx < static_cast<unsigned>(kEventStage)) {
             S.stage[idx] = rec;
           } else {
@@ -441,9 +523,10 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
             if (gi < a.capacity) a.events[gi] = rec;
           }
         }
+        __syncwarp();  // the next chunk reuses this warp's refractory scratch
       }
       if (has) {
-        if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(static_cast<float>(pol * n), th));
+        if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(pol > 0 ? nf : -nf, th));
         Lprev[j] = L;
         tprev[j] = ti;
       }
@@ -501,6 +584,18 @@ __global__ void prep_kernel(const PrepArgs a) {
       }
       if (a.mv_out) reinterpret_cast<float2 *>(a.mv_out)[p] = m;
       if (a.Z_out) a.Z_out[p] = z;
+      if (a.packA && a.ZA) {
+        // the depth at the other endpoint of each source's correspondence (Eq. 7), once per
+        // gap: B's sources look up A at p + m_B, A's sources look up B at p - m_A
+        const float fx = static_cast<float>(x), fy = static_cast<float>(y);
+        const float *ZAe = a.ZA + o, *ZBe = a.Z + o;
+        const float zoB = other_depth(ZAe, E.W, E.H, __fadd_rn(fx, m.x), __fadd_rn(fy, m.y), z);
+        a.packB[p] = make_float4(m.x, m.y, z, zoB);
+        const float2 mA = reinterpret_cast<const float2 *>(a.mvA)[p];
+        const float zA = a.ZA[p];
+        const float zoA = other_depth(ZBe, E.W, E.H, __fsub_rn(fx, mA.x), __fsub_rn(fy, mA.y), zA);
+        a.packA[p] = make_float4(mA.x, mA.y, zA, zoA);
+      }
       if (a.L_out) {
         float L;
         if (a.mode == EVIS_IN_LOG) {
@@ -580,17 +675,17 @@ cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, flo
   return cudaGetLastError();
 }
 
-template <int TX, int TY, bool TRACE>
+template <int TX, int TY, bool TRACE, bool PACKED>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, cudaStream_t s) {
   static bool configured = false;  // one attribute call per instantiation and process
   const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  step_kernel<TX, TY, TRACE><<<n_tiles, kThreads, smem, s>>>(a);
+  step_kernel<TX, TY, TRACE, PACKED><<<n_tiles, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -602,9 +697,14 @@ bool tile_shape_supported(int tw, int th) {
 cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_w, int tile_h, bool trace,
                         cudaStream_t s) {
   if (n_tiles <= 0) return cudaSuccess;
+  if (!a.packA) {  // unpacked sources: 64x16 tiles only
+    if (tile_w != 64 || tile_h != 16 || trace) return cudaErrorInvalidValue;
+    return launch_shape<64, 16, false, false>(a, n_tiles, s);
+  }
 #define EVIS_SHAPE(TX, TY)                                                               \
   if (tile_w == TX && tile_h == TY)                                                      \
-    return trace ? launch_shape<TX, TY, true>(a, n_tiles, s) : launch_shape<TX, TY, false>(a, n_tiles, s);
+    return trace ? launch_shape<TX, TY, true, true>(a, n_tiles, s)                       \
+                 : launch_shape<TX, TY, false, true>(a, n_tiles, s);
   EVIS_SHAPE(32, 16)
   EVIS_SHAPE(32, 32)
   EVIS_SHAPE(64, 16)
