@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=6, help="oracle sample size (environments)")
+    ap.add_argument("--workload", choices=["envs64", "batched"], default="envs64",
+                    help="envs64: the benchmarked 64-env workload; batched: the uneven 256-env "
+                         "batch, per-environment launches vs one batched context vs graph replay")
     return ap.parse_args()
 
 
@@ -350,9 +353,114 @@ def e2e_leg(ev, w, dev, args, capacity):
                     "(all events -> pinned host)"}
 
 
+def batched_arm(args):
+    """Uneven batch (256 envs: 128x128, 346x260, 640x480, 1280x720 in a 4:2:1:1 mix, K ~ U{4..32},
+    per-pixel thresholds): the same keyframe gaps run (a) as one context per environment,
+    (b) as one batched context with evis_step, (c) autotuned and replayed from a CUDA graph.
+    Prints one JSON line with the three rates (device time of the timed steps)."""
+    import torch
+    import paper_2607_08098_b300 as ev
+    import scenes
+    torch.cuda.set_device(0)
+    w = scenes.config3()
+    n_kf = args.warmup + args.steps + 1
+    off, total = scenes.pixel_offsets(w.envs)
+    dev = []
+    for k in range(n_kf):
+        kf = scenes.render(w.envs, k, want=("I", "mv", "Z"))
+        dev.append(tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)))
+    units = w.pixel_substeps
+    cap_env = [int(e.H * e.W * e.K * 0.8) + 4096 for e in w.envs]
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        # (a) one context per environment, stepped one after the other on one stream
+        ctxs = [ev.Context([e], eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS, capacity=c,
+                           stream=stream) for e, c in zip(w.envs, cap_env)]
+
+        def views(k, i):
+            e, o = w.envs[i], int(off[i])
+            n = e.H * e.W
+            I, mv, Z = dev[k]
+            return I[o:o + n], mv[2 * o:2 * (o + n)], Z[o:o + n]
+
+        def run_per_env(k):
+            for i, c in enumerate(ctxs):
+                c.clear_events()
+                c.step(*views(k, i), w.dt_ns)
+
+        # (b) one batched context, (c) the same autotuned and captured
+        big = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS,
+                         capacity=sum(cap_env), stream=stream)
+        graph = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM, capacity=sum(cap_env), stream=stream)
+
+        def timed(fn, first):
+            t = 0.0
+            for k in range(first, first + args.steps):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                pre = fn(k, prepare=True)
+                a_.record(stream)
+                fn(k, prepare=False)
+                b_.record(stream)
+                b_.synchronize()
+                t += a_.elapsed_time(b_)
+                del pre
+            return t
+
+        run_per_env(0)
+        for k in range(1, 1 + args.warmup):
+            run_per_env(k)
+        res["per_env_contexts"] = timed(lambda k, prepare: None if prepare else run_per_env(k),
+                                        1 + args.warmup)
+
+        def run_big(k, prepare):
+            if prepare:
+                big.clear_events()
+            else:
+                big.step(*dev[k], w.dt_ns)
+
+        big.step(*dev[0], w.dt_ns)
+        for k in range(1, 1 + args.warmup):
+            run_big(k, True)
+            run_big(k, False)
+        res["batched_step"] = timed(run_big, 1 + args.warmup)
+
+        graph.step(*dev[0], w.dt_ns)
+        best = graph.autotune(*dev[1], w.dt_ns, reps=2)
+        shapes = graph.tile_shapes()
+        for k in range(1, 1 + args.warmup):
+            graph.step(*dev[k], w.dt_ns)
+        graph.capture(w.dt_ns)
+
+        def run_graph(k, prepare):
+            if prepare:
+                graph.clear_events()
+                graph.write_inputs(*dev[k])
+            else:
+                graph.replay()
+
+        res["batched_graph_autotuned"] = timed(run_graph, 1 + args.warmup)
+        n_events = graph.event_count()
+    classes = {}
+    for e, sh in zip(w.envs, shapes):
+        classes[f"{e.W}x{e.H}"] = f"{sh[0]}x{sh[1]}"
+    line = {"bench": "batched uneven: 256 envs (128x128, 346x260, 640x480, 1280x720 in 4:2:1:1), "
+                     "K~U{4..32}, per-pixel C, linear inputs",
+            "metric": METRIC, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "pixel_substeps_per_step": units,
+            "value": {k: units * args.steps / (v / 1e3) / 1e6 for k, v in res.items()},
+            "ms_per_step": {k: v / args.steps for k, v in res.items()},
+            "events_last_step": n_events, "autotuned_tile_shapes": classes,
+            "autotune_best_ms": best}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_info()
+    if args.workload == "batched":
+        batched_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args, world, rank)
     else:

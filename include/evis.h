@@ -161,6 +161,42 @@ evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float 
  * speed does.  Synchronises the stream; EVIS_ERR_INVALID_ARG for another shape. */
 evis_status evis_set_tile_shape(evis_ctx *ctx, int32_t tile_w, int32_t tile_h);
 
+/* Per-environment tile shapes (host arrays of n_envs entries, each a supported shape; at
+ * most 8 distinct shapes).  Environments sharing a shape run in one launch of the
+ * synthesis kernel.  Synchronises; invalidates captured graphs. */
+evis_status evis_set_env_tile_shapes(evis_ctx *ctx, const int32_t *tile_w, const int32_t *tile_h);
+
+/* Copies the current per-environment tile shapes to host arrays of n_envs entries. */
+evis_status evis_get_tile_shapes(evis_ctx *ctx, int32_t *tile_w, int32_t *tile_h);
+
+/* Autotuner: for each resolution class (environments of equal width and height) times the
+ * synthesis kernel with every supported tile shape on the gap from the retained keyframe to
+ * the given keyframe B (device pointers, as for evis_step), best of reps runs after one
+ * warm-up, and keeps the fastest shape per class.  Nothing is consumed: the per-pixel
+ * state and the event buffer's count are restored, so the caller then steps with the same
+ * B as usual.  *best_ms (optional) receives the sum over classes of the best times.
+ * EVIS_ERR_STATE before the first keyframe.  Synchronises; invalidates captured graphs. */
+evis_status evis_autotune(evis_ctx *ctx, const float *frames, const float *mv,
+                          const float *depth, int64_t dt_ns, int32_t reps, float *best_ms);
+
+/* Library-owned device input buffers (packed layout; frames sized for the input mode) for
+ * callers that write the next keyframe in place, as evis_replay requires.  Two sets
+ * alternate from keyframe to keyframe: call this before writing each keyframe.  The first
+ * call allocates them. */
+evis_status evis_input_buffers(evis_ctx *ctx, float **frames, float **mv, float **depth);
+
+/* Captures one keyframe gap (preparation and synthesis kernels of every tile group, reading
+ * the input buffers) into CUDA graphs with the fixed interval dt_ns, so that evis_replay
+ * replaces evis_step for the following keyframes.  Needs a retained keyframe, a context
+ * without EVIS_KEEP_INPUTS and a non-default stream (EVIS_ERR_STATE otherwise).  Any later
+ * evis_step, evis_step_host, evis_step_trace or shape change discards the graphs. */
+evis_status evis_capture(evis_ctx *ctx, int64_t dt_ns);
+
+/* Replays the captured gap on the keyframe written to the current input buffers
+ * (evis_input_buffers): the same work and results as evis_step with those buffers and the
+ * captured dt_ns, as one graph launch.  Asynchronous. */
+evis_status evis_replay(evis_ctx *ctx);
+
 /* Per-kernel timing for profiling.  With max_steps > 0, each following evis_step (or
  * evis_step_host / evis_step_trace) records CUDA events on the context's stream around its
  * two phases, for at most max_steps steps; max_steps = 0 disables and forgets the records.

@@ -61,6 +61,13 @@ _SIGS = {
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "evis_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    "evis_set_env_tile_shapes": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "evis_get_tile_shapes": (ctypes.c_int, [ctypes.c_void_p] * 3),
+    "evis_autotune": (ctypes.c_int, [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_int32,
+                                                             ctypes.c_void_p]),
+    "evis_input_buffers": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "evis_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "evis_replay": (ctypes.c_int, [ctypes.c_void_p]),
     "evis_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "evis_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p]),
@@ -247,6 +254,52 @@ class Context:
     def set_tile_shape(self, tile_w: int, tile_h: int):
         """Target tile of the synthesis kernel (speed only; results are identical)."""
         _check(lib().evis_set_tile_shape(self._h, int(tile_w), int(tile_h)), self._h)
+
+    def set_env_tile_shapes(self, shapes):
+        """Per-environment (tile_w, tile_h) pairs."""
+        tw = np.array([t[0] for t in shapes], dtype=np.int32)
+        th = np.array([t[1] for t in shapes], dtype=np.int32)
+        _check(lib().evis_set_env_tile_shapes(self._h, tw.ctypes.data, th.ctypes.data), self._h)
+
+    def tile_shapes(self):
+        tw = np.zeros(len(self.envs), dtype=np.int32)
+        th = np.zeros(len(self.envs), dtype=np.int32)
+        _check(lib().evis_get_tile_shapes(self._h, tw.ctypes.data, th.ctypes.data), self._h)
+        return list(zip(tw.tolist(), th.tolist()))
+
+    def autotune(self, frames, mv, depth, dt_ns: int, reps: int = 3) -> float:
+        """Pick the fastest tile shape per resolution class on the gap to this keyframe (the
+        state is left unchanged); returns the summed best time in ms."""
+        self._check_inputs(frames, mv, depth)
+        best = ctypes.c_float()
+        _check(lib().evis_autotune(self._h, _ptr(frames), _ptr(mv), _ptr(depth), int(dt_ns),
+                                   int(reps), ctypes.byref(best)), self._h)
+        return best.value
+
+    def input_buffers(self):
+        """(frames, mv, depth) device pointers of the library's current input buffers."""
+        f, m, d = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().evis_input_buffers(self._h, ctypes.byref(f), ctypes.byref(m), ctypes.byref(d)),
+               self._h)
+        return f.value, m.value, d.value
+
+    def write_inputs(self, frames, mv, depth):
+        """Copy CUDA tensors into the current input buffers (stream-ordered, device to device)."""
+        from cuda.bindings import runtime as rt
+        self._check_inputs(frames, mv, depth)
+        dst = self.input_buffers()
+        strm = _stream_handle(self._stream)
+        for d, t in zip(dst, (frames, mv, depth)):
+            err, = rt.cudaMemcpyAsync(d, _ptr(t), t.numel() * 4,
+                                      rt.cudaMemcpyKind.cudaMemcpyDeviceToDevice, strm)
+            if err != rt.cudaError_t.cudaSuccess:
+                raise EvisError(ERR_CUDA, f"cudaMemcpyAsync: {err}")
+
+    def capture(self, dt_ns: int):
+        _check(lib().evis_capture(self._h, int(dt_ns)), self._h)
+
+    def replay(self):
+        _check(lib().evis_replay(self._h), self._h)
 
     def profile(self, max_steps: int):
         """Record per-phase CUDA events for the next ``max_steps`` steps (0 disables)."""

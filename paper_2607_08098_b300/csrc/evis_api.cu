@@ -26,13 +26,20 @@ struct evis_ctx {
   int max_px = 0;
   int max_segs = 0;
   int64_t total_segs = 0;
-  int tile_w = 64;
-  int tile_h = 16;
-  int n_tiles = 0;
+  // tile shape per environment; environments sharing a shape form one launch group
+  std::vector<int> env_tw, env_th;
+  struct Group {
+    int tw, th;
+    int64_t offset;  // first tile in d_tiles
+    int count;
+  };
+  std::vector<Group> groups;
+  int grid_cap = 1;        // persistent launches: one wave of resident CTAs per group
   bool any_refr = false;
 
   DevEnv *d_envs = nullptr;
   Tile *d_tiles = nullptr;
+  unsigned *d_work = nullptr;  // per-group work counters, zeroed every step
   float *d_L[2] = {nullptr, nullptr};
   float *d_mv[2] = {nullptr, nullptr};
   float *d_Z[2] = {nullptr, nullptr};
@@ -52,6 +59,15 @@ struct evis_ctx {
   int clk = 0;        // clock buffer holding the time of A
   bool have_A = false;
   const float *A_L = nullptr, *A_mv = nullptr, *A_Z = nullptr;
+
+  // graph replay: two graphs (the keyframe slots and clocks alternate every gap)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t graph_dt = 0;
+  int graph_phase = 0;
+  // autotuner scratch (allocated on first use)
+  float *d_tune_Lref = nullptr;
+  int64_t *d_tune_tlast = nullptr;
+  Tile *d_tune_tiles = nullptr;
 
   std::vector<cudaEvent_t> prof;   // 3 events per profiled step
   int prof_max = 0, prof_n = 0;
@@ -115,6 +131,10 @@ cudaError_t dalloc(evis_ctx *c, T **p, size_t count) {
 }
 
 void release(evis_ctx *c) {
+  for (auto &g : c->graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
   for (cudaEvent_t ev : c->prof) cudaEventDestroy(ev);
@@ -128,14 +148,18 @@ __global__ void fill_i64(int64_t *p, int64_t v, int64_t n) {
     p[i] = v;
 }
 
-// Tiles of every environment for the context's tile shape, longest-running (largest K)
-// first so that the tail of the launch holds the short ones.
-std::vector<Tile> build_tiles(const evis_ctx *c) {
+constexpr int kMaxGroups = 8;
+
+// Tiles of the environments whose index passes `take`, for shape tw x th, longest-running
+// (largest K) first so that the tail of a launch holds the short ones.
+template <class Pred>
+std::vector<Tile> tiles_for(const evis_ctx *c, int tw, int th, Pred take) {
   std::vector<Tile> tiles;
   for (int i = 0; i < c->n; ++i) {
+    if (!take(i)) continue;
     const evis_env_desc &d = c->envs[i];
-    for (int y = 0; y < d.height; y += c->tile_h)
-      for (int x = 0; x < d.width; x += c->tile_w) tiles.push_back(Tile{i, x, y, 0});
+    for (int y = 0; y < d.height; y += th)
+      for (int x = 0; x < d.width; x += tw) tiles.push_back(Tile{i, x, y, 0});
   }
   std::stable_sort(tiles.begin(), tiles.end(), [&](const Tile &a, const Tile &b) {
     return c->envs[a.env].K > c->envs[b.env].K;
@@ -150,20 +174,52 @@ int64_t max_tiles(const evis_ctx *c) {
   return n;
 }
 
-evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
-                    int64_t dt, uint64_t *tr_keys, float *tr_L) {
-  if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
-  if (dt <= 0 || dt > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
-  cudaError_t e = cudaSetDevice(c->device);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+// Regroups the environments by tile shape and uploads the tile lists (host-synchronous).
+cudaError_t rebuild_groups(evis_ctx *c) {
+  c->groups.clear();
+  std::vector<Tile> all;
+  for (int i = 0; i < c->n; ++i) {
+    bool seen = false;
+    for (const auto &g : c->groups) seen |= g.tw == c->env_tw[i] && g.th == c->env_th[i];
+    if (seen) continue;
+    const int tw = c->env_tw[i], th = c->env_th[i];
+    std::vector<Tile> t = tiles_for(c, tw, th, [&](int e) { return c->env_tw[e] == tw && c->env_th[e] == th; });
+    c->groups.push_back(evis_ctx::Group{tw, th, static_cast<int64_t>(all.size()), static_cast<int>(t.size())});
+    all.insert(all.end(), t.begin(), t.end());
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(c->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice);
+}
+
+// Launches the synthesis kernel for every tile group.
+cudaError_t launch_groups(evis_ctx *c, evis::StepArgs s, bool trace) {
+  for (size_t gi = 0; gi < c->groups.size(); ++gi) {
+    const auto &g = c->groups[gi];
+    s.tiles = c->d_tiles + g.offset;
+    s.n_tiles = g.count;
+    s.work_counter = c->d_work + gi;
+    cudaError_t e = evis::launch_step(s, g.tw, g.th, trace, c->grid_cap, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The new keyframe B as the synthesis kernel reads it.
+struct KeyframeB {
+  const float *L, *mv, *Z;
+};
+
+// Enqueues the preparation of keyframe B into slot b = slot ^ 1: clears the motion maxima and
+// work counters, converts / copies B, records its motion bounds and the per-source packs.
+cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, const float *depth,
+                         KeyframeB *out) {
   const int b = c->slot ^ 1;
-  const bool prof = c->prof_n < c->prof_max;
-  cudaEvent_t *pev = prof ? &c->prof[3 * c->prof_n] : nullptr;
-  if (prof && (e = cudaEventRecord(pev[0], c->stream)) != cudaSuccess)
-    return cuda_fail(c, e, "profile event");
   float *flowB = c->d_flow + b * c->n;
-  e = cudaMemsetAsync(flowB, 0, sizeof(float) * c->n, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "memset flow");
+  cudaError_t e = cudaMemsetAsync(flowB, 0, sizeof(float) * c->n, c->stream);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(c->d_work, 0, sizeof(unsigned) * kMaxGroups, c->stream)) != cudaSuccess)
+    return e;
   evis::PrepArgs pa{};
   pa.envs = c->d_envs;
   pa.frames = frames;
@@ -181,47 +237,67 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
   pa.eps = c->cfg.eps;
   pa.mode = c->mode;
   pa.max_segs = c->max_segs;
-  e = evis::launch_prep(pa, c->n, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "prep kernel");
-  const float *LB = c->need_L ? c->d_L[b] : frames;
-  const float *mvB = c->keep ? mv : c->d_mv[b];
-  const float *ZB = c->keep ? depth : c->d_Z[b];
+  if ((e = evis::launch_prep(pa, c->n, c->stream)) != cudaSuccess) return e;
+  out->L = c->need_L ? c->d_L[b] : frames;
+  out->mv = c->keep ? mv : c->d_mv[b];
+  out->Z = c->keep ? depth : c->d_Z[b];
+  return cudaSuccess;
+}
+
+// Arguments of the synthesis kernel for the gap from the retained A to B (tiles unset).
+evis::StepArgs step_args(const evis_ctx *c, const KeyframeB &B, int64_t dt) {
+  const int b = c->slot ^ 1;
+  evis::StepArgs s{};
+  s.envs = c->d_envs;
+  s.LA = c->A_L;
+  s.mvA = c->A_mv;
+  s.ZA = c->A_Z;
+  s.LB = B.L;
+  s.mvB = B.mv;
+  s.ZB = B.Z;
+  s.Lref = c->d_Lref;
+  s.tlast = c->d_tlast;
+  s.clock_in = c->d_clock + c->clk * c->n;
+  s.clock_out = c->d_clock + (c->clk ^ 1) * c->n;
+  s.flowA = c->d_flow + c->slot * c->n;
+  s.flowB = c->d_flow + b * c->n;
+  s.segA = c->d_seg[c->slot];
+  s.segB = c->d_seg[b];
+  s.packA = c->d_pack[0];
+  s.packB = c->d_pack[1];
+  s.events = c->d_events;
+  s.ev_count = c->d_count;
+  s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
+  s.dt = dt;
+  s.flags = c->cfg.flags;
+  s.tr_koff = c->d_tr_off;
+  s.tr_loff = c->d_tr_off + c->n;
+  return s;
+}
+
+evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
+                    int64_t dt, uint64_t *tr_keys, float *tr_L) {
+  if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
+  if (dt <= 0 || dt > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const bool prof = c->prof_n < c->prof_max;
+  cudaEvent_t *pev = prof ? &c->prof[3 * c->prof_n] : nullptr;
+  if (prof && (e = cudaEventRecord(pev[0], c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "profile event");
+  KeyframeB B{};
+  if ((e = enqueue_prep(c, frames, mv, depth, &B)) != cudaSuccess) return cuda_fail(c, e, "prep kernel");
   if (prof && (e = cudaEventRecord(pev[1], c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "profile event");
   if (c->have_A) {
-    evis::StepArgs s{};
-    s.envs = c->d_envs;
-    s.tiles = c->d_tiles;
-    s.LA = c->A_L;
-    s.mvA = c->A_mv;
-    s.ZA = c->A_Z;
-    s.LB = LB;
-    s.mvB = mvB;
-    s.ZB = ZB;
-    s.Lref = c->d_Lref;
-    s.tlast = c->d_tlast;
-    s.clock_in = c->d_clock + c->clk * c->n;
-    s.clock_out = c->d_clock + (c->clk ^ 1) * c->n;
-    s.flowA = c->d_flow + c->slot * c->n;
-    s.flowB = flowB;
-    s.segA = c->d_seg[c->slot];
-    s.segB = c->d_seg[b];
-    s.packA = c->d_pack[0];
-    s.packB = c->d_pack[1];
-    s.events = c->d_events;
-    s.ev_count = c->d_count;
-    s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
-    s.dt = dt;
-    s.flags = c->cfg.flags;
+    evis::StepArgs s = step_args(c, B, dt);
     s.tr_keys = tr_keys;
     s.tr_L = tr_L;
-    s.tr_koff = c->d_tr_off;
-    s.tr_loff = c->d_tr_off + c->n;
-    e = evis::launch_step(s, c->n_tiles, c->tile_w, c->tile_h, tr_keys != nullptr, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    if ((e = launch_groups(c, s, tr_keys != nullptr)) != cudaSuccess)
+      return cuda_fail(c, e, "step kernel");
     c->clk ^= 1;
   } else {
-    e = evis::launch_init_ref(LB, c->d_Lref, c->total, c->stream);
+    e = evis::launch_init_ref(B.L, c->d_Lref, c->total, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->have_A = true;
   }
@@ -229,11 +305,33 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
     if ((e = cudaEventRecord(pev[2], c->stream)) != cudaSuccess) return cuda_fail(c, e, "profile event");
     ++c->prof_n;
   }
-  c->slot = b;
-  c->A_L = LB;
-  c->A_mv = mvB;
-  c->A_Z = ZB;
+  c->slot ^= 1;
+  c->A_L = B.L;
+  c->A_mv = B.mv;
+  c->A_Z = B.Z;
   return EVIS_OK;
+}
+
+// Library-owned input buffers (two sets, alternating per keyframe), allocated once.
+cudaError_t ensure_inputs(evis_ctx *c) {
+  if (c->d_in[0][0]) return cudaSuccess;
+  const size_t fw = c->mode == EVIS_IN_RGB ? 3 : 1;
+  cudaError_t e;
+  for (int s = 0; s < 2; ++s) {
+    if ((e = dalloc(c, &c->d_in[s][0], fw * c->total)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_in[s][1], 2 * c->total)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_in[s][2], c->total)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+// Graphs bake the context's keyframe slots; any step taken outside them invalidates them.
+void drop_graphs(evis_ctx *c) {
+  for (auto &g : c->graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
 }
 
 }  // namespace
@@ -268,7 +366,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     v.W = d.width;
     v.H = d.height;
     v.K = d.K;
-    v.tile_h = c->tile_h;
+    v.tile_h = 16;
     v.pix_off = c->total;
     v.segs_x = (d.width + evis::kSegW - 1) / evis::kSegW;
     v.seg_off = c->total_segs;
@@ -287,8 +385,8 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     ko += int64_t(d.K) * 2 * px;
     lo += int64_t(d.K) * px;
   }
-  std::vector<Tile> tiles = build_tiles(c);
-  c->n_tiles = static_cast<int>(tiles.size());
+  c->env_tw.assign(n_envs, 64);
+  c->env_th.assign(n_envs, 16);
 
   cudaError_t e = cudaGetDevice(&c->device);
   auto bail = [&](cudaError_t err, const char *where) {
@@ -301,6 +399,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if (e != cudaSuccess) return bail(e, "cudaGetDevice");
   if ((e = dalloc(c, &c->d_envs, n_envs)) != cudaSuccess) return bail(e, "alloc envs");
   if ((e = dalloc(c, &c->d_tiles, max_tiles(c))) != cudaSuccess) return bail(e, "alloc tiles");
+  if ((e = dalloc(c, &c->d_work, kMaxGroups)) != cudaSuccess) return bail(e, "alloc work counters");
   if ((e = dalloc(c, &c->d_Lref, c->total)) != cudaSuccess) return bail(e, "alloc Lref");
   if (c->any_refr && (e = dalloc(c, &c->d_tlast, c->total)) != cudaSuccess)
     return bail(e, "alloc t_last");
@@ -324,7 +423,6 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   for (int i = 0; i < n_envs; ++i) clocks[i] = clocks[n_envs + i] = envs[i].t0_ns;
   cudaStream_t s = c->stream;
   if ((e = cudaMemcpyAsync(c->d_envs, denv.data(), sizeof(DevEnv) * n_envs, cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(c->d_clock, clocks.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(c->d_tr_off, troff.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s)) ||
@@ -335,6 +433,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "fill t_last");
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "create sync");
+  if ((e = rebuild_groups(c)) != cudaSuccess) return bail(e, "upload tiles");
   *out = c;
   return EVIS_OK;
 }
@@ -342,6 +441,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
 evis_status evis_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
                       int64_t dt_ns) {
   if (!c) return EVIS_ERR_INVALID_ARG;
+  drop_graphs(c);
   return do_step(c, frames, mv, depth, dt_ns, nullptr, nullptr);
 }
 
@@ -349,6 +449,7 @@ evis_status evis_step_trace(evis_ctx *c, const float *frames, const float *mv,
                             const float *depth, int64_t dt_ns, uint64_t *keys, float *Lint) {
   if (!c) return EVIS_ERR_INVALID_ARG;
   if (!keys || !Lint) return fail(c, EVIS_ERR_INVALID_ARG, "null trace buffer");
+  drop_graphs(c);
   return do_step(c, frames, mv, depth, dt_ns, keys, Lint);
 }
 
@@ -358,15 +459,9 @@ evis_status evis_step_host(evis_ctx *c, const float *frames, const float *mv,
   if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
   if (dt_ns <= 0 || dt_ns > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
   const size_t fw = c->mode == EVIS_IN_RGB ? 3 : 1;
-  cudaError_t e;
-  if (!c->d_in[0][0]) {
-    for (int s = 0; s < 2; ++s) {
-      if ((e = dalloc(c, &c->d_in[s][0], fw * c->total)) != cudaSuccess ||
-          (e = dalloc(c, &c->d_in[s][1], 2 * c->total)) != cudaSuccess ||
-          (e = dalloc(c, &c->d_in[s][2], c->total)) != cudaSuccess)
-        return cuda_fail(c, e, "alloc host-step buffers");
-    }
-  }
+  drop_graphs(c);
+  cudaError_t e = ensure_inputs(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "alloc input buffers");
   float **in = c->d_in[c->in_slot];
   if ((e = cudaMemcpyAsync(in[0], frames, sizeof(float) * fw * c->total, cudaMemcpyHostToDevice, c->stream)) ||
       (e = cudaMemcpyAsync(in[1], mv, sizeof(float) * 2 * c->total, cudaMemcpyHostToDevice, c->stream)) ||
@@ -453,13 +548,183 @@ evis_status evis_set_tile_shape(evis_ctx *c, int32_t tile_w, int32_t tile_h) {
     return fail(c, EVIS_ERR_INVALID_ARG, "unsupported tile shape");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "tile shape sync");
-  c->tile_w = tile_w;
-  c->tile_h = tile_h;
-  std::vector<Tile> tiles = build_tiles(c);
-  c->n_tiles = static_cast<int>(tiles.size());
-  if ((e = cudaMemcpy(c->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
-                      cudaMemcpyHostToDevice)) != cudaSuccess)
-    return cuda_fail(c, e, "upload tiles");
+  c->env_tw.assign(c->n, tile_w);
+  c->env_th.assign(c->n, tile_h);
+  if ((e = rebuild_groups(c)) != cudaSuccess) return cuda_fail(c, e, "upload tiles");
+  return EVIS_OK;
+}
+
+evis_status evis_set_env_tile_shapes(evis_ctx *c, const int32_t *tile_w, const int32_t *tile_h) {
+  if (!c || !tile_w || !tile_h) return EVIS_ERR_INVALID_ARG;
+  int distinct = 0;
+  for (int i = 0; i < c->n; ++i) {
+    if (!evis::tile_shape_supported(tile_w[i], tile_h[i]))
+      return fail(c, EVIS_ERR_INVALID_ARG, "unsupported tile shape");
+    bool seen = false;
+    for (int j = 0; j < i; ++j) seen |= tile_w[j] == tile_w[i] && tile_h[j] == tile_h[i];
+    distinct += seen ? 0 : 1;
+  }
+  if (distinct > kMaxGroups) return fail(c, EVIS_ERR_INVALID_ARG, "too many tile shapes");
+  c->env_tw.assign(tile_w, tile_w + c->n);
+  c->env_th.assign(tile_h, tile_h + c->n);
+  drop_graphs(c);
+  cudaError_t e = rebuild_groups(c);
+  return e == cudaSuccess ? EVIS_OK : cuda_fail(c, e, "upload tiles");
+}
+
+evis_status evis_get_tile_shapes(evis_ctx *c, int32_t *tile_w, int32_t *tile_h) {
+  if (!c || !tile_w || !tile_h) return EVIS_ERR_INVALID_ARG;
+  std::copy(c->env_tw.begin(), c->env_tw.end(), tile_w);
+  std::copy(c->env_th.begin(), c->env_th.end(), tile_h);
+  return EVIS_OK;
+}
+
+evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, const float *depth,
+                          int64_t dt_ns, int32_t reps, float *best_ms) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (!frames || !mv || !depth || reps < 1 || reps > 100 || dt_ns <= 0 || dt_ns > kMaxDt)
+    return fail(c, EVIS_ERR_INVALID_ARG, "bad autotune arguments");
+  if (!c->have_A) return fail(c, EVIS_ERR_STATE, "autotune needs a retained keyframe (step once first)");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune sync");
+  if (!c->d_tune_Lref) {
+    if ((e = dalloc(c, &c->d_tune_Lref, c->total)) != cudaSuccess ||
+        (c->d_tlast && (e = dalloc(c, &c->d_tune_tlast, c->total)) != cudaSuccess) ||
+        (e = dalloc(c, &c->d_tune_tiles, max_tiles(c))) != cudaSuccess)
+      return cuda_fail(c, e, "alloc autotune scratch");
+  }
+  // save the per-pixel state and the event counter; every trial starts from them
+  unsigned long long count0 = 0;
+  if ((e = cudaMemcpy(&count0, c->d_count, sizeof count0, cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(c->d_tune_Lref, c->d_Lref, sizeof(float) * c->total, cudaMemcpyDeviceToDevice)) ||
+      (c->d_tlast && (e = cudaMemcpy(c->d_tune_tlast, c->d_tlast, sizeof(int64_t) * c->total,
+                                     cudaMemcpyDeviceToDevice))))
+    return cuda_fail(c, e, "autotune save");
+  KeyframeB B{};
+  if ((e = enqueue_prep(c, frames, mv, depth, &B)) != cudaSuccess) return cuda_fail(c, e, "autotune prep");
+  evis::StepArgs base = step_args(c, B, dt_ns);
+  const int shapes[5][2] = {{32, 16}, {32, 32}, {64, 16}, {64, 32}, {128, 16}};
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  std::vector<int> tw(c->n, 64), th(c->n, 16);
+  std::vector<bool> done(c->n, false);
+  float total_best = 0.0f;
+  for (int i = 0; i < c->n && e == cudaSuccess; ++i) {
+    if (done[i]) continue;  // one trial per resolution class (same width and height)
+    const int W = c->envs[i].width, H = c->envs[i].height;
+    auto in_class = [&](int k) { return c->envs[k].width == W && c->envs[k].height == H; };
+    float best = 1e30f;
+    for (const auto &sh : shapes) {
+      std::vector<Tile> tiles = tiles_for(c, sh[0], sh[1], in_class);
+      if ((e = cudaMemcpy(c->d_tune_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
+                          cudaMemcpyHostToDevice)) != cudaSuccess)
+        break;
+      evis::StepArgs s = base;
+      s.tiles = c->d_tune_tiles;
+      s.n_tiles = static_cast<int>(tiles.size());
+      s.work_counter = c->d_work + kMaxGroups - 1;
+      float t_min = 1e30f;
+      for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // r = 0 warms up
+        if ((e = cudaMemcpyAsync(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->total,
+                                 cudaMemcpyDeviceToDevice, c->stream)) ||
+            (c->d_tlast && (e = cudaMemcpyAsync(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->total,
+                                                cudaMemcpyDeviceToDevice, c->stream))) ||
+            (e = cudaMemsetAsync(s.work_counter, 0, sizeof(unsigned), c->stream)) ||
+            (e = cudaEventRecord(ev0, c->stream)) ||
+            (e = evis::launch_step(s, sh[0], sh[1], false, c->grid_cap, c->stream)) ||
+            (e = cudaEventRecord(ev1, c->stream)) || (e = cudaEventSynchronize(ev1)))
+          break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        if (r > 0) t_min = std::min(t_min, ms);
+      }
+      if (e != cudaSuccess) break;
+      if (t_min < best) {
+        best = t_min;
+        for (int k = 0; k < c->n; ++k)
+          if (in_class(k)) tw[k] = sh[0], th[k] = sh[1];
+      }
+    }
+    for (int k = 0; k < c->n; ++k) done[k] = done[k] || in_class(k);
+    total_best += best;
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  // restore the state and the counter whatever happened above
+  cudaError_t r = cudaStreamSynchronize(c->stream);
+  if (r == cudaSuccess) r = cudaMemcpy(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->total, cudaMemcpyDeviceToDevice);
+  if (r == cudaSuccess && c->d_tlast)
+    r = cudaMemcpy(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->total, cudaMemcpyDeviceToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(c->d_count, &count0, sizeof count0, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = r;
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  if (best_ms) *best_ms = total_best;
+  return evis_set_env_tile_shapes(c, tw.data(), th.data());
+}
+
+evis_status evis_input_buffers(evis_ctx *c, float **frames, float **mv, float **depth) {
+  if (!c || !frames || !mv || !depth) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = ensure_inputs(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "alloc input buffers");
+  *frames = c->d_in[c->in_slot][0];
+  *mv = c->d_in[c->in_slot][1];
+  *depth = c->d_in[c->in_slot][2];
+  return EVIS_OK;
+}
+
+evis_status evis_capture(evis_ctx *c, int64_t dt_ns) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (dt_ns <= 0 || dt_ns > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
+  if (!c->have_A) return fail(c, EVIS_ERR_STATE, "capture needs a retained keyframe (step once first)");
+  if (c->keep) return fail(c, EVIS_ERR_STATE, "capture needs a context without EVIS_KEEP_INPUTS");
+  if (c->stream == nullptr) return fail(c, EVIS_ERR_STATE, "capture needs a non-default stream");
+  cudaError_t e = ensure_inputs(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "alloc input buffers");
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "capture sync");
+  drop_graphs(c);
+  const int prof_max = c->prof_max;
+  c->prof_max = c->prof_n;  // no profiling events inside graphs
+  evis_status st = EVIS_OK;
+  for (int ph = 0; ph < 2 && st == EVIS_OK; ++ph) {
+    if ((e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      st = cuda_fail(c, e, "begin capture");
+      break;
+    }
+    float **in = c->d_in[c->in_slot];
+    st = do_step(c, in[0], in[1], in[2], dt_ns, nullptr, nullptr);  // records, runs nothing
+    c->in_slot ^= 1;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->stream, &g);
+    if (st == EVIS_OK && e != cudaSuccess) st = cuda_fail(c, e, "end capture");
+    if (st == EVIS_OK && (e = cudaGraphInstantiate(&c->graph[ph], g, 0)) != cudaSuccess)
+      st = cuda_fail(c, e, "instantiate graph");
+    if (g) cudaGraphDestroy(g);
+  }
+  c->prof_max = prof_max;
+  if (st != EVIS_OK) {
+    drop_graphs(c);
+    return st;
+  }
+  // two recorded gaps brought the slots, clocks and input buffers back to where they were
+  c->graph_dt = dt_ns;
+  c->graph_phase = 0;
+  return EVIS_OK;
+}
+
+evis_status evis_replay(evis_ctx *c) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (!c->graph[c->graph_phase]) return fail(c, EVIS_ERR_STATE, "no captured graph (evis_capture)");
+  cudaError_t e = cudaGraphLaunch(c->graph[c->graph_phase], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  // the host-side bookkeeping of one evis_step from the input buffers
+  c->graph_phase ^= 1;
+  c->slot ^= 1;
+  c->clk ^= 1;
+  c->in_slot ^= 1;
+  c->A_L = c->d_L[c->slot];
+  c->A_mv = c->d_mv[c->slot];
+  c->A_Z = c->d_Z[c->slot];
   return EVIS_OK;
 }
 

@@ -38,7 +38,9 @@ struct Tile {
 // inside the kernel).
 struct StepArgs {
   const DevEnv *envs;
-  const Tile *tiles;
+  const Tile *tiles;          // the tiles of this launch, largest K first
+  int n_tiles;
+  unsigned *work_counter;     // zeroed before the launch
   const float *LA, *mvA, *ZA;
   const float *LB, *mvB, *ZB;
   float *Lref;
@@ -74,7 +76,9 @@ struct PrepArgs {
 
 cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
-cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_w, int tile_h, bool trace,
+// grid_cap > 0: persistent launch of at most grid_cap x (resident CTAs) blocks that take
+// tiles from a.work_counter; 0: one block per tile.
+cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, int grid_cap,
                         cudaStream_t s);
 bool tile_shape_supported(int tile_w, int tile_h);
 // Error text reported by evis_last_error(NULL) for calls made without a context.

@@ -212,7 +212,7 @@ struct StepSmem {
   ulonglong2 stage[kEventStage];           // events of this sub-frame before the flush
   float4 cand_b[2][kCandidates];           // candidate segments' motion bounds
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
-  unsigned hit[2 * kCandidates];           // candidates that can reach the tile this sub-frame
+  unsigned hit[2][2 * kCandidates];        // candidates reaching the tile, by sub-frame parity
   int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
   unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
 };
@@ -224,19 +224,19 @@ constexpr int step_min_blocks() {
   return TX * TY <= 512 ? 4 : (TX * TY <= 1024 ? 3 : 2);
 }
 
+// All K sub-frames of one target tile (the body of step_kernel).
 template <int TX, int TY, bool TRACE, bool PACKED>
-__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
+__device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NT = TX * TY / kThreads;   // targets per thread
   constexpr int NW = kThreads / 32;
   constexpr int ROWS = kThreads / TX;      // tile rows covered by one pass of the block
   static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
-  __shared__ unsigned s_n, s_flush, s_nhit;
+  __shared__ unsigned s_n, s_flush, s_nhit[2], s_arrive;
   __shared__ unsigned long long s_base;
   __shared__ int s_nc[2], s_over;
 
-  const Tile tl = a.tiles[blockIdx.x];
   const DevEnv E = a.envs[tl.env];
   const int W = E.W, H = E.H, K = E.K;
   const int64_t o = E.pix_off;
@@ -286,9 +286,18 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
   const int sy0 = max(0, tl.y0 - h), sy1 = min(H, tl.y0 + TY + h);
   if (tid == 0) {
     s_n = 0;
-    s_nhit = 0;
+    s_flush = 0;
+    s_base = 0;
+    s_nhit[0] = s_nhit[1] = 0;
+    s_arrive = 0;
     s_nc[0] = s_nc[1] = 0;
     s_over = 0;
+  }
+  // z-buffers start empty; afterwards each thread clears its own slots once it has read them
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    S.zb[0][tid + kThreads * j] = kEmptyKey;
+    S.zb[1][tid + kThreads * j] = kEmptyKey;
   }
   __syncthreads();
 
@@ -344,12 +353,10 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
     }
     const int64_t ti = T0 + tq;
 
-    // ---- phase 1: clear the z-buffers; list the candidates that reach the tile now ----
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      S.zb[0][tid + kThreads * j] = kEmptyKey;
-      S.zb[1][tid + kThreads * j] = kEmptyKey;
-    }
+    // Two barriers per sub-frame.  Phase 1 (list reaching candidates) may overlap other
+    // warps' phase 3 of the previous sub-frame; the hit list is double-buffered by parity.
+    const int par = i & 1;
+    // ---- phase 1: list the candidate segments that reach the tile at this f ----
     if (!over) {
       for (int c0 = 0; c0 < nAB; c0 += kThreads) {
         const int c = c0 + tid;
@@ -372,19 +379,29 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
         const unsigned m = __ballot_sync(kFull, hit);
         if (m) {
           unsigned base = 0;
-          if (lane == 0) base = atomicAdd(&s_nhit, static_cast<unsigned>(__popc(m)));
+          if (lane == 0) base = atomicAdd(&s_nhit[par], static_cast<unsigned>(__popc(m)));
           base = __shfl_sync(kFull, base, 0);
-          if (hit) S.hit[base + __popc(m & lanes_below)] = static_cast<unsigned>(c);
+          if (hit) S.hit[par][base + __popc(m & lanes_below)] = static_cast<unsigned>(c);
         }
       }
     }
     __syncthreads();
 
-    // ---- phase 2: splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
+    // ---- phase 2: flush the previous sub-frame's staged events (reserved by the last warp
+    // to finish it), then splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
+    if (tid == 0) s_nhit[par ^ 1] = 0;
+    {
+      const unsigned nf = s_flush;
+      const unsigned long long gbs = s_base;
+      for (unsigned r = tid; r < nf; r += kThreads) {
+        const unsigned long long gi = gbs + r;
+        if (gi < a.capacity) a.events[gi] = S.stage[r];
+      }
+    }
     if (!over) {
-      const unsigned nh = s_nhit;
+      const unsigned nh = s_nhit[par];
       for (unsigned hh = warp; hh < nh; hh += NW) {  // one warp per segment, one lane per source
-        const int c = static_cast<int>(S.hit[hh]);
+        const int c = static_cast<int>(S.hit[par][hh]);
         const int dir = c >= nA ? 1 : 0;
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int xs = static_cast<int>(xy & 0xFFFFu) * kSegW, sy = static_cast<int>(xy >> 16);
@@ -407,7 +424,6 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
     __syncthreads();
 
     // ---- phase 3: resolve, blend, threshold crossings, emission ----
-    if (tid == 0) s_nhit = 0;
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
       const int ty = ty0 + ROWS * j;
@@ -418,6 +434,8 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
       if (act[j]) {
         const unsigned long long kA = S.zb[0][tid + kThreads * j];
         const unsigned long long kB = S.zb[1][tid + kThreads * j];
+        S.zb[0][tid + kThreads * j] = kEmptyKey;  // ready for the next sub-frame
+        S.zb[1][tid + kThreads * j] = kEmptyKey;
         const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
         const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
         const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
@@ -531,16 +549,23 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
         tprev[j] = ti;
       }
     }
-    __syncthreads();
-
-    // ---- phase 4: flush the staging buffer: one global reservation, 16 B per thread ----
-    if (tid == 0) {
-      const unsigned nn = min(s_n, static_cast<unsigned>(kEventStage));
-      s_flush = nn;
-      s_base = nn ? atomicAdd(a.ev_count, static_cast<unsigned long long>(nn)) : 0ull;
-      s_n = 0;
+    // ---- end of phase 3: the last warp to finish reserves the global range of this
+    // sub-frame's staged events (one atomic per CTA); they are copied out in phase 2 of the
+    // next sub-frame, or after the loop ----
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&s_arrive, 1u) == static_cast<unsigned>(NW - 1)) {
+        const unsigned nn = min(s_n, static_cast<unsigned>(kEventStage));
+        s_flush = nn;
+        s_base = nn ? atomicAdd(a.ev_count, static_cast<unsigned long long>(nn)) : 0ull;
+        s_n = 0;
+        s_arrive = 0;
+      }
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  {
     const unsigned nf = s_flush;
     const unsigned long long gbs = s_base;
     for (unsigned r = tid; r < nf; r += kThreads) {
@@ -557,6 +582,21 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
     if (a.tlast) a.tlast[o + pix] = tlast[j];
   }
   if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) a.clock_out[tl.env] = T0 + a.dt;
+}
+
+// One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
+// first one by block index, the next ones from a work counter that starts at 0.
+template <int TX, int TY, bool TRACE, bool PACKED>
+__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
+  __shared__ int s_tile;
+  int t = blockIdx.x;
+  while (t < a.n_tiles) {
+    run_tile<TX, TY, TRACE, PACKED>(a, a.tiles[t]);
+    __syncthreads();  // the tile's shared memory is free again
+    if (threadIdx.x == 0) s_tile = static_cast<int>(gridDim.x + atomicAdd(a.work_counter, 1u));
+    __syncthreads();
+    t = s_tile;
+  }
 }
 
 // One warp per 32-pixel row segment: log-intensity, optional copies, and the segment's
@@ -676,16 +716,25 @@ cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, flo
 }
 
 template <int TX, int TY, bool TRACE, bool PACKED>
-cudaError_t launch_shape(const StepArgs &a, int n_tiles, cudaStream_t s) {
-  static bool configured = false;  // one attribute call per instantiation and process
+cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
+  static int resident = 0;  // CTAs per SM x SMs, looked up once per instantiation
   const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
-  if (!configured) {
+  if (!resident) {
     cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED>, kThreads, smem)) != cudaSuccess)
+      return e;
+    resident = max(1, per_sm) * sms;
   }
-  step_kernel<TX, TY, TRACE, PACKED><<<n_tiles, kThreads, smem, s>>>(a);
+  int grid = n_tiles;
+  if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
+  step_kernel<TX, TY, TRACE, PACKED><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -694,17 +743,18 @@ bool tile_shape_supported(int tw, int th) {
          (tw == 128 && th == 16);
 }
 
-cudaError_t launch_step(const StepArgs &a, int n_tiles, int tile_w, int tile_h, bool trace,
+cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, int grid_cap,
                         cudaStream_t s) {
+  const int n_tiles = a.n_tiles;
   if (n_tiles <= 0) return cudaSuccess;
   if (!a.packA) {  // unpacked sources: 64x16 tiles only
     if (tile_w != 64 || tile_h != 16 || trace) return cudaErrorInvalidValue;
-    return launch_shape<64, 16, false, false>(a, n_tiles, s);
+    return launch_shape<64, 16, false, false>(a, n_tiles, grid_cap, s);
   }
 #define EVIS_SHAPE(TX, TY)                                                               \
   if (tile_w == TX && tile_h == TY)                                                      \
-    return trace ? launch_shape<TX, TY, true, true>(a, n_tiles, s)                       \
-                 : launch_shape<TX, TY, false, true>(a, n_tiles, s);
+    return trace ? launch_shape<TX, TY, true, true>(a, n_tiles, grid_cap, s)             \
+                 : launch_shape<TX, TY, false, true>(a, n_tiles, grid_cap, s);
   EVIS_SHAPE(32, 16)
   EVIS_SHAPE(32, 32)
   EVIS_SHAPE(64, 16)

@@ -30,6 +30,7 @@ constexpr int kNaMaxSegs = 40960;           // >= ceil(W/32) * H within the limi
 // Byte layout of the scratch array.
 constexpr size_t kOffEnv = 0;
 constexpr size_t kOffClock = 256;                                     // int64 [2]
+constexpr size_t kOffWork = 384;                                      // unsigned work counter
 constexpr size_t kOffFlow = 512;                                      // float [2]
 constexpr size_t kOffTiles = 768;                                     // Tile [kNaMaxTiles]
 constexpr size_t kOffSeg = kOffTiles + sizeof(Tile) * kNaMaxTiles;    // float4 [2][kNaMaxSegs]
@@ -75,6 +76,7 @@ __global__ void noalloc_setup(unsigned char *scratch, DevEnv env, int tiles_x, i
     float *flow = reinterpret_cast<float *>(scratch + kOffFlow);
     flow[0] = 0.0f;
     flow[1] = 0.0f;
+    *reinterpret_cast<unsigned *>(scratch + kOffWork) = 0u;
   }
 }
 
@@ -162,6 +164,8 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
     evis::StepArgs sa{};
     sa.envs = s_env;
     sa.tiles = s_tiles;
+    sa.n_tiles = n_tiles;
+    sa.work_counter = reinterpret_cast<unsigned *>(scratch + kOffWork);
     sa.LA = L_A;
     sa.mvA = mv_A;
     sa.ZA = Z_A;
@@ -181,7 +185,8 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
     sa.capacity = static_cast<unsigned long long>(capacity);
     sa.dt = dt_ns;
     sa.flags = flags;
-    if ((e = evis::launch_step(sa, n_tiles, kNaTileW, kNaTileH, false, s)) != cudaSuccess)
+    if ((e = evis::launch_step(sa, kNaTileW, kNaTileH, /*trace=*/false, /*grid_cap=*/0, s)) !=
+        cudaSuccess)
       goto cuda_error;
   }
   return EVIS_OK;
