@@ -395,3 +395,179 @@ void orc_log_intensity(const float* in, int64_t n, int32_t mode, float eps, floa
 }
 
 }  // extern "C"
+
+// ==========================================================================================
+// Differentiable soft event-count surrogate (no counterpart in the paper, which has no
+// backward pass).  Definition, per environment, per sub-frame i and warp direction X:
+//  * discrete decisions, frozen and taken in binary32 exactly as in the event path: the
+//    z-buffer winners (Eqs. 5-7), hole flags, and the reference-level trajectory L_ref^(i)
+//    of the event model (Eq. 4) with C_on = C_off = C;
+//  * the winner surface W_X(t): footprint sources p of target t whose interpolated depth is
+//    within a relative delta of the winning depth, Z~(p) <= Z* (1 + delta) (binary32 test);
+//  * soft value S_X(t) = sum_W w(p,t) L_X(p) / sum_W w(p,t), w the bilinear weight of q(p)
+//    (smooth in the motion vectors through q = p - f m_A or p + (1-f) m_B);
+//  * L_i(t) = (1-f) S_A + f S_B where both directions have a sample, else the present one;
+//  * N_on(t) = sum_i sig((L_i - L_ref^(i-1) - C) / tau), N_off(t) = sum_i sig((L_ref^(i-1)
+//    - L_i - C) / tau), over the sub-frames where t has a sample.
+// The smooth part is evaluated in binary64; the gradient is hand-derived (and checked by
+// central differences in the tests).
+// ==========================================================================================
+namespace {
+
+struct SoftIn {
+  const float *LA, *LB, *mvA, *mvB, *ZA, *ZB, *Lref0;  // decisions (binary32)
+  const double *dLA, *dLB, *dmvA, *dmvB;               // smooth part (binary64)
+};
+
+inline double sigm(double u) { return 1.0 / (1.0 + std::exp(-u)); }
+
+// One environment, one keyframe gap.  counts: [2][H][W]; grads (optional): dL*, dmv* packed
+// like the inputs, dC scalar.
+void soft_env(int W, int H, int K, float Cf, double Cd, double tau, float delta,
+              const SoftIn &in, double *counts, const double *gcounts, double *gLA, double *gLB,
+              double *gmvA, double *gmvB, double *gC) {
+  const size_t HW = static_cast<size_t>(W) * H;
+  std::vector<float> Lref(in.Lref0, in.Lref0 + HW);
+  std::vector<uint64_t> zb[2] = {std::vector<uint64_t>(HW), std::vector<uint64_t>(HW)};
+  std::vector<double> SW[2], SWL[2], GX[2], SH[2];
+  for (int d = 0; d < 2; ++d) {
+    SW[d].resize(HW);
+    SWL[d].resize(HW);
+    GX[d].resize(HW);
+    SH[d].resize(HW);
+  }
+  std::fill(counts, counts + 2 * HW, 0.0);
+  for (int i = 1; i <= K; ++i) {
+    const float f = static_cast<float>(i) / static_cast<float>(K), g = 1.0f - f;
+    const double fd = static_cast<double>(i) / K, gd = 1.0 - fd;
+    std::fill(zb[0].begin(), zb[0].end(), EMPTY);
+    std::fill(zb[1].begin(), zb[1].end(), EMPTY);
+    splat_A(zb[0].data(), W, H, in.mvA, in.ZA, in.ZB, f, g, false);
+    splat_B(zb[1].data(), W, H, in.mvB, in.ZA, in.ZB, f, g, false);
+    // visits every (source, footprint cell) pair of the winner surfaces
+    auto for_members = [&](int dir, auto &&visit) {
+      const float *mv = dir ? in.mvB : in.mvA;
+      const float *Zs = dir ? in.ZB : in.ZA;
+      const float *Zo = dir ? in.ZA : in.ZB;
+      const double *mvd = dir ? in.dmvB : in.dmvA;
+      for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+          const size_t p = static_cast<size_t>(y) * W + x;
+          const float zs = Zs[p];
+          if (!valid_depth(zs)) continue;
+          const float mx = mv[2 * p], my = mv[2 * p + 1];
+          float qx, qy, zt;
+          if (dir == 0) {
+            qx = static_cast<float>(x) - f * mx;
+            qy = static_cast<float>(y) - f * my;
+            zt = g * zs + f * other_depth(Zo, W, H, static_cast<float>(x) - mx, static_cast<float>(y) - my, zs);
+          } else {
+            qx = static_cast<float>(x) + g * mx;
+            qy = static_cast<float>(y) + g * my;
+            zt = g * other_depth(Zo, W, H, static_cast<float>(x) + mx, static_cast<float>(y) + my, zs) + f * zs;
+          }
+          if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H))) continue;
+          const float fx0 = std::floor(qx), fy0 = std::floor(qy);
+          const float ax = qx - fx0, ay = qy - fy0;
+          const float wx[2] = {1.0f - ax, ax}, wy[2] = {1.0f - ay, ay};
+          const double s = dir ? gd : -fd;  // q = p + s m
+          const double qxd = x + s * mvd[2 * p], qyd = y + s * mvd[2 * p + 1];
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+              const int cx = static_cast<int>(fx0) + dx, cy = static_cast<int>(fy0) + dy;
+              if (!(wx[dx] * wy[dy] > 0.0f) || cx < 0 || cx >= W || cy < 0 || cy >= H) continue;
+              const size_t t = static_cast<size_t>(cy) * W + cx;
+              uint32_t zbits = static_cast<uint32_t>(zb[dir][t] >> 32);
+              float zstar;
+              std::memcpy(&zstar, &zbits, 4);
+              if (!(zt <= zstar * (1.0f + delta))) continue;
+              const double ex = qxd - cx, ey = qyd - cy;  // tent weights and their slopes
+              const double wxd = 1.0 - std::fabs(ex), wyd = 1.0 - std::fabs(ey);
+              const double sx = ex > 0 ? -1.0 : 1.0, sy = ey > 0 ? -1.0 : 1.0;
+              visit(p, t, wxd * wyd, sx * wyd * s, sy * wxd * s);
+            }
+        }
+    };
+    for (int d = 0; d < 2; ++d) {
+      std::fill(SW[d].begin(), SW[d].end(), 0.0);
+      std::fill(SWL[d].begin(), SWL[d].end(), 0.0);
+      const double *Ld = d ? in.dLB : in.dLA;
+      for_members(d, [&](size_t p, size_t t, double w, double, double) {
+        SW[d][t] += w;
+        SWL[d][t] += w * Ld[p];
+      });
+    }
+    for (size_t t = 0; t < HW; ++t) {
+      const bool hA = zb[0][t] != EMPTY, hB = zb[1][t] != EMPTY;
+      GX[0][t] = GX[1][t] = 0.0;
+      if (!hA && !hB) continue;
+      const double SA = hA ? SWL[0][t] / SW[0][t] : 0.0, SB = hB ? SWL[1][t] / SW[1][t] : 0.0;
+      SH[0][t] = SA;
+      SH[1][t] = SB;
+      const double Ls = (hA && hB) ? gd * SA + fd * SB : (hA ? SA : SB);
+      const double lr = Lref[t];
+      const double uon = (Ls - lr - Cd) / tau, uoff = (lr - Ls - Cd) / tau;
+      const double son = sigm(uon), soff = sigm(uoff);
+      counts[t] += son;
+      counts[HW + t] += soff;
+      if (gcounts) {
+        const double don = son * (1.0 - son) / tau, doff = soff * (1.0 - soff) / tau;
+        const double G = gcounts[t] * don - gcounts[HW + t] * doff;
+        *gC += -(gcounts[t] * don + gcounts[HW + t] * doff);
+        if (hA) GX[0][t] = G * (hB ? gd : 1.0) / SW[0][t];
+        if (hB) GX[1][t] = G * (hA ? fd : 1.0) / SW[1][t];
+      }
+      // frozen discrete trajectory of the reference level (binary32, Eq. 4)
+      const float la = hA ? in.LA[zb[0][t] & 0xFFFFFFu] : 0.0f, lb = hB ? in.LB[zb[1][t] & 0xFFFFFFu] : 0.0f;
+      const float L = (hA && hB) ? g * la + f * lb : (hA ? la : lb);
+      const float dd = L - Lref[t];
+      const int pol = dd > 0.0f ? 1 : -1;
+      const float q = std::fabs(dd) / Cf;
+      int n = 0;
+      if (q >= 1.0f) n = q >= static_cast<float>(MAX_CROSSINGS) ? MAX_CROSSINGS : static_cast<int>(std::floor(q));
+      if (n > 0) Lref[t] = Lref[t] + static_cast<float>(pol * n) * Cf;
+    }
+    if (gcounts) {
+      for (int d = 0; d < 2; ++d) {
+        const double *Ld = d ? in.dLB : in.dLA;
+        double *gL = d ? gLB : gLA;
+        double *gm = d ? gmvB : gmvA;
+        for_members(d, [&](size_t p, size_t t, double w, double dwdmx, double dwdmy) {
+          gL[p] += GX[d][t] * w;
+          gm[2 * p] += GX[d][t] * (Ld[p] - SH[d][t]) * dwdmx;
+          gm[2 * p + 1] += GX[d][t] * (Ld[p] - SH[d][t]) * dwdmy;
+        });
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Soft event counts of one keyframe gap for every environment (packed layout; counts are
+// [2][H][W] per environment at 2 * pix_off).  Decision inputs are binary32, the smooth
+// inputs binary64 (the same values, or perturbed ones for finite differences).  With
+// gcounts non-null, also accumulates the gradients (arrays zeroed by the caller).
+int32_t orc_soft(const orc_env *envs, int32_t n_envs, double tau, float delta,
+                 const float *LA, const float *LB, const float *mvA, const float *mvB,
+                 const float *ZA, const float *ZB, const float *Lref0, const float *Cf,
+                 const double *dLA, const double *dLB, const double *dmvA, const double *dmvB,
+                 const double *Cd, double *counts, const double *gcounts, double *gLA,
+                 double *gLB, double *gmvA, double *gmvB, double *gC) {
+  size_t off = 0;
+  for (int e = 0; e < n_envs; ++e) {
+    const int W = envs[e].width, H = envs[e].height;
+    SoftIn in{LA + off, LB + off, mvA + 2 * off, mvB + 2 * off, ZA + off, ZB + off, Lref0 + off,
+              dLA + off, dLB + off, dmvA + 2 * off, dmvB + 2 * off};
+    soft_env(W, H, envs[e].K, Cf[e], Cd[e], tau, delta, in, counts + 2 * off,
+             gcounts ? gcounts + 2 * off : nullptr, gLA ? gLA + off : nullptr,
+             gLB ? gLB + off : nullptr, gmvA ? gmvA + 2 * off : nullptr,
+             gmvB ? gmvB + 2 * off : nullptr, gC ? gC + e : nullptr);
+    off += (static_cast<size_t>(W) * H + 3) / 4 * 4;
+  }
+  return 0;
+}
+
+}  // extern "C"
