@@ -307,6 +307,7 @@ def evis_arm(args, world, rank, local):
         dist.destroy_process_group()
     if rank != 0:
         return
+    soft = soft_leg() if rank == 0 else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         r, evs, sec, desc = oracle_sample_rate(args.cpu_envs, 2)
@@ -319,9 +320,41 @@ def evis_arm(args, world, rank, local):
             "config": config_block(w, args.envs), "events_per_s": events_per_s,
             "events_per_step": n_events / args.steps, "step_ms": step_ms,
             "wall_s": wall, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "gpu_launches": 2 * args.steps, "clocks": clk, "soft_surrogate": soft,
             "parallelism": f"env shards x{world}, no collective on the data path"}
     print(json.dumps(line), flush=True)
+
+
+def soft_leg(reps=10):
+    """Differentiable workload (16 envs at 346x260, K=8, tau=0.02): device time of the soft
+    forward and of the backward under a random cotangent, and their ratio."""
+    import numpy as np
+    import torch
+    import paper_2607_08098_b300 as ev
+    import scenes
+    w = scenes.config5()
+    kf = [scenes.render(w.envs, k) for k in range(2)]
+    d = [torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+         for a in (kf[0].L, kf[1].L, kf[0].mv, kf[1].mv, kf[0].Z, kf[1].Z, kf[0].L)]
+    C = torch.full((len(w.envs),), 0.2, dtype=torch.float32, device="cuda")
+    counts, ws = ev._soft_forward(w.envs, 0.02, 1e-3, *d, C)
+    gc = torch.randn(counts.numel(), generator=torch.Generator().manual_seed(5)).cuda()
+    ev._soft_backward(w.envs, 0.02, 1e-3, *d[:6], C, ws, gc)
+    st = torch.cuda.current_stream()
+    tf = tb = 0.0
+    for _ in range(reps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        ev._soft_forward(w.envs, 0.02, 1e-3, *d, C, ws=ws)
+        e1.record(st)
+        ev._soft_backward(w.envs, 0.02, 1e-3, *d[:6], C, ws, gc)
+        e2.record(st)
+        e2.synchronize()
+        tf += e0.elapsed_time(e1)
+        tb += e1.elapsed_time(e2)
+    return {"workload": "16 envs at 346x260, K=8, tau=0.02, delta=1e-3, random cotangent",
+            "fwd_ms": tf / reps, "bwd_ms": tb / reps, "bwd_fwd_ratio": tb / tf,
+            "pixel_substeps": w.pixel_substeps}
 
 
 def e2e_leg(ev, w, dev, args, capacity):

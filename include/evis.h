@@ -197,6 +197,38 @@ evis_status evis_capture(evis_ctx *ctx, int64_t dt_ns);
  * captured dt_ns, as one graph launch.  Asynchronous. */
 evis_status evis_replay(evis_ctx *ctx);
 
+/* Differentiable soft event counts of one keyframe gap.  The paper has no backward pass;
+ * this surrogate keeps the event path's discrete decisions frozen (z-buffer winners,
+ * holes, and the reference trajectory L_ref^(i) of Eq. 4 with C_on = C_off = C) and makes
+ * the rest smooth.  Per direction and sub-frame, the value at a target is the bilinear
+ * splat of L normalised over the winner surface: footprint sources whose interpolated
+ * depth is <= Z* (1 + delta), Z* the winning depth.  The two directions are blended as in
+ * the event path, and the counts are
+ *   N_on  = sum_i sig((L_i - L_ref^(i-1) - C) / tau),
+ *   N_off = sum_i sig((L_ref^(i-1) - L_i - C) / tau)
+ * over the sub-frames with a sample.  envs gives width, height and K (other fields are
+ * ignored); inputs are device arrays in the packed layout (log-intensity L_A, L_B, motion
+ * vectors, depth, start-of-gap reference levels Lref0) and C [n_envs]; counts is
+ * [2][H][W] per environment at offset 2 * pix_off.  The workspace (device, at least
+ * evis_soft_workspace_size bytes) keeps what the backward needs; the forward is
+ * deterministic.  Asynchronous on stream. */
+evis_status evis_soft_workspace_size(const evis_env_desc *envs, int32_t n_envs, int64_t *bytes);
+evis_status evis_soft_forward(const evis_env_desc *envs, int32_t n_envs, float tau, float delta,
+                              const float *L_A, const float *L_B, const float *mv_A,
+                              const float *mv_B, const float *Z_A, const float *Z_B,
+                              const float *Lref0, const float *C, float *counts,
+                              void *workspace, int64_t workspace_bytes, evis_stream_t stream);
+
+/* Gradients of sum(gcounts * counts) with respect to L_A, L_B, mv_A, mv_B (packed like the
+ * inputs) and C [n_envs], from the workspace of the forward call with the same inputs
+ * (overwritten, not accumulated).  Gather form: no atomics except one per block for dC. */
+evis_status evis_soft_backward(const evis_env_desc *envs, int32_t n_envs, float tau, float delta,
+                               const float *L_A, const float *L_B, const float *mv_A,
+                               const float *mv_B, const float *Z_A, const float *Z_B,
+                               const float *C, const float *gcounts, float *dL_A, float *dL_B,
+                               float *dmv_A, float *dmv_B, float *dC, void *workspace,
+                               int64_t workspace_bytes, evis_stream_t stream);
+
 /* Per-kernel timing for profiling.  With max_steps > 0, each following evis_step (or
  * evis_step_host / evis_step_trace) records CUDA events on the context's stream around its
  * two phases, for at most max_steps steps; max_steps = 0 disables and forgets the records.

@@ -483,7 +483,8 @@ void soft_env(int W, int H, int K, float Cf, double Cd, double tau, float delta,
               if (!(zt <= zstar * (1.0f + delta))) continue;
               const double ex = qxd - cx, ey = qyd - cy;  // tent weights and their slopes
               const double wxd = 1.0 - std::fabs(ex), wyd = 1.0 - std::fabs(ey);
-              const double sx = ex > 0 ? -1.0 : 1.0, sy = ey > 0 ? -1.0 : 1.0;
+              // slope on the cell's own side at an exact kink (target on the cell)
+              const double sx = ex >= 0 ? -1.0 : 1.0, sy = ey >= 0 ? -1.0 : 1.0;
               visit(p, t, wxd * wyd, sx * wyd * s, sy * wxd * s);
             }
         }

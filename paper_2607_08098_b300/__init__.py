@@ -68,6 +68,13 @@ _SIGS = {
     "evis_input_buffers": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "evis_capture": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "evis_replay": (ctypes.c_int, [ctypes.c_void_p]),
+    "evis_soft_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "evis_soft_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                         ctypes.c_float] + [ctypes.c_void_p] * 10 +
+                          [ctypes.c_int64, ctypes.c_void_p]),
+    "evis_soft_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.c_float] + [ctypes.c_void_p] * 14 +
+                           [ctypes.c_int64, ctypes.c_void_p]),
     "evis_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "evis_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p]),
@@ -335,3 +342,78 @@ def log_intensity(x, mode: int = IN_LUM, eps: float = 1e-4):
 def sort_events(ev: np.ndarray) -> np.ndarray:
     """Order (env, t, y, x, p): the buffer order is arbitrary, this one is canonical."""
     return ev[np.lexsort((ev["p"], ev["x"], ev["y"], ev["t"], ev["env"]))]
+
+
+def _descs(envs):
+    arr = (EnvDesc * len(envs))()
+    for i, e in enumerate(envs):
+        arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), 0.2, 0.2, None, None, 0, 0)
+    return arr
+
+
+def soft_workspace_bytes(envs) -> int:
+    n = ctypes.c_int64()
+    arr = _descs(envs)
+    _check(lib().evis_soft_workspace_size(ctypes.addressof(arr), len(envs), ctypes.byref(n)))
+    return n.value
+
+
+def _soft_forward(envs, tau, delta, LA, LB, mvA, mvB, ZA, ZB, Lref0, C, ws=None):
+    import torch
+    arr = _descs(envs)
+    if ws is None:
+        ws = torch.empty(soft_workspace_bytes(envs), dtype=torch.uint8, device=LA.device)
+    counts = torch.empty(2 * LA.numel(), dtype=torch.float32, device=LA.device)
+    _check(lib().evis_soft_forward(ctypes.addressof(arr), len(envs), float(tau), float(delta),
+                                   *[_ptr(t) for t in (LA, LB, mvA, mvB, ZA, ZB, Lref0, C, counts,
+                                                        ws)],
+                                   ws.numel(), torch.cuda.current_stream().cuda_stream))
+    return counts, ws
+
+
+def _soft_backward(envs, tau, delta, LA, LB, mvA, mvB, ZA, ZB, C, ws, gcounts):
+    import torch
+    arr = _descs(envs)
+    out = [torch.empty_like(LA), torch.empty_like(LB), torch.empty_like(mvA),
+           torch.empty_like(mvB), torch.empty_like(C)]
+    _check(lib().evis_soft_backward(ctypes.addressof(arr), len(envs), float(tau), float(delta),
+                                    *[_ptr(t) for t in (LA, LB, mvA, mvB, ZA, ZB, C,
+                                                         gcounts.contiguous(), *out, ws)],
+                                    ws.numel(), torch.cuda.current_stream().cuda_stream))
+    return out
+
+
+def _make_soft_function():
+    import torch
+
+    class SoftEventCount(torch.autograd.Function):
+        """Soft ON/OFF event counts of one keyframe gap (include/evis.h, evis_soft_forward),
+        differentiable in L_A, L_B, mv_A, mv_B and C; depth and Lref0 are constants."""
+
+        @staticmethod
+        def forward(ctx, LA, LB, mvA, mvB, ZA, ZB, Lref0, C, envs, tau, delta):
+            ts = [t.contiguous().float() for t in (LA, LB, mvA, mvB, ZA, ZB, Lref0, C)]
+            counts, ws = _soft_forward(envs, tau, delta, *ts)
+            ctx.save_for_backward(*ts[:6], ts[7], ws)
+            ctx.envs, ctx.tau, ctx.delta = envs, tau, delta
+            return counts
+
+        @staticmethod
+        def backward(ctx, gcounts):
+            LA, LB, mvA, mvB, ZA, ZB, C, ws = ctx.saved_tensors
+            dLA, dLB, dmvA, dmvB, dC = _soft_backward(ctx.envs, ctx.tau, ctx.delta, LA, LB, mvA,
+                                                      mvB, ZA, ZB, C, ws, gcounts.float())
+            return dLA, dLB, dmvA, dmvB, None, None, None, dC, None, None, None
+
+    return SoftEventCount
+
+
+_soft_fn = None
+
+
+def soft_event_counts(LA, LB, mvA, mvB, ZA, ZB, Lref0, C, envs, tau=0.02, delta=1e-3):
+    """Differentiable soft event counts (packed [2][H][W] per environment) of one gap."""
+    global _soft_fn
+    if _soft_fn is None:
+        _soft_fn = _make_soft_function()
+    return _soft_fn.apply(LA, LB, mvA, mvB, ZA, ZB, Lref0, C, envs, tau, delta)

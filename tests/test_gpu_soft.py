@@ -1,0 +1,153 @@
+"""Differentiable soft event counts on the GPU against the binary64 oracle (needs a B300).
+
+The surrogate's decisions are the event path's (bit-exact winners), so the GPU's binary32
+counts and gradients are compared with the oracle's binary64 ones at 1e-3 relative, on a
+32x32 crop and on sampled environments of the 16 x 346x260 workload; central differences
+(h = 1e-3, fourth-order stencil, decisions frozen by the deterministic forward) check the
+GPU backward directly."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TAU, DELTA = 0.02, 1e-3
+
+
+@pytest.fixture(scope="module")
+def ev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_08098_b300 import build
+    build.build()
+    import paper_2607_08098_b300 as m
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).cuda()
+
+
+def _crop(scenes_mod, W=32, H=32, K=8, seed=7, sigma=0.5):
+    rng = np.random.default_rng(seed)
+    lay = scenes_mod._random_layers(rng, W, H, 3, vmax=4.0, wmax=0.05)
+    for l in lay:
+        l.sigma = sigma
+    es = scenes_mod.EnvScene(W=W, H=H, K=K, c_on=0.2, c_off=0.2, layers=lay)
+    return es, [scenes_mod.render([es], k) for k in range(2)]
+
+
+def _inputs(kf):
+    return kf[0].L, kf[1].L, kf[0].mv, kf[1].mv, kf[0].Z, kf[1].Z
+
+
+def _close(got, want, rtol=1e-3):
+    got, want = np.asarray(got, np.float64), np.asarray(want, np.float64)
+    scale = np.abs(want).max()
+    err = np.abs(got - want)
+    assert np.all(err <= rtol * (np.abs(want) + 0.1 * scale) + 1e-6), \
+        (err.max(), scale, np.argmax(err))
+
+
+def test_soft_matches_fp64_oracle_on_crop(ev, oracle_mod, scenes_mod):
+    es, kf = _crop(scenes_mod)
+    envs = [es]
+    LA, LB, mvA, mvB, ZA, ZB = _inputs(kf)
+    C = np.array([0.2], np.float32)
+    gc = np.random.default_rng(1).normal(size=2 * es.W * es.H)
+    want, gw = oracle_mod.soft_counts(envs, TAU, DELTA, LA, LB, mvA, mvB, ZA, ZB, LA, C, gcounts=gc)
+    d = [_dev(a) for a in (LA, LB, mvA, mvB, ZA, ZB, LA, C)]
+    for t in (d[0], d[1], d[2], d[3], d[7]):
+        t.requires_grad_(True)
+    counts = ev.soft_event_counts(*d, envs, TAU, DELTA)
+    _close(counts.detach().cpu().numpy(), want)
+    (counts * torch.from_numpy(gc).float().cuda()).sum().backward()
+    _close(d[0].grad.cpu().numpy(), gw["LA"])
+    _close(d[1].grad.cpu().numpy(), gw["LB"])
+    _close(d[2].grad.cpu().numpy(), gw["mvA"])
+    _close(d[3].grad.cpu().numpy(), gw["mvB"])
+    _close(d[7].grad.cpu().numpy(), gw["C"])
+    assert np.abs(gw["mvA"]).max() > 0 and np.abs(gw["mvB"]).max() > 0
+
+
+def test_soft_gpu_central_differences(ev, scenes_mod):
+    es, kf = _crop(scenes_mod, seed=9)
+    envs = [es]
+    LA, LB, mvA, mvB, ZA, ZB = [_dev(a) for a in _inputs(kf)]
+    C = _dev(np.array([0.2]))
+    gc = torch.from_numpy(np.random.default_rng(2).normal(size=2 * es.W * es.H)).float().cuda()
+    gc64 = gc.double().cpu().numpy()
+
+    def loss(LA_, LB_, mvA_, mvB_, C_):
+        counts, _ = ev._soft_forward(envs, TAU, DELTA, LA_, LB_, mvA_, mvB_, ZA, ZB, LA, C_)
+        return float(gc64 @ counts.double().cpu().numpy())
+
+    counts, ws = ev._soft_forward(envs, TAU, DELTA, LA, LB, mvA, mvB, ZA, ZB, LA, C)
+    grads = ev._soft_backward(envs, TAU, DELTA, LA, LB, mvA, mvB, ZA, ZB, C, ws, gc)
+    names = ["LA", "LB", "mvA", "mvB", "C"]
+    base = [LA, LB, mvA, mvB, C]
+    h = 1e-3
+    yy, xx = np.mgrid[0:es.H, 0:es.W]
+
+    def fd_safe(mv, sign_scale):
+        """Motion entries whose targets stay > 4h|s| from an integer at every sub-frame."""
+        m = mv.cpu().numpy().astype(np.float64).reshape(-1, 2)
+        ok = np.ones(m.shape, dtype=bool)
+        for i in range(1, es.K + 1):
+            sc = sign_scale(i / es.K)
+            if sc == 0:
+                continue
+            for c, b in ((0, xx.ravel()), (1, yy.ravel())):
+                fr = np.mod(b + sc * m[:, c], 1.0)
+                ok[:, c] &= (fr > 4 * h * abs(sc) + 1e-4) & (fr < 1 - 4 * h * abs(sc) - 1e-4)
+        return ok.ravel()
+
+    safe = {"mvA": fd_safe(mvA, lambda f: -f), "mvB": fd_safe(mvB, lambda f: 1 - f)}
+    rng = np.random.default_rng(3)
+    checked = 0
+    for k, name in enumerate(names):
+        g = grads[k].cpu().numpy()
+        cand = np.abs(g) >= 0.3 * np.abs(g).max()
+        if name in safe:
+            cand &= safe[name]
+        big = np.nonzero(cand)[0]
+        for idx in rng.choice(big, min(6, big.size), replace=False):
+            def at(step):
+                args = [t.clone() for t in base]
+                args[k][idx] += step
+                return loss(*args)
+            fd = (-at(2 * h) + 8 * at(h) - 8 * at(-h) + at(-2 * h)) / (12 * h)
+            assert abs(fd - g[idx]) <= 1e-3 * abs(g[idx]) + 1e-5, (name, idx, fd, g[idx])
+            checked += 1
+    assert checked >= 12
+
+
+def test_soft_workload_16x346x260(ev, oracle_mod, scenes_mod):
+    """The differentiable workload: 16 envs at 346x260, K=8, tau=0.02, a random cotangent;
+    deterministic forward, finite gradients, and sampled environments against the oracle."""
+    w = scenes_mod.config5()
+    kf = [scenes_mod.render(w.envs, k) for k in range(2)]
+    LA, LB, mvA, mvB, ZA, ZB = _inputs(kf)
+    C = np.full(len(w.envs), 0.2, np.float32)
+    d = [_dev(a) for a in (LA, LB, mvA, mvB, ZA, ZB, LA, C)]
+    c1, ws = ev._soft_forward(w.envs, TAU, DELTA, *d)
+    c2, _ = ev._soft_forward(w.envs, TAU, DELTA, *d)
+    assert torch.equal(c1, c2)
+    gc = torch.from_numpy(np.random.default_rng(5).normal(size=c1.numel())).float().cuda()
+    grads = ev._soft_backward(w.envs, TAU, DELTA, *d[:6], d[7], ws, gc)
+    for g in grads:
+        assert torch.isfinite(g).all()
+    off, _ = scenes_mod.pixel_offsets(w.envs)
+    for e in (0, 11):
+        env, o = w.envs[e], int(off[e])
+        n = env.W * env.H
+        sl = lambda a, k=1: a[k * o:k * (o + n)]  # noqa: E731
+        gce = gc.cpu().numpy()[2 * o:2 * o + 2 * n]
+        want, gw = oracle_mod.soft_counts([env], TAU, DELTA, sl(LA), sl(LB), sl(mvA.reshape(-1), 2),
+                                          sl(mvB.reshape(-1), 2), sl(ZA), sl(ZB), sl(LA),
+                                          C[e:e + 1], gcounts=gce)
+        _close(c1.cpu().numpy()[2 * o:2 * o + 2 * n], want)
+        _close(grads[0].cpu().numpy()[o:o + n], gw["LA"])
+        _close(grads[3].cpu().numpy()[2 * o:2 * (o + n)], gw["mvB"])
+        _close(grads[4].cpu().numpy()[e:e + 1], gw["C"])
