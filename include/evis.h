@@ -199,15 +199,16 @@ evis_status evis_replay(evis_ctx *ctx);
 
 /* Differentiable soft event counts of one keyframe gap.  The paper has no backward pass;
  * this surrogate keeps the event path's discrete decisions frozen (z-buffer winners,
- * holes, and the reference trajectory L_ref^(i) of Eq. 4 with C_on = C_off = C) and makes
- * the rest smooth.  Per direction and sub-frame, the value at a target is the bilinear
+ * holes, and the reference trajectory L_ref^(i) of Eq. 4 with each environment's c_on and
+ * c_off) and makes the rest smooth.  Per direction and sub-frame, the value at a target is the bilinear
  * splat of L normalised over the winner surface: footprint sources whose interpolated
  * depth is <= Z* (1 + delta), Z* the winning depth.  The two directions are blended as in
  * the event path, and the counts are
  *   N_on  = sum_i sig((L_i - L_ref^(i-1) - C) / tau),
  *   N_off = sum_i sig((L_ref^(i-1) - L_i - C) / tau)
- * over the sub-frames with a sample.  envs gives width, height and K (other fields are
- * ignored); inputs are device arrays in the packed layout (log-intensity L_A, L_B, motion
+ * over the sub-frames with a sample; C [n_envs] is the differentiable threshold and
+ * enters only the sigmoids.  envs gives width, height, K and the event thresholds c_on,
+ * c_off of the frozen trajectory (other fields are ignored); inputs are device arrays in the packed layout (log-intensity L_A, L_B, motion
  * vectors, depth, start-of-gap reference levels Lref0) and C [n_envs]; counts is
  * [2][H][W] per environment at offset 2 * pix_off.  The workspace (device, at least
  * evis_soft_workspace_size bytes) keeps what the backward needs; the forward is

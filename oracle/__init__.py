@@ -150,7 +150,9 @@ def sort_events(ev: np.ndarray) -> np.ndarray:
 def soft_counts(envs, tau, delta, LA, LB, mvA, mvB, ZA, ZB, Lref0, C, smooth=None, gcounts=None):
     """Soft event-count surrogate of one keyframe gap (binary64).
 
-    Decisions come from the binary32 inputs; ``smooth`` optionally overrides the values the
+    Decisions come from the binary32 inputs and each env's c_on / c_off (the frozen reference
+    trajectory); ``C`` is the smooth threshold of the sigmoids.  ``smooth`` optionally overrides
+    the values the
     smooth part uses (dict with keys LA, LB, mvA, mvB, C as float64), which is how finite
     differences keep the decisions frozen.  Returns counts (packed [2][H][W] per env) and,
     with ``gcounts``, the gradients dict (LA, LB, mvA, mvB, C)."""
@@ -158,19 +160,18 @@ def soft_counts(envs, tau, delta, LA, LB, mvA, mvB, ZA, ZB, Lref0, C, smooth=Non
     if not hasattr(lib, "_soft_sig"):
         lib.orc_soft.restype = ctypes.c_int32
         lib.orc_soft.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_float] + \
-            [ctypes.c_void_p] * 20
+            [ctypes.c_void_p] * 19
         lib._soft_sig = True
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32).reshape(-1)  # noqa: E731
     f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)  # noqa: E731
     dec = [f32(a) for a in (LA, LB, mvA, mvB, ZA, ZB, Lref0)]
-    Cf = f32(C)
     sm = smooth or {}
     sLA, sLB = f64(sm.get("LA", dec[0])), f64(sm.get("LB", dec[1]))
     smA, smB = f64(sm.get("mvA", dec[2])), f64(sm.get("mvB", dec[3]))
-    sC = f64(sm.get("C", Cf))
+    sC = f64(sm.get("C", f32(C)))
     arr = (_Env * len(envs))()
     for i, e in enumerate(envs):
-        arr[i] = _Env(e.W, e.H, e.K, 0.2, 0.2, None, None, 0, 0)
+        arr[i] = _Env(e.W, e.H, e.K, e.c_on, e.c_off, None, None, 0, 0)
     n = dec[0].size
     counts = np.zeros(2 * n, dtype=np.float64)
     grads = None
@@ -181,7 +182,7 @@ def soft_counts(envs, tau, delta, LA, LB, mvA, mvB, ZA, ZB, Lref0, C, smooth=Non
                  "mvB": np.zeros(2 * n), "C": np.zeros(len(envs))}
         gp = [grads[k].ctypes.data for k in ("LA", "LB", "mvA", "mvB", "C")]
     lib.orc_soft(ctypes.addressof(arr), len(envs), float(tau), float(delta),
-                 *[a.ctypes.data for a in dec], Cf.ctypes.data, sLA.ctypes.data, sLB.ctypes.data,
+                 *[a.ctypes.data for a in dec], sLA.ctypes.data, sLB.ctypes.data,
                  smA.ctypes.data, smB.ctypes.data, sC.ctypes.data, counts.ctypes.data,
                  None if gcounts is None else gcounts.ctypes.data, *gp)
     return (counts, grads) if gcounts is not None else counts

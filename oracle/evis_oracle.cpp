@@ -401,7 +401,8 @@ void orc_log_intensity(const float* in, int64_t n, int32_t mode, float eps, floa
 // backward pass).  Definition, per environment, per sub-frame i and warp direction X:
 //  * discrete decisions, frozen and taken in binary32 exactly as in the event path: the
 //    z-buffer winners (Eqs. 5-7), hole flags, and the reference-level trajectory L_ref^(i)
-//    of the event model (Eq. 4) with C_on = C_off = C;
+//    of the event model (Eq. 4) with the environment's thresholds c_on, c_off (the smooth
+//    threshold C below enters only the sigmoids);
 //  * the winner surface W_X(t): footprint sources p of target t whose interpolated depth is
 //    within a relative delta of the winning depth, Z~(p) <= Z* (1 + delta) (binary32 test);
 //  * soft value S_X(t) = sum_W w(p,t) L_X(p) / sum_W w(p,t), w the bilinear weight of q(p)
@@ -423,7 +424,7 @@ inline double sigm(double u) { return 1.0 / (1.0 + std::exp(-u)); }
 
 // One environment, one keyframe gap.  counts: [2][H][W]; grads (optional): dL*, dmv* packed
 // like the inputs, dC scalar.
-void soft_env(int W, int H, int K, float Cf, double Cd, double tau, float delta,
+void soft_env(int W, int H, int K, float Con, float Coff, double Cd, double tau, float delta,
               const SoftIn &in, double *counts, const double *gcounts, double *gLA, double *gLB,
               double *gmvA, double *gmvB, double *gC) {
   const size_t HW = static_cast<size_t>(W) * H;
@@ -523,10 +524,11 @@ void soft_env(int W, int H, int K, float Cf, double Cd, double tau, float delta,
       const float L = (hA && hB) ? g * la + f * lb : (hA ? la : lb);
       const float dd = L - Lref[t];
       const int pol = dd > 0.0f ? 1 : -1;
-      const float q = std::fabs(dd) / Cf;
+      const float th = pol > 0 ? Con : Coff;
+      const float q = std::fabs(dd) / th;
       int n = 0;
       if (q >= 1.0f) n = q >= static_cast<float>(MAX_CROSSINGS) ? MAX_CROSSINGS : static_cast<int>(std::floor(q));
-      if (n > 0) Lref[t] = Lref[t] + static_cast<float>(pol * n) * Cf;
+      if (n > 0) Lref[t] = Lref[t] + static_cast<float>(pol * n) * th;
     }
     if (gcounts) {
       for (int d = 0; d < 2; ++d) {
@@ -553,7 +555,7 @@ extern "C" {
 // gcounts non-null, also accumulates the gradients (arrays zeroed by the caller).
 int32_t orc_soft(const orc_env *envs, int32_t n_envs, double tau, float delta,
                  const float *LA, const float *LB, const float *mvA, const float *mvB,
-                 const float *ZA, const float *ZB, const float *Lref0, const float *Cf,
+                 const float *ZA, const float *ZB, const float *Lref0,
                  const double *dLA, const double *dLB, const double *dmvA, const double *dmvB,
                  const double *Cd, double *counts, const double *gcounts, double *gLA,
                  double *gLB, double *gmvA, double *gmvB, double *gC) {
@@ -562,7 +564,7 @@ int32_t orc_soft(const orc_env *envs, int32_t n_envs, double tau, float delta,
     const int W = envs[e].width, H = envs[e].height;
     SoftIn in{LA + off, LB + off, mvA + 2 * off, mvB + 2 * off, ZA + off, ZB + off, Lref0 + off,
               dLA + off, dLB + off, dmvA + 2 * off, dmvB + 2 * off};
-    soft_env(W, H, envs[e].K, Cf[e], Cd[e], tau, delta, in, counts + 2 * off,
+    soft_env(W, H, envs[e].K, envs[e].c_on, envs[e].c_off, Cd[e], tau, delta, in, counts + 2 * off,
              gcounts ? gcounts + 2 * off : nullptr, gLA ? gLA + off : nullptr,
              gLB ? gLB + off : nullptr, gmvA ? gmvA + 2 * off : nullptr,
              gmvB ? gmvB + 2 * off : nullptr, gC ? gC + e : nullptr);

@@ -347,7 +347,8 @@ def sort_events(ev: np.ndarray) -> np.ndarray:
 def _descs(envs):
     arr = (EnvDesc * len(envs))()
     for i, e in enumerate(envs):
-        arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), 0.2, 0.2, None, None, 0, 0)
+        arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), float(e.c_on), float(e.c_off), None, None,
+                         0, 0)
     return arr
 
 

@@ -2,7 +2,8 @@
 // backward).  The paper has no backward pass; the surrogate keeps the event path's discrete
 // decisions frozen and makes the rest smooth:
 //   * z-buffer winners (Eqs. 5-7), hole flags and the reference trajectory L_ref^(i) of the
-//     event model (Eq. 4, C_on = C_off = C) are taken exactly as in the event path;
+//     event model (Eq. 4 with the environment's c_on / c_off) are taken exactly as in the
+//     event path; the differentiable threshold C enters only the sigmoids;
 //   * per direction X, sub-frame i and target t, the winner surface W_X(t) holds the
 //     footprint sources whose interpolated depth is <= Z*(t) (1 + delta);
 //   * S_X(t) = sum_W w L_X / sum_W w with w the bilinear weight of the source's target q;
@@ -26,7 +27,9 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr int kMaxN = 4096;
 
 struct SoftEnv {
-  int32_t W, H, K, pad;
+  int32_t W, H, K;
+  float c_on, c_off;  // thresholds of the frozen discrete trajectory (the event model's)
+  int32_t pad;
   int64_t pix_off;  // packed pixel offset
   int64_t uo;       // first pixel-substep (i = 1) of this environment
 };
@@ -45,7 +48,9 @@ Layout layout_for(const evis_env_desc *envs, int n, std::vector<SoftEnv> *tab) {
   if (tab) tab->resize(n);
   for (int e = 0; e < n; ++e) {
     const int64_t hw = int64_t(envs[e].width) * envs[e].height;
-    if (tab) (*tab)[e] = SoftEnv{envs[e].width, envs[e].height, envs[e].K, 0, px, u};
+    if (tab)
+      (*tab)[e] = SoftEnv{envs[e].width, envs[e].height, envs[e].K, envs[e].c_on, envs[e].c_off, 0,
+                          px, u};
     px += (hw + 3) / 4 * 4;
     u += hw * envs[e].K;
   }
@@ -256,10 +261,11 @@ __global__ void soft_targets(const SoftArgs a) {
     const float L = (hA && hB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb)) : (hA ? la : lb);
     const float d = __fsub_rn(L, Lref);
     const int pol = d > 0.0f ? 1 : -1;
-    const float qn = __fdiv_rn(fabsf(d), C);
+    const float th = pol > 0 ? E.c_on : E.c_off;
+    const float qn = __fdiv_rn(fabsf(d), th);
     int n = 0;
     if (qn >= 1.0f) n = qn >= static_cast<float>(kMaxN) ? kMaxN : static_cast<int>(floorf(qn));
-    if (n > 0) Lref = __fadd_rn(Lref, __fmul_rn(static_cast<float>(pol * n), C));
+    if (n > 0) Lref = __fadd_rn(Lref, __fmul_rn(static_cast<float>(pol * n), th));
   }
   a.counts[2 * o + pix] = non;
   a.counts[2 * o + HW + pix] = noff;
@@ -344,7 +350,8 @@ evis_status soft_prepare(const evis_env_desc *envs, int32_t n, void *ws, int64_t
   for (int e = 0; e < n; ++e) {
     const evis_env_desc &d = envs[e];
     if (d.width < 1 || d.height < 1 || d.width > 65535 || d.height > 65535 ||
-        int64_t(d.width) * d.height > (int64_t(1) << 24) || d.K < 1 || d.K > 4096)
+        int64_t(d.width) * d.height > (int64_t(1) << 24) || d.K < 1 || d.K > 4096 ||
+        !(d.c_on > 0.0f && d.c_on < INFINITY) || !(d.c_off > 0.0f && d.c_off < INFINITY))
       return EVIS_ERR_INVALID_ARG;
     *max_hw = std::max(*max_hw, d.width * d.height);
   }
