@@ -482,10 +482,12 @@ void soft_env(int W, int H, int K, float Con, float Coff, double Cd, double tau,
               float zstar;
               std::memcpy(&zstar, &zbits, 4);
               if (!(zt <= zstar * (1.0f + delta))) continue;
-              const double ex = qxd - cx, ey = qyd - cy;  // tent weights and their slopes
-              const double wxd = 1.0 - std::fabs(ex), wyd = 1.0 - std::fabs(ey);
-              // slope on the cell's own side at an exact kink (target on the cell)
-              const double sx = ex >= 0 ? -1.0 : 1.0, sy = ey >= 0 ? -1.0 : 1.0;
+              // the footprint side of each cell is a frozen decision: the weight is the
+              // bilinear factor on that side (1 - e for the left/top cell, 1 + e for the
+              // right/bottom one), linear in the binary64 target
+              const double ex = qxd - cx, ey = qyd - cy;
+              const double wxd = dx ? 1.0 + ex : 1.0 - ex, wyd = dy ? 1.0 + ey : 1.0 - ey;
+              const double sx = dx ? 1.0 : -1.0, sy = dy ? 1.0 : -1.0;
               visit(p, t, wxd * wyd, sx * wyd * s, sy * wxd * s);
             }
         }
