@@ -24,6 +24,8 @@
 //                sub-frame and a coalesced 16-byte-per-thread flush.
 #include <cfloat>
 
+#include <cuda_fp16.h>
+
 #include "evis_device.cuh"
 #include "evis_internal.h"
 
@@ -197,9 +199,10 @@ template <int TX, int TY>
 struct StepSmem {
   unsigned long long zb[2][TX * TY];       // z-buffers, A forward and B backward
   ulonglong2 stage[kEventStage];           // events of this sub-frame before the flush
-  float4 cand_b[2][kCandidates];           // candidate segments' motion bounds
+  uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
+                                           // (min dx, max dx), (min dy, max dy) rounded outward
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
-  unsigned hit[2][2 * kCandidates];        // candidates reaching the tile, by sub-frame parity
+  unsigned short hit[2][2 * kCandidates];  // candidates reaching the tile, by sub-frame parity
   int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
   unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
 };
@@ -208,7 +211,7 @@ struct StepSmem {
 // sets the register budget.
 template <int TX, int TY>
 constexpr int step_min_blocks() {
-  return TX * TY <= 512 ? 4 : (TX * TY <= 1024 ? 3 : 2);
+  return TX * TY <= 512 ? 5 : (TX * TY <= 1024 ? 4 : 3);
 }
 
 // All K sub-frames of one target tile (the body of step_kernel).
@@ -315,7 +318,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       const int pos = atomicAdd(&s_nc[dir], 1);
       if (pos < kCandidates) {
         S.cand_xy[dir][pos] = (static_cast<unsigned>(cy) << 16) | static_cast<unsigned>(cx);
-        S.cand_b[dir][pos] = b;
+        // outward rounding keeps the bounds conservative (overflow goes to +-inf)
+        const __half2 bx = __halves2half2(__float2half_rd(b.x), __float2half_ru(b.y));
+        const __half2 by = __halves2half2(__float2half_rd(b.z), __float2half_ru(b.w));
+        S.cand_b[dir][pos] = make_uint2(*reinterpret_cast<const unsigned *>(&bx),
+                                        *reinterpret_cast<const unsigned *>(&by));
       } else {
         s_over = 1;
       }
@@ -351,7 +358,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         if (c < nAB) {
           const int dir = c >= nA ? 1 : 0;
           const int idx = c - dir * nA;
-          const float4 b = S.cand_b[dir][idx];
+          const uint2 hb = S.cand_b[dir][idx];
+          const float2 bx = __half22float2(*reinterpret_cast<const __half2 *>(&hb.x));
+          const float2 by = __half22float2(*reinterpret_cast<const __half2 *>(&hb.y));
+          const float4 b = make_float4(bx.x, bx.y, by.x, by.y);
           const unsigned xy = S.cand_xy[dir][idx];
           float dxl, dxh, dyl, dyh;
           if (dir == 0) {
@@ -368,7 +378,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           unsigned base = 0;
           if (lane == 0) base = atomicAdd(&s_nhit[par], static_cast<unsigned>(__popc(m)));
           base = __shfl_sync(kFull, base, 0);
-          if (hit) S.hit[par][base + __popc(m & lanes_below)] = static_cast<unsigned>(c);
+          if (hit) S.hit[par][base + __popc(m & lanes_below)] = static_cast<unsigned short>(c);
         }
       }
     }
