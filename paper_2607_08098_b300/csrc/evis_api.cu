@@ -385,7 +385,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     ko += int64_t(d.K) * 2 * px;
     lo += int64_t(d.K) * px;
   }
-  c->env_tw.assign(n_envs, 64);
+  c->env_tw.assign(n_envs, 32);
   c->env_th.assign(n_envs, 16);
 
   cudaError_t e = cudaGetDevice(&c->device);

@@ -211,7 +211,7 @@ struct StepSmem {
 // sets the register budget.
 template <int TX, int TY>
 constexpr int step_min_blocks() {
-  return TX * TY <= 512 ? 5 : (TX * TY <= 1024 ? 4 : 3);
+  return TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3);
 }
 
 // All K sub-frames of one target tile (the body of step_kernel).
