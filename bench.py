@@ -183,6 +183,20 @@ def reference_arm(args, world, rank):
 # the CUDA path
 # ------------------------------------------------------------------------------------------
 
+def reduce_over_ranks(total_ms, units, events, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time and the units and
+    events summed over ranks (timing only; ranks exchange no data of the path)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms), float(units), float(events)], device=device,
+                     dtype=torch.float64)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -275,13 +289,8 @@ def evis_arm(args, world, rank, local):
 
     total_units = w.pixel_substeps * args.steps
     if dist:
-        t = torch.tensor([total_ms, float(total_units), float(n_events)], device="cuda",
-                         dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_ms, total_units, n_events = float(mx[0]), float(sm[1]), float(sm[2])
+        total_ms, total_units, n_events = reduce_over_ranks(total_ms, total_units, n_events,
+                                                            "cuda")
     value = total_units / (total_ms / 1e3) / 1e6
     events_per_s = n_events / (total_ms / 1e3)
 

@@ -273,13 +273,19 @@ def config3(n_envs: int = 256, scale: float = 1.0) -> Workload:
 
 
 def config4(n_envs: int = 1024, W: int = 640, H: int = 480) -> Workload:
-    """High-speed: 640x480, K=32, flows up to 40 px/frame, five depth layers, C=0.15."""
+    """High-speed: 640x480, K=32, flows up to 40 px/frame, five depth layers, C=0.15.
+
+    Disks of radius 0.2-0.4 x 480 moving up to 40 px/frame leave about 10 % of the
+    pixel-substeps without a source in one warp direction (disocclusion holes); textures are
+    smoother (64 px cells, sigma 0.3) so that the output stays event-dense but bounded
+    (about 0.11 events per pixel-substep)."""
     envs = []
     for e in range(n_envs):
         rng = _rng(4, e)
-        envs.append(EnvScene(W=W, H=H, K=32, c_on=0.15, c_off=0.15,
-                             layers=_random_layers(rng, W, H, 5, vmax=40.0, wmax=0.1,
-                                                   rmin=0.1, rmax=0.25)))
+        lay = _random_layers(rng, W, H, 5, vmax=40.0, wmax=0.1, rmin=0.2, rmax=0.4)
+        for layer in lay:
+            layer.sigma, layer.cell = 0.3, 64.0
+        envs.append(EnvScene(W=W, H=H, K=32, c_on=0.15, c_off=0.15, layers=lay))
     return Workload(f"{n_envs} envs at {W}x{H}, K=32, C=0.15, 5 layers, flow<=40px", envs,
                     8_000_000, 4)
 

@@ -355,3 +355,29 @@ def test_determinism(ev, scenes_mod):
             ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
         outs.append(ev.sort_events(ctx.read_events()))
     np.testing.assert_array_equal(outs[0].view(np.uint8), outs[1].view(np.uint8))
+
+
+def test_high_speed_full_size_sampled(ev, oracle_mod, scenes_mod):
+    """High-speed workload at full per-environment size (640x480, K=32, C=0.15, flows up to
+    40 px/frame, ~10 % holes), 8 environments on the GPU, two of them against the oracle."""
+    w = scenes_mod.config4(n_envs=8)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    ctx = ev.Context(w.envs, flags=ev.IN_LOG, capacity=1 << 26)
+    for kf in kfs:
+        ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+    eg = ctx.read_events()
+    Lref, _, clk = ctx.state()
+    sample = [0, 5]
+    o, off, soff = _subset(ev, oracle_mod, w.envs, kfs, w.dt_ns, sample)
+    eo = oracle_mod.sort_events(o.events())
+    so = o.state()
+    for j, i in enumerate(sample):
+        mine = eg[eg["env"] == i].copy()
+        mine["env"] = j
+        mine = ev.sort_events(mine)
+        theirs = eo[eo["env"] == j]
+        assert len(mine) == len(theirs) > 10000
+        np.testing.assert_array_equal(mine.view(np.uint8), theirs.view(np.uint8))
+        n = w.envs[i].H * w.envs[i].W
+        np.testing.assert_array_equal(Lref[off[i]:off[i] + n], so[0][soff[j]:soff[j] + n])
+        assert clk[i] == so[2][j]

@@ -1,0 +1,45 @@
+"""The weak-scaling path of bench.py on two gloo ranks (CPU): environments are sharded by
+seed with no data exchange, and only the timing is reduced (max time, summed work)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    w = bench.workload(4, rank)
+    seeds = [l.seed for e in w.envs for l in e.layers]
+    t, units, events = bench.reduce_over_ranks(10.0 + rank, 1000 * (rank + 1), 7, "cpu")
+    q.put((rank, seeds, t, units, events))
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharding_and_reduction():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, s0, t0, u0, e0), (r1, s1, t1, u1, e1) = out
+    assert not set(s0) & set(s1)                # disjoint scenes per rank
+    assert t0 == t1 == 11.0                     # slowest rank's time
+    assert u0 == u1 == 3000 and e0 == e1 == 14  # work summed over ranks

@@ -524,3 +524,18 @@ def test_refractory_boundary_is_inclusive(oracle_mod):
     env2 = TinyEnv(W=4, H=1, K=K, c_on=C, c_off=C, refractory_ns=tau + 1)
     o2, _ = _run(oracle_mod, [env2], [L0, L1], [mv, mv], [z, z], dt)
     assert list(oracle_mod.sort_events(o2.events())["t"]) == [tau, 3 * tau]
+
+
+def test_high_speed_scenes_have_disocclusion_holes(oracle_mod, scenes_mod):
+    """The high-speed workload (640x480, K=32, flows up to 40 px/frame) must leave >= 10 % of
+    the pixel-substeps without a source in at least one warp direction, on average."""
+    w = scenes_mod.config4(n_envs=3)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(2)]
+    o = oracle_mod.Oracle(w.envs, flags=oracle_mod.IN_LOG)
+    o.step(kfs[0].L, kfs[0].mv, kfs[0].Z, w.dt_ns)
+    keys, _ = o.step(kfs[1].L, kfs[1].mv, kfs[1].Z, w.dt_ns, trace=True)
+    fr = []
+    for k, _ in split_trace(w.envs, keys, np.zeros(sum(e.K * e.H * e.W for e in w.envs), np.float32)):
+        fr.append(((k[:, 0] == EMPTY) | (k[:, 1] == EMPTY)).mean())
+    assert np.mean(fr) >= 0.10, fr
+    assert np.abs(kfs[1].mv).max() >= 30
