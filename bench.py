@@ -87,7 +87,7 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "--format=csv,noheader,nounits", "-lms", "20",
                                        "-i", str(device_index)], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
@@ -252,6 +252,7 @@ def evis_arm(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    clocks = ClockSampler(local)                    # sampled from the warm-up on (under load)
     ctx.step(*dev[0], w.dt_ns)                      # first keyframe: reference levels only
     tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=2)  # tile shape per resolution class
     shapes = ctx.tile_shapes()
@@ -265,7 +266,6 @@ def evis_arm(args, world, rank, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
     wall0 = time.perf_counter()
     for s in range(args.steps):
         flush.zero_()                               # L2 flush between timed steps
@@ -308,6 +308,15 @@ def evis_arm(args, world, rank, local):
                 "traffic": None if tr is None else tr["dram_bytes_per_launch_scaled"],
                 "kernel_ms": syn_ms, "prep_ms": prep_ms,
                 "tile_shape": f"{shapes[0][0]}x{shapes[0][1]} (autotuned, {tuned_ms:.2f} ms in the trial)"}
+    if tr is not None and "warp_instructions_per_launch_scaled" in tr and world == 1:
+        # the kernel's real ceiling: instruction issue (4 schedulers per SM, one warp
+        # instruction per clock each, at the maximum SM clock)
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak_issue = sms * 4 * 2.032e9
+        ach = tr["warp_instructions_per_launch_scaled"] / (syn_ms / 1e3)
+        roofline["issue"] = {"bound": "instruction issue", "achieved_warp_inst_per_s": ach,
+                             "peak_warp_inst_per_s": peak_issue, "frac": ach / peak_issue,
+                             "source": "ncu smsp__inst_executed.sum of the committed capture"}
 
     e2e = None
     if args.e2e_steps > 0:
