@@ -68,6 +68,9 @@ typedef struct {
  * or B primary with A filling only B's holes (Sec. 3.3). */
 #define EVIS_MODE_BLEND 0x0u
 #define EVIS_MODE_B_PRIMARY 0x10u
+/* Eq. 6 read literally: one argmin of interpolated depth over both directions' winners
+ * (equal depths go to B); not combinable with EVIS_MODE_B_PRIMARY. */
+#define EVIS_MODE_JOINT 0x40u
 /* z-buffer tie-break among equal depths: larger bilinear weight then lower source index
  * (default), or lower source index only. */
 #define EVIS_TIE_WEIGHT 0x0u
@@ -89,7 +92,7 @@ typedef struct {
 
 typedef struct {
   float eps;              /* added before the log (Sec. 3.2), finite and >= 0 */
-  uint32_t flags;         /* EVIS_IN_* | EVIS_MODE_* | EVIS_TIE_* | EVIS_KEEP_INPUTS */
+  uint32_t flags;         /* EVIS_IN_* | EVIS_MODE_* (one) | EVIS_TIE_* | EVIS_KEEP_INPUTS */
   int64_t event_capacity; /* events the device buffer holds between two reads, >= 1 */
 } evis_config;
 

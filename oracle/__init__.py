@@ -23,6 +23,7 @@ _lib = None
 IN_LOG, IN_LUM, IN_RGB = 0, 1, 2
 MODE_B_PRIMARY = 0x10
 TIE_INDEX = 0x20
+MODE_JOINT = 0x40
 
 EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2"), ("p", "<i2")])
 

@@ -26,6 +26,7 @@ namespace {
 // Flag bits of the oracle's configuration word (same numeric meaning as the library's).
 constexpr uint32_t IN_MASK = 0x3u, IN_LOG = 0u, IN_LUM = 1u, IN_RGB = 2u;
 constexpr uint32_t MODE_B_PRIMARY = 0x10u;  // Sec. 3.3: B primary, A only fills B's holes
+constexpr uint32_t MODE_JOINT = 0x40u;      // Eq. 6: one argmin of depth over both directions
 constexpr uint32_t TIE_INDEX = 0x20u;       // key = (depth, source index), no weight field
 
 constexpr uint64_t EMPTY = ~0ull;
@@ -217,6 +218,7 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
   const int64_t T0 = c.clock[e];
   const bool tie_index = (c.flags & TIE_INDEX) != 0;
   const bool b_primary = (c.flags & MODE_B_PRIMARY) != 0;
+  const bool joint = (c.flags & MODE_JOINT) != 0;
 
   std::vector<float> Lprev(LA, LA + HW);
   std::vector<int64_t> tprev(HW, T0);
@@ -240,7 +242,13 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
         float la = hasA ? LA[zA[t] & 0xFFFFFFu] : 0.0f;
         float lb = hasB ? LB[zB[t] & 0xFFFFFFu] : 0.0f;
         float L;
-        if (b_primary) {  // Sec. 3.3: backward-warped B is primary, A fills B's holes
+        if (joint) {      // Eq. 6: the nearer of the two winners; equal depths go to B
+          const uint32_t za = static_cast<uint32_t>(zA[t] >> 32), zb2 = static_cast<uint32_t>(zB[t] >> 32);
+          if (hasA && hasB) L = za < zb2 ? la : lb;
+          else if (hasA) L = la;
+          else if (hasB) L = lb;
+          else L = NAN;
+        } else if (b_primary) {  // Sec. 3.3: backward-warped B is primary, A fills B's holes
           if (hasB) L = lb;
           else if (hasA) L = la;
           else L = NAN;
@@ -295,6 +303,7 @@ typedef struct {
 void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags) {
   if (!envs || n_envs <= 0 || n_envs > 65536 || !(eps >= 0.0f)) return nullptr;
   if ((flags & IN_MASK) == 3u) return nullptr;
+  if ((flags & MODE_JOINT) && (flags & MODE_B_PRIMARY)) return nullptr;
   Ctx* c = new Ctx();
   c->eps = eps;
   c->flags = flags;

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libevis.so")
 
 IN_LOG, IN_LUM, IN_RGB = 0x0, 0x1, 0x2
-MODE_BLEND, MODE_B_PRIMARY = 0x0, 0x10
+MODE_BLEND, MODE_B_PRIMARY, MODE_JOINT = 0x0, 0x10, 0x40
 TIE_WEIGHT, TIE_INDEX = 0x0, 0x20
 KEEP_INPUTS = 0x100
 

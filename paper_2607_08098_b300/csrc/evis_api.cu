@@ -98,8 +98,10 @@ std::string validate(const evis_env_desc *envs, int32_t n, const evis_config *cf
   if (!cfg) return "cfg is null";
   if (n < 1 || n > 65535) return "n_envs must be in 1..65535";
   if (!std::isfinite(cfg->eps) || cfg->eps < 0.0f) return "eps must be finite and >= 0";
-  const uint32_t known = 0x3u | EVIS_MODE_B_PRIMARY | EVIS_TIE_INDEX | EVIS_KEEP_INPUTS;
+  const uint32_t known = 0x3u | EVIS_MODE_B_PRIMARY | EVIS_MODE_JOINT | EVIS_TIE_INDEX | EVIS_KEEP_INPUTS;
   if (cfg->flags & ~known) return "unknown flag bits";
+  if ((cfg->flags & EVIS_MODE_B_PRIMARY) && (cfg->flags & EVIS_MODE_JOINT))
+    return "EVIS_MODE_B_PRIMARY and EVIS_MODE_JOINT exclude each other";
   if ((cfg->flags & 0x3u) == 0x3u) return "invalid input mode";
   if (cfg->event_capacity < 1 || cfg->event_capacity > (int64_t(1) << 40))
     return "event_capacity must be in 1..2^40";

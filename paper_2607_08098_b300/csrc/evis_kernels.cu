@@ -236,6 +236,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const unsigned lanes_below = (1u << lane) - 1u;
   const float lane_f = small_int_to_float(lane);
   const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
+  const bool joint = (a.flags & EVIS_MODE_JOINT) != 0;
   const int64_t T0 = a.clock_in[tl.env];
   const int64_t refr = E.refractory_ns;
   const int tx = tl.x0 + tid % TX;
@@ -436,7 +437,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
         const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
         const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
-        if (b_primary) {
+        if (joint) {  // Eq. 6: the nearer winner; equal depths go to B
+          L = (hasA && hasB) ? ((kA >> 32) < (kB >> 32) ? la : lb)
+                             : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+        } else if (b_primary) {
           L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
         } else {
           L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))

@@ -69,7 +69,7 @@ def test_create_rejects_bad_descriptors_before_cuda(evis, bad):
     assert L.evis_last_error(None).decode() != ""
 
 
-@pytest.mark.parametrize("cfg", [(-1.0, 0, 10), (float("nan"), 0, 10), (1e-4, 0x3, 10),
+@pytest.mark.parametrize("cfg", [(-1.0, 0, 10), (float("nan"), 0, 10), (1e-4, 0x3, 10), (1e-4, 0x50, 10),
                                  (1e-4, 0x8000, 10), (1e-4, 0, 0), (1e-4, 0, 1 << 41)])
 def test_create_rejects_bad_config(evis, cfg):
     L = evis.lib()

@@ -125,9 +125,9 @@ def test_long_keyframe_gap_timestamps(ev, oracle_mod, scenes_mod):
     run_both(ev, oracle_mod, envs, kfs, 3_000_000_001, trace_steps=(1,))
 
 
-@pytest.mark.parametrize("flags", [0x10, 0x20, 0x30, 0x100, 0x110])
+@pytest.mark.parametrize("flags", [0x10, 0x20, 0x30, 0x40, 0x60, 0x100, 0x110])
 def test_modes(ev, oracle_mod, scenes_mod, flags):
-    """B-primary blend, index-only tie-break and in-place (kept) inputs."""
+    """B-primary blend, joint argmin, index-only tie-break and in-place (kept) inputs."""
     envs = _ragged_envs(scenes_mod)[:2] + _ragged_envs(scenes_mod)[5:]
     kfs = [scenes_mod.render(envs, k) for k in range(3)]
     run_both(ev, oracle_mod, envs, kfs, 16_666_667, flags=flags, trace_steps=(1, 2))

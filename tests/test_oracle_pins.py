@@ -539,3 +539,41 @@ def test_high_speed_scenes_have_disocclusion_holes(oracle_mod, scenes_mod):
         fr.append(((k[:, 0] == EMPTY) | (k[:, 1] == EMPTY)).mean())
     assert np.mean(fr) >= 0.10, fr
     assert np.abs(kfs[1].mv).max() >= 30
+
+
+def test_joint_mode_takes_the_nearer_surface(oracle_mod, scenes_mod):
+    """Eq. 6 read literally: one argmin of interpolated depth over the A-forward and
+    B-backward winners (equal depths go to B).  A disk passing in front of a plane: the value
+    is always one of the two winners' values, the nearer one where they disagree, and it
+    differs from the B-primary reading somewhere (where A's winner is the nearer one)."""
+    W, H, K = 40, 24, 4
+    plane = scenes_mod.Layer(kind=0, depth0=5.0, cx0=20, cy0=12, vx=1.0, tex_kind=1, mu=0.0)
+    # an off-centre spinning disk: reusing m_A as a velocity is only a linear approximation of
+    # the rotation, so the two directions disagree near its rim
+    disk = scenes_mod.Layer(kind=1, radius=8.0, depth0=2.0, cx0=16, cy0=12, vx=2.0,
+                            omega=0.6, tex_kind=1, mu=1.0)
+    es = scenes_mod.EnvScene(W=W, H=H, K=K, c_on=0.3, c_off=0.3, layers=[plane, disk])
+    kf = [scenes_mod.render([es], k) for k in range(2)]
+    outs = {}
+    for name, flags in (("joint", oracle_mod.MODE_JOINT), ("bprim", oracle_mod.MODE_B_PRIMARY)):
+        o = oracle_mod.Oracle([es], flags=flags)
+        o.step(kf[0].L, kf[0].mv, kf[0].Z, 1000)
+        outs[name] = split_trace([es], *o.step(kf[1].L, kf[1].mv, kf[1].Z, 1000, trace=True))[0]
+    keys, lint = outs["joint"]
+    LA, LB = kf[0].L, kf[1].L
+    differs = 0
+    for i in range(K):
+        kA, kB = keys[i, 0].ravel(), keys[i, 1].ravel()
+        both = (kA != EMPTY) & (kB != EMPTY)
+        la = LA[(kA[both] & np.uint64(0xFFFFFF)).astype(np.int64)]
+        lb = LB[(kB[both] & np.uint64(0xFFFFFF)).astype(np.int64)]
+        zA, zB = kA[both] >> np.uint64(32), kB[both] >> np.uint64(32)   # positive: bits order = value order
+        got = lint[i].ravel()[both]
+        assert np.all((got == la) | (got == lb))
+        np.testing.assert_array_equal(got[la == lb], la[la == lb])
+        dis = la != lb
+        np.testing.assert_array_equal(got[dis], np.where(zA[dis] < zB[dis], la[dis], lb[dis]))
+        differs += int((lint[i] != outs["bprim"][1][i]).sum())
+    assert differs > 0
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle([es], flags=oracle_mod.MODE_JOINT | oracle_mod.MODE_B_PRIMARY)
