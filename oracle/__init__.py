@@ -35,6 +35,21 @@ class _Env(ctypes.Structure):
                 ("refractory_ns", ctypes.c_int64), ("t0_ns", ctypes.c_int64)]
 
 
+class _Noise(ctypes.Structure):
+    _fields_ = [("leak_hz", ctypes.c_float), ("shot_hz", ctypes.c_float),
+                ("hot_hz", ctypes.c_float), ("hot_fraction", ctypes.c_float),
+                ("lo", ctypes.c_float), ("hi", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+def philox(n, c1=0, c2=0, c3=0, key=(0, 0), base=0) -> np.ndarray:
+    """n outputs [n, 4] of the oracle's Philox4x32-10 at counters (base + j, c1, c2, c3)."""
+    lib = _load()
+    lib.orc_philox.argtypes = [ctypes.c_uint32] * 6 + [ctypes.c_int64, ctypes.c_void_p]
+    out = np.empty((n, 4), dtype=np.uint32)
+    lib.orc_philox(base, c1, c2, c3, key[0], key[1], n, out.ctypes.data)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (g++, host only, no FMA contraction)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
@@ -124,6 +139,22 @@ class Oracle:
         out = np.empty(n, dtype=EVENT_DTYPE)
         got = _lib.orc_take_events(self._h, _ptr(out), n)
         return out[:got]
+
+    def set_noise(self, specs):
+        """Per-environment sensor noise (Sec. 3.4): dicts with leak_hz, shot_hz, hot_hz,
+        hot_fraction, lo, hi, seed (missing keys: off / defaults)."""
+        lib = _load()
+        if not hasattr(lib, "_noise_sig"):
+            lib.orc_set_noise.restype = ctypes.c_int32
+            lib.orc_set_noise.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            lib._noise_sig = True
+        arr = (_Noise * len(self.envs))()
+        for i, sp in enumerate(specs):
+            arr[i] = _Noise(sp.get("leak_hz", 0.0), sp.get("shot_hz", 0.0), sp.get("hot_hz", 0.0),
+                            sp.get("hot_fraction", 0.0), sp.get("lo", -5.0), sp.get("hi", 5.0),
+                            int(sp.get("seed", 0)))
+        if lib.orc_set_noise(self._h, ctypes.addressof(arr)) != 0:
+            raise ValueError("oracle rejected the noise parameters")
 
     def state(self):
         Lref = np.empty(self.total, dtype=np.float32)

@@ -46,8 +46,18 @@ struct Event {  // 16 bytes: t, x, y, env, polarity
   int16_t p;
 };
 
+// Sensor non-idealities of one environment (Sec. 3.4); all rates zero = off.
+struct Noise {
+  float leak_hz, shot_hz, hot_hz;  // event rates per pixel (1/s)
+  float hot_fraction;              // probability that a pixel is hot (fixed per pixel)
+  float lo, hi;                    // log-intensity range mapped to the normalised intensity
+  uint64_t seed;
+};
+
 struct Ctx {
   std::vector<Env> envs;
+  std::vector<Noise> noise;                // per env (zeros: no noise)
+  uint32_t gap = 0;                        // keyframe gaps processed (the noise counter)
   std::vector<int64_t> off;   // packed pixel offsets (H*W rounded up to 4)
   int64_t total = 0;
   float eps = 1e-4f;
@@ -201,6 +211,63 @@ void cross_pixel(Ctx& c, int env, int x, int y, float L, float& Lref, float& Lpr
   tprev = ti;
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as 1, 2,
+// 3", SC 2011): ten rounds of two 32x32->64 multiplies, the key bumped by the Weyl
+// constants between rounds.
+void philox4x32_10(uint32_t ctr[4], uint32_t k0, uint32_t k1) {
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * ctr[0];
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * ctr[2];
+    const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+    const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+    const uint32_t n0 = hi1 ^ ctr[1] ^ k0, n2 = hi0 ^ ctr[3] ^ k1;
+    ctr[0] = n0;
+    ctr[1] = lo1;
+    ctr[2] = n2;
+    ctr[3] = lo0;
+  }
+}
+
+// Bernoulli draw with probability p from a 32-bit uniform (24 bits used, binary32 compare).
+inline bool fires(uint32_t u, float p) { return static_cast<float>(u >> 8) < p * 16777216.0f; }
+
+// Leak, shot and hot-pixel events of one pixel in sub-frame i (Sec. 3.4).  Each fires at
+// most once per sub-frame with the stated probability over the interval [t0, t1); its time
+// is uniform in the interval.  Noise events bypass the refractory filter and leave the
+// reference level untouched.  Shot noise needs the sub-frame's sample (has).
+void noise_pixel(Ctx& c, int env, int x, int y, uint32_t pix, uint32_t i, int64_t t0, int64_t t1,
+                 bool has, float L) {
+  const Noise& nz = c.noise[env];
+  if (!(nz.leak_hz > 0.0f || nz.shot_hz > 0.0f || nz.hot_hz > 0.0f)) return;
+  const uint32_t k0 = static_cast<uint32_t>(nz.seed);
+  const uint32_t k1 = static_cast<uint32_t>(nz.seed >> 32) ^ static_cast<uint32_t>(env);
+  uint32_t r[4] = {pix, c.gap, i, 0u}, rt[4] = {pix, c.gap, i, 1u}, rh[4] = {pix, 0xFFFFFFFFu, 0u, 2u};
+  philox4x32_10(r, k0, k1);
+  philox4x32_10(rt, k0, k1);
+  philox4x32_10(rh, k0, k1);
+  const int64_t d = t1 - t0;
+  const float dts = static_cast<float>(d) * 1e-9f;
+  auto at = [&](uint32_t u) {
+    return t0 + static_cast<int64_t>((static_cast<uint64_t>(u) * static_cast<uint64_t>(d)) >> 32);
+  };
+  auto emit = [&](int64_t t, int p) {
+    c.events.push_back(Event{t, static_cast<uint16_t>(x), static_cast<uint16_t>(y),
+                             static_cast<uint16_t>(env), static_cast<int16_t>(p)});
+  };
+  if (nz.leak_hz > 0.0f && fires(r[0], nz.leak_hz * dts)) emit(at(rt[0]), 1);
+  if (nz.shot_hz > 0.0f && has) {
+    float ib = (L - nz.lo) / (nz.hi - nz.lo);
+    ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
+    if (fires(r[1], nz.shot_hz * dts * (1.0f - ib))) emit(at(rt[1]), (rt[3] & 1u) ? 1 : -1);
+  }
+  if (nz.hot_hz > 0.0f && fires(rh[0], nz.hot_fraction) && fires(r[2], nz.hot_hz * dts))
+    emit(at(rt[2]), 1);
+}
+
 // One keyframe gap of one environment: K substeps f = i/K (Sec. 3.3), each a bidirectional
 // splat, a time blend with hole filling, and the event model.  Optional trace outputs:
 // keys[(i-1)*2 + dir][p] and Lint[(i-1)][p] (NaN where the pixel got no sample).
@@ -259,6 +326,8 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
           else L = NAN;
         }
         if (Lint) Lint[static_cast<size_t>(i - 1) * HW + t] = L;
+        noise_pixel(c, e, x, y, static_cast<uint32_t>(t), static_cast<uint32_t>(i),
+                    T0 + (static_cast<int64_t>(i - 1) * dt) / K, ti, hasA || hasB, L);
         if (!hasA && !hasB) continue;  // no sample this substep: the pixel holds its state
         float th_on = en.c_on, th_off = en.c_off;
         if (en.has_map) {
@@ -333,6 +402,7 @@ void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags)
       std::memcpy(c->coff.data() + c->off[i], envs[i].c_off_map, n * 4);
     }
   }
+  c->noise.assign(n_envs, Noise{0, 0, 0, 0, 0, 1, 0});
   c->Lref.assign(c->total, 0.0f);
   c->t_last.assign(c->total, NO_EVENT);
   for (int i = 0; i < n_envs; ++i) c->clock.push_back(envs[i].t0_ns);
@@ -369,10 +439,40 @@ int32_t orc_step(void* h, const float* frames, const float* mv, const float* dep
     tl += static_cast<size_t>(c.envs[e].K) * HW;
     c.clock[e] += dt_ns;
   }
+  ++c.gap;
   c.LA = LB;
   c.mvA.assign(mv, mv + 2 * c.total);
   c.ZA.assign(depth, depth + c.total);
   return 0;
+}
+
+typedef struct {
+  float leak_hz, shot_hz, hot_hz, hot_fraction, lo, hi;
+  uint64_t seed;
+} orc_noise;
+
+// Per-environment noise parameters (array of n_envs); 0 on success.
+int32_t orc_set_noise(void* h, const orc_noise* nz) {
+  Ctx& c = *static_cast<Ctx*>(h);
+  for (size_t e = 0; e < c.envs.size(); ++e) {
+    const orc_noise& n = nz[e];
+    if (!(n.leak_hz >= 0 && n.shot_hz >= 0 && n.hot_hz >= 0 && n.hot_fraction >= 0 &&
+          n.hot_fraction <= 1 && n.hi > n.lo))
+      return 1;
+    c.noise[e] = Noise{n.leak_hz, n.shot_hz, n.hot_hz, n.hot_fraction, n.lo, n.hi, n.seed};
+  }
+  return 0;
+}
+
+// The generator alone, for its tests: n outputs of Philox4x32-10 at counters
+// (base + j, c1, c2, c3), written as 4 x n words.
+void orc_philox(uint32_t base, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                int64_t n, uint32_t* out) {
+  for (int64_t j = 0; j < n; ++j) {
+    uint32_t r[4] = {base + static_cast<uint32_t>(j), c1, c2, c3};
+    philox4x32_10(r, k0, k1);
+    std::memcpy(out + 4 * j, r, 16);
+  }
 }
 
 int64_t orc_num_events(void* h) { return static_cast<int64_t>(static_cast<Ctx*>(h)->events.size()); }
