@@ -128,3 +128,28 @@ def test_noise_is_deterministic_per_seed(oracle_mod):
     assert not np.array_equal(runs[0], runs[2])
     with pytest.raises(ValueError):
         oracle_mod.Oracle([env]).set_noise([dict(hot_fraction=1.5)])
+
+
+def test_leak_fires_in_holes_and_streams_differ_per_env(oracle_mod):
+    """Leak and hot-pixel noise do not need a sample: pixels whose sources all have invalid
+    depth (holes) still leak.  Two environments with the same seed draw distinct streams."""
+    env = TinyEnv(W=48, H=32, K=8, c_on=0.2, c_off=0.2)
+    envs = [env, env]
+    n = packed_total(envs)
+    mv = np.zeros((n, 2), np.float32)
+    z = np.ones(n, np.float32)
+    z[: env.W * env.H // 2] = 0.0              # top half of env 0: invalid depth, no sample
+    L = np.zeros(n, np.float32)
+    o = oracle_mod.Oracle(envs)
+    o.set_noise([dict(leak_hz=50.0, seed=5)] * 2)
+    for _ in range(3):
+        o.step(L, mv, z, 10_000_000)
+    ev = o.events()
+    e0, e1 = ev[ev["env"] == 0], ev[ev["env"] == 1]
+    top = e0[e0["y"] < env.H // 2]
+    half = env.W * env.H // 2 * env.K * 2
+    p = 50.0 * 10_000_000 / env.K * 1e-9
+    assert abs(len(top) - half * p) < 5 * np.sqrt(half * p)
+    k0 = set(zip(e0["x"].tolist(), e0["y"].tolist(), e0["t"].tolist()))
+    k1 = set(zip(e1["x"].tolist(), e1["y"].tolist(), e1["t"].tolist()))
+    assert len(k0 & k1) < 0.05 * min(len(k0), len(k1))
