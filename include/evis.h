@@ -144,6 +144,35 @@ evis_status evis_clear_events(evis_ctx *ctx);
  * environment of the context has a refractory period; otherwise all read INT64_MIN. */
 evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t *clocks);
 
+/* Sensor non-idealities of one environment (Sec. 3.4).  The paper lists leak events, shot
+ * noise and hot pixels without fixing their distributions; this library draws each as at most
+ * one event per pixel and sub-frame [t_{i-1}, t_i), d = t_i - t_{i-1} ns, from the counter-
+ * based generator Philox4x32-10 (Salmon et al., SC 2011) keyed by (seed low 32 bits, seed
+ * high 32 bits ^ environment index), so the events do not depend on the launch shape:
+ *   leak: probability leak_hz * d * 1e-9, polarity +1, at every pixel, sample or not;
+ *   shot: probability shot_hz * d * 1e-9 * (1 - clamp((L - lo) / (hi - lo), 0, 1)), with L
+ *         the sub-frame's blended log intensity (pixels without a sample have none), random
+ *         polarity; dark pixels fire most;
+ *   hot:  a fixed subset of pixels (each with probability hot_fraction, the same in every
+ *         gap) fires with probability hot_hz * d * 1e-9, polarity +1.
+ * Counters (pixel index y * W + x, gap g, sub-frame i, stream): draws (p, g, i, 0), times
+ * and shot polarity (p, g, i, 1), hot subset (p, 2^32 - 1, 0, 2); a Bernoulli draw with
+ * probability q from word u fires when (float)(u >> 8) < q * 2^24 in binary32; an event's
+ * time is t_{i-1} + floor(u * d / 2^32).  Noise events pass no refractory filter and leave
+ * the reference levels unchanged.  g counts the keyframe gaps the context has processed. */
+typedef struct {
+  float leak_hz, shot_hz, hot_hz; /* rates per pixel (1/s), finite and >= 0; all 0 = off */
+  float hot_fraction;             /* 0..1 */
+  float lo, hi;                   /* log-intensity range of the normalised intensity, hi > lo */
+  uint64_t seed;
+} evis_noise_desc;
+
+/* Sets the noise of every environment (host array of n_envs entries; NULL turns it off
+ * everywhere).  Stream-ordered: applies from the next step.  Drops a captured graph (capture
+ * again).  EVIS_ERR_INVALID_ARG for a negative or non-finite rate, hot_fraction outside 0..1
+ * or hi <= lo, checked before anything changes. */
+evis_status evis_set_noise(evis_ctx *ctx, const evis_noise_desc *noise);
+
 /* Debug form of evis_step: also writes, for every environment in order and every
  * sub-frame i = 1..K_e, the two z-buffers (keys[((i-1)*2 + dir) * H*W + p], dir 0 = A
  * forward, dir 1 = B backward; key = depth bits << 32 | quantised (1 - weight) << 24 |

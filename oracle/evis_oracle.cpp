@@ -251,8 +251,8 @@ void noise_pixel(Ctx& c, int env, int x, int y, uint32_t pix, uint32_t i, int64_
   philox4x32_10(rh, k0, k1);
   const int64_t d = t1 - t0;
   const float dts = static_cast<float>(d) * 1e-9f;
-  auto at = [&](uint32_t u) {
-    return t0 + static_cast<int64_t>((static_cast<uint64_t>(u) * static_cast<uint64_t>(d)) >> 32);
+  auto at = [&](uint32_t u) {  // t0 + floor(u d / 2^32); d reaches 2^40, so 128-bit product
+    return t0 + static_cast<int64_t>((static_cast<unsigned __int128>(u) * static_cast<uint64_t>(d)) >> 32);
   };
   auto emit = [&](int64_t t, int p) {
     c.events.push_back(Event{t, static_cast<uint16_t>(x), static_cast<uint16_t>(y),
@@ -456,8 +456,9 @@ int32_t orc_set_noise(void* h, const orc_noise* nz) {
   Ctx& c = *static_cast<Ctx*>(h);
   for (size_t e = 0; e < c.envs.size(); ++e) {
     const orc_noise& n = nz[e];
-    if (!(n.leak_hz >= 0 && n.shot_hz >= 0 && n.hot_hz >= 0 && n.hot_fraction >= 0 &&
-          n.hot_fraction <= 1 && n.hi > n.lo))
+    auto rate = [](float v) { return std::isfinite(v) && v >= 0.0f; };
+    if (!(rate(n.leak_hz) && rate(n.shot_hz) && rate(n.hot_hz) && n.hot_fraction >= 0 &&
+          n.hot_fraction <= 1 && std::isfinite(n.lo) && std::isfinite(n.hi) && n.hi > n.lo))
       return 1;
     c.noise[e] = Noise{n.leak_hz, n.shot_hz, n.hot_hz, n.hot_fraction, n.lo, n.hi, n.seed};
   }

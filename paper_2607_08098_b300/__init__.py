@@ -37,6 +37,12 @@ class Config(ctypes.Structure):
                 ("event_capacity", ctypes.c_int64)]
 
 
+class NoiseDesc(ctypes.Structure):
+    _fields_ = [("leak_hz", ctypes.c_float), ("shot_hz", ctypes.c_float),
+                ("hot_hz", ctypes.c_float), ("hot_fraction", ctypes.c_float),
+                ("lo", ctypes.c_float), ("hi", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 class EvisError(RuntimeError):
     def __init__(self, status: int, msg: str = ""):
         self.status = status
@@ -60,6 +66,7 @@ _SIGS = {
     "evis_get_state": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_set_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "evis_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "evis_set_env_tile_shapes": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "evis_get_tile_shapes": (ctypes.c_int, [ctypes.c_void_p] * 3),
@@ -255,6 +262,21 @@ class Context:
         cnt = ctypes.c_void_p()
         _check(lib().evis_events_device(self._h, ctypes.byref(ev), ctypes.byref(cnt)), self._h)
         return ev.value, cnt.value
+
+    def set_noise(self, specs):
+        """Sensor noise per environment (Sec. 3.4): a list of dicts with leak_hz, shot_hz,
+        hot_hz, hot_fraction, lo, hi, seed (missing keys off / defaults), or None for off."""
+        if specs is None:
+            _check(lib().evis_set_noise(self._h, None), self._h)
+            return
+        if len(specs) != len(self.envs):
+            raise ValueError("one noise spec per environment")
+        arr = (NoiseDesc * len(specs))()
+        for i, sp in enumerate(specs):
+            arr[i] = NoiseDesc(sp.get("leak_hz", 0.0), sp.get("shot_hz", 0.0), sp.get("hot_hz", 0.0),
+                               sp.get("hot_fraction", 0.0), sp.get("lo", -5.0), sp.get("hi", 5.0),
+                               int(sp.get("seed", 0)))
+        _check(lib().evis_set_noise(self._h, ctypes.addressof(arr)), self._h)
 
     TILE_SHAPES = ((32, 16), (32, 32), (64, 16), (64, 32), (128, 16))
 

@@ -37,6 +37,8 @@ struct evis_ctx {
   int grid_cap = 1;        // persistent launches: one wave of resident CTAs per group
   bool any_refr = false;
 
+  std::vector<DevEnv> h_envs;  // host copy of d_envs (noise parameters change it)
+  bool any_noise = false;
   DevEnv *d_envs = nullptr;
   Tile *d_tiles = nullptr;
   unsigned *d_work = nullptr;  // per-group work counters, zeroed every step
@@ -49,6 +51,7 @@ struct evis_ctx {
   float4 *d_seg[2] = {nullptr, nullptr};  // per keyframe slot: row-segment motion bounds
   float4 *d_pack[2] = {nullptr, nullptr}; // per-source packs of A and B for the current gap
   int64_t *d_clock = nullptr;  // [2][n]
+  uint32_t *d_gap = nullptr;   // [2][n]: keyframe gaps processed, alternating like d_clock
   ulonglong2 *d_events = nullptr;
   unsigned long long *d_count = nullptr;
   int64_t *d_tr_off = nullptr; // [2][n]: key offsets, then L offsets
@@ -261,6 +264,9 @@ evis::StepArgs step_args(const evis_ctx *c, const KeyframeB &B, int64_t dt) {
   s.tlast = c->d_tlast;
   s.clock_in = c->d_clock + c->clk * c->n;
   s.clock_out = c->d_clock + (c->clk ^ 1) * c->n;
+  s.gap_in = c->d_gap + c->clk * c->n;
+  s.gap_out = c->d_gap + (c->clk ^ 1) * c->n;
+  s.noise = c->any_noise;
   s.flowA = c->d_flow + c->slot * c->n;
   s.flowB = c->d_flow + b * c->n;
   s.segA = c->d_seg[c->slot];
@@ -411,6 +417,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   for (int s = 0; s < 2; ++s)
     if ((e = dalloc(c, &c->d_pack[s], c->total)) != cudaSuccess) return bail(e, "alloc source packs");
   if ((e = dalloc(c, &c->d_clock, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc clock");
+  if ((e = dalloc(c, &c->d_gap, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc gap counters");
   if ((e = dalloc(c, &c->d_events, cfg->event_capacity)) != cudaSuccess) return bail(e, "alloc events");
   if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");
   if ((e = dalloc(c, &c->d_tr_off, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc trace offsets");
@@ -428,6 +435,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
       (e = cudaMemcpyAsync(c->d_clock, clocks.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(c->d_tr_off, troff.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s)) ||
+      (e = cudaMemsetAsync(c->d_gap, 0, sizeof(uint32_t) * 2 * n_envs, s)) ||
       (e = cudaMemsetAsync(c->d_flow, 0, sizeof(float) * 2 * n_envs, s)))
     return bail(e, "upload tables");
   if (c->d_tlast) {
@@ -436,6 +444,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "create sync");
   if ((e = rebuild_groups(c)) != cudaSuccess) return bail(e, "upload tiles");
+  c->h_envs = std::move(denv);
   *out = c;
   return EVIS_OK;
 }
@@ -542,6 +551,44 @@ evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float 
     return EVIS_ERR_INVALID_ARG;
   cudaError_t e = evis::launch_log(in, n, mode, eps, out, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
+}
+
+evis_status evis_set_noise(evis_ctx *c, const evis_noise_desc *nz) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  auto rate = [](float v) { return std::isfinite(v) && v >= 0.0f; };
+  for (int i = 0; nz && i < c->n; ++i) {
+    const evis_noise_desc &d = nz[i];
+    if (!rate(d.leak_hz) || !rate(d.shot_hz) || !rate(d.hot_hz))
+      return fail(c, EVIS_ERR_INVALID_ARG, "noise rates must be finite and >= 0");
+    if (!(d.hot_fraction >= 0.0f && d.hot_fraction <= 1.0f))
+      return fail(c, EVIS_ERR_INVALID_ARG, "hot_fraction must be in 0..1");
+    if (!std::isfinite(d.lo) || !std::isfinite(d.hi) || !(d.hi > d.lo))
+      return fail(c, EVIS_ERR_INVALID_ARG, "noise range needs finite lo < hi");
+  }
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  drop_graphs(c);
+  bool any = false;
+  for (int i = 0; i < c->n; ++i) {
+    DevEnv &v = c->h_envs[i];
+    const evis_noise_desc d = nz ? nz[i] : evis_noise_desc{0, 0, 0, 0, 0, 1, 0};
+    v.leak_hz = d.leak_hz;
+    v.shot_hz = d.shot_hz;
+    v.hot_hz = d.hot_hz;
+    v.hot_fraction = d.hot_fraction;
+    v.noise_lo = d.lo;
+    v.noise_hi = d.hi;
+    v.key0 = static_cast<uint32_t>(d.seed);
+    v.key1 = static_cast<uint32_t>(d.seed >> 32) ^ static_cast<uint32_t>(i);
+    v.noise = (d.leak_hz > 0.0f || d.shot_hz > 0.0f || d.hot_hz > 0.0f) ? 1 : 0;
+    any |= v.noise != 0;
+  }
+  // pageable source: the call returns once the table is staged, so h_envs may change after
+  if ((e = cudaMemcpyAsync(c->d_envs, c->h_envs.data(), sizeof(DevEnv) * c->n,
+                           cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "upload noise parameters");
+  c->any_noise = any;
+  return EVIS_OK;
 }
 
 evis_status evis_set_tile_shape(evis_ctx *c, int32_t tile_w, int32_t tile_h) {

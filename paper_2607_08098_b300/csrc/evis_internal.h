@@ -27,6 +27,12 @@ struct DevEnv {
   float c_on, c_off;
   const float *con_map, *coff_map;   // this environment's maps (device) or null
   int64_t refractory_ns;
+  // sensor noise (Sec. 3.4); noise == 0 turns it off for this environment
+  float leak_hz, shot_hz, hot_hz;   // event rates per pixel (1/s)
+  float hot_fraction;               // probability that a pixel is hot
+  float noise_lo, noise_hi;         // log-intensity range of the normalised intensity
+  uint32_t key0, key1;              // Philox key: seed low word, seed high word ^ env
+  int32_t noise, pad1;
 };
 
 // One target tile: environment and top-left pixel.
@@ -47,6 +53,8 @@ struct StepArgs {
   int64_t *tlast;            // null when no environment has a refractory period
   const int64_t *clock_in;
   int64_t *clock_out;
+  const uint32_t *gap_in;    // per environment: keyframe gaps done (the noise counter), or null
+  uint32_t *gap_out;
   const float *flowA, *flowB;
   const float4 *segA, *segB;   // per row segment: (min dx, max dx, min dy, max dy)
   const float4 *packA, *packB; // per source: (mx, my, Z, Z at the other endpoint), or null
@@ -55,6 +63,7 @@ struct StepArgs {
   unsigned long long capacity;
   int64_t dt;
   uint32_t flags;
+  bool noise;                // some environment of the launch has noise on (needs gap_in)
   uint64_t *tr_keys;         // debug trace (null in the production path)
   float *tr_L;
   const int64_t *tr_koff, *tr_loff;

@@ -194,6 +194,33 @@ __device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int en
   return r;
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC 2011): ten rounds, each two 32 x 32 -> 64-bit products of the counter's even words
+// mixed into the odd words with the round key; the key advances by the Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Bernoulli draw with probability q from a 32-bit uniform word (24 bits, binary32 compare).
+__device__ __forceinline__ bool fires(unsigned u, float q) {
+  return __uint2float_rn(u >> 8) < __fmul_rn(q, 16777216.0f);
+}
+
+// t0 + floor(u d / 2^32) for d < 2^41: the product split at bit 32 of d.
+__device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d) {
+  const unsigned long long du = static_cast<unsigned long long>(d);
+  const unsigned long long lo = (static_cast<unsigned long long>(u) * (du & 0xFFFFFFFFull)) >> 32;
+  return t0 + static_cast<int64_t>(static_cast<unsigned long long>(u) * (du >> 32) + lo);
+}
+
 // Dynamic shared memory of one step CTA.
 template <int TX, int TY>
 struct StepSmem {
@@ -214,8 +241,39 @@ constexpr int step_min_blocks() {
   return TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3);
 }
 
-// All K sub-frames of one target tile (the body of step_kernel).
-template <int TX, int TY, bool TRACE, bool PACKED>
+// Stages the records of the warp's lanes that have emit set (the warp is converged): one
+// shared-memory reservation per warp; past the stage's capacity, one global reservation.
+template <int TX, int TY>
+__device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, const StepArgs &a,
+                                           bool emit, const ulonglong2 &rec, unsigned lanes_below,
+                                           int lane) {
+  const unsigned m = __ballot_sync(kFull, emit);
+  if (m == 0) return;
+  const unsigned cnt = static_cast<unsigned>(__popc(m));
+  unsigned base = 0;
+  unsigned long long gb = 0;
+  if (lane == 0) {
+    base = atomicAdd(s_n, cnt);
+    if (base + cnt > static_cast<unsigned>(kEventStage))
+      gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
+                                     base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+  }
+  base = __shfl_sync(kFull, base, 0);
+  gb = __shfl_sync(kFull, gb, 0);
+  if (emit) {
+    const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
+    if (idx < static_cast<unsigned>(kEventStage)) {
+      S.stage[idx] = rec;
+    } else {
+      const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
+      if (gi < a.capacity) a.events[gi] = rec;
+    }
+  }
+}
+
+// All K sub-frames of one target tile (the body of step_kernel).  NOISE compiles the sensor
+// noise of Sec. 3.4 in (environments with it off skip it at run time).
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
 __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NT = TX * TY / kThreads;   // targets per thread
   constexpr int NW = kThreads / 32;
@@ -336,10 +394,24 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   // t_i = T0 + floor(i dt / K), stepped with a quotient and a remainder
   const int64_t dq = a.dt / K, dr = a.dt % K;
   int64_t tq = 0, trem = 0;
+  // noise: this gap's counter and the hot pixels among this thread's targets (bit j)
+  const bool noisy = NOISE && E.noise != 0;
+  const unsigned gap = noisy ? a.gap_in[tl.env] : 0u;
+  unsigned hot = 0;
+  if (noisy && E.hot_hz > 0.0f) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const unsigned pix = static_cast<unsigned>((ty0 + ROWS * j) * W + tx);
+      if (act[j] && fires(philox4x32_10(make_uint4(pix, 0xFFFFFFFFu, 0u, 2u), E.key0, E.key1).x,
+                          E.hot_fraction))
+        hot |= 1u << j;
+    }
+  }
 
   for (int i = 1; i <= K; ++i) {
     const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
     const float g = __fsub_rn(1.0f, f);
+    const int64_t tim1 = T0 + tq;  // t_{i-1}
     tq += dq;
     trem += dr;
     if (trem >= K) {
@@ -544,6 +616,34 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         }
         __syncwarp();  // the next chunk reuses this warp's refractory scratch
       }
+      if (noisy) {  // leak, shot and hot-pixel events of this target (Sec. 3.4)
+        const int64_t d = ti - tim1;
+        const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
+        const unsigned npix = static_cast<unsigned>(pix);
+        bool fl = false, fs = false, fh = false;
+        if (act[j]) {
+          const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 0u), E.key0, E.key1);
+          fl = E.leak_hz > 0.0f && fires(r.x, __fmul_rn(E.leak_hz, dts));
+          if (E.shot_hz > 0.0f && has) {
+            float ib = __fdiv_rn(__fsub_rn(L, E.noise_lo), __fsub_rn(E.noise_hi, E.noise_lo));
+            ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
+            fs = fires(r.y, __fmul_rn(__fmul_rn(E.shot_hz, dts), __fsub_rn(1.0f, ib)));
+          }
+          fh = ((hot >> j) & 1u) && fires(r.z, __fmul_rn(E.hot_hz, dts));
+        }
+        if (__any_sync(kFull, fl || fs || fh)) {
+          uint4 rt = make_uint4(0u, 0u, 0u, 0u);
+          if (fl || fs || fh)
+            rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u), E.key0, E.key1);
+          stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), tx, ty, tl.env, 1),
+                     lanes_below, lane);
+          stage_warp(S, &s_n, a, fs,
+                     make_event(noise_time(rt.y, tim1, d), tx, ty, tl.env, (rt.w & 1u) ? 1 : -1),
+                     lanes_below, lane);
+          stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), tx, ty, tl.env, 1),
+                     lanes_below, lane);
+        }
+      }
       if (has) {
         if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(pol > 0 ? nf : -nf, th));
         Lprev[j] = L;
@@ -582,17 +682,20 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     a.Lref[o + pix] = Lref[j];
     if (a.tlast) a.tlast[o + pix] = tlast[j];
   }
-  if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) a.clock_out[tl.env] = T0 + a.dt;
+  if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) {
+    a.clock_out[tl.env] = T0 + a.dt;
+    if (a.gap_out) a.gap_out[tl.env] = a.gap_in[tl.env] + 1u;
+  }
 }
 
 // One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
 // first one by block index, the next ones from a work counter that starts at 0.
-template <int TX, int TY, bool TRACE, bool PACKED>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
 __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
   __shared__ int s_tile;
   int t = blockIdx.x;
   while (t < a.n_tiles) {
-    run_tile<TX, TY, TRACE, PACKED>(a, a.tiles[t]);
+    run_tile<TX, TY, TRACE, PACKED, NOISE>(a, a.tiles[t]);
     __syncthreads();  // the tile's shared memory is free again
     if (threadIdx.x == 0) s_tile = static_cast<int>(gridDim.x + atomicAdd(a.work_counter, 1u));
     __syncthreads();
@@ -716,12 +819,12 @@ cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, flo
   return cudaGetLastError();
 }
 
-template <int TX, int TY, bool TRACE, bool PACKED>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
   static int resident = 0;  // CTAs per SM x SMs, looked up once per instantiation
   const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
   if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -729,13 +832,13 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, step_kernel<TX, TY, TRACE, PACKED>, kThreads, smem)) != cudaSuccess)
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE>, kThreads, smem)) != cudaSuccess)
       return e;
     resident = max(1, per_sm) * sms;
   }
   int grid = n_tiles;
   if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
-  step_kernel<TX, TY, TRACE, PACKED><<<grid, kThreads, smem, s>>>(a);
+  step_kernel<TX, TY, TRACE, PACKED, NOISE><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -749,13 +852,16 @@ cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, i
   const int n_tiles = a.n_tiles;
   if (n_tiles <= 0) return cudaSuccess;
   if (!a.packA) {  // unpacked sources: 64x16 tiles only
-    if (tile_w != 64 || tile_h != 16 || trace) return cudaErrorInvalidValue;
-    return launch_shape<64, 16, false, false>(a, n_tiles, grid_cap, s);
+    if (tile_w != 64 || tile_h != 16 || trace || a.noise) return cudaErrorInvalidValue;
+    return launch_shape<64, 16, false, false, false>(a, n_tiles, grid_cap, s);
   }
+  if (a.noise && !a.gap_in) return cudaErrorInvalidValue;
+  // the trace variant always carries the noise code; the production one only when asked
 #define EVIS_SHAPE(TX, TY)                                                               \
   if (tile_w == TX && tile_h == TY)                                                      \
-    return trace ? launch_shape<TX, TY, true, true>(a, n_tiles, grid_cap, s)             \
-                 : launch_shape<TX, TY, false, true>(a, n_tiles, grid_cap, s);
+    return trace ? launch_shape<TX, TY, true, true, true>(a, n_tiles, grid_cap, s)       \
+                 : (a.noise ? launch_shape<TX, TY, false, true, true>(a, n_tiles, grid_cap, s) \
+                            : launch_shape<TX, TY, false, true, false>(a, n_tiles, grid_cap, s));
   EVIS_SHAPE(32, 16)
   EVIS_SHAPE(32, 32)
   EVIS_SHAPE(64, 16)

@@ -38,13 +38,16 @@ def _frames(kf, mode):
 
 
 def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), capacity=1 << 22,
-             check_state=True, tile=None):
+             check_state=True, tile=None, noise=None):
     """Feed the same keyframes to the oracle and the library; compare everything."""
     mode = flags & 0x3
     o = oracle_mod.Oracle(envs, eps=eps, flags=flags & 0xFF)
     ctx = ev.Context(envs, eps=eps, flags=flags, capacity=capacity)
     if tile is not None:
         ctx.set_tile_shape(*tile)
+    if noise is not None:
+        o.set_noise(noise)
+        ctx.set_noise(noise)
     alive = []  # keeps inputs alive for EVIS_KEEP_INPUTS
     for s, kf in enumerate(kfs):
         fr = _frames(kf, mode)
@@ -298,13 +301,18 @@ def test_overflow_reports_total_and_keeps_state(ev, oracle_mod, scenes_mod):
     assert ctx.event_count() == len(o.events())
 
 
-def _subset(ev, oracle_mod, envs, kfs, dt, sample, flags=0):
-    """Oracle on a sample of environments (re-packed), for comparison with a full-size run."""
+def _subset(ev, oracle_mod, envs, kfs, dt, sample, flags=0, noise=None):
+    """Oracle on a sample of environments (re-packed), for comparison with a full-size run.
+    Noise seeds are remapped so that sampled environment j draws environment i's stream
+    (the generator's key mixes the environment index into the seed's high word)."""
     import scenes
     sub = [envs[i] for i in sample]
     off, _ = scenes.pixel_offsets(envs)
     soff, stotal = scenes.pixel_offsets(sub)
     o = oracle_mod.Oracle(sub, flags=flags)
+    if noise is not None:
+        o.set_noise([dict(noise[i], seed=int(noise[i].get("seed", 0)) ^ ((i ^ j) << 32))
+                     for j, i in enumerate(sample)])
     for kf in kfs:
         L = np.zeros(stotal, np.float32)
         mv = np.zeros((stotal, 2), np.float32)
@@ -381,3 +389,111 @@ def test_high_speed_full_size_sampled(ev, oracle_mod, scenes_mod):
         n = w.envs[i].H * w.envs[i].W
         np.testing.assert_array_equal(Lref[off[i]:off[i] + n], so[0][soff[j]:soff[j] + n])
         assert clk[i] == so[2][j]
+
+
+def _noise_specs(n):
+    """All three noise sources at rates that fire often, one environment without noise, and
+    environments sharing a seed (their streams still differ by the environment index)."""
+    out = []
+    for i in range(n):
+        if i == 1:
+            out.append({})
+        else:
+            out.append(dict(leak_hz=40.0 + 10.0 * i, shot_hz=80.0, hot_hz=300.0, hot_fraction=0.03,
+                            lo=-3.0, hi=3.0, seed=0x1234_5678_9ABC + (i % 3)))
+    return out
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
+def test_noise_ragged_multi_env(ev, oracle_mod, scenes_mod, tile):
+    """Leak, shot and hot-pixel events (Sec. 3.4) with the signal events, refractory periods
+    and threshold maps of the ragged set, through the production and the trace kernels."""
+    envs = _ragged_envs(scenes_mod)
+    kfs = [scenes_mod.render(envs, k) for k in range(4)]
+    evs = run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(1, 3), tile=tile,
+                   noise=_noise_specs(len(envs)))
+    assert len(evs) > 1000
+
+
+@pytest.mark.parametrize("flags", [0x10, 0x40])
+def test_noise_modes(ev, oracle_mod, scenes_mod, flags):
+    """Shot noise reads the blended sample, so the blend modes change it."""
+    envs = _ragged_envs(scenes_mod)[:2] + _ragged_envs(scenes_mod)[5:]
+    kfs = [scenes_mod.render(envs, k) for k in range(3)]
+    run_both(ev, oracle_mod, envs, kfs, 16_666_667, flags=flags, noise=_noise_specs(len(envs)))
+
+
+def test_noise_sub_frames_longer_than_2_32_ns(ev, oracle_mod, scenes_mod):
+    """Noise times t_{i-1} + floor(u d / 2^32) with d above 2^32 (the high word of d)."""
+    w = scenes_mod.config1()
+    envs = [scenes_mod.EnvScene(W=40, H=24, K=1, c_on=0.2, c_off=0.2, layers=w.envs[0].layers),
+            scenes_mod.EnvScene(W=40, H=24, K=3, c_on=0.2, c_off=0.2, layers=w.envs[0].layers)]
+    kfs = [scenes_mod.render(envs, k) for k in range(3)]
+    noise = [dict(leak_hz=0.05, shot_hz=0.1, hot_hz=0.2, hot_fraction=0.1, seed=3)] * 2
+    evs = run_both(ev, oracle_mod, envs, kfs, (1 << 33) + 12345, noise=noise)
+    assert np.sum(evs["t"] > (1 << 32)) > 100
+
+
+def test_noise_graph_replay_and_switching(ev, oracle_mod, scenes_mod):
+    """The gap counter lives on the device, so replayed gaps draw fresh noise like stepped
+    ones; set_noise drops the captured graph; None turns noise off."""
+    envs = _ragged_envs(scenes_mod)
+    kfs = [scenes_mod.render(envs, k) for k in range(5)]
+    noise = _noise_specs(len(envs))
+    o = oracle_mod.Oracle(envs)
+    o.set_noise(noise)
+    for kf in kfs:
+        o.step(kf.L, kf.mv, kf.Z, 16_666_667)
+    want = oracle_mod.sort_events(o.events())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = ev.Context(envs, capacity=1 << 22, stream=stream)
+        ctx.set_noise(noise)
+        ctx.step(_dev(kfs[0].L), _dev(kfs[0].mv), _dev(kfs[0].Z), 16_666_667)
+        ctx.step(_dev(kfs[1].L), _dev(kfs[1].mv), _dev(kfs[1].Z), 16_666_667)
+        ctx.capture(16_666_667)
+        for kf in kfs[2:]:
+            ctx.write_inputs(_dev(kf.L), _dev(kf.mv), _dev(kf.Z))
+            ctx.replay()
+        got = ev.sort_events(ctx.read_events())
+        np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+        ctx.set_noise(None)
+        with pytest.raises(ev.EvisError):
+            ctx.replay()
+        with pytest.raises(ev.EvisError):
+            ctx.set_noise([dict(hot_fraction=1.5)] * len(envs))
+        with pytest.raises(ev.EvisError):
+            ctx.set_noise([dict(leak_hz=float("inf"))] * len(envs))
+        with pytest.raises(ev.EvisError):
+            ctx.set_noise([dict(lo=1.0, hi=1.0)] * len(envs))
+        ctx.close()
+    # off again: the plain event stream
+    run_both(ev, oracle_mod, envs, kfs[:3], 16_666_667, noise=[{}] * len(envs))
+
+
+def test_noise_high_speed_full_size_sampled(ev, oracle_mod, scenes_mod):
+    """All noise sources on the 8-env high-speed workload at full size, in the persistent
+    autotuned launch with caller-kept inputs; two environments against the oracle."""
+    w = scenes_mod.config4(n_envs=8)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    noise = [dict(leak_hz=2.0, shot_hz=5.0, hot_hz=50.0, hot_fraction=0.01, lo=-1.0, hi=5.0,
+                  seed=77)] * len(w.envs)
+    ctx = ev.Context(w.envs, flags=ev.IN_LOG | ev.KEEP_INPUTS, capacity=1 << 26)
+    ctx.set_noise(noise)
+    g = [(_dev(kf.L), _dev(kf.mv), _dev(kf.Z)) for kf in kfs]
+    ctx.step(*g[0], w.dt_ns)
+    ctx.autotune(*g[1], w.dt_ns, reps=1)
+    for t in g[1:]:
+        ctx.step(*t, w.dt_ns)
+    eg = ctx.read_events()
+    ctx.close()
+    sample = [0, 5]
+    o, _, _ = _subset(ev, oracle_mod, w.envs, kfs, w.dt_ns, sample, noise=noise)
+    eo = oracle_mod.sort_events(o.events())
+    for j, i in enumerate(sample):
+        mine = eg[eg["env"] == i].copy()
+        mine["env"] = j
+        mine = ev.sort_events(mine)
+        theirs = eo[eo["env"] == j]
+        assert len(mine) == len(theirs) > 10000
+        np.testing.assert_array_equal(mine.view(np.uint8), theirs.view(np.uint8))
