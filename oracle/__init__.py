@@ -30,7 +30,7 @@ EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2")
 
 class _Env(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("K", ctypes.c_int32),
-                ("c_on", ctypes.c_float), ("c_off", ctypes.c_float),
+                ("c_on", ctypes.c_float), ("c_off", ctypes.c_float), ("margin", ctypes.c_int32),
                 ("c_on_map", ctypes.c_void_p), ("c_off_map", ctypes.c_void_p),
                 ("refractory_ns", ctypes.c_int64), ("t0_ns", ctypes.c_int64)]
 
@@ -97,7 +97,7 @@ class Oracle:
                 con = np.ascontiguousarray(e.c_on_map, dtype=np.float32)
                 coff = np.ascontiguousarray(e.c_off_map, dtype=np.float32)
                 self._keep += [con, coff]
-            arr[i] = _Env(e.W, e.H, e.K, e.c_on, e.c_off, _ptr(con), _ptr(coff),
+            arr[i] = _Env(e.W, e.H, e.K, e.c_on, e.c_off, int(getattr(e, "margin", 0)), _ptr(con), _ptr(coff),
                           int(e.refractory_ns), int(e.t0_ns))
         self._h = lib.orc_create(ctypes.addressof(arr), len(envs), float(eps), int(flags))
         if not self._h:
@@ -203,7 +203,7 @@ def soft_counts(envs, tau, delta, LA, LB, mvA, mvB, ZA, ZB, Lref0, C, smooth=Non
     sC = f64(sm.get("C", f32(C)))
     arr = (_Env * len(envs))()
     for i, e in enumerate(envs):
-        arr[i] = _Env(e.W, e.H, e.K, e.c_on, e.c_off, None, None, 0, 0)
+        arr[i] = _Env(e.W, e.H, e.K, e.c_on, e.c_off, int(getattr(e, "margin", 0)), None, None, 0, 0)
     n = dec[0].size
     counts = np.zeros(2 * n, dtype=np.float64)
     grads = None

@@ -36,6 +36,7 @@ constexpr int64_t NO_EVENT = std::numeric_limits<int64_t>::min();
 struct Env {
   int W, H, K;
   float c_on, c_off;
+  int margin;            // rendered pixels cropped on each side (Appendix B); events cover the rest
   int64_t refractory_ns, t0_ns;
   bool has_map;
 };
@@ -302,9 +303,13 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
       std::memcpy(keys + (static_cast<size_t>(i - 1) * 2) * HW, zA.data(), HW * 8);
       std::memcpy(keys + (static_cast<size_t>(i - 1) * 2 + 1) * HW, zB.data(), HW * 8);
     }
-    for (int y = 0; y < H; ++y) {
-      for (int x = 0; x < W; ++x) {
+    // targets: the sensor, i.e. the rendered frame without its margin (Appendix B); every
+    // rendered pixel splats, and events carry sensor coordinates
+    const int m = en.margin, SW = W - 2 * m;
+    for (int y = m; y < H - m; ++y) {
+      for (int x = m; x < W - m; ++x) {
         size_t t = static_cast<size_t>(y) * W + x;
+        const int sx = x - m, sy = y - m;
         bool hasA = zA[t] != EMPTY, hasB = zB[t] != EMPTY;
         float la = hasA ? LA[zA[t] & 0xFFFFFFu] : 0.0f;
         float lb = hasB ? LB[zB[t] & 0xFFFFFFu] : 0.0f;
@@ -326,7 +331,7 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
           else L = NAN;
         }
         if (Lint) Lint[static_cast<size_t>(i - 1) * HW + t] = L;
-        noise_pixel(c, e, x, y, static_cast<uint32_t>(t), static_cast<uint32_t>(i),
+        noise_pixel(c, e, sx, sy, static_cast<uint32_t>(sy * SW + sx), static_cast<uint32_t>(i),
                     T0 + (static_cast<int64_t>(i - 1) * dt) / K, ti, hasA || hasB, L);
         if (!hasA && !hasB) continue;  // no sample this substep: the pixel holds its state
         float th_on = en.c_on, th_off = en.c_off;
@@ -334,7 +339,7 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
           th_on = c.con[o + t];
           th_off = c.coff[o + t];
         }
-        cross_pixel(c, e, x, y, L, Lref[t], Lprev[t], tprev[t], ti, tlast[t], th_on, th_off,
+        cross_pixel(c, e, sx, sy, L, Lref[t], Lprev[t], tprev[t], ti, tlast[t], th_on, th_off,
                     en.refractory_ns);
       }
     }
@@ -362,6 +367,7 @@ extern "C" {
 typedef struct {
   int32_t width, height, K;
   float c_on, c_off;
+  int32_t margin;          // over-render margin per side, 0 <= 2 margin < min(width, height)
   const float* c_on_map;   // optional host [H*W]
   const float* c_off_map;
   int64_t refractory_ns;
@@ -382,12 +388,13 @@ void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags)
     if (d.width <= 0 || d.height <= 0 || d.width > 65535 || d.height > 65535 ||
         static_cast<int64_t>(d.width) * d.height > (1 << 24) || d.K < 1 ||
         !(d.c_on > 0.0f) || !(d.c_off > 0.0f) || d.refractory_ns < 0 ||
-        ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))) {
+        ((d.c_on_map == nullptr) != (d.c_off_map == nullptr)) || d.margin < 0 ||
+        2 * static_cast<int64_t>(d.margin) >= d.width || 2 * static_cast<int64_t>(d.margin) >= d.height) {
       delete c;
       return nullptr;
     }
-    c->envs.push_back(Env{d.width, d.height, d.K, d.c_on, d.c_off, d.refractory_ns, d.t0_ns,
-                          d.c_on_map != nullptr});
+    c->envs.push_back(Env{d.width, d.height, d.K, d.c_on, d.c_off, d.margin, d.refractory_ns,
+                          d.t0_ns, d.c_on_map != nullptr});
     c->off.push_back(c->total);
     c->total += (static_cast<int64_t>(d.width) * d.height + 3) / 4 * 4;
     any_map |= d.c_on_map != nullptr;
@@ -671,6 +678,8 @@ int32_t orc_soft(const orc_env *envs, int32_t n_envs, double tau, float delta,
                  const double *dLA, const double *dLB, const double *dmvA, const double *dmvB,
                  const double *Cd, double *counts, const double *gcounts, double *gLA,
                  double *gLB, double *gmvA, double *gmvB, double *gC) {
+  for (int e = 0; e < n_envs; ++e)
+    if (envs[e].margin != 0) return 1;  // the surrogate covers the whole rendered frame
   size_t off = 0;
   for (int e = 0; e < n_envs; ++e) {
     const int W = envs[e].width, H = envs[e].height;

@@ -97,6 +97,7 @@ class EnvScene:
     layers: list = field(default_factory=list)
     c_on_map: np.ndarray | None = None   # optional per-pixel thresholds [H*W] float32
     c_off_map: np.ndarray | None = None
+    margin: int = 0                      # over-render margin per side (W, H include it)
 
 
 def pixel_offsets(envs) -> tuple[np.ndarray, int]:

@@ -19,6 +19,7 @@ class TinyEnv:
     t0_ns: int = 0
     c_on_map: np.ndarray | None = None
     c_off_map: np.ndarray | None = None
+    margin: int = 0
 
 
 def packed_total(envs):
