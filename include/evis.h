@@ -81,9 +81,14 @@ typedef struct {
 #define EVIS_KEEP_INPUTS 0x100u
 
 typedef struct {
-  int32_t width, height; /* 1..65535 each, width * height <= 2^24 */
+  int32_t width, height; /* rendered frame, 1..65535 each, width * height <= 2^24 */
   int32_t K;             /* sub-frames per keyframe gap, 1..4096 (f = i/K, i = 1..K) */
   float c_on, c_off;     /* contrast thresholds (log units), finite and > 0 */
+  int32_t margin;        /* over-render margin (Appendix B): every rendered pixel splats, but
+                          * only the sensor, the frame without `margin` pixels on each side,
+                          * is synthesised; events carry sensor coordinates (x - margin,
+                          * y - margin).  0 <= 2 * margin < min(width, height); 0 = none.
+                          * Per-pixel arrays (state, threshold maps) stay rendered-frame sized. */
   const float *c_on_map; /* optional device [H*W] per-pixel thresholds (Eq. 8); both or */
   const float *c_off_map;/* neither; caller-owned, read at every step, must outlive ctx */
   int64_t refractory_ns; /* 0 = off (Sec. 3.4) */
@@ -178,7 +183,8 @@ evis_status evis_set_noise(evis_ctx *ctx, const evis_noise_desc *noise);
  * forward, dir 1 = B backward; key = depth bits << 32 | quantised (1 - weight) << 24 |
  * source index, all ones = no source) and the blended log-intensity (Lint[(i-1) * H*W + p],
  * NaN where the pixel got no sample).  keys / Lint are device arrays of
- * sum_e K_e * 2 * H_e * W_e uint64 and sum_e K_e * H_e * W_e floats. */
+ * sum_e K_e * 2 * H_e * W_e uint64 and sum_e K_e * H_e * W_e floats.  With a margin, only
+ * the sensor's entries are written; the margin's are left as they were. */
 evis_status evis_step_trace(evis_ctx *ctx, const float *frames, const float *mv,
                             const float *depth, int64_t dt_ns, uint64_t *keys, float *Lint);
 
@@ -240,7 +246,8 @@ evis_status evis_replay(evis_ctx *ctx);
  *   N_off = sum_i sig((L_ref^(i-1) - L_i - C) / tau)
  * over the sub-frames with a sample; C [n_envs] is the differentiable threshold and
  * enters only the sigmoids.  envs gives width, height, K and the event thresholds c_on,
- * c_off of the frozen trajectory (other fields are ignored); inputs are device arrays in the packed layout (log-intensity L_A, L_B, motion
+ * c_off of the frozen trajectory (margin must be 0: the counts cover the whole rendered
+ * frame; other fields are ignored); inputs are device arrays in the packed layout (log-intensity L_A, L_B, motion
  * vectors, depth, start-of-gap reference levels Lref0) and C [n_envs]; counts is
  * [2][H][W] per environment at offset 2 * pix_off.  The workspace (device, at least
  * evis_soft_workspace_size bytes) keeps what the backward needs; the forward is

@@ -27,7 +27,7 @@ EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2")
 
 class EnvDesc(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("K", ctypes.c_int32),
-                ("c_on", ctypes.c_float), ("c_off", ctypes.c_float),
+                ("c_on", ctypes.c_float), ("c_off", ctypes.c_float), ("margin", ctypes.c_int32),
                 ("c_on_map", ctypes.c_void_p), ("c_off_map", ctypes.c_void_p),
                 ("refractory_ns", ctypes.c_int64), ("t0_ns", ctypes.c_int64)]
 
@@ -163,7 +163,8 @@ class Context:
                 coff = torch.as_tensor(coff, dtype=torch.float32).cuda().contiguous()
                 self._keep += [con, coff]
             arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), float(e.c_on), float(e.c_off),
-                             _ptr(con), _ptr(coff), int(getattr(e, "refractory_ns", 0)),
+                             int(getattr(e, "margin", 0)), _ptr(con), _ptr(coff),
+                             int(getattr(e, "refractory_ns", 0)),
                              int(getattr(e, "t0_ns", 0)))
         cfg = Config(float(eps), self.flags, self.capacity)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
@@ -369,8 +370,8 @@ def sort_events(ev: np.ndarray) -> np.ndarray:
 def _descs(envs):
     arr = (EnvDesc * len(envs))()
     for i, e in enumerate(envs):
-        arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), float(e.c_on), float(e.c_off), None, None,
-                         0, 0)
+        arr[i] = EnvDesc(int(e.W), int(e.H), int(e.K), float(e.c_on), float(e.c_off),
+                         int(getattr(e, "margin", 0)), None, None, 0, 0)
     return arr
 
 

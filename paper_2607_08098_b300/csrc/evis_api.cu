@@ -121,6 +121,8 @@ std::string validate(const evis_env_desc *envs, int32_t n, const evis_config *cf
     if ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))
       return p + "give both threshold maps or neither";
     if (d.refractory_ns < 0) return p + "refractory_ns must be >= 0";
+    if (d.margin < 0 || 2 * int64_t(d.margin) >= d.width || 2 * int64_t(d.margin) >= d.height)
+      return p + "margin must satisfy 0 <= 2 * margin < min(width, height)";
   }
   return "";
 }
@@ -162,9 +164,9 @@ std::vector<Tile> tiles_for(const evis_ctx *c, int tw, int th, Pred take) {
   std::vector<Tile> tiles;
   for (int i = 0; i < c->n; ++i) {
     if (!take(i)) continue;
-    const evis_env_desc &d = c->envs[i];
-    for (int y = 0; y < d.height; y += th)
-      for (int x = 0; x < d.width; x += tw) tiles.push_back(Tile{i, x, y, 0});
+    const evis_env_desc &d = c->envs[i];  // tiles cover the sensor (inside the margin)
+    for (int y = d.margin; y < d.height - d.margin; y += th)
+      for (int x = d.margin; x < d.width - d.margin; x += tw) tiles.push_back(Tile{i, x, y, 0});
   }
   std::stable_sort(tiles.begin(), tiles.end(), [&](const Tile &a, const Tile &b) {
     return c->envs[a.env].K > c->envs[b.env].K;
@@ -385,6 +387,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     v.con_map = d.c_on_map;
     v.coff_map = d.c_off_map;
     v.refractory_ns = d.refractory_ns;
+    v.margin = d.margin;
     c->total += (px + 3) / 4 * 4;
     c->max_px = std::max<int>(c->max_px, static_cast<int>(px));
     c->any_refr |= d.refractory_ns > 0;

@@ -23,7 +23,8 @@ struct DevEnv {
   int32_t W, H, K, tile_h;
   int64_t pix_off;
   int64_t seg_off;    // first row segment of this environment
-  int32_t segs_x, pad0;  // row segments per image row
+  int32_t segs_x;     // row segments per image row
+  int32_t margin;     // over-render margin: targets are [margin, W - margin) x [margin, H - margin)
   float c_on, c_off;
   const float *con_map, *coff_map;   // this environment's maps (device) or null
   int64_t refractory_ns;

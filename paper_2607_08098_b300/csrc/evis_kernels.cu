@@ -310,7 +310,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   for (int j = 0; j < NT; ++j) {
     const int ty = ty0 + ROWS * j;
     const int pix = ty * W + tx;
-    act[j] = tx < W && ty < H;
+    act[j] = tx < W - E.margin && ty < H - E.margin;  // tiles start inside the margin
     tprev[j] = T0;
     tlast[j] = kNoEvent;
     Lref[j] = 0.0f;
@@ -604,8 +604,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         if (emit) {
           const int otid = warp * 32 + own;
           const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
-          const ulonglong2 rec = make_event(t, tl.x0 + otid % TX, tl.y0 + otid / TX + ROWS * j,
-                                            tl.env, opol);
+          const ulonglong2 rec = make_event(t, tl.x0 - E.margin + otid % TX,
+                                            tl.y0 - E.margin + otid / TX + ROWS * j, tl.env, opol);
           if (idx < static_cast<unsigned>(kEventStage)) {
             S.stage[idx] = rec;
           } else {
@@ -619,7 +619,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       if (noisy) {  // leak, shot and hot-pixel events of this target (Sec. 3.4)
         const int64_t d = ti - tim1;
         const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
-        const unsigned npix = static_cast<unsigned>(pix);
+        const int ex = tx - E.margin, ey = ty - E.margin;  // sensor coordinates
+        const unsigned npix = static_cast<unsigned>(ey * (W - 2 * E.margin) + ex);
         bool fl = false, fs = false, fh = false;
         if (act[j]) {
           const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 0u), E.key0, E.key1);
@@ -635,12 +636,12 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           uint4 rt = make_uint4(0u, 0u, 0u, 0u);
           if (fl || fs || fh)
             rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u), E.key0, E.key1);
-          stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), tx, ty, tl.env, 1),
+          stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, 1),
                      lanes_below, lane);
           stage_warp(S, &s_n, a, fs,
-                     make_event(noise_time(rt.y, tim1, d), tx, ty, tl.env, (rt.w & 1u) ? 1 : -1),
+                     make_event(noise_time(rt.y, tim1, d), ex, ey, tl.env, (rt.w & 1u) ? 1 : -1),
                      lanes_below, lane);
-          stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), tx, ty, tl.env, 1),
+          stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, 1),
                      lanes_below, lane);
         }
       }
@@ -682,7 +683,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     a.Lref[o + pix] = Lref[j];
     if (a.tlast) a.tlast[o + pix] = tlast[j];
   }
-  if (tid == 0 && tl.x0 == 0 && tl.y0 == 0) {
+  if (tid == 0 && tl.x0 == E.margin && tl.y0 == E.margin) {  // the environment's first tile
     a.clock_out[tl.env] = T0 + a.dt;
     if (a.gap_out) a.gap_out[tl.env] = a.gap_in[tl.env] + 1u;
   }

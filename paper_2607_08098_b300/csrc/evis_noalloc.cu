@@ -67,7 +67,7 @@ __global__ void noalloc_setup(unsigned char *scratch, DevEnv env, int tiles_x, i
                               int64_t t_a) {
   Tile *tiles = reinterpret_cast<Tile *>(scratch + kOffTiles);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tiles; i += gridDim.x * blockDim.x)
-    tiles[i] = Tile{0, (i % tiles_x) * kNaTileW, (i / tiles_x) * kNaTileH, 0};
+    tiles[i] = Tile{0, env.margin + (i % tiles_x) * kNaTileW, env.margin + (i / tiles_x) * kNaTileH, 0};
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *reinterpret_cast<DevEnv *>(scratch + kOffEnv) = env;
     int64_t *clock = reinterpret_cast<int64_t *>(scratch + kOffClock);
@@ -105,6 +105,8 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
   if ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))
     return reject("give both threshold maps or neither");
   if (d.refractory_ns < 0) return reject("refractory_ns must be >= 0");
+  if (d.margin < 0 || 2 * d.margin >= d.width || 2 * d.margin >= d.height)
+    return reject("margin must satisfy 0 <= 2 * margin < min(width, height)");
   if (flags & ~(EVIS_MODE_B_PRIMARY | EVIS_TIE_INDEX))
     return reject("only EVIS_MODE_B_PRIMARY and EVIS_TIE_INDEX are accepted (inputs are log-intensity)");
   if (!L_A || !mv_A || !Z_A || !L_B || !mv_B || !Z_B || !Lref || !count)
@@ -135,8 +137,9 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
   de.con_map = d.c_on_map;
   de.coff_map = d.c_off_map;
   de.refractory_ns = d.refractory_ns;
-  const int tiles_x = (d.width + kNaTileW - 1) / kNaTileW;
-  const int n_tiles = tiles_x * ((d.height + kNaTileH - 1) / kNaTileH);
+  de.margin = d.margin;
+  const int tiles_x = (d.width - 2 * d.margin + kNaTileW - 1) / kNaTileW;  // sensor tiles
+  const int n_tiles = tiles_x * ((d.height - 2 * d.margin + kNaTileH - 1) / kNaTileH);
   const int n_segs = de.segs_x * d.height;
 
   DevEnv *s_env = reinterpret_cast<DevEnv *>(scratch + kOffEnv);

@@ -351,7 +351,8 @@ evis_status soft_prepare(const evis_env_desc *envs, int32_t n, void *ws, int64_t
     const evis_env_desc &d = envs[e];
     if (d.width < 1 || d.height < 1 || d.width > 65535 || d.height > 65535 ||
         int64_t(d.width) * d.height > (int64_t(1) << 24) || d.K < 1 || d.K > 4096 ||
-        !(d.c_on > 0.0f && d.c_on < INFINITY) || !(d.c_off > 0.0f && d.c_off < INFINITY))
+        !(d.c_on > 0.0f && d.c_on < INFINITY) || !(d.c_off > 0.0f && d.c_off < INFINITY) ||
+        d.margin != 0)  // the surrogate counts over the whole rendered frame
       return EVIS_ERR_INVALID_ARG;
     *max_hw = std::max(*max_hw, d.width * d.height);
   }

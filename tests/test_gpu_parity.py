@@ -37,6 +37,20 @@ def _frames(kf, mode):
     return kf.rgb.reshape(-1)
 
 
+def _trace_masks(envs):
+    """Sensor pixels (inside each environment's margin) of the trace layouts: keys
+    [K][2][H*W] and interpolated L [K][H*W] per environment, in order."""
+    mk, ml = [], []
+    for e in envs:
+        m = int(getattr(e, "margin", 0))
+        g = np.zeros((e.H, e.W), bool)
+        g[m:e.H - m, m:e.W - m] = True
+        g = g.ravel()
+        mk.append(np.tile(g, 2 * e.K))
+        ml.append(np.tile(g, e.K))
+    return np.concatenate(mk), np.concatenate(ml)
+
+
 def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), capacity=1 << 22,
              check_state=True, tile=None, noise=None):
     """Feed the same keyframes to the oracle and the library; compare everything."""
@@ -57,8 +71,10 @@ def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), c
             ok, ol = o.step(fr, kf.mv, kf.Z, dt, trace=True)
             gk, gl = ctx.step_trace(*g_in, dt)
             torch.cuda.synchronize()
-            gk = gk.cpu().numpy().view(np.uint64)
-            gl = gl.cpu().numpy()
+            mk, ml = _trace_masks(envs)   # with a margin only sensor pixels are traced
+            gk = gk.cpu().numpy().view(np.uint64)[mk]
+            gl = gl.cpu().numpy()[ml]
+            ok, ol = ok[mk], ol[ml]
             bad = np.nonzero(gk != ok)[0]
             assert bad.size == 0, f"step {s}: {bad.size} splat keys differ, first at {bad[:5]}"
             np.testing.assert_array_equal(gl, ol, err_msg=f"step {s}: interpolated L")
@@ -74,7 +90,10 @@ def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), c
         so, sg = o.state(), ctx.state()
         valid = np.zeros(so[0].size, dtype=bool)
         for e, off in zip(envs, o.offsets):
-            valid[off:off + e.H * e.W] = True
+            m = int(getattr(e, "margin", 0))
+            g = np.zeros((e.H, e.W), bool)
+            g[m:e.H - m, m:e.W - m] = True
+            valid[off:off + e.H * e.W] = g.ravel()
         np.testing.assert_array_equal(sg[0][valid], so[0][valid])
         if any(e.refractory_ns > 0 for e in envs):   # t_last is tracked only then
             np.testing.assert_array_equal(sg[1][valid], so[1][valid])
@@ -497,3 +516,21 @@ def test_noise_high_speed_full_size_sampled(ev, oracle_mod, scenes_mod):
         theirs = eo[eo["env"] == j]
         assert len(mine) == len(theirs) > 10000
         np.testing.assert_array_equal(mine.view(np.uint8), theirs.view(np.uint8))
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (64, 32), (128, 16)])
+def test_margin_crop(ev, oracle_mod, scenes_mod, tile):
+    """Over-render margins (Appendix B) of 0..9 pixels, including a sensor one pixel wide and
+    tails of every tile, with refractory periods, maps and noise drawn per sensor pixel."""
+    envs = _ragged_envs(scenes_mod)
+    margins = [3, 0, 0, 0, 2, 9]         # (37x23, 70x41, 1x1, 33x1, 5x40, 96x64)
+    for e, m in zip(envs, margins):
+        e.margin = m
+    envs[0].margin = 11                  # 37x23 -> a 15x1 sensor
+    kfs = [scenes_mod.render(envs, k) for k in range(4)]
+    noise = [dict(leak_hz=30.0, hot_hz=200.0, hot_fraction=0.05, shot_hz=50.0, seed=9)] * len(envs)
+    evs = run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(1, 3), tile=tile, noise=noise)
+    for e in envs:
+        m = e.margin
+        sel = evs[evs["env"] == envs.index(e)]
+        assert np.all(sel["x"] < e.W - 2 * m) and np.all(sel["y"] < e.H - 2 * m)

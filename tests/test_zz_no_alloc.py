@@ -53,7 +53,8 @@ def test_noalloc_matches_evis_step_on_two_gaps(ev, scenes_mod, refractory_ns):
     ctx.close()
 
     # the same two gaps through the allocation-free entry point
-    desc = ev.EnvDesc(es.W, es.H, es.K, es.c_on, es.c_off, None, None, refractory_ns, es.t0_ns)
+    desc = ev.EnvDesc(width=es.W, height=es.H, K=es.K, c_on=es.c_on, c_off=es.c_off,
+                      refractory_ns=refractory_ns, t0_ns=es.t0_ns)
     Lref = dev[0][0].clone()
     t_last = torch.full((n,), np.iinfo(np.int64).min, dtype=torch.int64, device="cuda")
     cap = 1 << 21
@@ -83,12 +84,46 @@ def test_noalloc_matches_evis_step_on_two_gaps(ev, scenes_mod, refractory_ns):
             np.testing.assert_array_equal(t_last.cpu().numpy(), ref_state[gap][1])
 
 
+def test_noalloc_with_margin_matches_oracle(ev, oracle_mod, scenes_mod):
+    """A 7-pixel over-render margin (Appendix B) through the allocation-free entry point."""
+    rng = np.random.default_rng(4)
+    es = scenes_mod.EnvScene(W=150, H=90, K=6, c_on=0.2, c_off=0.25, refractory_ns=40_000,
+                             layers=scenes_mod._random_layers(rng, 150, 90, 3, 6.0, 0.08), margin=7)
+    n = es.W * es.H
+    kfs = [scenes_mod.render([es], k) for k in range(2)]
+    o = oracle_mod.Oracle([es])
+    for kf in kfs:
+        o.step(kf.L, kf.mv, kf.Z, 16_666_667)
+    want = oracle_mod.sort_events(o.events())
+    A, B = [tuple(_dev(a[:n]) for a in (kf.L, kf.mv, kf.Z)) for kf in kfs]
+    desc = ev.EnvDesc(width=es.W, height=es.H, K=es.K, c_on=es.c_on, c_off=es.c_off,
+                      margin=es.margin, refractory_ns=es.refractory_ns)
+    Lref = A[0].clone()
+    t_last = torch.full((n,), np.iinfo(np.int64).min, dtype=torch.int64, device="cuda")
+    cap = 1 << 20
+    events = torch.empty(cap * 2, dtype=torch.int64, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    L = ev.lib()
+    st = L.evis_step_noalloc(ctypes.byref(desc), 0, A[0].data_ptr(), A[1].data_ptr(),
+                             A[2].data_ptr(), B[0].data_ptr(), B[1].data_ptr(), B[2].data_ptr(),
+                             Lref.data_ptr(), t_last.data_ptr(), 0, 16_666_667, events.data_ptr(),
+                             count.data_ptr(), cap, torch.cuda.current_stream().cuda_stream)
+    assert st == ev.OK, L.evis_last_error(None).decode()
+    torch.cuda.synchronize()
+    got = ev.sort_events(events[:2 * int(count.item())].cpu().numpy().view(ev.EVENT_DTYPE))
+    assert len(got) == len(want) > 100
+    np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+    grid = np.zeros((es.H, es.W), bool)
+    grid[7:es.H - 7, 7:es.W - 7] = True
+    np.testing.assert_array_equal(Lref.cpu().numpy()[grid.ravel()], o.state()[0][:n][grid.ravel()])
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(ev):
     L = ev.lib()
     buf = torch.zeros(16, dtype=torch.float32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     for W, H in ((4097, 8), (8, 4097), (2048, 1024)):
-        desc = ev.EnvDesc(W, H, 4, 0.2, 0.2, None, None, 0, 0)
+        desc = ev.EnvDesc(width=W, height=H, K=4, c_on=0.2, c_off=0.2)
         p = buf.data_ptr()
         st = L.evis_step_noalloc(ctypes.byref(desc), 0, p, p, p, p, p, p, p, None, 0, 1000,
                                  p, cnt.data_ptr(), 1, torch.cuda.current_stream().cuda_stream)
