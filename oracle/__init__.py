@@ -41,6 +41,36 @@ class _Noise(ctypes.Structure):
                 ("lo", ctypes.c_float), ("hi", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
+def rec709(rgb) -> np.ndarray:
+    """Rec. 709 luminance (Eq. 3) of [n, 3] linear RGB, binary32."""
+    lib = _load()
+    lib.orc_rec709.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    a = np.ascontiguousarray(rgb, dtype=np.float32).reshape(-1, 3)
+    out = np.empty(a.shape[0], dtype=np.float32)
+    lib.orc_rec709(a.ctypes.data, a.shape[0], out.ctypes.data)
+    return out
+
+
+def defocus(plane, sigma: float) -> np.ndarray:
+    """Separable Gaussian blur of one linear plane [H, W] (Sec. 3.4), binary32."""
+    lib = _load()
+    lib.orc_defocus.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                ctypes.c_void_p]
+    a = np.ascontiguousarray(plane, dtype=np.float32)
+    out = np.empty_like(a)
+    lib.orc_defocus(a.ctypes.data, a.shape[1], a.shape[0], float(sigma), out.ctypes.data)
+    return out
+
+
+def defocus_weights(sigma: float) -> np.ndarray:
+    lib = _load()
+    lib.orc_defocus_weights.restype = ctypes.c_int32
+    lib.orc_defocus_weights.argtypes = [ctypes.c_float, ctypes.c_void_p]
+    buf = np.empty(128, dtype=np.float32)
+    r = lib.orc_defocus_weights(float(sigma), buf.ctypes.data)
+    return buf[:2 * r + 1].copy()
+
+
 def philox(n, c1=0, c2=0, c3=0, key=(0, 0), base=0) -> np.ndarray:
     """n outputs [n, 4] of the oracle's Philox4x32-10 at counters (base + j, c1, c2, c3)."""
     lib = _load()
@@ -155,6 +185,15 @@ class Oracle:
                             int(sp.get("seed", 0)))
         if lib.orc_set_noise(self._h, ctypes.addressof(arr)) != 0:
             raise ValueError("oracle rejected the noise parameters")
+
+    def set_defocus(self, sigmas):
+        """Per-environment defocus sigma in pixels (Sec. 3.4); linear inputs only."""
+        lib = _load()
+        lib.orc_set_defocus.restype = ctypes.c_int32
+        lib.orc_set_defocus.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        sg = np.ascontiguousarray(sigmas, dtype=np.float32)
+        if sg.size != len(self.envs) or lib.orc_set_defocus(self._h, sg.ctypes.data) != 0:
+            raise ValueError("oracle rejected the defocus parameters")
 
     def state(self):
         Lref = np.empty(self.total, dtype=np.float32)

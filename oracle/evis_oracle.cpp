@@ -15,6 +15,7 @@
 // Parity status: every function below is pinned by a test under tests/ (brute force,
 // closed forms or invariants) except the full event stream of a textured scene, which has
 // nothing but this oracle to compare against (parity unpinned beyond these pins).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -58,6 +59,7 @@ struct Noise {
 struct Ctx {
   std::vector<Env> envs;
   std::vector<Noise> noise;                // per env (zeros: no noise)
+  std::vector<float> defocus;              // per env Gaussian sigma in pixels (0: none)
   uint32_t gap = 0;                        // keyframe gaps processed (the noise counter)
   std::vector<int64_t> off;   // packed pixel offsets (H*W rounded up to 4)
   int64_t total = 0;
@@ -346,12 +348,66 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
   }
 }
 
+// Defocus (Sec. 3.4): the linear intensity convolved with a separable Gaussian of standard
+// deviation sigma pixels.  Taps k = -r..r with r = int(3 sigma + 0.5); weights
+// exp(-k^2 / (2 sigma^2)) normalised to sum 1 in binary64, then rounded to binary32.  Edges
+// repeat the border pixel.  The horizontal pass runs first, then the vertical pass on its
+// result; each sums its taps in binary32 in the order k = -r..r.
+int defocus_radius(float sigma) { return sigma > 0.0f ? static_cast<int>(3.0 * sigma + 0.5) : 0; }
+
+std::vector<float> defocus_weights(float sigma) {
+  const int r = defocus_radius(sigma);
+  if (r == 0) return {1.0f};
+  std::vector<double> w(2 * r + 1);
+  double sum = 0.0;
+  for (int k = -r; k <= r; ++k) {
+    w[k + r] = std::exp(-(static_cast<double>(k) * k) / (2.0 * sigma * static_cast<double>(sigma)));
+    sum += w[k + r];
+  }
+  std::vector<float> out(w.size());
+  for (size_t i = 0; i < w.size(); ++i) out[i] = static_cast<float>(w[i] / sum);
+  return out;
+}
+
+void defocus_plane(const float* in, int W, int H, float sigma, float* out) {
+  const std::vector<float> w = defocus_weights(sigma);
+  const int r = static_cast<int>(w.size() / 2);
+  std::vector<float> h(static_cast<size_t>(W) * H);
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      float acc = 0.0f;
+      for (int k = -r; k <= r; ++k) {
+        const int xs = std::min(std::max(x + k, 0), W - 1);
+        acc += w[k + r] * in[static_cast<size_t>(y) * W + xs];
+      }
+      h[static_cast<size_t>(y) * W + x] = acc;
+    }
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      float acc = 0.0f;
+      for (int k = -r; k <= r; ++k) {
+        const int ys = std::min(std::max(y + k, 0), H - 1);
+        acc += w[k + r] * h[static_cast<size_t>(ys) * W + x];
+      }
+      out[static_cast<size_t>(y) * W + x] = acc;
+    }
+}
+
 void to_log(const Ctx& c, const float* frames, std::vector<float>& L) {
   L.assign(c.total, 0.0f);
   uint32_t mode = c.flags & IN_MASK;
   for (size_t e = 0; e < c.envs.size(); ++e) {
     size_t o = static_cast<size_t>(c.off[e]);
     size_t n = static_cast<size_t>(c.envs[e].W) * c.envs[e].H;
+    if (mode != IN_LOG && c.defocus[e] > 0.0f) {  // luminance, blur, then the log
+      std::vector<float> I(n), B(n);
+      for (size_t p = 0; p < n; ++p)
+        I[p] = mode == IN_LUM ? frames[o + p]
+                              : rec709(frames[3 * (o + p)], frames[3 * (o + p) + 1], frames[3 * (o + p) + 2]);
+      defocus_plane(I.data(), c.envs[e].W, c.envs[e].H, c.defocus[e], B.data());
+      for (size_t p = 0; p < n; ++p) L[o + p] = log_intensity(B[p], c.eps);
+      continue;
+    }
     for (size_t p = o; p < o + n; ++p) {
       if (mode == IN_LOG) L[p] = frames[p];
       else if (mode == IN_LUM) L[p] = log_intensity(frames[p], c.eps);
@@ -410,6 +466,7 @@ void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags)
     }
   }
   c->noise.assign(n_envs, Noise{0, 0, 0, 0, 0, 1, 0});
+  c->defocus.assign(n_envs, 0.0f);
   c->Lref.assign(c->total, 0.0f);
   c->t_last.assign(c->total, NO_EVENT);
   for (int i = 0; i < n_envs; ++i) c->clock.push_back(envs[i].t0_ns);
@@ -470,6 +527,36 @@ int32_t orc_set_noise(void* h, const orc_noise* nz) {
     c.noise[e] = Noise{n.leak_hz, n.shot_hz, n.hot_hz, n.hot_fraction, n.lo, n.hi, n.seed};
   }
   return 0;
+}
+
+// Per-environment defocus sigma in pixels (array of n_envs; 0 = none, at most 8).  Needs
+// linear inputs (luminance or RGB).  0 on success.
+int32_t orc_set_defocus(void* h, const float* sigma) {
+  Ctx& c = *static_cast<Ctx*>(h);
+  for (size_t e = 0; e < c.envs.size(); ++e)
+    if (!(sigma[e] >= 0.0f && sigma[e] <= 8.0f)) return 1;
+  bool any = false;
+  for (size_t e = 0; e < c.envs.size(); ++e) any |= sigma[e] > 0.0f;
+  if (any && (c.flags & IN_MASK) == IN_LOG) return 1;
+  c.defocus.assign(sigma, sigma + c.envs.size());
+  return 0;
+}
+
+// Rec. 709 luminance of n RGB triples (Eq. 3).
+void orc_rec709(const float* rgb, int64_t n, float* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = rec709(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
+}
+
+// Defocus of one linear plane [H][W] (for the blur's own tests).
+void orc_defocus(const float* in, int32_t W, int32_t H, float sigma, float* out) {
+  defocus_plane(in, W, H, sigma, out);
+}
+
+// The binary32 weights of a defocus sigma (2 r + 1 of them; returns r).
+int32_t orc_defocus_weights(float sigma, float* out) {
+  const std::vector<float> w = defocus_weights(sigma);
+  std::memcpy(out, w.data(), w.size() * sizeof(float));
+  return static_cast<int32_t>(w.size() / 2);
 }
 
 // The generator alone, for its tests: n outputs of Philox4x32-10 at counters

@@ -77,3 +77,101 @@ def test_margin_noise_belongs_to_the_sensor(oracle_mod):
 def test_margin_must_leave_a_sensor(oracle_mod, W, H, m):
     with pytest.raises(Exception):
         oracle_mod.Oracle([TinyEnv(W=W, H=H, K=2, margin=m)])
+
+
+# ---- defocus (Sec. 3.4): separable Gaussian on the linear intensity before the log ----
+
+ndimage = pytest.importorskip("scipy.ndimage")
+
+
+def _radius(sigma):
+    return int(3.0 * np.float64(np.float32(sigma)) + 0.5)
+
+
+@pytest.mark.parametrize("sigma", [0.1, 0.3, 0.5, 0.7, 1.3, 2.5])
+def test_defocus_weights_are_scipys_gaussian(oracle_mod, sigma):
+    r = _radius(sigma)
+    w = oracle_mod.defocus_weights(sigma)
+    assert w.size == 2 * r + 1
+    delta = np.zeros(2 * r + 1)
+    delta[r] = 1.0
+    ref = ndimage.gaussian_filter1d(delta, float(np.float32(sigma)), mode="constant", radius=r)
+    np.testing.assert_array_equal(w, ref[::-1].astype(np.float32))   # correlation = flip
+
+
+@pytest.mark.parametrize("sigma", [0.3, 0.5, 1.3, 2.5])
+def test_defocus_is_scipys_separable_filter(oracle_mod, sigma):
+    rng = np.random.default_rng(11)
+    img = rng.uniform(0.01, 4.0, (37, 53)).astype(np.float32)
+    got = oracle_mod.defocus(img, sigma)
+    s64 = float(np.float32(sigma))
+    r = _radius(sigma)
+    ref = ndimage.gaussian_filter1d(img.astype(np.float64), s64, axis=1, mode="nearest", radius=r)
+    ref = ndimage.gaussian_filter1d(ref, s64, axis=0, mode="nearest", radius=r)
+    np.testing.assert_allclose(got, ref, rtol=2e-6, atol=0)
+
+
+def test_defocus_closed_forms(oracle_mod):
+    sigma = 0.8
+    w = oracle_mod.defocus_weights(sigma).astype(np.float32)
+    r = w.size // 2
+    # impulse response: the outer product of the weights, one binary32 product each
+    img = np.zeros((31, 29), np.float32)
+    img[15, 14] = 1.0
+    out = oracle_mod.defocus(img, sigma)
+    want = np.zeros_like(img)
+    want[15 - r:15 + r + 1, 14 - r:14 + r + 1] = w[:, None] * w[None, :]
+    np.testing.assert_array_equal(out, want)
+    # a constant stays constant (weights sum to 1 within rounding)
+    c = np.full((20, 30), 2.75, np.float32)
+    np.testing.assert_allclose(oracle_mod.defocus(c, sigma), c, rtol=4 * 2.0**-23)
+    # a linear ramp stays linear away from the borders (symmetric kernel)
+    ramp = (0.5 + 0.01 * np.arange(40, dtype=np.float32))[None, :].repeat(12, 0)
+    out = oracle_mod.defocus(ramp, sigma)
+    np.testing.assert_allclose(out[:, r:-r], ramp[:, r:-r], rtol=1e-6)
+    # mass is conserved for an impulse far from the borders
+    assert abs(float(oracle_mod.defocus(img, 1.7).astype(np.float64).sum()) - 1.0) < 1e-6
+    # sigma 0 is the identity, bit for bit
+    rng = np.random.default_rng(2)
+    x = rng.uniform(0, 3, (9, 14)).astype(np.float32)
+    np.testing.assert_array_equal(oracle_mod.defocus(x, 0.0), x)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_defocus_comes_before_the_log(oracle_mod, scenes_mod, mode):
+    """Events of a defocused run equal those of a plain run fed the blurred luminance:
+    the blur acts on linear intensity (after Rec. 709 for RGB), before the log."""
+    env = _scene(scenes_mod, 48, 36, 4, seed=8)
+    envs = [env, dataclasses.replace(env)]
+    sig = [0.6, 0.0]
+    kfs = [scenes_mod.render(envs, k, want=("I", "rgb", "mv", "Z")) for k in range(3)]
+    a = oracle_mod.Oracle(envs, flags=mode)
+    a.set_defocus(sig)
+    b = oracle_mod.Oracle(envs, flags=1)
+    n = env.W * env.H
+    per = (n + 3) // 4 * 4
+    for kf in kfs:
+        fr = kf.I if mode == 1 else kf.rgb.reshape(-1)
+        a.step(fr, kf.mv, kf.Z, 16_666_667)
+        if mode == 1:
+            lum = kf.I.copy()
+        else:
+            lum = oracle_mod.rec709(kf.rgb.reshape(-1, 3))
+        pre = lum.copy()
+        pre[:n] = oracle_mod.defocus(lum[:n].reshape(env.H, env.W), sig[0]).ravel()
+        assert not np.array_equal(pre[:n], lum[:n]) and np.array_equal(pre[per:per + n], lum[per:per + n])
+        b.step(pre, kf.mv, kf.Z, 16_666_667)
+    ea, eb = oracle_mod.sort_events(a.events()), oracle_mod.sort_events(b.events())
+    assert len(ea) > 100
+    np.testing.assert_array_equal(ea.view(np.uint8), eb.view(np.uint8))
+
+
+def test_defocus_parameters_are_checked(oracle_mod):
+    env = TinyEnv(W=8, H=8, K=2)
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle([env], flags=0).set_defocus([0.5])       # log input: nothing to blur
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle([env], flags=1).set_defocus([9.0])
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle([env], flags=1).set_defocus([float("nan")])
+    oracle_mod.Oracle([env], flags=0).set_defocus([0.0])
