@@ -178,6 +178,23 @@ typedef struct {
  * or hi <= lo, checked before anything changes. */
 evis_status evis_set_noise(evis_ctx *ctx, const evis_noise_desc *noise);
 
+/* Defocus (Sec. 3.4): before the log, each keyframe's linear luminance is convolved with a
+ * separable Gaussian of standard deviation sigma pixels: taps k = -r..r, r = int(3 sigma +
+ * 0.5), weights exp(-k^2 / (2 sigma^2)) normalised to sum 1 in binary64 and rounded to
+ * binary32; edge pixels repeat; the horizontal pass runs first, then the vertical one, each
+ * summing its taps in order in binary32.  For RGB input the blur acts on the Rec. 709
+ * luminance.  sigma_px is a host array of n_envs values in 0..8 (0: none), or NULL for none;
+ * any sigma > 0 needs EVIS_IN_LUM or EVIS_IN_RGB (EVIS_ERR_INVALID_ARG otherwise, nothing
+ * changed).  Synchronises the stream; applies from the next keyframe; drops a captured graph.
+ * Allocates a keyframe-sized buffer on first use. */
+evis_status evis_set_defocus(evis_ctx *ctx, const float *sigma_px);
+
+/* The defocus of one image alone: in is [height][width] luminance (mode EVIS_IN_LUM) or
+ * [height][width][3] linear RGB (EVIS_IN_RGB); out is the blurred luminance [height][width].
+ * Device pointers; asynchronous on stream; sizes as for an environment. */
+evis_status evis_defocus(const float *in, int32_t width, int32_t height, uint32_t mode,
+                         float sigma_px, float *out, evis_stream_t stream);
+
 /* Debug form of evis_step: also writes, for every environment in order and every
  * sub-frame i = 1..K_e, the two z-buffers (keys[((i-1)*2 + dir) * H*W + p], dir 0 = A
  * forward, dir 1 = B backward; key = depth bits << 32 | quantised (1 - weight) << 24 |

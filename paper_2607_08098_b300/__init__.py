@@ -67,6 +67,10 @@ _SIGS = {
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "evis_set_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_set_defocus": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_defocus": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
     "evis_set_tile_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "evis_set_env_tile_shapes": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "evis_get_tile_shapes": (ctypes.c_int, [ctypes.c_void_p] * 3),
@@ -279,6 +283,16 @@ class Context:
                                int(sp.get("seed", 0)))
         _check(lib().evis_set_noise(self._h, ctypes.addressof(arr)), self._h)
 
+    def set_defocus(self, sigmas):
+        """Per-environment defocus sigma in pixels (Sec. 3.4), or None for none."""
+        if sigmas is None:
+            _check(lib().evis_set_defocus(self._h, None), self._h)
+            return
+        sg = np.ascontiguousarray(sigmas, dtype=np.float32)
+        if sg.size != len(self.envs):
+            raise ValueError("one sigma per environment")
+        _check(lib().evis_set_defocus(self._h, sg.ctypes.data), self._h)
+
     TILE_SHAPES = ((32, 16), (32, 32), (64, 16), (64, 32), (128, 16))
 
     def set_tile_shape(self, tile_w: int, tile_h: int):
@@ -359,6 +373,20 @@ def log_intensity(x, mode: int = IN_LUM, eps: float = 1e-4):
     out = torch.empty(n, dtype=torch.float32, device=x.device)
     _check(lib().evis_log_intensity(_ptr(x), n, int(mode), float(eps), _ptr(out),
                                     torch.cuda.current_stream().cuda_stream))
+    return out
+
+
+def defocus(image, sigma: float, stream=None):
+    """Blurred luminance [H, W] of a CUDA float32 image [H, W] (luminance) or [H, W, 3]
+    (linear RGB), by the library's defocus kernel (Sec. 3.4)."""
+    import torch
+    if image.dim() not in (2, 3) or (image.dim() == 3 and image.shape[2] != 3):
+        raise ValueError("image must be [H, W] or [H, W, 3]")
+    img = image.contiguous()
+    H, W = img.shape[0], img.shape[1]
+    out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    mode = IN_RGB if img.dim() == 3 else IN_LUM
+    _check(lib().evis_defocus(_ptr(img), W, H, mode, float(sigma), _ptr(out), _stream_handle(stream)))
     return out
 
 

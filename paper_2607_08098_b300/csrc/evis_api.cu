@@ -37,8 +37,11 @@ struct evis_ctx {
   int grid_cap = 1;        // persistent launches: one wave of resident CTAs per group
   bool any_refr = false;
 
-  std::vector<DevEnv> h_envs;  // host copy of d_envs (noise parameters change it)
+  std::vector<DevEnv> h_envs;  // host copy of d_envs (noise and defocus parameters change it)
   bool any_noise = false;
+  int blur_r_max = -1;         // largest defocus radius; -1: no defocus pass
+  float *d_blur = nullptr;     // [total] blurred luminance of the keyframe being prepared
+  float *d_blur_w = nullptr;   // [n][2 kMaxBlurR + 1] defocus weights
   DevEnv *d_envs = nullptr;
   Tile *d_tiles = nullptr;
   unsigned *d_work = nullptr;  // per-group work counters, zeroed every step
@@ -227,6 +230,21 @@ cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, cons
   if (e != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(c->d_work, 0, sizeof(unsigned) * kMaxGroups, c->stream)) != cudaSuccess)
     return e;
+  uint32_t mode = c->mode;
+  if (c->blur_r_max >= 0) {  // defocus: blurred luminance first, then prepared like luminance input
+    evis::BlurArgs ba{};
+    ba.envs = c->d_envs;
+    ba.wtab = c->d_blur_w;
+    ba.in = frames;
+    ba.out = c->d_blur;
+    ba.mode = c->mode;
+    ba.max_r = c->blur_r_max;
+    int max_t = 1;
+    for (const evis_env_desc &d : c->envs) max_t = std::max(max_t, ((d.width + 31) / 32) * ((d.height + 7) / 8));
+    if ((e = evis::launch_defocus(ba, c->n, max_t, c->stream)) != cudaSuccess) return e;
+    frames = c->d_blur;
+    mode = EVIS_IN_LUM;
+  }
   evis::PrepArgs pa{};
   pa.envs = c->d_envs;
   pa.frames = frames;
@@ -242,7 +260,7 @@ cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, cons
   pa.packA = c->d_pack[0];
   pa.packB = c->d_pack[1];
   pa.eps = c->cfg.eps;
-  pa.mode = c->mode;
+  pa.mode = mode;
   pa.max_segs = c->max_segs;
   if ((e = evis::launch_prep(pa, c->n, c->stream)) != cudaSuccess) return e;
   out->L = c->need_L ? c->d_L[b] : frames;
@@ -554,6 +572,79 @@ evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float 
     return EVIS_ERR_INVALID_ARG;
   cudaError_t e = evis::launch_log(in, n, mode, eps, out, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
+}
+
+// Defocus weights (Sec. 3.4): exp(-k^2 / (2 sigma^2)) for k = -r..r, r = int(3 sigma + 0.5),
+// normalised to sum 1 in binary64 and rounded to binary32.  Returns r (0: the identity).
+static int defocus_weights(float sigma, float *w) {
+  const int r = sigma > 0.0f ? static_cast<int>(3.0 * sigma + 0.5) : 0;
+  if (r == 0) {
+    w[0] = 1.0f;
+    return 0;
+  }
+  double v[2 * evis::kMaxBlurR + 1], sum = 0.0;
+  const double s2 = 2.0 * sigma * static_cast<double>(sigma);
+  for (int k = -r; k <= r; ++k) sum += (v[k + r] = std::exp(-(static_cast<double>(k) * k) / s2));
+  for (int i = 0; i <= 2 * r; ++i) w[i] = static_cast<float>(v[i] / sum);
+  return r;
+}
+
+static bool defocus_sigma_ok(float s) { return s >= 0.0f && s <= 8.0f; }
+
+evis_status evis_defocus(const float *in, int32_t width, int32_t height, uint32_t mode,
+                         float sigma_px, float *out, evis_stream_t stream) {
+  if (!in || !out || width < 1 || height < 1 || width > 65535 || height > 65535 ||
+      int64_t(width) * height > (int64_t(1) << 24) || (mode != EVIS_IN_LUM && mode != EVIS_IN_RGB) ||
+      !defocus_sigma_ok(sigma_px))
+    return EVIS_ERR_INVALID_ARG;
+  evis::BlurArgs ba{};
+  ba.W = width;
+  ba.H = height;
+  ba.r = defocus_weights(sigma_px, ba.w);
+  ba.in = in;
+  ba.out = out;
+  ba.mode = mode;
+  ba.max_r = ba.r;
+  const int tiles = ((width + 31) / 32) * ((height + 7) / 8);
+  cudaError_t e = evis::launch_defocus(ba, 1, tiles, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
+}
+
+evis_status evis_set_defocus(evis_ctx *c, const float *sigma_px) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  bool any = false;
+  for (int i = 0; sigma_px && i < c->n; ++i) {
+    if (!defocus_sigma_ok(sigma_px[i]))
+      return fail(c, EVIS_ERR_INVALID_ARG, "defocus sigma must be in 0..8 pixels");
+    any |= sigma_px[i] > 0.0f;
+  }
+  if (any && c->mode == EVIS_IN_LOG)
+    return fail(c, EVIS_ERR_INVALID_ARG, "defocus acts on linear intensity: needs EVIS_IN_LUM or EVIS_IN_RGB");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const int taps = 2 * evis::kMaxBlurR + 1;
+  if (any && !c->d_blur) {
+    if ((e = dalloc(c, &c->d_blur, c->total)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_blur_w, static_cast<int64_t>(taps) * c->n)) != cudaSuccess)
+      return cuda_fail(c, e, "alloc defocus buffers");
+  }
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "defocus sync");
+  drop_graphs(c);
+  std::vector<float> w(static_cast<size_t>(taps) * c->n, 0.0f);
+  int rmax = -1;
+  for (int i = 0; i < c->n; ++i) {
+    const float sg = sigma_px ? sigma_px[i] : 0.0f;
+    DevEnv &v = c->h_envs[i];
+    v.blur_r = defocus_weights(sg, w.data() + static_cast<size_t>(taps) * i);
+    v.blur_off = taps * i;
+    rmax = std::max(rmax, v.blur_r);
+  }
+  if (any && (e = cudaMemcpy(c->d_blur_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "upload defocus weights");
+  if ((e = cudaMemcpy(c->d_envs, c->h_envs.data(), sizeof(DevEnv) * c->n, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(c, e, "upload defocus radii");
+  c->blur_r_max = any ? rmax : -1;
+  return EVIS_OK;
 }
 
 evis_status evis_set_noise(evis_ctx *c, const evis_noise_desc *nz) {

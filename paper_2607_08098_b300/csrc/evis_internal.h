@@ -34,6 +34,7 @@ struct DevEnv {
   float noise_lo, noise_hi;         // log-intensity range of the normalised intensity
   uint32_t key0, key1;              // Philox key: seed low word, seed high word ^ env
   int32_t noise, pad1;
+  int32_t blur_r, blur_off;         // defocus radius and first weight in the weight table
 };
 
 // One target tile: environment and top-left pixel.
@@ -84,7 +85,24 @@ struct PrepArgs {
   int max_segs;                  // largest environment (row segments)
 };
 
+constexpr int kMaxBlurR = 24;                 // defocus radius limit (sigma <= 8 px)
+
+// Arguments of the defocus kernel (Sec. 3.4): blurred linear luminance of every environment,
+// or of one plane when envs is null (then W, H, r, w describe it).
+struct BlurArgs {
+  const DevEnv *envs;
+  const float *wtab;            // weights of all environments, each at its blur_off
+  int W, H, r;                  // the single-plane form
+  float w[2 * kMaxBlurR + 1];
+  const float *in;              // packed frames: luminance, or RGB triples
+  float *out;                   // packed blurred luminance
+  uint32_t mode;                // EVIS_IN_LUM or EVIS_IN_RGB
+  int max_r;                    // largest radius of the launch (sizes shared memory)
+};
+
 cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);
+// max_tiles: the largest environment's count of 32 x 8 tiles
+cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStream_t s);
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
 // grid_cap > 0: persistent launch of at most grid_cap x (resident CTAs) blocks that take
 // tiles from a.work_counter; 0: one block per tile.

@@ -777,6 +777,66 @@ __global__ void prep_kernel(const PrepArgs a) {
   }
 }
 
+// Defocus (Sec. 3.4): separable Gaussian on linear luminance.  One CTA per 32 x 8 output
+// tile (grid-stride over an environment's tiles, blockIdx.y = environment): the tile and a
+// halo of r pixels (edge pixels repeated) are loaded as luminance into shared memory, the
+// horizontal pass writes (8 + 2r) x 32 sums, the vertical pass the 32 x 8 outputs.  Each
+// sum runs over k = -r..r in order in binary32, as the definition states.
+constexpr int kBlurTX = 32, kBlurTY = 8;
+
+__global__ void __launch_bounds__(kBlurTX * kBlurTY) defocus_kernel(const BlurArgs a) {
+  extern __shared__ float blur_sm[];
+  __shared__ float sw[2 * kMaxBlurR + 1];
+  int W, H, r;
+  int64_t o = 0;
+  if (a.envs) {
+    const DevEnv &E = a.envs[blockIdx.y];
+    W = E.W;
+    H = E.H;
+    r = E.blur_r;
+    o = E.pix_off;
+    for (int i = threadIdx.x; i <= 2 * r; i += blockDim.x) sw[i] = a.wtab[E.blur_off + i];
+  } else {
+    W = a.W;
+    H = a.H;
+    r = a.r;
+    for (int i = threadIdx.x; i <= 2 * r; i += blockDim.x) sw[i] = a.w[i];
+  }
+  __syncthreads();
+  const int AW = kBlurTX + 2 * r, AH = kBlurTY + 2 * r;
+  float *A = blur_sm;            // [AH][AW] luminance with halo
+  float *B = blur_sm + AH * AW;  // [AH][32] horizontal sums
+  const int tiles_x = (W + kBlurTX - 1) / kBlurTX;
+  const int n_t = tiles_x * ((H + kBlurTY - 1) / kBlurTY);
+  for (int t = blockIdx.x; t < n_t; t += gridDim.x) {
+    const int x0 = (t % tiles_x) * kBlurTX, y0 = (t / tiles_x) * kBlurTY;
+    for (int i = threadIdx.x; i < AH * AW; i += blockDim.x) {
+      const int ry = i / AW, rx = i - ry * AW;
+      const int ys = min(max(y0 - r + ry, 0), H - 1), xs = min(max(x0 - r + rx, 0), W - 1);
+      const int64_t p = o + static_cast<int64_t>(ys) * W + xs;
+      A[i] = a.mode == EVIS_IN_RGB ? rec709(a.in[3 * p], a.in[3 * p + 1], a.in[3 * p + 2]) : a.in[p];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < AH * kBlurTX; i += blockDim.x) {
+      const int ry = i / kBlurTX, cx = i - ry * kBlurTX;
+      float acc = 0.0f;
+      for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], A[ry * AW + cx + k]));
+      B[i] = acc;
+    }
+    __syncthreads();
+    {
+      const int cx = threadIdx.x % kBlurTX, row = threadIdx.x / kBlurTX;
+      const int x = x0 + cx, y = y0 + row;
+      if (x < W && y < H) {
+        float acc = 0.0f;
+        for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], B[(row + k) * kBlurTX + cx]));
+        a.out[o + static_cast<int64_t>(y) * W + x] = acc;
+      }
+    }
+    __syncthreads();  // A and B are reused by the next tile
+  }
+}
+
 __global__ void init_ref_kernel(const float *__restrict__ L, float *__restrict__ Lref, int64_t n) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -806,6 +866,20 @@ cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s) {
   int bx = (a.max_segs + 4 * (threads / 32) - 1) / (4 * (threads / 32));
   if (bx < 1) bx = 1;
   prep_kernel<<<dim3(bx, n_envs), threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStream_t s) {
+  if (a.max_r < 0 || a.max_r > kMaxBlurR || n_envs < 1 || max_tiles < 1) return cudaErrorInvalidValue;
+  const int R = a.max_r;
+  const size_t smem = sizeof(float) * static_cast<size_t>(kBlurTY + 2 * R) * (kBlurTX + 2 * R + kBlurTX);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  // about eight CTAs per SM over the whole launch, at least one per environment
+  const int gx = max(1, min(max_tiles, (8 * sms + n_envs - 1) / n_envs));
+  defocus_kernel<<<dim3(gx, n_envs), kBlurTX * kBlurTY, smem, s>>>(a);
   return cudaGetLastError();
 }
 
