@@ -400,8 +400,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   unsigned hot = 0;
   if (noisy && E.hot_hz > 0.0f) {
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const unsigned pix = static_cast<unsigned>((ty0 + ROWS * j) * W + tx);
+    for (int j = 0; j < NT; ++j) {  // counters use the sensor pixel index (inside the margin)
+      const unsigned pix = static_cast<unsigned>((ty0 + ROWS * j - E.margin) * (W - 2 * E.margin) +
+                                                 (tx - E.margin));
       if (act[j] && fires(philox4x32_10(make_uint4(pix, 0xFFFFFFFFu, 0u, 2u), E.key0, E.key1).x,
                           E.hot_fraction))
         hot |= 1u << j;
