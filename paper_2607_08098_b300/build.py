@@ -31,29 +31,51 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def _headers():
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    return hs + [os.path.join(INCLUDE, "evis.h")]
+
+
+def _newest(paths) -> float:
+    return max(os.path.getmtime(p) for p in paths)
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
-    t = os.path.getmtime(LIB)
-    deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
-    deps.append(os.path.join(INCLUDE, "evis.h"))
-    return any(os.path.getmtime(d) > t for d in deps)
+    return _newest(sources() + _headers()) > os.path.getmtime(LIB)
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libevis.so (static CUDA runtime)."""
+    """Compile every .cu under csrc/ (in parallel; an object is rebuilt when its source or
+    any header is newer) and link libevis.so (static CUDA runtime)."""
     if not force and not _stale():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     os.makedirs(BUILD, exist_ok=True)
-    objs = []
     cc = nvcc()
+    hdr_t = _newest(_headers())
+    jobs, objs = [], []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [cc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
+        objs.append(obj)
+        if force or ptxas_info or not os.path.exists(obj) or \
+                os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_t):
+            cmd = [cc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
+            jobs.append(cmd)
+
+    def run(cmd):
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
-        objs.append(obj)
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    workers = max(1, min(len(jobs), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        results = list(pool.map(run, jobs))
+    for cmd, r in zip(jobs, results):
+        sys.stderr.write(r.stderr if (verbose or ptxas_info or r.returncode) else "")
+        if r.returncode:
+            raise subprocess.CalledProcessError(r.returncode, cmd, r.stdout, r.stderr)
     tmp = LIB + ".tmp"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     subprocess.check_call(cmd)

@@ -1,9 +1,26 @@
-// Device helpers shared by the event path and the soft-count surrogate of libevis.
+// Device helpers shared by the kernels of libevis (event path, preparation, surrogate).
 #pragma once
+
+#include <cfloat>
 
 #include <cuda_runtime.h>
 
 namespace evis {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;  // all lanes of a warp
+
+// L = log(I + eps), Sec. 3.2; non-positive or NaN arguments clamp to the smallest normal.
+__device__ __forceinline__ float log_intensity(float I, float eps) {
+  float s = __fadd_rn(I, eps);
+  if (!(s > 0.0f)) s = FLT_MIN;
+  return logf(s);
+}
+
+// Rec. 709 luminance, Eq. 3: ((0.2126 R + 0.7152 G) + 0.0722 B), each product rounded.
+__device__ __forceinline__ float rec709(float R, float G, float B) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, R), __fmul_rn(0.7152f, G)),
+                   __fmul_rn(0.0722f, B));
+}
 
 // A source splats iff its depth is finite and > 0.
 __device__ __forceinline__ bool valid_depth(float z) { return z > 0.0f && z < INFINITY; }

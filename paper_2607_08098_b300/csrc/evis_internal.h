@@ -104,6 +104,11 @@ cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);
 // max_tiles: the largest environment's count of 32 x 8 tiles
 cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStream_t s);
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
+// One tile shape and variant of the synthesis kernel (defined in evis_step.cuh and
+// instantiated in the evis_step_*.cu translation units).
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s);
+
 // grid_cap > 0: persistent launch of at most grid_cap x (resident CTAs) blocks that take
 // tiles from a.work_counter; 0: one block per tile.
 cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, int grid_cap,

@@ -1,0 +1,716 @@
+// The synthesis kernel of the EVIS event path (sm_103a), as templates: the translation
+// units evis_step_*.cu instantiate its variants (tile shapes, trace, noise), so that they
+// compile in parallel.
+//
+// Compiled with -fmad=false and written with explicit round-to-nearest intrinsics so that
+// every floating-point step that decides a z-buffer winner or an event count is the same
+// single IEEE-754 binary32 operation, in the same order, as in the method's definition:
+// splat winners, event counts, pixels and polarities are then reproducible bit for bit on
+// any IEEE host.
+//
+// step_kernel: per keyframe gap: one CTA owns a TX x TY target tile of one environment
+//   and keeps, for all K sub-frames, its pixels' event state in registers.
+//   Once per gap it lists the row segments whose motion bounds let them reach
+//   the tile; per sub-frame all threads re-test the listed segments at once,
+//   and each warp splats the sources of one reaching segment of A (forward)
+//   or B (backward) into two shared-memory
+//   z-buffers with 64-bit atomicMin on (depth, weight, source) keys
+//   (Eqs. 5-7).  It then resolves the winners,
+//   blends in time with hole filling, runs the event model (Eq. 4, Eq. 8,
+//   refractory period) and compacts the events: a warp-wide reservation per
+//   crossing index in a shared staging buffer, one global atomic per CTA per
+//   sub-frame and a coalesced 16-byte-per-thread flush.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "evis_device.cuh"
+#include "evis_internal.h"
+
+namespace evis {
+namespace {
+
+// floor(v) of |v| < 2^22 without a conversion instruction: adding 1.5 * 2^23 with rounding
+// toward -infinity lands on the integer grid (ulp 1), whose low significand bits hold the
+// integer.  *fv receives floor(v) as a float (exact).
+__device__ __forceinline__ int floor_small(float v, float *fv) {
+  const float t = __fadd_rd(v, 12582912.0f);
+  *fv = __fsub_rn(t, 12582912.0f);
+  return __float_as_int(t) - 0x4B400000;
+}
+
+// (float)i for 0 <= i < 2^23 without a conversion instruction.
+__device__ __forceinline__ float small_int_to_float(int i) {
+  return __fsub_rn(__int_as_float(0x4B000000 + i), 8388608.0f);
+}
+
+// Splat of one source into the tile's z-buffer (Sec. 3.3).  Direction 0 moves a source of A
+// forward to q = p - f m_A with depth (1-f) Z_A(p) + f Z_B(p - m_A); direction 1 moves a source
+// of B backward to q = p + (1-f) m_B with depth (1-f) Z_A(p + m_B) + f Z_B(p) (Eqs. 5, 7).
+// Every integer pixel of the bilinear footprint of q with weight > 0, inside the image and
+// inside the tile, keeps the minimum key [depth bits | quantised (1 - w) | source index]
+// (Eq. 6).  PACKED reads (mx, my, Z, Z at the other endpoint) prepared once per keyframe gap;
+// otherwise the motion and depth maps are read and the other endpoint's depth is gathered
+// for sources that reach the tile.
+template <int TX, int TY, bool PACKED>
+__device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, int sx, int sy,
+                                             float fx, float fy, int W, int H, int x0, int y0,
+                                             float f, float g, const StepArgs &a, int64_t o) {
+  const int p = sy * W + sx;
+  float mx, my, zs, zo = 0.0f;
+  if (PACKED) {
+    const float4 v = __ldg((dir ? a.packB : a.packA) + o + p);
+    mx = v.x;
+    my = v.y;
+    zs = v.z;
+    zo = v.w;
+    if (!valid_depth(zs)) return;
+  } else {
+    zs = __ldg((dir ? a.ZB : a.ZA) + o + p);
+    if (!valid_depth(zs)) return;
+    const float2 m = __ldg(reinterpret_cast<const float2 *>(dir ? a.mvB : a.mvA) + o + p);
+    mx = m.x;
+    my = m.y;
+  }
+  float qx, qy;
+  if (dir == 0) {
+    qx = __fsub_rn(fx, __fmul_rn(f, mx));
+    qy = __fsub_rn(fy, __fmul_rn(f, my));
+  } else {
+    qx = __fadd_rn(fx, __fmul_rn(g, mx));
+    qy = __fadd_rn(fy, __fmul_rn(g, my));
+  }
+  // No footprint pixel can be inside unless -1 < q < size; this also rejects NaN.
+  if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H)))
+    return;
+  float fx0, fy0;
+  const int lx0 = floor_small(qx, &fx0) - x0, ly0 = floor_small(qy, &fy0) - y0;
+  if (lx0 < -1 || lx0 >= TX || ly0 < -1 || ly0 >= TY) return;
+  if (!PACKED) {
+    zo = dir == 0 ? other_depth(a.ZB + o, W, H, __fsub_rn(fx, mx), __fsub_rn(fy, my), zs)
+                  : other_depth(a.ZA + o, W, H, __fadd_rn(fx, mx), __fadd_rn(fy, my), zs);
+  }
+  const float zt = dir == 0 ? __fadd_rn(__fmul_rn(g, zs), __fmul_rn(f, zo))
+                            : __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zs));
+  const float ax = __fsub_rn(qx, fx0), ay = __fsub_rn(qy, fy0);
+  const float wx[2] = {__fsub_rn(1.0f, ax), ax};
+  const float wy[2] = {__fsub_rn(1.0f, ay), ay};
+  const unsigned long long hi = (static_cast<unsigned long long>(__float_as_uint(zt)) << 32) |
+                                static_cast<unsigned>(p);
+  const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy) {
+    const int ly = ly0 + dy;
+    if (ly < 0 || ly >= TY || y0 + ly >= H) continue;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const int lx = lx0 + dx;
+      if (lx < 0 || lx >= TX || x0 + lx >= W) continue;
+      const float w = __fmul_rn(wx[dx], wy[dy]);
+      if (!(w > 0.0f)) continue;
+      unsigned wq = 0;
+      if (!tie_index) {
+        float unused;  // truncation of (1 - w) * 256 in [0, 256]
+        wq = min(static_cast<unsigned>(floor_small(__fmul_rn(__fsub_rn(1.0f, w), 256.0f), &unused)), 255u);
+      }
+      atomicMin(&zb[ly * TX + lx], hi | (static_cast<unsigned long long>(wq) << 24));
+    }
+  }
+}
+
+// True when no source of a row segment [xs, xs+31] x {ys}, displaced by an amount in
+// [dxl, dxh] x [dyl, dyh], can put a footprint pixel into the TX x TY tile at (x0, y0).  The
+// 2-pixel margin covers the footprint (1 pixel) and the rounding of the exact target
+// computation; NaN bounds never count as a miss.
+template <int TX, int TY>
+__device__ __forceinline__ bool seg_misses(float xs, float ys, float dxl, float dxh, float dyl,
+                                           float dyh, int x0, int y0) {
+  return (xs + 31.0f + dxh + 2.0f < static_cast<float>(x0)) ||
+         (xs + dxl - 2.0f > static_cast<float>(x0 + TX - 1)) ||
+         (ys + dyh + 2.0f < static_cast<float>(y0)) ||
+         (ys + dyl - 2.0f > static_cast<float>(y0 + TY - 1));
+}
+
+// t_prev + llrint(fr * (t_i - t_prev)) with the product taken in binary64 and rounded half to
+// even.  When t_i - t_prev < 2^29 the binary64 product of the binary32 fraction (24-bit
+// significand) and the interval is exact, so the same integer is obtained with a 64-bit
+// integer multiply, a shift and a round-half-even on the discarded bits.  Longer intervals
+// take the binary64 route.
+__device__ __forceinline__ int64_t interp_time(float fr, int64_t tprev, int64_t ti) {
+  const int64_t d = ti - tprev;
+  if (d < (int64_t(1) << 29)) {
+    const unsigned b = __float_as_uint(fr);          // fr in [0, 1]
+    const unsigned ex = b >> 23;
+    const unsigned m = ex ? ((b & 0x7FFFFFu) | 0x800000u) : (b & 0x7FFFFFu);
+    const int sh = ex ? 150 - static_cast<int>(ex) : 149;   // fr = m * 2^-sh, sh >= 23
+    const unsigned long long P = static_cast<unsigned long long>(m) *
+                                 static_cast<unsigned>(d);   // 24 x 29 bits: < 2^53
+    if (sh >= 64) return tprev;                      // fr * d < 2^-11
+    unsigned long long q = P >> sh;
+    const unsigned long long r = P & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (r > half || (r == half && (q & 1ull))) ++q;
+    return tprev + static_cast<int64_t>(q);
+  }
+  return tprev + __double2ll_rn(__dmul_rn(static_cast<double>(fr), static_cast<double>(d)));
+}
+
+// Time of the k-th crossing of a pixel in this sub-frame: the level Lref + p k theta,
+// interpolated linearly between the previous sample (tprev, Lprev) and this one (ti, L).
+__device__ __forceinline__ int64_t crossing_time(float Lref, float pk, float th, float Lprev,
+                                                 float L, int64_t tprev, int64_t ti) {
+  const float lev = __fadd_rn(Lref, __fmul_rn(pk, th));
+  const float num = __fsub_rn(lev, Lprev);
+  const float den = __fsub_rn(L, Lprev);
+  float fr = den == 0.0f ? 1.0f : __fdiv_rn(num, den);
+  if (!(fr > 0.0f)) fr = 0.0f;
+  else if (fr > 1.0f) fr = 1.0f;
+  return interp_time(fr, tprev, ti);
+}
+
+__device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int env, int p) {
+  ulonglong2 r;
+  r.x = static_cast<unsigned long long>(t);
+  r.y = static_cast<unsigned long long>(x & 0xFFFF) |
+        (static_cast<unsigned long long>(y & 0xFFFF) << 16) |
+        (static_cast<unsigned long long>(env & 0xFFFF) << 32) |
+        (static_cast<unsigned long long>(static_cast<uint16_t>(static_cast<int16_t>(p))) << 48);
+  return r;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC 2011): ten rounds, each two 32 x 32 -> 64-bit products of the counter's even words
+// mixed into the odd words with the round key; the key advances by the Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Bernoulli draw with probability q from a 32-bit uniform word (24 bits, binary32 compare).
+__device__ __forceinline__ bool fires(unsigned u, float q) {
+  return __uint2float_rn(u >> 8) < __fmul_rn(q, 16777216.0f);
+}
+
+// t0 + floor(u d / 2^32) for d < 2^41: the product split at bit 32 of d.
+__device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d) {
+  const unsigned long long du = static_cast<unsigned long long>(d);
+  const unsigned long long lo = (static_cast<unsigned long long>(u) * (du & 0xFFFFFFFFull)) >> 32;
+  return t0 + static_cast<int64_t>(static_cast<unsigned long long>(u) * (du >> 32) + lo);
+}
+
+// Dynamic shared memory of one step CTA.
+template <int TX, int TY>
+struct StepSmem {
+  unsigned long long zb[2][TX * TY];       // z-buffers, A forward and B backward
+  ulonglong2 stage[kEventStage];           // events of this sub-frame before the flush
+  uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
+                                           // (min dx, max dx), (min dy, max dy) rounded outward
+  unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
+  unsigned short hit[2][2 * kCandidates];  // candidates reaching the tile, by sub-frame parity
+  int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
+  unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
+};
+
+// Resident CTAs per SM each tile shape is compiled for (bounded by its shared memory); it
+// sets the register budget.
+template <int TX, int TY>
+constexpr int step_min_blocks() {
+  return TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3);
+}
+
+// Stages the records of the warp's lanes that have emit set (the warp is converged): one
+// shared-memory reservation per warp; past the stage's capacity, one global reservation.
+template <int TX, int TY>
+__device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, const StepArgs &a,
+                                           bool emit, const ulonglong2 &rec, unsigned lanes_below,
+                                           int lane) {
+  const unsigned m = __ballot_sync(kFull, emit);
+  if (m == 0) return;
+  const unsigned cnt = static_cast<unsigned>(__popc(m));
+  unsigned base = 0;
+  unsigned long long gb = 0;
+  if (lane == 0) {
+    base = atomicAdd(s_n, cnt);
+    if (base + cnt > static_cast<unsigned>(kEventStage))
+      gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
+                                     base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+  }
+  base = __shfl_sync(kFull, base, 0);
+  gb = __shfl_sync(kFull, gb, 0);
+  if (emit) {
+    const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
+    if (idx < static_cast<unsigned>(kEventStage)) {
+      S.stage[idx] = rec;
+    } else {
+      const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
+      if (gi < a.capacity) a.events[gi] = rec;
+    }
+  }
+}
+
+// All K sub-frames of one target tile (the body of step_kernel).  NOISE compiles the sensor
+// noise of Sec. 3.4 in (environments with it off skip it at run time).
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+__device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
+  constexpr int NT = TX * TY / kThreads;   // targets per thread
+  constexpr int NW = kThreads / 32;
+  constexpr int ROWS = kThreads / TX;      // tile rows covered by one pass of the block
+  static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
+  __shared__ unsigned s_n, s_flush, s_nhit[2], s_arrive;
+  __shared__ unsigned long long s_base;
+  __shared__ int s_nc[2], s_over;
+
+  const DevEnv E = a.envs[tl.env];
+  const int W = E.W, H = E.H, K = E.K;
+  const int64_t o = E.pix_off;
+  const float *__restrict__ LA = a.LA + o;
+  const float *__restrict__ LB = a.LB + o;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lanes_below = (1u << lane) - 1u;
+  const float lane_f = small_int_to_float(lane);
+  const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
+  const bool joint = (a.flags & EVIS_MODE_JOINT) != 0;
+  const int64_t T0 = a.clock_in[tl.env];
+  const int64_t refr = E.refractory_ns;
+  const int tx = tl.x0 + tid % TX;
+  const int ty0 = tl.y0 + tid / TX;
+  const int64_t HW = static_cast<int64_t>(W) * H;
+
+  // per-pixel event state of this thread's targets (rows ty0 + ROWS j), in registers for
+  // the whole keyframe gap
+  float Lref[NT], Lprev[NT], thon[NT], thoff[NT];
+  int64_t tprev[NT], tlast[NT];
+  bool act[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int ty = ty0 + ROWS * j;
+    const int pix = ty * W + tx;
+    act[j] = tx < W - E.margin && ty < H - E.margin;  // tiles start inside the margin
+    tprev[j] = T0;
+    tlast[j] = kNoEvent;
+    Lref[j] = 0.0f;
+    Lprev[j] = 0.0f;
+    thon[j] = E.c_on;
+    thoff[j] = E.c_off;
+    if (act[j]) {
+      Lref[j] = a.Lref[o + pix];
+      Lprev[j] = LA[pix];
+      if (a.tlast) tlast[j] = a.tlast[o + pix];
+      if (E.con_map) {
+        thon[j] = E.con_map[pix];
+        thoff[j] = E.coff_map[pix];
+      }
+    }
+  }
+
+  // Sources that can reach the tile lie within the largest |mv| (+ footprint) of it.
+  const float mf = fmaxf(a.flowA[tl.env], a.flowB[tl.env]);
+  const int h = mf < 65536.0f ? static_cast<int>(ceilf(mf)) + 2 : 65536;
+  const int sx0 = max(0, tl.x0 - h), sx1 = min(W, tl.x0 + TX + h);
+  const int sy0 = max(0, tl.y0 - h), sy1 = min(H, tl.y0 + TY + h);
+  if (tid == 0) {
+    s_n = 0;
+    s_flush = 0;
+    s_base = 0;
+    s_nhit[0] = s_nhit[1] = 0;
+    s_arrive = 0;
+    s_nc[0] = s_nc[1] = 0;
+    s_over = 0;
+  }
+  // z-buffers start empty; afterwards each thread clears its own slots once it has read them
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    S.zb[0][tid + kThreads * j] = kEmptyKey;
+    S.zb[1][tid + kThreads * j] = kEmptyKey;
+  }
+  __syncthreads();
+
+  // Candidate row segments for this keyframe gap: those whose motion bounds let them reach
+  // the tile at some f in [0, 1].  A full list falls back to scanning the whole region.
+  {
+    const int cx_lo = sx0 / kSegW, cx_hi = (sx1 - 1) / kSegW;
+    const int ncx = cx_hi - cx_lo + 1;
+    const int nreg = ncx * (sy1 - sy0);
+    for (int r = tid; r < 2 * nreg; r += kThreads) {
+      const int dir = r >= nreg ? 1 : 0;
+      const int rr = r - dir * nreg;
+      const int row = rr / ncx;
+      const int cy = sy0 + row, cx = cx_lo + (rr - row * ncx);
+      const float4 b = (dir ? a.segB : a.segA)[E.seg_off + static_cast<int64_t>(cy) * E.segs_x + cx];
+      if (!(b.x <= b.y)) continue;  // no source of this segment can splat
+      float dxl, dxh, dyl, dyh;     // displacement range over f in [0, 1]
+      if (dir == 0) {
+        dxl = fminf(0.0f, -b.y); dxh = fmaxf(0.0f, -b.x);
+        dyl = fminf(0.0f, -b.w); dyh = fmaxf(0.0f, -b.z);
+      } else {
+        dxl = fminf(0.0f, b.x); dxh = fmaxf(0.0f, b.y);
+        dyl = fminf(0.0f, b.z); dyh = fmaxf(0.0f, b.w);
+      }
+      if (seg_misses<TX, TY>(static_cast<float>(cx * kSegW), static_cast<float>(cy), dxl, dxh,
+                             dyl, dyh, tl.x0, tl.y0))
+        continue;
+      const int pos = atomicAdd(&s_nc[dir], 1);
+      if (pos < kCandidates) {
+        S.cand_xy[dir][pos] = (static_cast<unsigned>(cy) << 16) | static_cast<unsigned>(cx);
+        // outward rounding keeps the bounds conservative (overflow goes to +-inf)
+        const __half2 bx = __halves2half2(__float2half_rd(b.x), __float2half_ru(b.y));
+        const __half2 by = __halves2half2(__float2half_rd(b.z), __float2half_ru(b.w));
+        S.cand_b[dir][pos] = make_uint2(*reinterpret_cast<const unsigned *>(&bx),
+                                        *reinterpret_cast<const unsigned *>(&by));
+      } else {
+        s_over = 1;
+      }
+    }
+  }
+  __syncthreads();
+  const bool over = s_over != 0;
+  const int nA = min(s_nc[0], kCandidates);
+  const int nAB = nA + min(s_nc[1], kCandidates);
+  // t_i = T0 + floor(i dt / K), stepped with a quotient and a remainder
+  const int64_t dq = a.dt / K, dr = a.dt % K;
+  int64_t tq = 0, trem = 0;
+  // noise: this gap's counter and the hot pixels among this thread's targets (bit j)
+  const bool noisy = NOISE && E.noise != 0;
+  const unsigned gap = noisy ? a.gap_in[tl.env] : 0u;
+  unsigned hot = 0;
+  if (noisy && E.hot_hz > 0.0f) {
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {  // counters use the sensor pixel index (inside the margin)
+      const unsigned pix = static_cast<unsigned>((ty0 + ROWS * j - E.margin) * (W - 2 * E.margin) +
+                                                 (tx - E.margin));
+      if (act[j] && fires(philox4x32_10(make_uint4(pix, 0xFFFFFFFFu, 0u, 2u), E.key0, E.key1).x,
+                          E.hot_fraction))
+        hot |= 1u << j;
+    }
+  }
+
+  for (int i = 1; i <= K; ++i) {
+    const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
+    const float g = __fsub_rn(1.0f, f);
+    const int64_t tim1 = T0 + tq;  // t_{i-1}
+    tq += dq;
+    trem += dr;
+    if (trem >= K) {
+      trem -= K;
+      ++tq;
+    }
+    const int64_t ti = T0 + tq;
+
+    // Two barriers per sub-frame.  Phase 1 (list reaching candidates) may overlap other
+    // warps' phase 3 of the previous sub-frame; the hit list is double-buffered by parity.
+    const int par = i & 1;
+    // ---- phase 1: list the candidate segments that reach the tile at this f ----
+    if (!over) {
+      for (int c0 = 0; c0 < nAB; c0 += kThreads) {
+        const int c = c0 + tid;
+        bool hit = false;
+        if (c < nAB) {
+          const int dir = c >= nA ? 1 : 0;
+          const int idx = c - dir * nA;
+          const uint2 hb = S.cand_b[dir][idx];
+          const float2 bx = __half22float2(*reinterpret_cast<const __half2 *>(&hb.x));
+          const float2 by = __half22float2(*reinterpret_cast<const __half2 *>(&hb.y));
+          const float4 b = make_float4(bx.x, bx.y, by.x, by.y);
+          const unsigned xy = S.cand_xy[dir][idx];
+          float dxl, dxh, dyl, dyh;
+          if (dir == 0) {
+            dxl = -f * b.y; dxh = -f * b.x; dyl = -f * b.w; dyh = -f * b.z;
+          } else {
+            dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
+          }
+          hit = !seg_misses<TX, TY>(small_int_to_float(static_cast<int>(xy & 0xFFFFu) * kSegW),
+                                    small_int_to_float(static_cast<int>(xy >> 16)), dxl, dxh,
+                                    dyl, dyh, tl.x0, tl.y0);
+        }
+        const unsigned m = __ballot_sync(kFull, hit);
+        if (m) {
+          unsigned base = 0;
+          if (lane == 0) base = atomicAdd(&s_nhit[par], static_cast<unsigned>(__popc(m)));
+          base = __shfl_sync(kFull, base, 0);
+          if (hit) S.hit[par][base + __popc(m & lanes_below)] = static_cast<unsigned short>(c);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 2: flush the previous sub-frame's staged events (reserved by the last warp
+    // to finish it), then splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
+    if (tid == 0) s_nhit[par ^ 1] = 0;
+    {
+      const unsigned nf = s_flush;
+      const unsigned long long gbs = s_base;
+      for (unsigned r = tid; r < nf; r += kThreads) {
+        const unsigned long long gi = gbs + r;
+        if (gi < a.capacity) a.events[gi] = S.stage[r];
+      }
+    }
+    if (!over) {
+      const unsigned nh = s_nhit[par];
+      for (unsigned hh = warp; hh < nh; hh += NW) {  // one warp per segment, one lane per source
+        const int c = static_cast<int>(S.hit[par][hh]);
+        const int dir = c >= nA ? 1 : 0;
+        const unsigned xy = S.cand_xy[dir][c - dir * nA];
+        const int xs = static_cast<int>(xy & 0xFFFFu) * kSegW, sy = static_cast<int>(xy >> 16);
+        const int sx = xs + lane;
+        if (sx < W)
+          splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy,
+                                       __fadd_rn(small_int_to_float(xs), lane_f),
+                                       small_int_to_float(sy), W, H, tl.x0, tl.y0, f, g, a, o);
+      }
+    } else {
+      for (int sy = sy0 + warp; sy < sy1; sy += NW) {
+        const float fy = small_int_to_float(sy);
+        for (int sx = sx0 + lane; sx < sx1; sx += 32) {
+          const float fx = small_int_to_float(sx);
+          splat_source<TX, TY, PACKED>(S.zb[0], 0, sx, sy, fx, fy, W, H, tl.x0, tl.y0, f, g, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[1], 1, sx, sy, fx, fy, W, H, tl.x0, tl.y0, f, g, a, o);
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 3: resolve, blend, threshold crossings, emission ----
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int ty = ty0 + ROWS * j;
+      const int pix = ty * W + tx;
+      bool has = false;
+      float L = 0.0f, th = thon[j], nf = 0.0f;
+      int n = 0, pol = 1;
+      if (act[j]) {
+        const unsigned long long kA = S.zb[0][tid + kThreads * j];
+        const unsigned long long kB = S.zb[1][tid + kThreads * j];
+        S.zb[0][tid + kThreads * j] = kEmptyKey;  // ready for the next sub-frame
+        S.zb[1][tid + kThreads * j] = kEmptyKey;
+        const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
+        const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
+        const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
+        if (joint) {  // Eq. 6: the nearer winner; equal depths go to B
+          L = (hasA && hasB) ? ((kA >> 32) < (kB >> 32) ? la : lb)
+                             : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+        } else if (b_primary) {
+          L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
+        } else {
+          L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))
+                             : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+        }
+        if (TRACE) {
+          const int64_t kb = a.tr_koff[tl.env] + static_cast<int64_t>(i - 1) * 2 * HW + pix;
+          a.tr_keys[kb] = kA;
+          a.tr_keys[kb + HW] = kB;
+          a.tr_L[a.tr_loff[tl.env] + static_cast<int64_t>(i - 1) * HW + pix] = L;
+        }
+        has = hasA || hasB;  // no sample: the pixel holds its state this sub-frame
+        if (has) {
+          const float d = __fsub_rn(L, Lref[j]);
+          pol = d > 0.0f ? 1 : -1;
+          th = pol > 0 ? thon[j] : thoff[j];
+          const float q = __fdiv_rn(fabsf(d), th);
+          if (q >= 1.0f) {
+            if (q >= static_cast<float>(kMaxCrossings)) {
+              n = kMaxCrossings;
+              nf = static_cast<float>(kMaxCrossings);
+            } else {
+              n = floor_small(q, &nf);
+            }
+          }
+        }
+      }
+      // ---- crossings k = 1..n of the warp's 32 pixels, spread over its lanes ----
+      // Item c of the warp (pixels in lane order, k ascending) is computed by lane c % 32.
+      int incl = n;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += v;
+      }
+      const int total = __shfl_sync(kFull, incl, 31);
+      const int excl = incl - n;
+      for (int c0 = 0; c0 < total; c0 += 32) {
+        const int c = c0 + lane;
+        // owner = number of lanes whose items all lie before c
+        int own = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+          const int v = __shfl_sync(kFull, incl, own + st - 1);
+          if (v <= c) own += st;
+        }
+        own = min(own, 31);
+        const int k = c - __shfl_sync(kFull, excl, own) + 1;
+        const float oL = __shfl_sync(kFull, L, own);
+        const float oLref = __shfl_sync(kFull, Lref[j], own);
+        const float oLprev = __shfl_sync(kFull, Lprev[j], own);
+        const float oth = __shfl_sync(kFull, th, own);
+        const int opol = __shfl_sync(kFull, pol, own);
+        const int64_t otprev = __shfl_sync(kFull, tprev[j], own);
+        int64_t t = 0;
+        if (c < total) {
+          const float kf = small_int_to_float(k);
+          t = crossing_time(oLref, opol > 0 ? kf : -kf, oth, oLprev, oL, otprev, ti);
+        }
+        bool emit = c < total;
+        if (a.tlast) {
+          // refractory filter (Sec. 3.4) in order along each pixel's crossings: each owner
+          // walks its items of this chunk; t_last carries over to the next chunk
+          S.rt[warp][lane] = t;
+          __syncwarp();
+          const int lo = max(excl, c0), hi = min(incl, c0 + 32);
+          for (int cc = lo; cc < hi; ++cc) {
+            const int64_t tt = S.rt[warp][cc - c0];
+            const bool keep = refr <= 0 || tlast[j] == kNoEvent || tt - tlast[j] >= refr;
+            if (keep) tlast[j] = tt;
+            S.rkeep[warp][cc - c0] = keep ? 1 : 0;
+          }
+          __syncwarp();
+          emit = emit && S.rkeep[warp][lane] != 0;
+        }
+        const unsigned m = __ballot_sync(kFull, emit);
+        if (m == 0) continue;
+        const unsigned cnt = static_cast<unsigned>(__popc(m));
+        unsigned base = 0;
+        unsigned long long gb = 0;
+        if (lane == 0) {
+          base = atomicAdd(&s_n, cnt);
+          if (base + cnt > static_cast<unsigned>(kEventStage))  // staging full: go global
+            gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
+                                           base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+        }
+        base = __shfl_sync(kFull, base, 0);
+        gb = __shfl_sync(kFull, gb, 0);
+        if (emit) {
+          const int otid = warp * 32 + own;
+          const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
+          const ulonglong2 rec = make_event(t, tl.x0 - E.margin + otid % TX,
+                                            tl.y0 - E.margin + otid / TX + ROWS * j, tl.env, opol);
+          if (idx < static_cast<unsigned>(kEventStage)) {
+            S.stage[idx] = rec;
+          } else {
+            const unsigned long long gi =
+                gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
+            if (gi < a.capacity) a.events[gi] = rec;
+          }
+        }
+        __syncwarp();  // the next chunk reuses this warp's refractory scratch
+      }
+      if (noisy) {  // leak, shot and hot-pixel events of this target (Sec. 3.4)
+        const int64_t d = ti - tim1;
+        const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
+        const int ex = tx - E.margin, ey = ty - E.margin;  // sensor coordinates
+        const unsigned npix = static_cast<unsigned>(ey * (W - 2 * E.margin) + ex);
+        bool fl = false, fs = false, fh = false;
+        if (act[j]) {
+          const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 0u), E.key0, E.key1);
+          fl = E.leak_hz > 0.0f && fires(r.x, __fmul_rn(E.leak_hz, dts));
+          if (E.shot_hz > 0.0f && has) {
+            float ib = __fdiv_rn(__fsub_rn(L, E.noise_lo), __fsub_rn(E.noise_hi, E.noise_lo));
+            ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
+            fs = fires(r.y, __fmul_rn(__fmul_rn(E.shot_hz, dts), __fsub_rn(1.0f, ib)));
+          }
+          fh = ((hot >> j) & 1u) && fires(r.z, __fmul_rn(E.hot_hz, dts));
+        }
+        if (__any_sync(kFull, fl || fs || fh)) {
+          uint4 rt = make_uint4(0u, 0u, 0u, 0u);
+          if (fl || fs || fh)
+            rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u), E.key0, E.key1);
+          stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, 1),
+                     lanes_below, lane);
+          stage_warp(S, &s_n, a, fs,
+                     make_event(noise_time(rt.y, tim1, d), ex, ey, tl.env, (rt.w & 1u) ? 1 : -1),
+                     lanes_below, lane);
+          stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, 1),
+                     lanes_below, lane);
+        }
+      }
+      if (has) {
+        if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(pol > 0 ? nf : -nf, th));
+        Lprev[j] = L;
+        tprev[j] = ti;
+      }
+    }
+    // ---- end of phase 3: the last warp to finish reserves the global range of this
+    // sub-frame's staged events (one atomic per CTA); they are copied out in phase 2 of the
+    // next sub-frame, or after the loop ----
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&s_arrive, 1u) == static_cast<unsigned>(NW - 1)) {
+        const unsigned nn = min(s_n, static_cast<unsigned>(kEventStage));
+        s_flush = nn;
+        s_base = nn ? atomicAdd(a.ev_count, static_cast<unsigned long long>(nn)) : 0ull;
+        s_n = 0;
+        s_arrive = 0;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    const unsigned nf = s_flush;
+    const unsigned long long gbs = s_base;
+    for (unsigned r = tid; r < nf; r += kThreads) {
+      const unsigned long long gi = gbs + r;
+      if (gi < a.capacity) a.events[gi] = S.stage[r];
+    }
+  }
+
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    if (!act[j]) continue;
+    const int pix = (ty0 + ROWS * j) * W + tx;
+    a.Lref[o + pix] = Lref[j];
+    if (a.tlast) a.tlast[o + pix] = tlast[j];
+  }
+  if (tid == 0 && tl.x0 == E.margin && tl.y0 == E.margin) {  // the environment's first tile
+    a.clock_out[tl.env] = T0 + a.dt;
+    if (a.gap_out) a.gap_out[tl.env] = a.gap_in[tl.env] + 1u;
+  }
+}
+
+// One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
+// first one by block index, the next ones from a work counter that starts at 0.
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
+  __shared__ int s_tile;
+  int t = blockIdx.x;
+  while (t < a.n_tiles) {
+    run_tile<TX, TY, TRACE, PACKED, NOISE>(a, a.tiles[t]);
+    __syncthreads();  // the tile's shared memory is free again
+    if (threadIdx.x == 0) s_tile = static_cast<int>(gridDim.x + atomicAdd(a.work_counter, 1u));
+    __syncthreads();
+    t = s_tile;
+  }
+}
+
+}  // namespace
+
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
+  static int resident = 0;  // CTAs per SM x SMs, looked up once per instantiation
+  const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
+  if (!resident) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE>, kThreads, smem)) != cudaSuccess)
+      return e;
+    resident = max(1, per_sm) * sms;
+  }
+  int grid = n_tiles;
+  if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
+  step_kernel<TX, TY, TRACE, PACKED, NOISE><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace evis

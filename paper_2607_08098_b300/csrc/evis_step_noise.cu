@@ -1,0 +1,12 @@
+// Explicit instantiations of the synthesis kernel: production variants with sensor noise, every tile shape.
+#include "evis_step.cuh"
+
+namespace evis {
+
+template cudaError_t launch_shape<32, 16, false, true, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, false, true, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, false, true, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, false, true, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, false, true, true>(const StepArgs &, int, int, cudaStream_t);
+
+}  // namespace evis
