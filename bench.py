@@ -210,7 +210,7 @@ def traffic_record():
     source was committed (profiles/step_kernel_traffic.json), else None."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2607_08098_b300", "csrc", "evis_kernels.cu")
+    src = os.path.join(ROOT, "paper_2607_08098_b300", "csrc", "evis_step.cuh")
     try:
         rec = json.load(open(p))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()

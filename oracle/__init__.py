@@ -24,6 +24,7 @@ IN_LOG, IN_LUM, IN_RGB = 0, 1, 2
 MODE_B_PRIMARY = 0x10
 TIE_INDEX = 0x20
 MODE_JOINT = 0x40
+COLOR = 0x200          # Sec. 3.2: events of the R, G and B channels (polarity field +-(1 + c))
 
 EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2"), ("p", "<i2")])
 
@@ -133,6 +134,7 @@ class Oracle:
         if not self._h:
             raise ValueError("oracle rejected the environment table")
         self.envs = list(envs)
+        self.nc = 3 if flags & COLOR else 1   # planes of L, Lref and t_last
         self.total = 0
         self.offsets = []
         for e in envs:
@@ -146,7 +148,7 @@ class Oracle:
 
     def trace_sizes(self):
         nk = sum(e.K * 2 * e.H * e.W for e in self.envs)
-        nl = sum(e.K * e.H * e.W for e in self.envs)
+        nl = sum(e.K * self.nc * e.H * e.W for e in self.envs)
         return nk, nl
 
     def step(self, frames, mv, depth, dt_ns: int, trace: bool = False):
@@ -196,8 +198,8 @@ class Oracle:
             raise ValueError("oracle rejected the defocus parameters")
 
     def state(self):
-        Lref = np.empty(self.total, dtype=np.float32)
-        tl = np.empty(self.total, dtype=np.int64)
+        Lref = np.empty(self.nc * self.total, dtype=np.float32)
+        tl = np.empty(self.nc * self.total, dtype=np.int64)
         clk = np.empty(len(self.envs), dtype=np.int64)
         _lib.orc_get_state(self._h, _ptr(Lref), _ptr(tl), _ptr(clk))
         return Lref, tl, clk

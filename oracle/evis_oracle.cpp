@@ -29,6 +29,7 @@ constexpr uint32_t IN_MASK = 0x3u, IN_LOG = 0u, IN_LUM = 1u, IN_RGB = 2u;
 constexpr uint32_t MODE_B_PRIMARY = 0x10u;  // Sec. 3.3: B primary, A only fills B's holes
 constexpr uint32_t MODE_JOINT = 0x40u;      // Eq. 6: one argmin of depth over both directions
 constexpr uint32_t TIE_INDEX = 0x20u;       // key = (depth, source index), no weight field
+constexpr uint32_t COLOR = 0x200u;          // Sec. 3.2: the event model on R, G and B apart
 
 constexpr uint64_t EMPTY = ~0ull;
 constexpr int MAX_CROSSINGS = 4096;          // per pixel per substep
@@ -65,10 +66,12 @@ struct Ctx {
   int64_t total = 0;
   float eps = 1e-4f;
   uint32_t flags = 0;
+  int nc = 1;                              // event channels: 1, or 3 (R, G, B) in colour mode
   bool have_A = false;
   std::vector<float> LA, mvA, ZA;          // retained keyframe A (Sec. 3.3 needs A and B)
-  std::vector<float> Lref;                 // per-pixel reference level (Sec. 3.2)
-  std::vector<int64_t> t_last;             // last emitted event time (refractory, Sec. 3.4)
+  std::vector<float> Lref;                 // per channel and pixel: reference level (Sec. 3.2)
+  std::vector<int64_t> t_last;             // per channel and pixel: last event time (Sec. 3.4)
+  // L, Lref and t_last hold nc planes of `total` values each (channel c at c * total)
   std::vector<float> con, coff;            // per-pixel thresholds (Eq. 8), if any env has them
   std::vector<int64_t> clock;              // time of keyframe A per env
   std::vector<Event> events;
@@ -184,7 +187,7 @@ void splat_B(uint64_t* zbuf, int W, int H, const float* mvB, const float* ZA, co
 // Sec. 3.2, with the per-pixel thresholds of Eq. 8 and the refractory period of Sec. 3.4).
 // Each crossed level Lref + p k theta is timestamped by linear interpolation between the
 // previous defined sample (t_prev, L_prev) and this one (t_i, L).
-void cross_pixel(Ctx& c, int env, int x, int y, float L, float& Lref, float& Lprev,
+void cross_pixel(Ctx& c, int env, int x, int y, int ch, float L, float& Lref, float& Lprev,
                  int64_t& tprev, int64_t ti, int64_t& tlast, float th_on, float th_off,
                  int64_t refr) {
   float d = L - Lref;
@@ -205,7 +208,7 @@ void cross_pixel(Ctx& c, int env, int x, int y, float L, float& Lref, float& Lpr
     int64_t t = tprev + std::llrint(static_cast<double>(fr) * static_cast<double>(ti - tprev));
     if (refr <= 0 || tlast == NO_EVENT || t - tlast >= refr) {
       c.events.push_back(Event{t, static_cast<uint16_t>(x), static_cast<uint16_t>(y),
-                               static_cast<uint16_t>(env), static_cast<int16_t>(pol)});
+                               static_cast<uint16_t>(env), static_cast<int16_t>(pol * (1 + ch))});
       tlast = t;
     }
   }
@@ -238,17 +241,20 @@ void philox4x32_10(uint32_t ctr[4], uint32_t k0, uint32_t k1) {
 // Bernoulli draw with probability p from a 32-bit uniform (24 bits used, binary32 compare).
 inline bool fires(uint32_t u, float p) { return static_cast<float>(u >> 8) < p * 16777216.0f; }
 
-// Leak, shot and hot-pixel events of one pixel in sub-frame i (Sec. 3.4).  Each fires at
-// most once per sub-frame with the stated probability over the interval [t0, t1); its time
-// is uniform in the interval.  Noise events bypass the refractory filter and leave the
-// reference level untouched.  Shot noise needs the sub-frame's sample (has).
-void noise_pixel(Ctx& c, int env, int x, int y, uint32_t pix, uint32_t i, int64_t t0, int64_t t1,
-                 bool has, float L) {
+// Leak, shot and hot-pixel events of one pixel (and channel ch) in sub-frame i (Sec. 3.4).
+// Each fires at most once per sub-frame with the stated probability over the interval
+// [t0, t1); its time is uniform in the interval.  Noise events bypass the refractory filter
+// and leave the reference level untouched.  Shot noise needs the sub-frame's sample (has).
+// Channels draw independent streams: the last counter word is stream + 4 ch.
+void noise_pixel(Ctx& c, int env, int x, int y, int ch, uint32_t pix, uint32_t i, int64_t t0,
+                 int64_t t1, bool has, float L) {
   const Noise& nz = c.noise[env];
   if (!(nz.leak_hz > 0.0f || nz.shot_hz > 0.0f || nz.hot_hz > 0.0f)) return;
   const uint32_t k0 = static_cast<uint32_t>(nz.seed);
   const uint32_t k1 = static_cast<uint32_t>(nz.seed >> 32) ^ static_cast<uint32_t>(env);
-  uint32_t r[4] = {pix, c.gap, i, 0u}, rt[4] = {pix, c.gap, i, 1u}, rh[4] = {pix, 0xFFFFFFFFu, 0u, 2u};
+  const uint32_t cw = 4u * static_cast<uint32_t>(ch);
+  uint32_t r[4] = {pix, c.gap, i, cw}, rt[4] = {pix, c.gap, i, 1u + cw},
+           rh[4] = {pix, 0xFFFFFFFFu, 0u, 2u + cw};
   philox4x32_10(r, k0, k1);
   philox4x32_10(rt, k0, k1);
   philox4x32_10(rh, k0, k1);
@@ -259,7 +265,7 @@ void noise_pixel(Ctx& c, int env, int x, int y, uint32_t pix, uint32_t i, int64_
   };
   auto emit = [&](int64_t t, int p) {
     c.events.push_back(Event{t, static_cast<uint16_t>(x), static_cast<uint16_t>(y),
-                             static_cast<uint16_t>(env), static_cast<int16_t>(p)});
+                             static_cast<uint16_t>(env), static_cast<int16_t>(p * (1 + ch))});
   };
   if (nz.leak_hz > 0.0f && fires(r[0], nz.leak_hz * dts)) emit(at(rt[0]), 1);
   if (nz.shot_hz > 0.0f && has) {
@@ -273,25 +279,26 @@ void noise_pixel(Ctx& c, int env, int x, int y, uint32_t pix, uint32_t i, int64_
 
 // One keyframe gap of one environment: K substeps f = i/K (Sec. 3.3), each a bidirectional
 // splat, a time blend with hole filling, and the event model.  Optional trace outputs:
-// keys[(i-1)*2 + dir][p] and Lint[(i-1)][p] (NaN where the pixel got no sample).
+// keys[(i-1)*2 + dir][p] and Lint[(i-1)*nc + channel][p] (NaN where the pixel got no sample).
 void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB, int64_t dt,
               uint64_t* keys, float* Lint) {
   const Env& en = c.envs[e];
   const int W = en.W, H = en.H, K = en.K;
   const size_t HW = static_cast<size_t>(W) * H;
   const size_t o = static_cast<size_t>(c.off[e]);
-  const float* LA = c.LA.data() + o;
+  const size_t plane = static_cast<size_t>(c.total);  // channel stride of L, Lref, t_last
+  const int nc = c.nc;
   const float* mvA = c.mvA.data() + 2 * o;
   const float* ZA = c.ZA.data() + o;
-  float* Lref = c.Lref.data() + o;
-  int64_t* tlast = c.t_last.data() + o;
   const int64_t T0 = c.clock[e];
   const bool tie_index = (c.flags & TIE_INDEX) != 0;
   const bool b_primary = (c.flags & MODE_B_PRIMARY) != 0;
   const bool joint = (c.flags & MODE_JOINT) != 0;
 
-  std::vector<float> Lprev(LA, LA + HW);
-  std::vector<int64_t> tprev(HW, T0);
+  std::vector<float> Lprev(nc * HW);
+  for (int ch = 0; ch < nc; ++ch)
+    std::copy(c.LA.data() + ch * plane + o, c.LA.data() + ch * plane + o + HW, Lprev.begin() + ch * HW);
+  std::vector<int64_t> tprev(nc * HW, T0);
   std::vector<uint64_t> zA(HW), zB(HW);
   for (int i = 1; i <= K; ++i) {
     float f = static_cast<float>(i) / static_cast<float>(K);
@@ -313,36 +320,42 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
         size_t t = static_cast<size_t>(y) * W + x;
         const int sx = x - m, sy = y - m;
         bool hasA = zA[t] != EMPTY, hasB = zB[t] != EMPTY;
-        float la = hasA ? LA[zA[t] & 0xFFFFFFu] : 0.0f;
-        float lb = hasB ? LB[zB[t] & 0xFFFFFFu] : 0.0f;
-        float L;
-        if (joint) {      // Eq. 6: the nearer of the two winners; equal depths go to B
-          const uint32_t za = static_cast<uint32_t>(zA[t] >> 32), zb2 = static_cast<uint32_t>(zB[t] >> 32);
-          if (hasA && hasB) L = za < zb2 ? la : lb;
-          else if (hasA) L = la;
-          else if (hasB) L = lb;
-          else L = NAN;
-        } else if (b_primary) {  // Sec. 3.3: backward-warped B is primary, A fills B's holes
-          if (hasB) L = lb;
-          else if (hasA) L = la;
-          else L = NAN;
-        } else {          // time blend of both directions, hole filled from the other one
-          if (hasA && hasB) L = g * la + f * lb;
-          else if (hasA) L = la;
-          else if (hasB) L = lb;
-          else L = NAN;
+        // one set of winners serves every channel (it depends on motion and depth only)
+        for (int ch = 0; ch < nc; ++ch) {
+          const float* LAc = c.LA.data() + ch * plane + o;
+          const float* LBc = LB + ch * plane;
+          float la = hasA ? LAc[zA[t] & 0xFFFFFFu] : 0.0f;
+          float lb = hasB ? LBc[zB[t] & 0xFFFFFFu] : 0.0f;
+          float L;
+          if (joint) {      // Eq. 6: the nearer of the two winners; equal depths go to B
+            const uint32_t za = static_cast<uint32_t>(zA[t] >> 32), zb2 = static_cast<uint32_t>(zB[t] >> 32);
+            if (hasA && hasB) L = za < zb2 ? la : lb;
+            else if (hasA) L = la;
+            else if (hasB) L = lb;
+            else L = NAN;
+          } else if (b_primary) {  // Sec. 3.3: backward-warped B is primary, A fills B's holes
+            if (hasB) L = lb;
+            else if (hasA) L = la;
+            else L = NAN;
+          } else {          // time blend of both directions, hole filled from the other one
+            if (hasA && hasB) L = g * la + f * lb;
+            else if (hasA) L = la;
+            else if (hasB) L = lb;
+            else L = NAN;
+          }
+          if (Lint) Lint[(static_cast<size_t>(i - 1) * nc + ch) * HW + t] = L;
+          noise_pixel(c, e, sx, sy, ch, static_cast<uint32_t>(sy * SW + sx), static_cast<uint32_t>(i),
+                      T0 + (static_cast<int64_t>(i - 1) * dt) / K, ti, hasA || hasB, L);
+          if (!hasA && !hasB) continue;  // no sample this substep: the pixel holds its state
+          float th_on = en.c_on, th_off = en.c_off;
+          if (en.has_map) {  // one threshold map for all channels
+            th_on = c.con[o + t];
+            th_off = c.coff[o + t];
+          }
+          cross_pixel(c, e, sx, sy, ch, L, c.Lref[ch * plane + o + t], Lprev[ch * HW + t],
+                      tprev[ch * HW + t], ti, c.t_last[ch * plane + o + t], th_on, th_off,
+                      en.refractory_ns);
         }
-        if (Lint) Lint[static_cast<size_t>(i - 1) * HW + t] = L;
-        noise_pixel(c, e, sx, sy, static_cast<uint32_t>(sy * SW + sx), static_cast<uint32_t>(i),
-                    T0 + (static_cast<int64_t>(i - 1) * dt) / K, ti, hasA || hasB, L);
-        if (!hasA && !hasB) continue;  // no sample this substep: the pixel holds its state
-        float th_on = en.c_on, th_off = en.c_off;
-        if (en.has_map) {
-          th_on = c.con[o + t];
-          th_off = c.coff[o + t];
-        }
-        cross_pixel(c, e, sx, sy, L, Lref[t], Lprev[t], tprev[t], ti, tlast[t], th_on, th_off,
-                    en.refractory_ns);
       }
     }
   }
@@ -393,25 +406,33 @@ void defocus_plane(const float* in, int W, int H, float sigma, float* out) {
     }
 }
 
+// Log-intensity planes of a keyframe (Sec. 3.2, Eq. 3): one plane (log of the luminance, or
+// the given log-intensity), or in colour mode the R, G and B planes (log of each channel, or
+// the given planar log-intensities).  Defocus blurs the linear plane before the log.
 void to_log(const Ctx& c, const float* frames, std::vector<float>& L) {
-  L.assign(c.total, 0.0f);
+  const size_t plane = static_cast<size_t>(c.total);
+  L.assign(c.nc * plane, 0.0f);
   uint32_t mode = c.flags & IN_MASK;
   for (size_t e = 0; e < c.envs.size(); ++e) {
     size_t o = static_cast<size_t>(c.off[e]);
     size_t n = static_cast<size_t>(c.envs[e].W) * c.envs[e].H;
-    if (mode != IN_LOG && c.defocus[e] > 0.0f) {  // luminance, blur, then the log
-      std::vector<float> I(n), B(n);
-      for (size_t p = 0; p < n; ++p)
-        I[p] = mode == IN_LUM ? frames[o + p]
-                              : rec709(frames[3 * (o + p)], frames[3 * (o + p) + 1], frames[3 * (o + p) + 2]);
-      defocus_plane(I.data(), c.envs[e].W, c.envs[e].H, c.defocus[e], B.data());
-      for (size_t p = 0; p < n; ++p) L[o + p] = log_intensity(B[p], c.eps);
-      continue;
-    }
-    for (size_t p = o; p < o + n; ++p) {
-      if (mode == IN_LOG) L[p] = frames[p];
-      else if (mode == IN_LUM) L[p] = log_intensity(frames[p], c.eps);
-      else L[p] = log_intensity(rec709(frames[3 * p], frames[3 * p + 1], frames[3 * p + 2]), c.eps);
+    for (int ch = 0; ch < c.nc; ++ch) {
+      float* Lc = L.data() + ch * plane + o;
+      if (mode == IN_LOG) {
+        std::copy(frames + ch * plane + o, frames + ch * plane + o + n, Lc);
+        continue;
+      }
+      std::vector<float> I(n);  // the linear plane
+      for (size_t p = 0; p < n; ++p) {
+        const float* px = frames + 3 * (o + p);
+        I[p] = mode == IN_LUM ? frames[o + p] : (c.nc == 3 ? px[ch] : rec709(px[0], px[1], px[2]));
+      }
+      if (c.defocus[e] > 0.0f) {
+        std::vector<float> B(n);
+        defocus_plane(I.data(), c.envs[e].W, c.envs[e].H, c.defocus[e], B.data());
+        I.swap(B);
+      }
+      for (size_t p = 0; p < n; ++p) Lc[p] = log_intensity(I[p], c.eps);
     }
   }
 }
@@ -435,9 +456,11 @@ void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags)
   if (!envs || n_envs <= 0 || n_envs > 65536 || !(eps >= 0.0f)) return nullptr;
   if ((flags & IN_MASK) == 3u) return nullptr;
   if ((flags & MODE_JOINT) && (flags & MODE_B_PRIMARY)) return nullptr;
+  if ((flags & COLOR) && (flags & IN_MASK) == IN_LUM) return nullptr;  // colour needs RGB or planes
   Ctx* c = new Ctx();
   c->eps = eps;
   c->flags = flags;
+  c->nc = (flags & COLOR) ? 3 : 1;
   bool any_map = false;
   for (int i = 0; i < n_envs; ++i) {
     const orc_env& d = envs[i];
@@ -467,8 +490,8 @@ void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags)
   }
   c->noise.assign(n_envs, Noise{0, 0, 0, 0, 0, 1, 0});
   c->defocus.assign(n_envs, 0.0f);
-  c->Lref.assign(c->total, 0.0f);
-  c->t_last.assign(c->total, NO_EVENT);
+  c->Lref.assign(c->nc * c->total, 0.0f);
+  c->t_last.assign(c->nc * c->total, NO_EVENT);
   for (int i = 0; i < n_envs; ++i) c->clock.push_back(envs[i].t0_ns);
   return c;
 }
@@ -500,7 +523,7 @@ int32_t orc_step(void* h, const float* frames, const float* mv, const float* dep
     run_pair(c, static_cast<int>(e), LB.data() + o, mv + 2 * o, depth + o, dt_ns,
              trace_keys ? trace_keys + tk : nullptr, trace_L ? trace_L + tl : nullptr);
     tk += static_cast<size_t>(c.envs[e].K) * 2 * HW;
-    tl += static_cast<size_t>(c.envs[e].K) * HW;
+    tl += static_cast<size_t>(c.envs[e].K) * c.nc * HW;
     c.clock[e] += dt_ns;
   }
   ++c.gap;

@@ -175,3 +175,113 @@ def test_defocus_parameters_are_checked(oracle_mod):
     with pytest.raises(ValueError):
         oracle_mod.Oracle([env], flags=1).set_defocus([float("nan")])
     oracle_mod.Oracle([env], flags=0).set_defocus([0.0])
+
+
+# ---- colour events (Sec. 3.2): the event model on each of R, G and B ----
+
+def _tinted(scenes_mod, W, H, K, seed, refractory_ns=30_000):
+    env = _scene(scenes_mod, W, H, K, seed, refractory_ns=refractory_ns)
+    rng = np.random.default_rng(seed + 100)
+    for lay in env.layers:
+        lay.tint_r, lay.tint_g, lay.tint_b = rng.uniform(0.3, 1.6, 3)
+    return env
+
+
+def _colour_vs_mono(oracle_mod, envs, kfs, dt, noise=None, sigma=None):
+    col = oracle_mod.Oracle(envs, flags=oracle_mod.IN_RGB | oracle_mod.COLOR)
+    if noise is not None:
+        col.set_noise(noise)
+    if sigma is not None:
+        col.set_defocus(sigma)
+    monos = []
+    for c in range(3):
+        m = oracle_mod.Oracle(envs, flags=oracle_mod.IN_LUM)
+        if noise is not None:
+            m.set_noise(noise)
+        if sigma is not None:
+            m.set_defocus(sigma)
+        monos.append(m)
+    for kf in kfs:
+        rgb = kf.rgb.reshape(-1, 3)
+        col.step(rgb.reshape(-1), kf.mv, kf.Z, dt)
+        for c, m in enumerate(monos):
+            m.step(np.ascontiguousarray(rgb[:, c]), kf.mv, kf.Z, dt)
+    return col, monos
+
+
+def test_colour_is_three_independent_event_models(oracle_mod, scenes_mod):
+    """Sec. 3.2: replacing I by each of R, G and B and running the event model on each gives
+    colour events.  Channel c of a colour run is a luminance run fed channel c, with the
+    polarity field carrying +-(1 + c); reference levels and refractory times per channel."""
+    env = _tinted(scenes_mod, 52, 40, 5, seed=12)
+    kfs = [scenes_mod.render([env], k, want=("rgb", "mv", "Z")) for k in range(4)]
+    col, monos = _colour_vs_mono(oracle_mod, [env], kfs, 16_666_667)
+    ec = oracle_mod.sort_events(col.events())
+    sc = col.state()
+    n = col.total
+    counts = []
+    for c, m in enumerate(monos):
+        mine = ec[np.abs(ec["p"]) == c + 1].copy()
+        mine["p"] = np.sign(mine["p"])
+        want = oracle_mod.sort_events(m.events())
+        counts.append(len(want))
+        np.testing.assert_array_equal(mine.view(np.uint8), want.view(np.uint8))
+        sm = m.state()
+        np.testing.assert_array_equal(sc[0][c * n:(c + 1) * n], sm[0])
+        np.testing.assert_array_equal(sc[1][c * n:(c + 1) * n], sm[1])
+    assert min(counts) > 100 and len(set(counts)) == 3     # the tints make the channels differ
+    assert len(ec) == sum(counts)
+
+
+def test_colour_noise_defocus_and_planar_log(oracle_mod, scenes_mod):
+    """Channel 0 draws the luminance run's noise; channels 1 and 2 draw their own streams.
+    Defocus blurs each channel.  Planar log-intensity input equals linear RGB input."""
+    env = _tinted(scenes_mod, 40, 30, 4, seed=13, refractory_ns=0)
+    kfs = [scenes_mod.render([env], k, want=("rgb", "mv", "Z")) for k in range(3)]
+    noise = [dict(leak_hz=40.0, hot_hz=300.0, hot_fraction=0.05, shot_hz=60.0, seed=5)]
+    col, monos = _colour_vs_mono(oracle_mod, [env], kfs, 16_666_667, noise=noise, sigma=[0.7])
+    ec = oracle_mod.sort_events(col.events())
+    per = []
+    for c, m in enumerate(monos):
+        mine = ec[np.abs(ec["p"]) == c + 1].copy()
+        mine["p"] = np.sign(mine["p"])
+        want = oracle_mod.sort_events(m.events())
+        per.append((mine, want))
+    np.testing.assert_array_equal(per[0][0].view(np.uint8), per[0][1].view(np.uint8))
+    for c in (1, 2):
+        assert not np.array_equal(per[c][0].view(np.uint8), per[c][1].view(np.uint8))
+    # planar log input: the same stream as the RGB run without noise or defocus
+    a = oracle_mod.Oracle([env], flags=oracle_mod.IN_RGB | oracle_mod.COLOR)
+    b = oracle_mod.Oracle([env], flags=oracle_mod.IN_LOG | oracle_mod.COLOR)
+    n = (env.W * env.H + 3) // 4 * 4
+    for kf in kfs:
+        rgb = kf.rgb.reshape(-1, 3)
+        a.step(rgb.reshape(-1), kf.mv, kf.Z, 16_666_667)
+        planes = np.concatenate([oracle_mod.log_intensity(np.ascontiguousarray(rgb[:, c]), mode=1,
+                                                          eps=1e-4) for c in range(3)])
+        assert planes.size == 3 * n
+        b.step(planes, kf.mv, kf.Z, 16_666_667)
+    ea, eb = oracle_mod.sort_events(a.events()), oracle_mod.sort_events(b.events())
+    assert len(ea) > 100
+    np.testing.assert_array_equal(ea.view(np.uint8), eb.view(np.uint8))
+
+
+def test_colour_grey_scene_gives_equal_channels(oracle_mod, scenes_mod):
+    env = _scene(scenes_mod, 36, 28, 4, seed=14)
+    kfs = [scenes_mod.render([env], k, want=("rgb", "mv", "Z")) for k in range(3)]
+    o = oracle_mod.Oracle([env], flags=oracle_mod.IN_RGB | oracle_mod.COLOR)
+    for kf in kfs:
+        rgb = kf.rgb.reshape(-1, 3)
+        grey = np.repeat(rgb[:, 1:2], 3, axis=1)
+        o.step(grey.reshape(-1), kf.mv, kf.Z, 16_666_667)
+    e = oracle_mod.sort_events(o.events())
+    chans = []
+    for c in range(3):
+        x = e[np.abs(e["p"]) == c + 1].copy()
+        x["p"] = np.sign(x["p"])
+        chans.append(x)
+    assert len(chans[0]) > 100
+    for c in (1, 2):
+        np.testing.assert_array_equal(chans[c].view(np.uint8), chans[0].view(np.uint8))
+    with pytest.raises(ValueError):
+        oracle_mod.Oracle([env], flags=oracle_mod.IN_LUM | oracle_mod.COLOR)
