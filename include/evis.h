@@ -79,6 +79,16 @@ typedef struct {
  * frames) alive and unmodified until the next evis_step has completed on the stream, so the
  * library reads them in place instead of keeping its own copy. */
 #define EVIS_KEEP_INPUTS 0x100u
+/* Colour events (Sec. 3.2): the event model runs on the R, G and B log intensities
+ * independently, over one set of warp winners (they depend on motion and depth only).
+ * Frames are linear RGB triples (EVIS_IN_RGB, [total][3], L_c = log(c + eps)) or three
+ * log-intensity planes (EVIS_IN_LOG, [3][total]: R, G, B); EVIS_IN_LUM is rejected.  An
+ * event's polarity field is +-(1 + c), c = 0, 1, 2 for R, G, B.  Reference levels and
+ * refractory times are kept per channel: the per-pixel state arrays of evis_get_state hold
+ * three planes [3][total], and the traced log-intensity is [K][3][H*W] per environment.
+ * Threshold maps serve all channels; each channel draws its own noise streams (the last
+ * counter word is stream + 4 c); defocus blurs each channel. */
+#define EVIS_COLOR 0x200u
 
 typedef struct {
   int32_t width, height; /* rendered frame, 1..65535 each, width * height <= 2^24 */
@@ -97,7 +107,8 @@ typedef struct {
 
 typedef struct {
   float eps;              /* added before the log (Sec. 3.2), finite and >= 0 */
-  uint32_t flags;         /* EVIS_IN_* | EVIS_MODE_* (one) | EVIS_TIE_* | EVIS_KEEP_INPUTS */
+  uint32_t flags;         /* EVIS_IN_* | EVIS_MODE_* (one) | EVIS_TIE_* | EVIS_KEEP_INPUTS |
+                           * EVIS_COLOR */
   int64_t event_capacity; /* events the device buffer holds between two reads, >= 1 */
 } evis_config;
 

@@ -19,6 +19,7 @@ IN_LOG, IN_LUM, IN_RGB = 0x0, 0x1, 0x2
 MODE_BLEND, MODE_B_PRIMARY, MODE_JOINT = 0x0, 0x10, 0x40
 TIE_WEIGHT, TIE_INDEX = 0x0, 0x20
 KEEP_INPUTS = 0x100
+COLOR = 0x200   # R, G, B events (Sec. 3.2); polarity field +-(1 + channel)
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_STATE, ERR_TIMEOUT = range(7)
 
@@ -181,7 +182,8 @@ class Context:
         n = ctypes.c_int64()
         _check(L.evis_total_pixels(self._h, ctypes.byref(n)), self._h)
         self.total = n.value
-        self.n_frame = self.total * (3 if (self.flags & 0x3) == IN_RGB else 1)
+        self.nc = 3 if self.flags & COLOR else 1
+        self.n_frame = self.total * (3 if ((self.flags & 0x3) == IN_RGB or self.nc == 3) else 1)
 
     @property
     def handle(self):
@@ -217,7 +219,7 @@ class Context:
         import torch
         self._check_inputs(frames, mv, depth)
         nk = sum(e.K * 2 * e.H * e.W for e in self.envs)
-        nl = sum(e.K * e.H * e.W for e in self.envs)
+        nl = sum(e.K * self.nc * e.H * e.W for e in self.envs)
         keys = torch.empty(nk, dtype=torch.int64, device=frames.device)
         lint = torch.empty(nl, dtype=torch.float32, device=frames.device)
         _check(lib().evis_step_trace(self._h, _ptr(frames), _ptr(mv), _ptr(depth), int(dt_ns),
@@ -357,8 +359,9 @@ class Context:
         return buf[:2 * n.value].reshape(-1, 2)
 
     def state(self):
-        Lref = np.empty(self.total, dtype=np.float32)
-        tl = np.empty(self.total, dtype=np.int64)
+        """(Lref, t_last, clocks); Lref and t_last hold nc planes of total pixels."""
+        Lref = np.empty(self.nc * self.total, dtype=np.float32)
+        tl = np.empty(self.nc * self.total, dtype=np.int64)
         clk = np.empty(len(self.envs), dtype=np.int64)
         _check(lib().evis_get_state(self._h, Lref.ctypes.data, tl.ctypes.data, clk.ctypes.data),
                self._h)

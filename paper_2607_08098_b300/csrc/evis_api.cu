@@ -19,6 +19,7 @@ struct evis_ctx {
   uint32_t mode = 0;
   bool keep = false;
   bool need_L = false;     // library holds converted / copied log-intensity slots
+  int nc = 1;              // event channels: 3 in colour mode (L, Lref, t_last hold nc planes)
   int n = 0;
   std::vector<evis_env_desc> envs;
   std::vector<int64_t> off;
@@ -104,8 +105,11 @@ std::string validate(const evis_env_desc *envs, int32_t n, const evis_config *cf
   if (!cfg) return "cfg is null";
   if (n < 1 || n > 65535) return "n_envs must be in 1..65535";
   if (!std::isfinite(cfg->eps) || cfg->eps < 0.0f) return "eps must be finite and >= 0";
-  const uint32_t known = 0x3u | EVIS_MODE_B_PRIMARY | EVIS_MODE_JOINT | EVIS_TIE_INDEX | EVIS_KEEP_INPUTS;
+  const uint32_t known = 0x3u | EVIS_MODE_B_PRIMARY | EVIS_MODE_JOINT | EVIS_TIE_INDEX |
+                         EVIS_KEEP_INPUTS | EVIS_COLOR;
   if (cfg->flags & ~known) return "unknown flag bits";
+  if ((cfg->flags & EVIS_COLOR) && (cfg->flags & 0x3u) == EVIS_IN_LUM)
+    return "EVIS_COLOR needs EVIS_IN_RGB (linear RGB) or EVIS_IN_LOG (three log-intensity planes)";
   if ((cfg->flags & EVIS_MODE_B_PRIMARY) && (cfg->flags & EVIS_MODE_JOINT))
     return "EVIS_MODE_B_PRIMARY and EVIS_MODE_JOINT exclude each other";
   if ((cfg->flags & 0x3u) == 0x3u) return "invalid input mode";
@@ -238,6 +242,8 @@ cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, cons
     ba.in = frames;
     ba.out = c->d_blur;
     ba.mode = c->mode;
+    ba.nc = c->nc;
+    ba.plane = c->total;
     ba.max_r = c->blur_r_max;
     int max_t = 1;
     for (const evis_env_desc &d : c->envs) max_t = std::max(max_t, ((d.width + 31) / 32) * ((d.height + 7) / 8));
@@ -261,6 +267,8 @@ cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, cons
   pa.packB = c->d_pack[1];
   pa.eps = c->cfg.eps;
   pa.mode = mode;
+  pa.nc = c->nc;
+  pa.plane = c->total;
   pa.max_segs = c->max_segs;
   if ((e = evis::launch_prep(pa, c->n, c->stream)) != cudaSuccess) return e;
   out->L = c->need_L ? c->d_L[b] : frames;
@@ -298,6 +306,8 @@ evis::StepArgs step_args(const evis_ctx *c, const KeyframeB &B, int64_t dt) {
   s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
   s.dt = dt;
   s.flags = c->cfg.flags;
+  s.nc = c->nc;
+  s.plane = c->total;
   s.tr_koff = c->d_tr_off;
   s.tr_loff = c->d_tr_off + c->n;
   return s;
@@ -325,7 +335,7 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
       return cuda_fail(c, e, "step kernel");
     c->clk ^= 1;
   } else {
-    e = evis::launch_init_ref(B.L, c->d_Lref, c->total, c->stream);
+    e = evis::launch_init_ref(B.L, c->d_Lref, c->nc * c->total, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->have_A = true;
   }
@@ -343,7 +353,7 @@ evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const flo
 // Library-owned input buffers (two sets, alternating per keyframe), allocated once.
 cudaError_t ensure_inputs(evis_ctx *c) {
   if (c->d_in[0][0]) return cudaSuccess;
-  const size_t fw = c->mode == EVIS_IN_RGB ? 3 : 1;
+  const size_t fw = (c->mode == EVIS_IN_RGB || c->nc == 3) ? 3 : 1;
   cudaError_t e;
   for (int s = 0; s < 2; ++s) {
     if ((e = dalloc(c, &c->d_in[s][0], fw * c->total)) != cudaSuccess ||
@@ -379,6 +389,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   c->stream = reinterpret_cast<cudaStream_t>(stream);
   c->cfg = *cfg;
   c->mode = cfg->flags & 0x3u;
+  c->nc = (cfg->flags & EVIS_COLOR) ? 3 : 1;
   c->keep = (cfg->flags & EVIS_KEEP_INPUTS) != 0;
   c->need_L = c->mode != EVIS_IN_LOG || !c->keep;
   c->n = n_envs;
@@ -412,7 +423,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     troff[i] = ko;
     troff[n_envs + i] = lo;
     ko += int64_t(d.K) * 2 * px;
-    lo += int64_t(d.K) * px;
+    lo += int64_t(d.K) * c->nc * px;
   }
   c->env_tw.assign(n_envs, 32);
   c->env_th.assign(n_envs, 16);
@@ -429,8 +440,8 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if ((e = dalloc(c, &c->d_envs, n_envs)) != cudaSuccess) return bail(e, "alloc envs");
   if ((e = dalloc(c, &c->d_tiles, max_tiles(c))) != cudaSuccess) return bail(e, "alloc tiles");
   if ((e = dalloc(c, &c->d_work, kMaxGroups)) != cudaSuccess) return bail(e, "alloc work counters");
-  if ((e = dalloc(c, &c->d_Lref, c->total)) != cudaSuccess) return bail(e, "alloc Lref");
-  if (c->any_refr && (e = dalloc(c, &c->d_tlast, c->total)) != cudaSuccess)
+  if ((e = dalloc(c, &c->d_Lref, c->nc * c->total)) != cudaSuccess) return bail(e, "alloc Lref");
+  if (c->any_refr && (e = dalloc(c, &c->d_tlast, c->nc * c->total)) != cudaSuccess)
     return bail(e, "alloc t_last");
   if ((e = dalloc(c, &c->d_flow, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc flow");
   for (int s = 0; s < 2; ++s)
@@ -443,7 +454,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");
   if ((e = dalloc(c, &c->d_tr_off, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc trace offsets");
   for (int s = 0; s < 2; ++s) {
-    if (c->need_L && (e = dalloc(c, &c->d_L[s], c->total)) != cudaSuccess) return bail(e, "alloc L");
+    if (c->need_L && (e = dalloc(c, &c->d_L[s], c->nc * c->total)) != cudaSuccess) return bail(e, "alloc L");
     if (!c->keep) {
       if ((e = dalloc(c, &c->d_mv[s], 2 * c->total)) != cudaSuccess) return bail(e, "alloc mv");
       if ((e = dalloc(c, &c->d_Z[s], c->total)) != cudaSuccess) return bail(e, "alloc Z");
@@ -457,10 +468,13 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
       (e = cudaMemcpyAsync(c->d_tr_off, troff.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s)) ||
       (e = cudaMemsetAsync(c->d_gap, 0, sizeof(uint32_t) * 2 * n_envs, s)) ||
+      // packing pads of the L slots are never written by a step: zero them once
+      (c->d_L[0] && (e = cudaMemsetAsync(c->d_L[0], 0, sizeof(float) * c->nc * c->total, s))) ||
+      (c->d_L[1] && (e = cudaMemsetAsync(c->d_L[1], 0, sizeof(float) * c->nc * c->total, s))) ||
       (e = cudaMemsetAsync(c->d_flow, 0, sizeof(float) * 2 * n_envs, s)))
     return bail(e, "upload tables");
   if (c->d_tlast) {
-    fill_i64<<<1024, 256, 0, s>>>(c->d_tlast, evis::kNoEvent, c->total);
+    fill_i64<<<1024, 256, 0, s>>>(c->d_tlast, evis::kNoEvent, c->nc * c->total);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "fill t_last");
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bail(e, "create sync");
@@ -490,7 +504,7 @@ evis_status evis_step_host(evis_ctx *c, const float *frames, const float *mv,
   if (!c) return EVIS_ERR_INVALID_ARG;
   if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
   if (dt_ns <= 0 || dt_ns > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
-  const size_t fw = c->mode == EVIS_IN_RGB ? 3 : 1;
+  const size_t fw = (c->mode == EVIS_IN_RGB || c->nc == 3) ? 3 : 1;
   drop_graphs(c);
   cudaError_t e = ensure_inputs(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "alloc input buffers");
@@ -549,14 +563,14 @@ evis_status evis_get_state(evis_ctx *c, float *Lref, int64_t *t_last, int64_t *c
   if (!c) return EVIS_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "state sync");
-  if (Lref && (e = cudaMemcpy(Lref, c->d_Lref, sizeof(float) * c->total, cudaMemcpyDefault)))
+  if (Lref && (e = cudaMemcpy(Lref, c->d_Lref, sizeof(float) * c->nc * c->total, cudaMemcpyDefault)))
     return cuda_fail(c, e, "copy Lref");
   if (t_last) {
     if (c->d_tlast) {
-      if ((e = cudaMemcpy(t_last, c->d_tlast, sizeof(int64_t) * c->total, cudaMemcpyDefault)))
+      if ((e = cudaMemcpy(t_last, c->d_tlast, sizeof(int64_t) * c->nc * c->total, cudaMemcpyDefault)))
         return cuda_fail(c, e, "copy t_last");
     } else {
-      std::fill(t_last, t_last + c->total, evis::kNoEvent);
+      std::fill(t_last, t_last + c->nc * c->total, evis::kNoEvent);
     }
   }
   if (clocks && (e = cudaMemcpy(clocks, c->d_clock + c->clk * c->n, sizeof(int64_t) * c->n,
@@ -624,7 +638,7 @@ evis_status evis_set_defocus(evis_ctx *c, const float *sigma_px) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   const int taps = 2 * evis::kMaxBlurR + 1;
   if (any && !c->d_blur) {
-    if ((e = dalloc(c, &c->d_blur, c->total)) != cudaSuccess ||
+    if ((e = dalloc(c, &c->d_blur, c->nc * c->total)) != cudaSuccess ||
         (e = dalloc(c, &c->d_blur_w, static_cast<int64_t>(taps) * c->n)) != cudaSuccess)
       return cuda_fail(c, e, "alloc defocus buffers");
   }
@@ -731,16 +745,16 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune sync");
   if (!c->d_tune_Lref) {
-    if ((e = dalloc(c, &c->d_tune_Lref, c->total)) != cudaSuccess ||
-        (c->d_tlast && (e = dalloc(c, &c->d_tune_tlast, c->total)) != cudaSuccess) ||
+    if ((e = dalloc(c, &c->d_tune_Lref, c->nc * c->total)) != cudaSuccess ||
+        (c->d_tlast && (e = dalloc(c, &c->d_tune_tlast, c->nc * c->total)) != cudaSuccess) ||
         (e = dalloc(c, &c->d_tune_tiles, max_tiles(c))) != cudaSuccess)
       return cuda_fail(c, e, "alloc autotune scratch");
   }
   // save the per-pixel state and the event counter; every trial starts from them
   unsigned long long count0 = 0;
   if ((e = cudaMemcpy(&count0, c->d_count, sizeof count0, cudaMemcpyDeviceToHost)) ||
-      (e = cudaMemcpy(c->d_tune_Lref, c->d_Lref, sizeof(float) * c->total, cudaMemcpyDeviceToDevice)) ||
-      (c->d_tlast && (e = cudaMemcpy(c->d_tune_tlast, c->d_tlast, sizeof(int64_t) * c->total,
+      (e = cudaMemcpy(c->d_tune_Lref, c->d_Lref, sizeof(float) * c->nc * c->total, cudaMemcpyDeviceToDevice)) ||
+      (c->d_tlast && (e = cudaMemcpy(c->d_tune_tlast, c->d_tlast, sizeof(int64_t) * c->nc * c->total,
                                      cudaMemcpyDeviceToDevice))))
     return cuda_fail(c, e, "autotune save");
   KeyframeB B{};
@@ -769,9 +783,9 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
       s.work_counter = c->d_work + kMaxGroups - 1;
       float t_min = 1e30f;
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // r = 0 warms up
-        if ((e = cudaMemcpyAsync(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->total,
+        if ((e = cudaMemcpyAsync(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->nc * c->total,
                                  cudaMemcpyDeviceToDevice, c->stream)) ||
-            (c->d_tlast && (e = cudaMemcpyAsync(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->total,
+            (c->d_tlast && (e = cudaMemcpyAsync(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->nc * c->total,
                                                 cudaMemcpyDeviceToDevice, c->stream))) ||
             (e = cudaMemsetAsync(s.work_counter, 0, sizeof(unsigned), c->stream)) ||
             (e = cudaEventRecord(ev0, c->stream)) ||
@@ -796,9 +810,9 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
   cudaEventDestroy(ev1);
   // restore the state and the counter whatever happened above
   cudaError_t r = cudaStreamSynchronize(c->stream);
-  if (r == cudaSuccess) r = cudaMemcpy(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->total, cudaMemcpyDeviceToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->nc * c->total, cudaMemcpyDeviceToDevice);
   if (r == cudaSuccess && c->d_tlast)
-    r = cudaMemcpy(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->total, cudaMemcpyDeviceToDevice);
+    r = cudaMemcpy(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->nc * c->total, cudaMemcpyDeviceToDevice);
   if (r == cudaSuccess) r = cudaMemcpy(c->d_count, &count0, sizeof count0, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = r;
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune");

@@ -66,6 +66,8 @@ struct StepArgs {
   int64_t dt;
   uint32_t flags;
   bool noise;                // some environment of the launch has noise on (needs gap_in)
+  int nc;                    // event channels: 1, or 3 in colour mode (0 reads as 1)
+  int64_t plane;             // channel stride of LA, LB, Lref, tlast (packed pixels)
   uint64_t *tr_keys;         // debug trace (null in the production path)
   float *tr_L;
   const int64_t *tr_koff, *tr_loff;
@@ -81,7 +83,11 @@ struct PrepArgs {
   const float *mvA, *ZA;         // previous keyframe (null for the first one)
   float4 *packA, *packB;         // per-source packs of A and B for the gap (null: none)
   float eps;
-  uint32_t mode;
+  uint32_t mode;                 // EVIS_IN_LOG, EVIS_IN_LUM, or EVIS_IN_RGB; with nc = 3 the
+                                 // frames are planar log (LOG), planar linear (LUM, what the
+                                 // defocus pass writes) or interleaved linear RGB (RGB)
+  int nc;                        // planes of L_out: 1, or 3 in colour mode (0 reads as 1)
+  int64_t plane;                 // channel stride of frames (planar) and L_out
   int max_segs;                  // largest environment (row segments)
 };
 
@@ -95,8 +101,10 @@ struct BlurArgs {
   int W, H, r;                  // the single-plane form
   float w[2 * kMaxBlurR + 1];
   const float *in;              // packed frames: luminance, or RGB triples
-  float *out;                   // packed blurred luminance
+  float *out;                   // packed blurred luminance (or nc planes of blurred channels)
   uint32_t mode;                // EVIS_IN_LUM or EVIS_IN_RGB
+  int nc;                       // 3: blur each channel of the RGB input into its own plane
+  int64_t plane;                // channel stride of out
   int max_r;                    // largest radius of the launch (sizes shared memory)
 };
 
@@ -106,7 +114,7 @@ cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStr
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
 // One tile shape and variant of the synthesis kernel (defined in evis_step.cuh and
 // instantiated in the evis_step_*.cu translation units).
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s);
 
 // grid_cap > 0: persistent launch of at most grid_cap x (resident CTAs) blocks that take

@@ -57,16 +57,26 @@ __global__ void prep_kernel(const PrepArgs a) {
         a.packA[p] = make_float4(mA.x, mA.y, zA, zoA);
       }
       if (a.L_out) {
-        float L;
-        if (a.mode == EVIS_IN_LOG) {
-          L = a.frames[p];
-        } else if (a.mode == EVIS_IN_LUM) {
-          L = log_intensity(a.frames[p], a.eps);
+        if (a.nc == 3) {  // colour: R, G, B planes
+          for (int c = 0; c < 3; ++c) {
+            float L;
+            if (a.mode == EVIS_IN_LOG) L = a.frames[c * a.plane + p];
+            else if (a.mode == EVIS_IN_LUM) L = log_intensity(a.frames[c * a.plane + p], a.eps);
+            else L = log_intensity(a.frames[3 * p + c], a.eps);
+            a.L_out[c * a.plane + p] = L;
+          }
         } else {
-          const float *c = a.frames + 3 * p;
-          L = log_intensity(rec709(c[0], c[1], c[2]), a.eps);
+          float L;
+          if (a.mode == EVIS_IN_LOG) {
+            L = a.frames[p];
+          } else if (a.mode == EVIS_IN_LUM) {
+            L = log_intensity(a.frames[p], a.eps);
+          } else {
+            const float *c = a.frames + 3 * p;
+            L = log_intensity(rec709(c[0], c[1], c[2]), a.eps);
+          }
+          a.L_out[p] = L;
         }
-        a.L_out[p] = L;
       }
     }
 #pragma unroll
@@ -129,7 +139,9 @@ __global__ void __launch_bounds__(kBlurTX * kBlurTY) defocus_kernel(const BlurAr
       const int ry = i / AW, rx = i - ry * AW;
       const int ys = min(max(y0 - r + ry, 0), H - 1), xs = min(max(x0 - r + rx, 0), W - 1);
       const int64_t p = o + static_cast<int64_t>(ys) * W + xs;
-      A[i] = a.mode == EVIS_IN_RGB ? rec709(a.in[3 * p], a.in[3 * p + 1], a.in[3 * p + 2]) : a.in[p];
+      A[i] = a.nc == 3 ? a.in[3 * p + blockIdx.z]
+                       : (a.mode == EVIS_IN_RGB ? rec709(a.in[3 * p], a.in[3 * p + 1], a.in[3 * p + 2])
+                                                : a.in[p]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < AH * kBlurTX; i += blockDim.x) {
@@ -145,7 +157,7 @@ __global__ void __launch_bounds__(kBlurTX * kBlurTY) defocus_kernel(const BlurAr
       if (x < W && y < H) {
         float acc = 0.0f;
         for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], B[(row + k) * kBlurTX + cx]));
-        a.out[o + static_cast<int64_t>(y) * W + x] = acc;
+        a.out[blockIdx.z * a.plane + o + static_cast<int64_t>(y) * W + x] = acc;
       }
     }
     __syncthreads();  // A and B are reused by the next tile
@@ -194,7 +206,7 @@ cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStr
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   // about eight CTAs per SM over the whole launch, at least one per environment
   const int gx = max(1, min(max_tiles, (8 * sms + n_envs - 1) / n_envs));
-  defocus_kernel<<<dim3(gx, n_envs), kBlurTX * kBlurTY, smem, s>>>(a);
+  defocus_kernel<<<dim3(gx, n_envs, a.nc == 3 ? 3 : 1), kBlurTX * kBlurTY, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -220,15 +232,20 @@ cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, i
   if (n_tiles <= 0) return cudaSuccess;
   if (!a.packA) {  // unpacked sources: 64x16 tiles only
     if (tile_w != 64 || tile_h != 16 || trace || a.noise) return cudaErrorInvalidValue;
-    return launch_shape<64, 16, false, false, false>(a, n_tiles, grid_cap, s);
+    if (a.nc == 3) return cudaErrorInvalidValue;
+    return launch_shape<64, 16, false, false, false, 1>(a, n_tiles, grid_cap, s);
   }
   if (a.noise && !a.gap_in) return cudaErrorInvalidValue;
-  // the trace variant always carries the noise code; the production one only when asked
+  // the trace and colour variants always carry the noise code; the mono production one only
+  // when asked
 #define EVIS_SHAPE(TX, TY)                                                               \
   if (tile_w == TX && tile_h == TY)                                                      \
-    return trace ? launch_shape<TX, TY, true, true, true>(a, n_tiles, grid_cap, s)       \
-                 : (a.noise ? launch_shape<TX, TY, false, true, true>(a, n_tiles, grid_cap, s) \
-                            : launch_shape<TX, TY, false, true, false>(a, n_tiles, grid_cap, s));
+    return a.nc == 3                                                                     \
+               ? (trace ? launch_shape<TX, TY, true, true, true, 3>(a, n_tiles, grid_cap, s) \
+                        : launch_shape<TX, TY, false, true, true, 3>(a, n_tiles, grid_cap, s)) \
+               : (trace ? launch_shape<TX, TY, true, true, true, 1>(a, n_tiles, grid_cap, s) \
+                        : (a.noise ? launch_shape<TX, TY, false, true, true, 1>(a, n_tiles, grid_cap, s) \
+                                   : launch_shape<TX, TY, false, true, false, 1>(a, n_tiles, grid_cap, s)));
   EVIS_SHAPE(32, 16)
   EVIS_SHAPE(32, 32)
   EVIS_SHAPE(64, 16)

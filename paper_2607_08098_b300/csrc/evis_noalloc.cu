@@ -160,6 +160,7 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
     pa.flow = s_flow + k;
     pa.seg = s_seg + k * kNaMaxSegs;
     pa.mode = EVIS_IN_LOG;
+    pa.nc = 1;
     pa.max_segs = n_segs;
     if ((e = evis::launch_prep(pa, 1, s)) != cudaSuccess) goto cuda_error;
   }
@@ -188,6 +189,7 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
     sa.capacity = static_cast<unsigned long long>(capacity);
     sa.dt = dt_ns;
     sa.flags = flags;
+    sa.nc = 1;
     if ((e = evis::launch_step(sa, kNaTileW, kNaTileH, /*trace=*/false, /*grid_cap=*/0, s)) !=
         cudaSuccess)
       goto cuda_error;

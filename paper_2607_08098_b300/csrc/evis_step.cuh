@@ -218,10 +218,10 @@ struct StepSmem {
 };
 
 // Resident CTAs per SM each tile shape is compiled for (bounded by its shared memory); it
-// sets the register budget.
-template <int TX, int TY>
+// sets the register budget.  Colour (NC = 3) triples the per-pixel state held in registers.
+template <int TX, int TY, int NC>
 constexpr int step_min_blocks() {
-  return TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3);
+  return NC == 1 ? (TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3)) : (TX * TY <= 512 ? 3 : 2);
 }
 
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
@@ -255,8 +255,9 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, c
 }
 
 // All K sub-frames of one target tile (the body of step_kernel).  NOISE compiles the sensor
-// noise of Sec. 3.4 in (environments with it off skip it at run time).
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+// noise of Sec. 3.4 in (environments with it off skip it at run time); NC = 3 runs the event
+// model on the R, G and B planes (Sec. 3.2), NC = 1 on the one log-intensity plane.
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
 __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NT = TX * TY / kThreads;   // targets per thread
   constexpr int NW = kThreads / 32;
@@ -286,8 +287,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 
   // per-pixel event state of this thread's targets (rows ty0 + ROWS j), in registers for
   // the whole keyframe gap
-  float Lref[NT], Lprev[NT], thon[NT], thoff[NT];
-  int64_t tprev[NT], tlast[NT];
+  float Lref[NT][NC], Lprev[NT][NC], thon[NT], thoff[NT];
+  int64_t tprev[NT], tlast[NT][NC];
   bool act[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
@@ -295,15 +296,20 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     const int pix = ty * W + tx;
     act[j] = tx < W - E.margin && ty < H - E.margin;  // tiles start inside the margin
     tprev[j] = T0;
-    tlast[j] = kNoEvent;
-    Lref[j] = 0.0f;
-    Lprev[j] = 0.0f;
     thon[j] = E.c_on;
     thoff[j] = E.c_off;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      tlast[j][c] = kNoEvent;
+      Lref[j][c] = 0.0f;
+      Lprev[j][c] = 0.0f;
+      if (act[j]) {
+        Lref[j][c] = a.Lref[c * a.plane + o + pix];
+        Lprev[j][c] = LA[c * a.plane + pix];
+        if (a.tlast) tlast[j][c] = a.tlast[c * a.plane + o + pix];
+      }
+    }
     if (act[j]) {
-      Lref[j] = a.Lref[o + pix];
-      Lprev[j] = LA[pix];
-      if (a.tlast) tlast[j] = a.tlast[o + pix];
       if (E.con_map) {
         thon[j] = E.con_map[pix];
         thoff[j] = E.coff_map[pix];
@@ -377,7 +383,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   // t_i = T0 + floor(i dt / K), stepped with a quotient and a remainder
   const int64_t dq = a.dt / K, dr = a.dt % K;
   int64_t tq = 0, trem = 0;
-  // noise: this gap's counter and the hot pixels among this thread's targets (bit j)
+  // noise: this gap's counter and the hot pixels among this thread's targets (bit j NC + c)
   const bool noisy = NOISE && E.noise != 0;
   const unsigned gap = noisy ? a.gap_in[tl.env] : 0u;
   unsigned hot = 0;
@@ -386,9 +392,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     for (int j = 0; j < NT; ++j) {  // counters use the sensor pixel index (inside the margin)
       const unsigned pix = static_cast<unsigned>((ty0 + ROWS * j - E.margin) * (W - 2 * E.margin) +
                                                  (tx - E.margin));
-      if (act[j] && fires(philox4x32_10(make_uint4(pix, 0xFFFFFFFFu, 0u, 2u), E.key0, E.key1).x,
-                          E.hot_fraction))
-        hot |= 1u << j;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (act[j] && fires(philox4x32_10(make_uint4(pix, 0xFFFFFFFFu, 0u, 2u + 4u * c), E.key0,
+                                          E.key1).x, E.hot_fraction))
+          hot |= 1u << (j * NC + c);
     }
   }
 
@@ -477,162 +485,174 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     }
     __syncthreads();
 
-    // ---- phase 3: resolve, blend, threshold crossings, emission ----
+    // ---- phase 3: resolve, blend, threshold crossings, emission (per channel: the winners
+    // depend on motion and depth only, so one resolve serves all NC channels) ----
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
       const int ty = ty0 + ROWS * j;
       const int pix = ty * W + tx;
-      bool has = false;
-      float L = 0.0f, th = thon[j], nf = 0.0f;
-      int n = 0, pol = 1;
-      if (act[j]) {
-        const unsigned long long kA = S.zb[0][tid + kThreads * j];
-        const unsigned long long kB = S.zb[1][tid + kThreads * j];
-        S.zb[0][tid + kThreads * j] = kEmptyKey;  // ready for the next sub-frame
-        S.zb[1][tid + kThreads * j] = kEmptyKey;
-        const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
-        const float la = hasA ? __ldg(LA + (kA & 0xFFFFFFull)) : 0.0f;
-        const float lb = hasB ? __ldg(LB + (kB & 0xFFFFFFull)) : 0.0f;
-        if (joint) {  // Eq. 6: the nearer winner; equal depths go to B
-          L = (hasA && hasB) ? ((kA >> 32) < (kB >> 32) ? la : lb)
-                             : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
-        } else if (b_primary) {
-          L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
-        } else {
-          L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))
-                             : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
-        }
-        if (TRACE) {
-          const int64_t kb = a.tr_koff[tl.env] + static_cast<int64_t>(i - 1) * 2 * HW + pix;
-          a.tr_keys[kb] = kA;
-          a.tr_keys[kb + HW] = kB;
-          a.tr_L[a.tr_loff[tl.env] + static_cast<int64_t>(i - 1) * HW + pix] = L;
-        }
-        has = hasA || hasB;  // no sample: the pixel holds its state this sub-frame
-        if (has) {
-          const float d = __fsub_rn(L, Lref[j]);
-          pol = d > 0.0f ? 1 : -1;
-          th = pol > 0 ? thon[j] : thoff[j];
-          const float q = __fdiv_rn(fabsf(d), th);
-          if (q >= 1.0f) {
-            if (q >= static_cast<float>(kMaxCrossings)) {
-              n = kMaxCrossings;
-              nf = static_cast<float>(kMaxCrossings);
-            } else {
-              n = floor_small(q, &nf);
+      unsigned long long kA = kEmptyKey, kB = kEmptyKey;  // read at channel 0
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        bool has = false;
+        float L = 0.0f, th = thon[j], nf = 0.0f;
+        int n = 0, pol = 1;
+        if (act[j]) {
+          if (c == 0) {
+            kA = S.zb[0][tid + kThreads * j];
+            kB = S.zb[1][tid + kThreads * j];
+            S.zb[0][tid + kThreads * j] = kEmptyKey;  // ready for the next sub-frame
+            S.zb[1][tid + kThreads * j] = kEmptyKey;
+          }
+          const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
+          const float la = hasA ? __ldg(LA + c * a.plane + (kA & 0xFFFFFFull)) : 0.0f;
+          const float lb = hasB ? __ldg(LB + c * a.plane + (kB & 0xFFFFFFull)) : 0.0f;
+          if (joint) {  // Eq. 6: the nearer winner; equal depths go to B
+            L = (hasA && hasB) ? ((kA >> 32) < (kB >> 32) ? la : lb)
+                               : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+          } else if (b_primary) {
+            L = hasB ? lb : (hasA ? la : __int_as_float(0x7fc00000));
+          } else {
+            L = (hasA && hasB) ? __fadd_rn(__fmul_rn(g, la), __fmul_rn(f, lb))
+                               : (hasA ? la : (hasB ? lb : __int_as_float(0x7fc00000)));
+          }
+          if (TRACE) {
+            if (c == 0) {
+              const int64_t kb = a.tr_koff[tl.env] + static_cast<int64_t>(i - 1) * 2 * HW + pix;
+              a.tr_keys[kb] = kA;
+              a.tr_keys[kb + HW] = kB;
+            }
+            a.tr_L[a.tr_loff[tl.env] + (static_cast<int64_t>(i - 1) * NC + c) * HW + pix] = L;
+          }
+          has = hasA || hasB;  // no sample: the pixel holds its state this sub-frame
+          if (has) {
+            const float d = __fsub_rn(L, Lref[j][c]);
+            pol = d > 0.0f ? 1 : -1;
+            th = pol > 0 ? thon[j] : thoff[j];
+            const float q = __fdiv_rn(fabsf(d), th);
+            if (q >= 1.0f) {
+              if (q >= static_cast<float>(kMaxCrossings)) {
+                n = kMaxCrossings;
+                nf = static_cast<float>(kMaxCrossings);
+              } else {
+                n = floor_small(q, &nf);
+              }
             }
           }
         }
-      }
-      // ---- crossings k = 1..n of the warp's 32 pixels, spread over its lanes ----
-      // Item c of the warp (pixels in lane order, k ascending) is computed by lane c % 32.
-      int incl = n;
+        // ---- crossings k = 1..n of the warp's 32 pixels, spread over its lanes ----
+        // Item c of the warp (pixels in lane order, k ascending) is computed by lane c % 32.
+        int incl = n;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += v;
-      }
-      const int total = __shfl_sync(kFull, incl, 31);
-      const int excl = incl - n;
-      for (int c0 = 0; c0 < total; c0 += 32) {
-        const int c = c0 + lane;
-        // owner = number of lanes whose items all lie before c
-        int own = 0;
+        for (int d = 1; d < 32; d <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - n;
+        for (int c0 = 0; c0 < total; c0 += 32) {
+          const int it = c0 + lane;
+          // owner = number of lanes whose items all lie before it
+          int own = 0;
 #pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-          const int v = __shfl_sync(kFull, incl, own + st - 1);
-          if (v <= c) own += st;
-        }
-        own = min(own, 31);
-        const int k = c - __shfl_sync(kFull, excl, own) + 1;
-        const float oL = __shfl_sync(kFull, L, own);
-        const float oLref = __shfl_sync(kFull, Lref[j], own);
-        const float oLprev = __shfl_sync(kFull, Lprev[j], own);
-        const float oth = __shfl_sync(kFull, th, own);
-        const int opol = __shfl_sync(kFull, pol, own);
-        const int64_t otprev = __shfl_sync(kFull, tprev[j], own);
-        int64_t t = 0;
-        if (c < total) {
-          const float kf = small_int_to_float(k);
-          t = crossing_time(oLref, opol > 0 ? kf : -kf, oth, oLprev, oL, otprev, ti);
-        }
-        bool emit = c < total;
-        if (a.tlast) {
-          // refractory filter (Sec. 3.4) in order along each pixel's crossings: each owner
-          // walks its items of this chunk; t_last carries over to the next chunk
-          S.rt[warp][lane] = t;
-          __syncwarp();
-          const int lo = max(excl, c0), hi = min(incl, c0 + 32);
-          for (int cc = lo; cc < hi; ++cc) {
-            const int64_t tt = S.rt[warp][cc - c0];
-            const bool keep = refr <= 0 || tlast[j] == kNoEvent || tt - tlast[j] >= refr;
-            if (keep) tlast[j] = tt;
-            S.rkeep[warp][cc - c0] = keep ? 1 : 0;
+          for (int st = 16; st > 0; st >>= 1) {
+            const int v = __shfl_sync(kFull, incl, own + st - 1);
+            if (v <= it) own += st;
           }
-          __syncwarp();
-          emit = emit && S.rkeep[warp][lane] != 0;
+          own = min(own, 31);
+          const int k = it - __shfl_sync(kFull, excl, own) + 1;
+          const float oL = __shfl_sync(kFull, L, own);
+          const float oLref = __shfl_sync(kFull, Lref[j][c], own);
+          const float oLprev = __shfl_sync(kFull, Lprev[j][c], own);
+          const float oth = __shfl_sync(kFull, th, own);
+          const int opol = __shfl_sync(kFull, pol, own);
+          const int64_t otprev = __shfl_sync(kFull, tprev[j], own);
+          int64_t t = 0;
+          if (it < total) {
+            const float kf = small_int_to_float(k);
+            t = crossing_time(oLref, opol > 0 ? kf : -kf, oth, oLprev, oL, otprev, ti);
+          }
+          bool emit = it < total;
+          if (a.tlast) {
+            // refractory filter (Sec. 3.4) in order along each pixel's crossings: each owner
+            // walks its items of this chunk; t_last carries over to the next chunk
+            S.rt[warp][lane] = t;
+            __syncwarp();
+            const int lo = max(excl, c0), hi = min(incl, c0 + 32);
+            for (int cc = lo; cc < hi; ++cc) {
+              const int64_t tt = S.rt[warp][cc - c0];
+              const bool keep = refr <= 0 || tlast[j][c] == kNoEvent || tt - tlast[j][c] >= refr;
+              if (keep) tlast[j][c] = tt;
+              S.rkeep[warp][cc - c0] = keep ? 1 : 0;
+            }
+            __syncwarp();
+            emit = emit && S.rkeep[warp][lane] != 0;
+          }
+          const unsigned m = __ballot_sync(kFull, emit);
+          if (m == 0) continue;
+          const unsigned cnt = static_cast<unsigned>(__popc(m));
+          unsigned base = 0;
+          unsigned long long gb = 0;
+          if (lane == 0) {
+            base = atomicAdd(&s_n, cnt);
+            if (base + cnt > static_cast<unsigned>(kEventStage))  // staging full: go global
+              gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
+                                             base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+          }
+          base = __shfl_sync(kFull, base, 0);
+          gb = __shfl_sync(kFull, gb, 0);
+          if (emit) {
+            const int otid = warp * 32 + own;
+            const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
+            const ulonglong2 rec = make_event(t, tl.x0 - E.margin + otid % TX,
+                                              tl.y0 - E.margin + otid / TX + ROWS * j, tl.env,
+                                              opol * (1 + c));
+            if (idx < static_cast<unsigned>(kEventStage)) {
+              S.stage[idx] = rec;
+            } else {
+              const unsigned long long gi =
+                  gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
+              if (gi < a.capacity) a.events[gi] = rec;
+            }
+          }
+          __syncwarp();  // the next chunk reuses this warp's refractory scratch
         }
-        const unsigned m = __ballot_sync(kFull, emit);
-        if (m == 0) continue;
-        const unsigned cnt = static_cast<unsigned>(__popc(m));
-        unsigned base = 0;
-        unsigned long long gb = 0;
-        if (lane == 0) {
-          base = atomicAdd(&s_n, cnt);
-          if (base + cnt > static_cast<unsigned>(kEventStage))  // staging full: go global
-            gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
-                                           base + cnt - max(base, static_cast<unsigned>(kEventStage))));
-        }
-        base = __shfl_sync(kFull, base, 0);
-        gb = __shfl_sync(kFull, gb, 0);
-        if (emit) {
-          const int otid = warp * 32 + own;
-          const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
-          const ulonglong2 rec = make_event(t, tl.x0 - E.margin + otid % TX,
-                                            tl.y0 - E.margin + otid / TX + ROWS * j, tl.env, opol);
-          if (idx < static_cast<unsigned>(kEventStage)) {
-            S.stage[idx] = rec;
-          } else {
-            const unsigned long long gi =
-                gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
-            if (gi < a.capacity) a.events[gi] = rec;
+        if (noisy) {  // leak, shot and hot-pixel events of this target and channel (Sec. 3.4)
+          const int64_t d = ti - tim1;
+          const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
+          const int ex = tx - E.margin, ey = ty - E.margin;  // sensor coordinates
+          const unsigned npix = static_cast<unsigned>(ey * (W - 2 * E.margin) + ex);
+          const unsigned cw = 4u * c;                        // the channel's streams
+          bool fl = false, fs = false, fh = false;
+          if (act[j]) {
+            const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), cw), E.key0, E.key1);
+            fl = E.leak_hz > 0.0f && fires(r.x, __fmul_rn(E.leak_hz, dts));
+            if (E.shot_hz > 0.0f && has) {
+              float ib = __fdiv_rn(__fsub_rn(L, E.noise_lo), __fsub_rn(E.noise_hi, E.noise_lo));
+              ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
+              fs = fires(r.y, __fmul_rn(__fmul_rn(E.shot_hz, dts), __fsub_rn(1.0f, ib)));
+            }
+            fh = ((hot >> (j * NC + c)) & 1u) && fires(r.z, __fmul_rn(E.hot_hz, dts));
+          }
+          if (__any_sync(kFull, fl || fs || fh)) {
+            uint4 rt = make_uint4(0u, 0u, 0u, 0u);
+            if (fl || fs || fh)
+              rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u + cw), E.key0, E.key1);
+            const int cp = 1 + c;
+            stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, cp),
+                       lanes_below, lane);
+            stage_warp(S, &s_n, a, fs,
+                       make_event(noise_time(rt.y, tim1, d), ex, ey, tl.env, (rt.w & 1u) ? cp : -cp),
+                       lanes_below, lane);
+            stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, cp),
+                       lanes_below, lane);
           }
         }
-        __syncwarp();  // the next chunk reuses this warp's refractory scratch
-      }
-      if (noisy) {  // leak, shot and hot-pixel events of this target (Sec. 3.4)
-        const int64_t d = ti - tim1;
-        const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
-        const int ex = tx - E.margin, ey = ty - E.margin;  // sensor coordinates
-        const unsigned npix = static_cast<unsigned>(ey * (W - 2 * E.margin) + ex);
-        bool fl = false, fs = false, fh = false;
-        if (act[j]) {
-          const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 0u), E.key0, E.key1);
-          fl = E.leak_hz > 0.0f && fires(r.x, __fmul_rn(E.leak_hz, dts));
-          if (E.shot_hz > 0.0f && has) {
-            float ib = __fdiv_rn(__fsub_rn(L, E.noise_lo), __fsub_rn(E.noise_hi, E.noise_lo));
-            ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
-            fs = fires(r.y, __fmul_rn(__fmul_rn(E.shot_hz, dts), __fsub_rn(1.0f, ib)));
-          }
-          fh = ((hot >> j) & 1u) && fires(r.z, __fmul_rn(E.hot_hz, dts));
+        if (has) {
+          if (n > 0) Lref[j][c] = __fadd_rn(Lref[j][c], __fmul_rn(pol > 0 ? nf : -nf, th));
+          Lprev[j][c] = L;
+          if (c == NC - 1) tprev[j] = ti;  // after every channel's crossings used it
         }
-        if (__any_sync(kFull, fl || fs || fh)) {
-          uint4 rt = make_uint4(0u, 0u, 0u, 0u);
-          if (fl || fs || fh)
-            rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u), E.key0, E.key1);
-          stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, 1),
-                     lanes_below, lane);
-          stage_warp(S, &s_n, a, fs,
-                     make_event(noise_time(rt.y, tim1, d), ex, ey, tl.env, (rt.w & 1u) ? 1 : -1),
-                     lanes_below, lane);
-          stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, 1),
-                     lanes_below, lane);
-        }
-      }
-      if (has) {
-        if (n > 0) Lref[j] = __fadd_rn(Lref[j], __fmul_rn(pol > 0 ? nf : -nf, th));
-        Lprev[j] = L;
-        tprev[j] = ti;
       }
     }
     // ---- end of phase 3: the last warp to finish reserves the global range of this
@@ -664,8 +684,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   for (int j = 0; j < NT; ++j) {
     if (!act[j]) continue;
     const int pix = (ty0 + ROWS * j) * W + tx;
-    a.Lref[o + pix] = Lref[j];
-    if (a.tlast) a.tlast[o + pix] = tlast[j];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      a.Lref[c * a.plane + o + pix] = Lref[j][c];
+      if (a.tlast) a.tlast[c * a.plane + o + pix] = tlast[j][c];
+    }
   }
   if (tid == 0 && tl.x0 == E.margin && tl.y0 == E.margin) {  // the environment's first tile
     a.clock_out[tl.env] = T0 + a.dt;
@@ -675,12 +698,12 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 
 // One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
 // first one by block index, the next ones from a work counter that starts at 0.
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
-__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kernel(const StepArgs a) {
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
+__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY, NC>()) step_kernel(const StepArgs a) {
   __shared__ int s_tile;
   int t = blockIdx.x;
   while (t < a.n_tiles) {
-    run_tile<TX, TY, TRACE, PACKED, NOISE>(a, a.tiles[t]);
+    run_tile<TX, TY, TRACE, PACKED, NOISE, NC>(a, a.tiles[t]);
     __syncthreads();  // the tile's shared memory is free again
     if (threadIdx.x == 0) s_tile = static_cast<int>(gridDim.x + atomicAdd(a.work_counter, 1u));
     __syncthreads();
@@ -690,12 +713,12 @@ __global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY>()) step_kern
 
 }  // namespace
 
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
   static int resident = 0;  // CTAs per SM x SMs, looked up once per instantiation
   const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
   if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE>,
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -703,13 +726,13 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE>, kThreads, smem)) != cudaSuccess)
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>, kThreads, smem)) != cudaSuccess)
       return e;
     resident = max(1, per_sm) * sms;
   }
   int grid = n_tiles;
   if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
-  step_kernel<TX, TY, TRACE, PACKED, NOISE><<<grid, kThreads, smem, s>>>(a);
+  step_kernel<TX, TY, TRACE, PACKED, NOISE, NC><<<grid, kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,13 @@
+// Explicit instantiations of the synthesis kernel: debug-trace variants of colour events,
+// every tile shape.
+#include "evis_step.cuh"
+
+namespace evis {
+
+template cudaError_t launch_shape<32, 16, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
+
+}  // namespace evis

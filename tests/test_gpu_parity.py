@@ -29,7 +29,13 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).reshape(-1)).cuda()
 
 
-def _frames(kf, mode):
+def _frames(kf, mode, nc=1):
+    if nc == 3:   # colour: three log-intensity planes, or linear RGB triples
+        rgb = kf.rgb.reshape(-1, 3)
+        if mode == 0:
+            return np.concatenate([np.log(np.maximum(rgb[:, c] + 1e-4, 1e-30)).astype(np.float32)
+                                   for c in range(3)])
+        return kf.rgb.reshape(-1)
     if mode == 0:
         return kf.L
     if mode == 1:
@@ -37,9 +43,9 @@ def _frames(kf, mode):
     return kf.rgb.reshape(-1)
 
 
-def _trace_masks(envs):
+def _trace_masks(envs, nc=1):
     """Sensor pixels (inside each environment's margin) of the trace layouts: keys
-    [K][2][H*W] and interpolated L [K][H*W] per environment, in order."""
+    [K][2][H*W] and interpolated L [K][nc][H*W] per environment, in order."""
     mk, ml = [], []
     for e in envs:
         m = int(getattr(e, "margin", 0))
@@ -47,7 +53,7 @@ def _trace_masks(envs):
         g[m:e.H - m, m:e.W - m] = True
         g = g.ravel()
         mk.append(np.tile(g, 2 * e.K))
-        ml.append(np.tile(g, e.K))
+        ml.append(np.tile(g, e.K * nc))
     return np.concatenate(mk), np.concatenate(ml)
 
 
@@ -55,7 +61,8 @@ def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), c
              check_state=True, tile=None, noise=None):
     """Feed the same keyframes to the oracle and the library; compare everything."""
     mode = flags & 0x3
-    o = oracle_mod.Oracle(envs, eps=eps, flags=flags & 0xFF)
+    nc = 3 if flags & 0x200 else 1
+    o = oracle_mod.Oracle(envs, eps=eps, flags=flags & 0x2FF)
     ctx = ev.Context(envs, eps=eps, flags=flags, capacity=capacity)
     if tile is not None:
         ctx.set_tile_shape(*tile)
@@ -64,14 +71,14 @@ def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), c
         ctx.set_noise(noise)
     alive = []  # keeps inputs alive for EVIS_KEEP_INPUTS
     for s, kf in enumerate(kfs):
-        fr = _frames(kf, mode)
+        fr = _frames(kf, mode, nc)
         g_in = (_dev(fr), _dev(kf.mv), _dev(kf.Z))
         alive.append(g_in)
         if s in trace_steps and s > 0:
             ok, ol = o.step(fr, kf.mv, kf.Z, dt, trace=True)
             gk, gl = ctx.step_trace(*g_in, dt)
             torch.cuda.synchronize()
-            mk, ml = _trace_masks(envs)   # with a margin only sensor pixels are traced
+            mk, ml = _trace_masks(envs, nc)   # with a margin only sensor pixels are traced
             gk = gk.cpu().numpy().view(np.uint64)[mk]
             gl = gl.cpu().numpy()[ml]
             ok, ol = ok[mk], ol[ml]
@@ -88,12 +95,13 @@ def run_both(ev, oracle_mod, envs, kfs, dt, flags=0, eps=1e-4, trace_steps=(), c
     np.testing.assert_array_equal(eg.view(np.uint8), eo.view(np.uint8))
     if check_state:
         so, sg = o.state(), ctx.state()
-        valid = np.zeros(so[0].size, dtype=bool)
+        valid = np.zeros(o.total, dtype=bool)
         for e, off in zip(envs, o.offsets):
             m = int(getattr(e, "margin", 0))
             g = np.zeros((e.H, e.W), bool)
             g[m:e.H - m, m:e.W - m] = True
             valid[off:off + e.H * e.W] = g.ravel()
+        valid = np.tile(valid, nc)   # state arrays hold nc planes
         np.testing.assert_array_equal(sg[0][valid], so[0][valid])
         if any(e.refractory_ns > 0 for e in envs):   # t_last is tracked only then
             np.testing.assert_array_equal(sg[1][valid], so[1][valid])
@@ -594,3 +602,80 @@ def test_defocus_in_the_pipeline(ev, oracle_mod, scenes_mod, mode):
         a.set_defocus([9.0] * len(envs))
     with pytest.raises(ev.EvisError):
         ev.Context(envs, flags=ev.IN_LOG).set_defocus(sig)
+
+
+def _tint(envs, seed=31):
+    rng = np.random.default_rng(seed)
+    for e in envs:
+        for lay in e.layers:
+            lay.tint_r, lay.tint_g, lay.tint_b = rng.uniform(0.3, 1.6, 3)
+    return envs
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
+def test_colour_planes_exact(ev, oracle_mod, scenes_mod, tile):
+    """Colour events (Sec. 3.2) from three log-intensity planes: bit-exact events, traced
+    winners and per-channel log-intensity, per-channel reference levels and refractory
+    times, with noise, refractory periods, maps and margins, on every tile shape."""
+    envs = _tint(_ragged_envs(scenes_mod))
+    envs[5].margin = 3
+    kfs = [scenes_mod.render(envs, k, want=("rgb", "mv", "Z")) for k in range(4)]
+    noise = [dict(leak_hz=30.0, hot_hz=200.0, hot_fraction=0.05, shot_hz=50.0, lo=-3.0, hi=3.0,
+                  seed=17)] * len(envs)
+    evs = run_both(ev, oracle_mod, envs, kfs, 16_666_667, flags=ev.IN_LOG | ev.COLOR,
+                   trace_steps=(1, 3), tile=tile, noise=noise)
+    ch = np.abs(evs["p"])
+    assert set(np.unique(ch)) == {1, 2, 3} and len(evs) > 3000
+
+
+@pytest.mark.parametrize("flags", [0x10, 0x40, 0x100])
+def test_colour_modes(ev, oracle_mod, scenes_mod, flags):
+    envs = _tint(_ragged_envs(scenes_mod)[4:])
+    kfs = [scenes_mod.render(envs, k, want=("rgb", "mv", "Z")) for k in range(3)]
+    run_both(ev, oracle_mod, envs, kfs, 16_666_667, flags=ev.IN_LOG | ev.COLOR | flags,
+             trace_steps=(2,))
+
+
+def test_colour_linear_rgb_and_defocus(ev, oracle_mod, scenes_mod):
+    """Linear RGB in colour mode: (a) exactly the events of a planar-log colour context fed
+    the GPU's per-channel logs, with and without per-channel defocus; (b) the oracle's events
+    per pixel, up to the log's ulp."""
+    envs = _tint(_ragged_envs(scenes_mod))
+    kfs = [scenes_mod.render(envs, k, want=("rgb", "mv", "Z")) for k in range(3)]
+    dt = 16_666_667
+    for sig in (None, [0.6, 0.0, 1.2, 0.4, 2.0, 0.8]):
+        a = ev.Context(envs, flags=ev.IN_RGB | ev.COLOR, capacity=1 << 22)
+        b = ev.Context(envs, flags=ev.IN_LOG | ev.COLOR, capacity=1 << 22)
+        o = oracle_mod.Oracle(envs, flags=oracle_mod.IN_RGB | oracle_mod.COLOR)
+        if sig is not None:
+            a.set_defocus(sig)
+            o.set_defocus(sig)
+        keep = []
+        for kf in kfs:
+            rgb = kf.rgb.reshape(-1, 3)
+            a.step(_dev(rgb), _dev(kf.mv), _dev(kf.Z), dt)
+            o.step(rgb.reshape(-1), kf.mv, kf.Z, dt)
+            planes = torch.zeros(3 * rgb.shape[0], dtype=torch.float32, device="cuda")
+            n_tot = rgb.shape[0]
+            for c in range(3):
+                lin = torch.from_numpy(np.ascontiguousarray(rgb[:, c])).cuda()
+                if sig is not None:
+                    for e, s_, ofs in zip(envs, sig, o.offsets):
+                        n = e.W * e.H
+                        lin[ofs:ofs + n] = ev.defocus(lin[ofs:ofs + n].reshape(e.H, e.W).contiguous(),
+                                                      s_).reshape(-1)
+                planes[c * n_tot:(c + 1) * n_tot] = ev.log_intensity(lin, mode=ev.IN_LUM, eps=1e-4)
+            keep.append(planes)
+            b.step(planes, _dev(kf.mv), _dev(kf.Z), dt)
+        ga, gb = ev.sort_events(a.read_events()), ev.sort_events(b.read_events())
+        assert len(ga) > 1000
+        np.testing.assert_array_equal(ga.view(np.uint8), gb.view(np.uint8))
+        real = np.zeros(o.total, dtype=bool)   # packing pads hold no pixel
+        for e, ofs in zip(envs, o.offsets):
+            real[ofs:ofs + e.W * e.H] = True
+        np.testing.assert_array_equal(a.state()[0][np.tile(real, 3)], b.state()[0][np.tile(real, 3)])
+        eo = o.events()
+        for c in range(3):
+            _per_pixel_close(eo[np.abs(eo["p"]) == c + 1], ga[np.abs(ga["p"]) == c + 1])
+    with pytest.raises(ev.EvisError):
+        ev.Context(envs, flags=ev.IN_LUM | ev.COLOR)
