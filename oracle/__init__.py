@@ -42,6 +42,31 @@ class _Noise(ctypes.Structure):
                 ("lo", ctypes.c_float), ("hi", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
+class _VoxelEnv(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("t0_ns", ctypes.c_int64), ("t1_ns", ctypes.c_int64)]
+
+
+def voxel_grid(events, envs, bins: int = 128):
+    """Event voxel grid of each environment's segment: envs is a list of (width, height,
+    t0_ns, t1_ns); returns (acc uint32, grid float32), each the concatenation over
+    environments of [2][bins][H][W] (polarity 0 = ON)."""
+    lib = _load()
+    lib.orc_voxel_grid.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+    arr = (_VoxelEnv * len(envs))()
+    total = 0
+    for i, (W, H, t0, t1) in enumerate(envs):
+        arr[i] = _VoxelEnv(int(W), int(H), int(t0), int(t1))
+        total += 2 * bins * int(W) * int(H)
+    acc = np.empty(total, dtype=np.uint32)
+    out = np.empty(total, dtype=np.float32)
+    lib.orc_voxel_grid(ev.ctypes.data, ev.size, ctypes.addressof(arr), len(envs), int(bins),
+                       acc.ctypes.data, out.ctypes.data)
+    return acc, out
+
+
 def rec709(rgb) -> np.ndarray:
     """Rec. 709 luminance (Eq. 3) of [n, 3] linear RGB, binary32."""
     lib = _load()

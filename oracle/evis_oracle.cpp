@@ -582,6 +582,57 @@ int32_t orc_defocus_weights(float sigma, float* out) {
   return static_cast<int32_t>(w.size() / 2);
 }
 
+typedef struct {
+  int32_t width, height;  // sensor
+  int64_t t0_ns, t1_ns;   // the segment [t0, t1]; 0 < t1 - t0 < 2^32
+} orc_voxel_env;
+
+// Event voxel grid (the speed-regression input of the paper's appendix): per environment,
+// polarity (0: ON, p > 0; 1: OFF, p < 0) and bin b = 0..B-1, the events linearly
+// interpolated along time and each bin divided by its largest value.  An event at time t
+// sits at tau = (B - 1)(t - t0) / (t1 - t0) and adds 1 - frac(tau) to bin floor(tau) and
+// frac(tau) to the next one.  Weights are in units of 2^-16 so that the sums are exact
+// integers: with D = t1 - t0, N = (B - 1)(t - t0), b = N / D and r = N mod D,
+// w_next = floor(r 2^16 / D) and w_b = 2^16 - w_next.  Events outside the segment or the
+// sensor, or of an environment >= n_envs, are skipped.  acc [sum 2 B H W] receives the
+// sums (uint32), out the normalised grid: acc / max(acc over the bin's plane), 0 for an empty
+// plane, one binary32 division of the two sums rounded to binary32.
+void orc_voxel_grid(const Event* ev, int64_t n, const orc_voxel_env* envs, int32_t n_envs,
+                    int32_t bins, uint32_t* acc, float* out) {
+  std::vector<int64_t> off(n_envs + 1, 0);
+  for (int e = 0; e < n_envs; ++e)
+    off[e + 1] = off[e] + 2LL * bins * envs[e].width * envs[e].height;
+  std::fill(acc, acc + off[n_envs], 0u);
+  for (int64_t k = 0; k < n; ++k) {
+    const Event& v = ev[k];
+    if (v.env >= n_envs) continue;
+    const orc_voxel_env& E = envs[v.env];
+    if (v.x >= E.width || v.y >= E.height || v.p == 0) continue;
+    if (v.t_ns < E.t0_ns || v.t_ns > E.t1_ns) continue;
+    const int64_t D = E.t1_ns - E.t0_ns;
+    const int64_t N = static_cast<int64_t>(bins - 1) * (v.t_ns - E.t0_ns);
+    const int64_t b = N / D, r = N % D;
+    const uint32_t w_next = static_cast<uint32_t>((static_cast<uint64_t>(r) << 16) / static_cast<uint64_t>(D));
+    const uint32_t w_b = 65536u - w_next;
+    const int pol = v.p > 0 ? 0 : 1;
+    const size_t plane = static_cast<size_t>(E.width) * E.height;
+    const size_t px = static_cast<size_t>(v.y) * E.width + v.x;
+    acc[off[v.env] + (static_cast<size_t>(pol) * bins + b) * plane + px] += w_b;
+    if (w_next > 0 && b + 1 < bins) acc[off[v.env] + (static_cast<size_t>(pol) * bins + b + 1) * plane + px] += w_next;
+  }
+  for (int e = 0; e < n_envs; ++e) {
+    const size_t plane = static_cast<size_t>(envs[e].width) * envs[e].height;
+    for (int q = 0; q < 2 * bins; ++q) {
+      const uint32_t* a = acc + off[e] + q * plane;
+      float* o = out + off[e] + q * plane;
+      uint32_t mx = 0;
+      for (size_t i = 0; i < plane; ++i) mx = std::max(mx, a[i]);
+      for (size_t i = 0; i < plane; ++i)
+        o[i] = mx ? static_cast<float>(a[i]) / static_cast<float>(mx) : 0.0f;
+    }
+  }
+}
+
 // The generator alone, for its tests: n outputs of Philox4x32-10 at counters
 // (base + j, c1, c2, c3), written as 4 x n words.
 void orc_philox(uint32_t base, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
