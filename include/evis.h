@@ -206,6 +206,38 @@ evis_status evis_set_defocus(evis_ctx *ctx, const float *sigma_px);
 evis_status evis_defocus(const float *in, int32_t width, int32_t height, uint32_t mode,
                          float sigma_px, float *out, evis_stream_t stream);
 
+/* Event voxel grid (the speed-regression input of the paper's appendix): for each
+ * environment's segment [t0_ns, t1_ns], per polarity (slot 0: ON, p > 0; slot 1: OFF, p < 0;
+ * colour events count by their sign) and time bin b = 0..bins-1, the events linearly
+ * interpolated along time, each (environment, polarity, bin) plane divided by its largest
+ * value.  An event at t sits at tau = (bins - 1)(t - t0) / (t1 - t0) and adds 1 - frac(tau)
+ * to bin floor(tau) and frac(tau) to the next, in units of 2^-16: with D = t1 - t0,
+ * N = (bins - 1)(t - t0), b = N / D, r = N mod D, w_next = floor(r 2^16 / D) and
+ * w_b = 2^16 - w_next, summed exactly in uint32 (exact while a voxel receives fewer than
+ * 65536 events).  The normalised value is the binary32 quotient of the sum by the plane's
+ * maximum (0 for an empty plane).  Events outside the segment or the sensor, of an
+ * environment >= n_envs, or with p = 0, are skipped. */
+typedef struct {
+  int32_t width, height;   /* sensor, 1..65535 each, width * height <= 2^24 */
+  int64_t t0_ns, t1_ns;    /* segment, 0 < t1_ns - t0_ns < 2^32 */
+} evis_voxel_env;
+
+/* Device workspace bytes of evis_voxel_grid (a descriptor table and one uint32 per voxel). */
+evis_status evis_voxel_workspace_size(const evis_voxel_env *envs, int32_t n_envs, int32_t bins,
+                                      int64_t *bytes);
+
+/* Builds the grid of every environment (host array envs of n_envs, bins in 1..1024) from
+ * the device event records events[0 .. n), n = min(*count, max_events) with count a device
+ * pointer (for example evis_events_device's, so no host synchronisation is needed) or
+ * max_events when count is NULL.  grid is a device float array, per environment in order
+ * [2][bins][height][width].  workspace is device memory of evis_voxel_workspace_size bytes
+ * (its contents need not be initialised).  Asynchronous on stream; EVIS_ERR_INVALID_ARG
+ * (evis_last_error(NULL) says why) before any work for a bad argument. */
+evis_status evis_voxel_grid(const evis_event *events, const uint64_t *count, int64_t max_events,
+                            const evis_voxel_env *envs, int32_t n_envs, int32_t bins,
+                            void *workspace, int64_t workspace_bytes, float *grid,
+                            evis_stream_t stream);
+
 /* Debug form of evis_step: also writes, for every environment in order and every
  * sub-frame i = 1..K_e, the two z-buffers (keys[((i-1)*2 + dir) * H*W + p], dir 0 = A
  * forward, dir 1 = B backward; key = depth bits << 32 | quantised (1 - weight) << 24 |

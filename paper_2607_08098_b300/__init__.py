@@ -44,6 +44,11 @@ class NoiseDesc(ctypes.Structure):
                 ("lo", ctypes.c_float), ("hi", ctypes.c_float), ("seed", ctypes.c_uint64)]
 
 
+class VoxelEnv(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("t0_ns", ctypes.c_int64), ("t1_ns", ctypes.c_int64)]
+
+
 class EvisError(RuntimeError):
     def __init__(self, status: int, msg: str = ""):
         self.status = status
@@ -68,6 +73,12 @@ _SIGS = {
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "evis_set_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "evis_voxel_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_void_p]),
+    "evis_voxel_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "evis_set_defocus": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "evis_defocus": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
@@ -295,6 +306,13 @@ class Context:
             raise ValueError("one sigma per environment")
         _check(lib().evis_set_defocus(self._h, sg.ctypes.data), self._h)
 
+    def voxel_grid(self, segments, bins: int = 128, workspace=None):
+        """Voxel grid of the events currently in the device buffer (read in place, count
+        taken on the device): segments as for the module-level voxel_grid, one per
+        environment; sensor sizes are the environments' minus their margins."""
+        ev, cnt = self.events_device()
+        return voxel_grid(ev, cnt, self.capacity, segments, bins, workspace, self._stream)
+
     TILE_SHAPES = ((32, 16), (32, 32), (64, 16), (64, 32), (128, 16))
 
     def set_tile_shape(self, tile_w: int, tile_h: int):
@@ -390,6 +408,40 @@ def defocus(image, sigma: float, stream=None):
     out = torch.empty((H, W), dtype=torch.float32, device=img.device)
     mode = IN_RGB if img.dim() == 3 else IN_LUM
     _check(lib().evis_defocus(_ptr(img), W, H, mode, float(sigma), _ptr(out), _stream_handle(stream)))
+    return out
+
+
+def _voxel_envs(segments):
+    arr = (VoxelEnv * len(segments))()
+    for i, (W, H, t0, t1) in enumerate(segments):
+        arr[i] = VoxelEnv(int(W), int(H), int(t0), int(t1))
+    return arr
+
+
+def voxel_workspace_size(segments, bins: int = 128) -> int:
+    n = ctypes.c_int64()
+    arr = _voxel_envs(segments)
+    _check(lib().evis_voxel_workspace_size(ctypes.addressof(arr), len(segments), int(bins),
+                                           ctypes.byref(n)))
+    return n.value
+
+
+def voxel_grid(events_ptr: int, count_ptr, max_events: int, segments, bins: int = 128,
+               workspace=None, stream=None):
+    """Event voxel grid (per polarity, linear interpolation in time, per-bin max
+    normalisation) of device event records: segments is a list of (width, height, t0_ns,
+    t1_ns) per environment; count_ptr a device uint64 pointer or None.  Returns a CUDA float
+    tensor, per environment [2][bins][H][W] concatenated."""
+    import torch
+    arr = _voxel_envs(segments)
+    wsb = voxel_workspace_size(segments, bins)
+    if workspace is None or workspace.numel() < wsb:
+        workspace = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    n_vox = sum(2 * bins * int(W) * int(H) for W, H, _, _ in segments)
+    out = torch.empty(n_vox, dtype=torch.float32, device="cuda")
+    _check(lib().evis_voxel_grid(events_ptr, count_ptr, int(max_events), ctypes.addressof(arr),
+                                 len(segments), int(bins), workspace.data_ptr(), int(workspace.numel()),
+                                 out.data_ptr(), _stream_handle(stream)))
     return out
 
 

@@ -108,3 +108,15 @@ def test_binding_fails_loudly_without_library(evis, monkeypatch):
     monkeypatch.setattr(evis, "LIB_PATH", "/nonexistent/libevis.so")
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         evis.lib()
+
+
+@pytest.mark.parametrize("seg,bins", [((0, 4, 0, 10), 8), ((4, 4, 10, 10), 8), ((4, 4, 0, 1 << 32), 8),
+                                      ((4, 4, 0, 10), 0), ((4, 4, 0, 10), 1025), ((70000, 1, 0, 10), 8)])
+def test_voxel_arguments_checked_without_a_gpu(evis, seg, bins):
+    with pytest.raises(evis.EvisError):
+        evis.voxel_workspace_size([seg], bins)
+
+
+def test_voxel_workspace_size(evis):
+    n = evis.voxel_workspace_size([(640, 480, 0, 500_000_000), (3, 2, 5, 9)], 128)
+    assert n >= 4 * 2 * 128 * (640 * 480 + 6) and n < 4 * 2 * 128 * (640 * 480 + 6) + 4096
