@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-envs", type=int, default=6, help="oracle sample size (environments)")
-    ap.add_argument("--workload", choices=["envs64", "batched"], default="envs64",
+    ap.add_argument("--workload", choices=["envs64", "batched", "stages"], default="envs64",
                     help="envs64: the benchmarked 64-env workload; batched: the uneven 256-env "
-                         "batch, per-environment launches vs one batched context vs graph replay")
+                         "batch, per-environment launches vs one batched context vs graph replay; "
+                         "stages: sensor noise, colour, margin, defocus and the voxel grid")
     return ap.parse_args()
 
 
@@ -510,11 +511,163 @@ def batched_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed_gaps(ev, envs, dev, dt, steps, warmup, flags, setup=None):
+    """ms per keyframe gap (CUDA events on the context's stream, L2 flushed between gaps) and
+    events per gap of a context over dev[k] = (frames, mv, depth) device tensors."""
+    import torch
+    probe = ev.Context(envs, eps=1e-4, flags=flags, capacity=1 << 27)
+    if setup:
+        setup(probe)
+    probe.step(*dev[0], dt)
+    probe.step(*dev[1], dt)
+    per = probe.event_count()
+    probe.close()
+    ctx = ev.Context(envs, eps=1e-4, flags=flags, capacity=int(per * 1.5 * (steps + 1)) + (1 << 20))
+    if setup:
+        setup(ctx)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ctx.step(*dev[0], dt)
+    ctx.autotune(*dev[1], dt, reps=2)
+    for k in range(1, 1 + warmup):
+        ctx.step(*dev[k], dt)
+    ctx.clear_events()
+    st = torch.cuda.current_stream()
+    ms = 0.0
+    for s_ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ctx.step(*dev[1 + warmup + s_], dt)
+        b.record(st)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    n = ctx.event_count()
+    ctx.close()
+    return ms / steps, n / steps
+
+
+def stages_arm(args):
+    """Device timings of the stages around the synthesis: sensor noise and colour events on
+    the 64 x 346x260 workload (against the plain step), an 8-pixel over-render margin, the
+    defocus kernel and the event voxel grid with their HBM rooflines."""
+    import numpy as np
+    import torch
+    import paper_2607_08098_b300 as ev
+    import scenes
+    peak, peak_src = measured_peak()
+    steps, warmup = args.steps, args.warmup
+    n_kf = warmup + steps + 1
+    w = scenes.config2(n_envs=args.envs)
+    rng = np.random.default_rng(7)
+    for e in w.envs:                                  # colour needs channels that differ
+        for lay in e.layers:
+            lay.tint_r, lay.tint_g, lay.tint_b = rng.uniform(0.4, 1.5, 3)
+    out = {"bench": "stages", "steps": steps, "warmup": warmup,
+           "workload": f"{args.envs} envs at 346x260, K=16, C=0.25, refractory 100us"}
+    units = w.pixel_substeps
+    kfs = [scenes.render(w.envs, k, want=("I", "rgb", "mv", "Z")) for k in range(n_kf)]
+    mono = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)) for kf in kfs]
+    base_ms, base_ev = _timed_gaps(ev, w.envs, mono, w.dt_ns, steps, warmup, ev.IN_LUM | ev.KEEP_INPUTS)
+    out["plain"] = {"ms_per_gap": base_ms, "mpx_substeps_per_s": units / base_ms / 1e3,
+                    "events_per_gap": base_ev}
+    noise = [dict(leak_hz=0.1, shot_hz=5.0, hot_hz=100.0, hot_fraction=1e-3, lo=-3.0, hi=3.0,
+                  seed=11)] * len(w.envs)
+    nz_ms, nz_ev = _timed_gaps(ev, w.envs, mono, w.dt_ns, steps, warmup, ev.IN_LUM | ev.KEEP_INPUTS,
+                               setup=lambda c: c.set_noise(noise))
+    out["noise"] = {"rates": "leak 0.1 Hz, shot 5 Hz (dark), hot 100 Hz on 0.1 % of pixels",
+                    "ms_per_gap": nz_ms, "mpx_substeps_per_s": units / nz_ms / 1e3,
+                    "events_per_gap": nz_ev, "cost_vs_plain": nz_ms / base_ms}
+    del mono
+    colour = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.rgb, kf.mv, kf.Z)) for kf in kfs]
+    c_ms, c_ev = _timed_gaps(ev, w.envs, colour, w.dt_ns, steps, warmup,
+                             ev.IN_RGB | ev.COLOR | ev.KEEP_INPUTS)
+    out["colour"] = {"ms_per_gap": c_ms, "mpx_substeps_per_s": units / c_ms / 1e3,
+                     "events_per_gap": c_ev, "cost_vs_plain": c_ms / base_ms,
+                     "note": "three event models per pixel-substep over one splat"}
+    del colour, kfs
+    # margin: the same scenes rendered 8 pixels larger on each side, the sensor unchanged
+    m = 8
+    wm = scenes.config2(n_envs=args.envs)
+    for e in wm.envs:
+        e.W, e.H, e.margin = e.W + 2 * m, e.H + 2 * m, m
+    kfm = [scenes.render(wm.envs, k, want=("I", "mv", "Z")) for k in range(n_kf)]
+    devm = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)) for kf in kfm]
+    m_ms, m_ev = _timed_gaps(ev, wm.envs, devm, wm.dt_ns, steps, warmup, ev.IN_LUM | ev.KEEP_INPUTS)
+    out["margin"] = {"margin_px": m, "ms_per_gap": m_ms,
+                     "sensor_mpx_substeps_per_s": units / m_ms / 1e3, "cost_vs_plain": m_ms / base_ms}
+    del devm, kfm
+    # defocus kernel on four 4096 x 4096 planes in a row (256 MB read for luminance: beyond
+    # L2), sigma 0.5 px (5 taps)
+    out["defocus"] = {}
+    for mode, ch in (("luminance", 1), ("rgb", 3)):
+        imgs = [torch.rand((4096, 4096, 3) if ch == 3 else (4096, 4096), device="cuda") + 0.01
+                for _ in range(4)]
+        st = torch.cuda.current_stream()
+        for img in imgs:
+            ev.defocus(img, 0.5)
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            outs = [ev.defocus(img, 0.5) for img in imgs]
+            b.record(st)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            del outs
+        t = float(np.median(ts))
+        alg = 4 * 4096 * 4096 * (4 * ch + 4)
+        out["defocus"][mode] = {"ms": t, "roofline": {"bound": "hbm", "achieved": alg / t / 1e6,
+                                "peak": peak, "unit": "GB/s", "frac": alg / t / 1e6 / peak,
+                                "algorithmic_bytes": alg, "peak_source": peak_src}}
+        del imgs
+    # voxel grid of a 16-gap segment (128 ms) of the high-speed workload, 8 envs at 640x480
+    w4 = scenes.config4(n_envs=8)
+    gaps = 16
+    k4 = [scenes.render(w4.envs, k, want=("L", "mv", "Z")) for k in range(gaps + 1)]
+    d4 = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.L, kf.mv, kf.Z)) for kf in k4]
+    ctx = ev.Context(w4.envs, flags=ev.IN_LOG | ev.KEEP_INPUTS, capacity=1 << 28)
+    for d in d4:
+        ctx.step(*d, w4.dt_ns)
+    n_ev = ctx.event_count()
+    segs = [(e.W, e.H, e.t0_ns, e.t0_ns + gaps * w4.dt_ns) for e in w4.envs]
+    bins = 128
+    wsb = ev.voxel_workspace_size(segs, bins)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    ctx.voxel_grid(segs, bins, ws)
+    st = torch.cuda.current_stream()
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        g = ctx.voxel_grid(segs, bins, ws)
+        b.record(st)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+        del g
+    t = float(np.median(ts))
+    vox = sum(2 * bins * W * H for W, H, _, _ in segs)
+    alg = n_ev * 16 + vox * 12
+    out["voxel_grid"] = {"workload": "8 envs at 640x480, 16 keyframe gaps (128 ms) of the "
+                                     "high-speed scenes, 128 bins per polarity",
+                         "events": n_ev, "voxels": vox, "ms": t,
+                         "events_per_s": n_ev / t * 1e3,
+                         "roofline": {"bound": "hbm", "achieved": alg / t / 1e6, "peak": peak,
+                                      "unit": "GB/s", "frac": alg / t / 1e6 / peak,
+                                      "algorithmic_bytes": alg, "peak_source": peak_src,
+                                      "bytes_model": "16 B per event read + per voxel 4 B "
+                                                     "cleared, 4 B read, 4 B written"}}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_info()
     if args.workload == "batched":
         batched_arm(args)
+        return
+    if args.workload == "stages":
+        stages_arm(args)
         return
     if args.impl == "reference":
         reference_arm(args, world, rank)
