@@ -246,7 +246,7 @@ cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, cons
     ba.plane = c->total;
     ba.max_r = c->blur_r_max;
     int max_t = 1;
-    for (const evis_env_desc &d : c->envs) max_t = std::max(max_t, ((d.width + 31) / 32) * ((d.height + 7) / 8));
+    for (const evis_env_desc &d : c->envs) max_t = std::max(max_t, ((d.width + 63) / 64) * ((d.height + 31) / 32));
     if ((e = evis::launch_defocus(ba, c->n, max_t, c->stream)) != cudaSuccess) return e;
     frames = c->d_blur;
     mode = EVIS_IN_LUM;
@@ -619,7 +619,7 @@ evis_status evis_defocus(const float *in, int32_t width, int32_t height, uint32_
   ba.out = out;
   ba.mode = mode;
   ba.max_r = ba.r;
-  const int tiles = ((width + 31) / 32) * ((height + 7) / 8);
+  const int tiles = ((width + 63) / 64) * ((height + 31) / 32);
   cudaError_t e = evis::launch_defocus(ba, 1, tiles, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
 }

@@ -109,7 +109,7 @@ struct BlurArgs {
 };
 
 cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s);
-// max_tiles: the largest environment's count of 32 x 8 tiles
+// max_tiles: the largest environment's count of 64 x 32 tiles
 cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStream_t s);
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
 // One tile shape and variant of the synthesis kernel (defined in evis_step.cuh and

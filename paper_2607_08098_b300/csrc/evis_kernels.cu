@@ -102,15 +102,78 @@ __global__ void prep_kernel(const PrepArgs a) {
   }
 }
 
-// Defocus (Sec. 3.4): separable Gaussian on linear luminance.  One CTA per 32 x 8 output
-// tile (grid-stride over an environment's tiles, blockIdx.y = environment): the tile and a
+// Defocus (Sec. 3.4): separable Gaussian on linear luminance.  One CTA per 64 x 32 output
+// tile (blockIdx.x = tile, blockIdx.y = environment, blockIdx.z = channel): the tile and a
 // halo of r pixels (edge pixels repeated) are loaded as luminance into shared memory, the
-// horizontal pass writes (8 + 2r) x 32 sums, the vertical pass the 32 x 8 outputs.  Each
-// sum runs over k = -r..r in order in binary32, as the definition states.
-constexpr int kBlurTX = 32, kBlurTY = 8;
+// horizontal pass writes (32 + 2r) x 64 sums, the vertical pass the 64 x 32 outputs.  Each
+// sum runs over k = -r..r in order in binary32, as the definition states.  Radii 0..3
+// (sigma up to 1.16 px) run unrolled with the weights in registers and a sliding window of
+// taps per thread (4 outputs of a row, 8 of a column); larger radii take a plain loop.
+constexpr int kBlurTX = 64, kBlurTY = 32, kBlurThreads = 256;
 
-__global__ void __launch_bounds__(kBlurTX * kBlurTY) defocus_kernel(const BlurArgs a) {
-  extern __shared__ float blur_sm[];
+template <int R>
+__device__ __forceinline__ void blur_passes(const float *A, float *B, const float *sw, int AW,
+                                            float *out, int W, int H, int x0, int y0) {
+  constexpr int AH = kBlurTY + 2 * R;
+  float w[2 * R + 1];
+#pragma unroll
+  for (int k = 0; k <= 2 * R; ++k) w[k] = sw[k];
+  // horizontal: thread -> one row, four adjacent columns
+  for (int i = threadIdx.x; i < AH * (kBlurTX / 4); i += kBlurThreads) {
+    const int ry = i / (kBlurTX / 4), c4 = (i % (kBlurTX / 4)) * 4;
+    float v[4 + 2 * R];
+#pragma unroll
+    for (int j = 0; j < 4 + 2 * R; ++j) v[j] = A[ry * AW + c4 + j];
+    float4 o4;
+    float *o = &o4.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k <= 2 * R; ++k) acc = __fadd_rn(acc, __fmul_rn(w[k], v[q + k]));
+      o[q] = acc;
+    }
+    *reinterpret_cast<float4 *>(B + ry * kBlurTX + c4) = o4;
+  }
+  __syncthreads();
+  // vertical: thread -> one column, eight adjacent rows
+  const int cx = threadIdx.x % kBlurTX, r8 = (threadIdx.x / kBlurTX) * 8;
+  float v[8 + 2 * R];
+#pragma unroll
+  for (int j = 0; j < 8 + 2 * R; ++j) v[j] = B[(r8 + j) * kBlurTX + cx];
+  const int x = x0 + cx;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= 2 * R; ++k) acc = __fadd_rn(acc, __fmul_rn(w[k], v[q + k]));
+    const int y = y0 + r8 + q;
+    if (x < W && y < H) out[y * W + x] = acc;
+  }
+}
+
+__device__ __forceinline__ void blur_passes_any(const float *A, float *B, const float *sw, int r,
+                                                int AW, float *out, int W, int H, int x0, int y0) {
+  const int AH = kBlurTY + 2 * r;
+  for (int i = threadIdx.x; i < AH * kBlurTX; i += kBlurThreads) {
+    const int ry = i / kBlurTX, cx = i % kBlurTX;
+    float acc = 0.0f;
+    for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], A[ry * AW + cx + k]));
+    B[i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBlurTY * kBlurTX; i += kBlurThreads) {
+    const int row = i / kBlurTX, cx = i % kBlurTX;
+    const int x = x0 + cx, y = y0 + row;
+    if (x >= W || y >= H) continue;
+    float acc = 0.0f;
+    for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], B[(row + k) * kBlurTX + cx]));
+    out[y * W + x] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kBlurThreads) defocus_kernel(const BlurArgs a) {
+  extern __shared__ __align__(16) float blur_sm[];
   __shared__ float sw[2 * kMaxBlurR + 1];
   int W, H, r;
   int64_t o = 0;
@@ -127,40 +190,55 @@ __global__ void __launch_bounds__(kBlurTX * kBlurTY) defocus_kernel(const BlurAr
     r = a.r;
     for (int i = threadIdx.x; i <= 2 * r; i += blockDim.x) sw[i] = a.w[i];
   }
-  __syncthreads();
+  const int tiles_x = (W + kBlurTX - 1) / kBlurTX;
+  const int t = blockIdx.x;
+  if (t >= tiles_x * ((H + kBlurTY - 1) / kBlurTY)) return;  // uniform over the CTA
+  const int x0 = (t % tiles_x) * kBlurTX, y0 = (t / tiles_x) * kBlurTY;
   const int AW = kBlurTX + 2 * r, AH = kBlurTY + 2 * r;
   float *A = blur_sm;            // [AH][AW] luminance with halo
-  float *B = blur_sm + AH * AW;  // [AH][32] horizontal sums
-  const int tiles_x = (W + kBlurTX - 1) / kBlurTX;
-  const int n_t = tiles_x * ((H + kBlurTY - 1) / kBlurTY);
-  for (int t = blockIdx.x; t < n_t; t += gridDim.x) {
-    const int x0 = (t % tiles_x) * kBlurTX, y0 = (t / tiles_x) * kBlurTY;
-    for (int i = threadIdx.x; i < AH * AW; i += blockDim.x) {
-      const int ry = i / AW, rx = i - ry * AW;
-      const int ys = min(max(y0 - r + ry, 0), H - 1), xs = min(max(x0 - r + rx, 0), W - 1);
-      const int64_t p = o + static_cast<int64_t>(ys) * W + xs;
-      A[i] = a.nc == 3 ? a.in[3 * p + blockIdx.z]
-                       : (a.mode == EVIS_IN_RGB ? rec709(a.in[3 * p], a.in[3 * p + 1], a.in[3 * p + 2])
-                                                : a.in[p]);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < AH * kBlurTX; i += blockDim.x) {
-      const int ry = i / kBlurTX, cx = i - ry * kBlurTX;
-      float acc = 0.0f;
-      for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], A[ry * AW + cx + k]));
-      B[i] = acc;
-    }
-    __syncthreads();
-    {
-      const int cx = threadIdx.x % kBlurTX, row = threadIdx.x / kBlurTX;
-      const int x = x0 + cx, y = y0 + row;
-      if (x < W && y < H) {
-        float acc = 0.0f;
-        for (int k = 0; k <= 2 * r; ++k) acc = __fadd_rn(acc, __fmul_rn(sw[k], B[(row + k) * kBlurTX + cx]));
-        a.out[blockIdx.z * a.plane + o + static_cast<int64_t>(y) * W + x] = acc;
+  float *B = blur_sm + ((AH * AW + 3) & ~3);  // [AH][64] horizontal sums (16-byte aligned)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, NW = kBlurThreads / 32;
+  const int ch = a.nc == 3 ? static_cast<int>(blockIdx.z) : 0;
+  const float *in = a.in + (a.nc == 3 || a.mode == EVIS_IN_RGB ? 3 * o : o);  // this environment
+  const int stride = (a.nc == 3 || a.mode == EVIS_IN_RGB) ? 3 : 1;
+  const bool lum = a.nc != 3 && a.mode == EVIS_IN_RGB;
+  // loads in batches of two rows per warp, every column chunk of a row issued before the
+  // first shared-memory store (AW <= 64 + 2 kMaxBlurR <= 128: four chunks)
+  static_assert(kBlurTX + 2 * kMaxBlurR <= 4 * 32, "four column chunks cover a halo row");
+  for (int ry0 = warp; ry0 < AH; ry0 += 2 * NW) {
+    float v[2][4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int ry = ry0 + q * NW;
+      const int row = min(max(y0 - r + ry, 0), H - 1) * W;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int rx = lane + 32 * m;
+        v[q][m] = 0.0f;
+        if (ry < AH && rx < AW) {
+          const int p = (row + min(max(x0 - r + rx, 0), W - 1)) * stride;
+          v[q][m] = lum ? rec709(__ldg(in + p), __ldg(in + p + 1), __ldg(in + p + 2)) : __ldg(in + p + ch);
+        }
       }
     }
-    __syncthreads();  // A and B are reused by the next tile
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int ry = ry0 + q * NW;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int rx = lane + 32 * m;
+        if (ry < AH && rx < AW) A[ry * AW + rx] = v[q][m];
+      }
+    }
+  }
+  __syncthreads();
+  float *out = a.out + static_cast<int64_t>(blockIdx.z) * a.plane + o;
+  switch (r) {
+    case 0: blur_passes<0>(A, B, sw, AW, out, W, H, x0, y0); break;
+    case 1: blur_passes<1>(A, B, sw, AW, out, W, H, x0, y0); break;
+    case 2: blur_passes<2>(A, B, sw, AW, out, W, H, x0, y0); break;
+    case 3: blur_passes<3>(A, B, sw, AW, out, W, H, x0, y0); break;
+    default: blur_passes_any(A, B, sw, r, AW, out, W, H, x0, y0);
   }
 }
 
@@ -199,14 +277,16 @@ cudaError_t launch_prep(const PrepArgs &a, int n_envs, cudaStream_t s) {
 cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStream_t s) {
   if (a.max_r < 0 || a.max_r > kMaxBlurR || n_envs < 1 || max_tiles < 1) return cudaErrorInvalidValue;
   const int R = a.max_r;
-  const size_t smem = sizeof(float) * static_cast<size_t>(kBlurTY + 2 * R) * (kBlurTX + 2 * R + kBlurTX);
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  // about eight CTAs per SM over the whole launch, at least one per environment
-  const int gx = max(1, min(max_tiles, (8 * sms + n_envs - 1) / n_envs));
-  defocus_kernel<<<dim3(gx, n_envs, a.nc == 3 ? 3 : 1), kBlurTX * kBlurTY, smem, s>>>(a);
+  const size_t smem = sizeof(float) * (static_cast<size_t>(kBlurTY + 2 * R) * (kBlurTX + 2 * R + kBlurTX) + 4);
+  static bool attr = false;  // up to 56 KB of shared memory at the largest radius
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(defocus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sizeof(float) * ((kBlurTY + 2 * kMaxBlurR) *
+                                                          (2 * kBlurTX + 2 * kMaxBlurR) + 4)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  defocus_kernel<<<dim3(max_tiles, n_envs, a.nc == 3 ? 3 : 1), kBlurThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
