@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--envs", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stage", choices=["all", "synthesis", "defocus", "voxel"], default="all",
+                    help="with --workload stages: the part to run")
+    ap.add_argument("--voxel-envs", type=int, default=8,
+                    help="environments (640x480) of the voxel-grid stage")
     ap.add_argument("--cpu-envs", type=int, default=6, help="oracle sample size (environments)")
     ap.add_argument("--workload", choices=["envs64", "batched", "stages"], default="envs64",
                     help="envs64: the benchmarked 64-env workload; batched: the uneven 256-env "
@@ -556,7 +560,6 @@ def stages_arm(args):
     import scenes
     peak, peak_src = measured_peak()
     steps, warmup = args.steps, args.warmup
-    n_kf = warmup + steps + 1
     w = scenes.config2(n_envs=args.envs)
     rng = np.random.default_rng(7)
     for e in w.envs:                                  # colour needs channels that differ
@@ -564,6 +567,20 @@ def stages_arm(args):
             lay.tint_r, lay.tint_g, lay.tint_b = rng.uniform(0.4, 1.5, 3)
     out = {"bench": "stages", "steps": steps, "warmup": warmup,
            "workload": f"{args.envs} envs at 346x260, K=16, C=0.25, refractory 100us"}
+    if args.stage in ("all", "synthesis"):
+        out.update(_stage_synthesis(ev, scenes, w, args))
+    if args.stage in ("all", "defocus"):
+        out["defocus"] = _stage_defocus(ev, peak, peak_src)
+    if args.stage in ("all", "voxel"):
+        out["voxel_grid"] = _stage_voxel(ev, scenes, peak, peak_src, args.voxel_envs)
+    print(json.dumps(out), flush=True)
+
+
+def _stage_synthesis(ev, scenes, w, args):
+    import torch
+    steps, warmup = args.steps, args.warmup
+    n_kf = warmup + steps + 1
+    out = {}
     units = w.pixel_substeps
     kfs = [scenes.render(w.envs, k, want=("I", "rgb", "mv", "Z")) for k in range(n_kf)]
     mono = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)) for kf in kfs]
@@ -596,9 +613,15 @@ def stages_arm(args):
     out["margin"] = {"margin_px": m, "ms_per_gap": m_ms,
                      "sensor_mpx_substeps_per_s": units / m_ms / 1e3, "cost_vs_plain": m_ms / base_ms}
     del devm, kfm
-    # defocus kernel on four 4096 x 4096 planes in a row (256 MB read for luminance: beyond
-    # L2), sigma 0.5 px (5 taps)
-    out["defocus"] = {}
+    return out
+
+
+def _stage_defocus(ev, peak, peak_src):
+    """The defocus kernel on four 4096 x 4096 planes in a row (256 MB read for luminance:
+    beyond L2), sigma 0.5 px (5 taps)."""
+    import numpy as np
+    import torch
+    res = {}
     for mode, ch in (("luminance", 1), ("rgb", 3)):
         imgs = [torch.rand((4096, 4096, 3) if ch == 3 else (4096, 4096), device="cuda") + 0.01
                 for _ in range(4)]
@@ -616,12 +639,19 @@ def stages_arm(args):
             del outs
         t = float(np.median(ts))
         alg = 4 * 4096 * 4096 * (4 * ch + 4)
-        out["defocus"][mode] = {"ms": t, "roofline": {"bound": "hbm", "achieved": alg / t / 1e6,
-                                "peak": peak, "unit": "GB/s", "frac": alg / t / 1e6 / peak,
-                                "algorithmic_bytes": alg, "peak_source": peak_src}}
+        res[mode] = {"ms": t, "roofline": {"bound": "hbm", "achieved": alg / t / 1e6,
+                     "peak": peak, "unit": "GB/s", "frac": alg / t / 1e6 / peak,
+                     "algorithmic_bytes": alg, "peak_source": peak_src}}
         del imgs
-    # voxel grid of a 16-gap segment (128 ms) of the high-speed workload, 8 envs at 640x480
-    w4 = scenes.config4(n_envs=8)
+    return res
+
+
+def _stage_voxel(ev, scenes, peak, peak_src, n_envs=8):
+    """The voxel grid of a 16-gap segment (128 ms) of the high-speed workload, n_envs envs
+    at 640x480, 128 bins per polarity."""
+    import numpy as np
+    import torch
+    w4 = scenes.config4(n_envs=n_envs)
     gaps = 16
     k4 = [scenes.render(w4.envs, k, want=("L", "mv", "Z")) for k in range(gaps + 1)]
     d4 = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.L, kf.mv, kf.Z)) for kf in k4]
@@ -647,8 +677,8 @@ def stages_arm(args):
     t = float(np.median(ts))
     vox = sum(2 * bins * W * H for W, H, _, _ in segs)
     alg = n_ev * 16 + vox * 12
-    out["voxel_grid"] = {"workload": "8 envs at 640x480, 16 keyframe gaps (128 ms) of the "
-                                     "high-speed scenes, 128 bins per polarity",
+    res = {"workload": f"{n_envs} envs at 640x480, 16 keyframe gaps (128 ms) of the "
+                       "high-speed scenes, 128 bins per polarity",
                          "events": n_ev, "voxels": vox, "ms": t,
                          "events_per_s": n_ev / t * 1e3,
                          "roofline": {"bound": "hbm", "achieved": alg / t / 1e6, "peak": peak,
@@ -657,7 +687,7 @@ def stages_arm(args):
                                       "bytes_model": "16 B per event read + per voxel 4 B "
                                                      "cleared, 4 B read, 4 B written"}}
     ctx.close()
-    print(json.dumps(out), flush=True)
+    return res
 
 
 def main():

@@ -24,6 +24,34 @@ struct VoxelEnvDev {
 };
 
 constexpr int kVoxThreads = 256;
+constexpr int kNormUnroll = 8;  // independent loads per thread per pass of voxel_normalize
+
+// q = floor(n / d) and n - q d for n < 2^48 and 0 < d < 2^32 whose quotient is below 2^20,
+// without a 64-bit division: a binary32 estimate of the quotient (relative error below
+// 2^-22, so off by at most one) corrected with exact integer arithmetic.
+__device__ __forceinline__ uint64_t div_small(uint64_t n, uint64_t d, uint64_t *rem) {
+  const float qf = floorf(__fdiv_rn(__ull2float_rn(n), __ull2float_rn(d)));
+  int64_t q = static_cast<int64_t>(qf);
+  int64_t r = static_cast<int64_t>(n) - q * static_cast<int64_t>(d);
+  if (r < 0) {
+    --q;
+    r += static_cast<int64_t>(d);
+  }
+  if (r < 0) {
+    --q;
+    r += static_cast<int64_t>(d);
+  }
+  if (r >= static_cast<int64_t>(d)) {
+    ++q;
+    r -= static_cast<int64_t>(d);
+  }
+  if (r >= static_cast<int64_t>(d)) {
+    ++q;
+    r -= static_cast<int64_t>(d);
+  }
+  *rem = static_cast<uint64_t>(r);
+  return static_cast<uint64_t>(q);
+}
 
 __global__ void __launch_bounds__(kVoxThreads) voxel_scatter(const ulonglong2 *__restrict__ ev,
                                                              const uint64_t *count, int64_t max_events,
@@ -44,8 +72,9 @@ __global__ void __launch_bounds__(kVoxThreads) voxel_scatter(const ulonglong2 *_
     if (x >= E.W || y >= E.H || t < E.t0 || t > E.t1) continue;
     const uint64_t D = static_cast<uint64_t>(E.t1 - E.t0);
     const uint64_t N = static_cast<uint64_t>(bins - 1) * static_cast<uint64_t>(t - E.t0);
-    const uint64_t b = N / D, rem = N - b * D;
-    const unsigned w_next = static_cast<unsigned>((rem << 16) / D);
+    uint64_t rem = 0, unused = 0;
+    const uint64_t b = div_small(N, D, &rem);                           // b <= bins - 1
+    const unsigned w_next = static_cast<unsigned>(div_small(rem << 16, D, &unused));  // < 2^16
     const int64_t plane = static_cast<int64_t>(E.W) * E.H;
     const int64_t base = E.off + (static_cast<int64_t>(p > 0 ? 0 : 1) * bins + static_cast<int64_t>(b)) * plane +
                          static_cast<int64_t>(y) * E.W + x;
@@ -65,7 +94,16 @@ __global__ void __launch_bounds__(kVoxThreads) voxel_normalize(const VoxelEnvDev
   const int64_t start = E.off + (q - static_cast<int64_t>(e) * 2 * bins) * plane;
   const unsigned *a = acc + start;
   unsigned mx = 0;
-  for (int64_t i = threadIdx.x; i < plane; i += kVoxThreads) mx = max(mx, a[i]);
+  for (int64_t base = threadIdx.x; base < plane; base += kVoxThreads * kNormUnroll) {
+    unsigned v[kNormUnroll];
+#pragma unroll
+    for (int u = 0; u < kNormUnroll; ++u) {
+      const int64_t i = base + u * kVoxThreads;
+      v[u] = i < plane ? __ldg(a + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kNormUnroll; ++u) mx = max(mx, v[u]);
+  }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(evis::kFull, mx, d));
   __shared__ unsigned s_mx[kVoxThreads / 32];
@@ -75,8 +113,19 @@ __global__ void __launch_bounds__(kVoxThreads) voxel_normalize(const VoxelEnvDev
   for (int w = 0; w < kVoxThreads / 32; ++w) mx = max(mx, s_mx[w]);
   float *o = out + start;
   const float fm = __uint2float_rn(mx);
-  for (int64_t i = threadIdx.x; i < plane; i += kVoxThreads)
-    o[i] = mx ? __fdiv_rn(__uint2float_rn(a[i]), fm) : 0.0f;
+  for (int64_t base = threadIdx.x; base < plane; base += kVoxThreads * kNormUnroll) {
+    unsigned v[kNormUnroll];
+#pragma unroll
+    for (int u = 0; u < kNormUnroll; ++u) {
+      const int64_t i = base + u * kVoxThreads;
+      v[u] = i < plane ? a[i] : 0u;   // the plane was just read: mostly L2 hits
+    }
+#pragma unroll
+    for (int u = 0; u < kNormUnroll; ++u) {
+      const int64_t i = base + u * kVoxThreads;
+      if (i < plane) o[i] = mx ? __fdiv_rn(__uint2float_rn(v[u]), fm) : 0.0f;
+    }
+  }
 }
 
 constexpr size_t kTableAlign = 256;
