@@ -212,7 +212,8 @@ struct StepSmem {
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
-  unsigned short hit[2][2 * kCandidates];  // candidates reaching the tile, by sub-frame parity
+  unsigned short items[kSplatItems];       // sources to splat this sub-frame: candidate | lane << 10
+  unsigned ovf[kSplatOverflow];            // candidates beyond the item list: c | lo << 16 | hi << 24
   int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
   unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
 };
@@ -265,9 +266,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
-  __shared__ unsigned s_n, s_flush, s_nhit[2], s_arrive;
+  __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_arrive;
   __shared__ unsigned long long s_base;
-  __shared__ int s_nc[2], s_over;
+  __shared__ int s_nc[2], s_over, s_ovf_full[2];
 
   const DevEnv E = a.envs[tl.env];
   const int W = E.W, H = E.H, K = E.K;
@@ -326,7 +327,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     s_n = 0;
     s_flush = 0;
     s_base = 0;
-    s_nhit[0] = s_nhit[1] = 0;
+    s_nitems[0] = s_nitems[1] = 0;
+    s_novf[0] = s_novf[1] = 0;
+    s_ovf_full[0] = s_ovf_full[1] = 0;
     s_arrive = 0;
     s_nc[0] = s_nc[1] = 0;
     s_over = 0;
@@ -415,11 +418,14 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     // Two barriers per sub-frame.  Phase 1 (list reaching candidates) may overlap other
     // warps' phase 3 of the previous sub-frame; the hit list is double-buffered by parity.
     const int par = i & 1;
-    // ---- phase 1: list the candidate segments that reach the tile at this f ----
+    // ---- phase 1: list the sources that can reach the tile at this f: for each candidate
+    // segment whose motion bounds reach the tile, the interval of its lanes (sources) whose
+    // displaced position can put a footprint pixel into the tile; the sources go into one
+    // flat list so that every lane of phase 2 splats a source that may land ----
     if (!over) {
       for (int c0 = 0; c0 < nAB; c0 += kThreads) {
         const int c = c0 + tid;
-        bool hit = false;
+        int lo = 0, cnt = 0;
         if (c < nAB) {
           const int dir = c >= nA ? 1 : 0;
           const int idx = c - dir * nA;
@@ -434,16 +440,62 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           } else {
             dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
           }
-          hit = !seg_misses<TX, TY>(small_int_to_float(static_cast<int>(xy & 0xFFFFu) * kSegW),
-                                    small_int_to_float(static_cast<int>(xy >> 16)), dxl, dxh,
-                                    dyl, dyh, tl.x0, tl.y0);
+          const int xs = static_cast<int>(xy & 0xFFFFu) * kSegW;
+          const float xsf = small_int_to_float(xs);
+          if (!seg_misses<TX, TY>(xsf, small_int_to_float(static_cast<int>(xy >> 16)), dxl, dxh,
+                                  dyl, dyh, tl.x0, tl.y0)) {
+            // a source x can reach only if x + dxh >= x0 - 1 and x + dxl < x0 + TX (its
+            // footprint spans floor(q) and floor(q) + 1); half a pixel more on each side
+            // covers rounding.  NaN bounds keep every lane.
+            const float flo = ceilf(static_cast<float>(tl.x0) - 1.5f - dxh - xsf);
+            const float fhi = ceilf(static_cast<float>(tl.x0 + TX) + 0.5f - dxl - xsf);
+            lo = flo > 0.0f ? (flo < 32.0f ? static_cast<int>(flo) : 32) : 0;
+            int hi = fhi < 32.0f ? (fhi > 0.0f ? static_cast<int>(fhi) : 0) : 32;
+            hi = min(hi, W - xs);
+            cnt = max(0, hi - lo);
+          }
         }
-        const unsigned m = __ballot_sync(kFull, hit);
-        if (m) {
-          unsigned base = 0;
-          if (lane == 0) base = atomicAdd(&s_nhit[par], static_cast<unsigned>(__popc(m)));
-          base = __shfl_sync(kFull, base, 0);
-          if (hit) S.hit[par][base + __popc(m & lanes_below)] = static_cast<unsigned short>(c);
+        // allocate the warp's items (a scan of the counts, one atomic) and write them
+        // cooperatively; what does not fit goes to the overflow list, one entry per segment
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int v = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += v;
+        }
+        const int wtot = __shfl_sync(kFull, incl, 31);
+        if (wtot == 0) continue;
+        unsigned wbase = 0;
+        if (lane == 0) wbase = atomicAdd(&s_nitems[par], static_cast<unsigned>(wtot));
+        wbase = __shfl_sync(kFull, wbase, 0);
+        const int excl = incl - cnt;
+        // items that fit in the list (uniform over the warp: every lane shuffles)
+        const int lim = wbase >= static_cast<unsigned>(kSplatItems)
+                            ? 0 : min(wtot, kSplatItems - static_cast<int>(wbase));
+        for (int j0 = 0; j0 < lim; j0 += 32) {
+          const int j = j0 + lane;
+          int own = 0;  // the lane whose interval holds item j
+#pragma unroll
+          for (int st = 16; st > 0; st >>= 1) {
+            const int v = __shfl_sync(kFull, incl, own + st - 1);
+            if (v <= j) own += st;
+          }
+          own = min(own, 31);
+          const int oc = __shfl_sync(kFull, c, own);
+          const int olo = __shfl_sync(kFull, lo, own);
+          const int oex = __shfl_sync(kFull, excl, own);
+          if (j < lim) S.items[wbase + j] = static_cast<unsigned short>(oc | ((olo + j - oex) << 10));
+        }
+        const unsigned my_start = wbase + static_cast<unsigned>(excl);
+        if (cnt > 0 && my_start + cnt > static_cast<unsigned>(kSplatItems)) {
+          const int skip = my_start < static_cast<unsigned>(kSplatItems)
+                               ? static_cast<int>(kSplatItems - my_start) : 0;
+          const unsigned pos = atomicAdd(&s_novf[par], 1u);
+          if (pos < static_cast<unsigned>(kSplatOverflow))
+            S.ovf[pos] = static_cast<unsigned>(c) | (static_cast<unsigned>(lo + skip) << 16) |
+                         (static_cast<unsigned>(lo + cnt) << 24);
+          else
+            s_ovf_full[par] = 1;
         }
       }
     }
@@ -451,7 +503,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 
     // ---- phase 2: flush the previous sub-frame's staged events (reserved by the last warp
     // to finish it), then splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
-    if (tid == 0) s_nhit[par ^ 1] = 0;
+    if (tid == 0) {
+      s_nitems[par ^ 1] = 0;
+      s_novf[par ^ 1] = 0;
+      s_ovf_full[par ^ 1] = 0;
+    }
     {
       const unsigned nf = s_flush;
       const unsigned long long gbs = s_base;
@@ -460,20 +516,30 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         if (gi < a.capacity) a.events[gi] = S.stage[r];
       }
     }
-    if (!over) {
-      const unsigned nh = s_nhit[par];
-      for (unsigned hh = warp; hh < nh; hh += NW) {  // one warp per segment, one lane per source
-        const int c = static_cast<int>(S.hit[par][hh]);
+    if (!over && !s_ovf_full[par]) {
+      const unsigned ni = min(s_nitems[par], static_cast<unsigned>(kSplatItems));
+      for (unsigned it = tid; it < ni; it += kThreads) {  // one source per lane
+        const unsigned v = S.items[it];
+        const int c = static_cast<int>(v & 1023u), l = static_cast<int>(v >> 10);
         const int dir = c >= nA ? 1 : 0;
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
-        const int xs = static_cast<int>(xy & 0xFFFFu) * kSegW, sy = static_cast<int>(xy >> 16);
-        const int sx = xs + lane;
-        if (sx < W)
-          splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy,
-                                       __fadd_rn(small_int_to_float(xs), lane_f),
+        const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + l, sy = static_cast<int>(xy >> 16);
+        splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy, small_int_to_float(sx),
+                                     small_int_to_float(sy), W, H, tl.x0, tl.y0, f, g, a, o);
+      }
+      const unsigned no = min(s_novf[par], static_cast<unsigned>(kSplatOverflow));
+      for (unsigned e = warp; e < no; e += NW) {  // overflow: one warp per segment
+        const unsigned v = S.ovf[e];
+        const int c = static_cast<int>(v & 0xFFFFu);
+        const int lo = static_cast<int>((v >> 16) & 0xFFu), hi = static_cast<int>(v >> 24);
+        const int dir = c >= nA ? 1 : 0;
+        const unsigned xy = S.cand_xy[dir][c - dir * nA];
+        const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + lane, sy = static_cast<int>(xy >> 16);
+        if (lane >= lo && lane < hi)
+          splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy, small_int_to_float(sx),
                                        small_int_to_float(sy), W, H, tl.x0, tl.y0, f, g, a, o);
       }
-    } else {
+    } else {  // the candidate or overflow lists were full: every source of the region
       for (int sy = sy0 + warp; sy < sy1; sy += NW) {
         const float fy = small_int_to_float(sy);
         for (int sx = sx0 + lane; sx < sx1; sx += 32) {

@@ -213,6 +213,29 @@ def test_wild_motion_overflows_candidate_lists(ev, oracle_mod):
         run_both(ev, oracle_mod, envs, kfs, 1_000_000, trace_steps=(1,), tile=tile)
 
 
+@pytest.mark.parametrize("amp,tile", [(3.0, (64, 16)), (3.0, (64, 32)), (14.0, (128, 16)),
+                                      (14.0, (32, 16))])
+def test_splat_work_list_overflow(ev, oracle_mod, amp, tile):
+    """Random per-pixel motion of +-amp px widens every segment's lane interval: at +-3 px on
+    64-wide tiles the sources overflow the per-sub-frame item list into the per-segment
+    overflow list; at +-14 px that list fills too and the kernel scans the region."""
+    rng = np.random.default_rng(int(amp * 10) + tile[0])
+    envs = [TinyEnv(W=200, H=120, K=3, c_on=0.2, c_off=0.2, refractory_ns=20_000)]
+    n = packed_total(envs)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(3):
+        k = KF()
+        k.mv = rng.uniform(-amp, amp, size=(n, 2)).astype(np.float32)
+        k.Z = rng.uniform(1, 5, size=n).astype(np.float32)
+        k.L = rng.normal(0, 1, size=n).astype(np.float32)
+        kfs.append(k)
+    run_both(ev, oracle_mod, envs, kfs, 1_000_000, trace_steps=(1, 2), tile=tile)
+
+
 def test_static_scene_is_per_pixel_linear_esim(ev, oracle_mod):
     envs = [TinyEnv(W=50, H=30, K=8, c_on=0.2, c_off=0.2)]
     n = packed_total(envs)
