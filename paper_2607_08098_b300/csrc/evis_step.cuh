@@ -640,19 +640,35 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           }
           bool emit = it < total;
           if (a.tlast) {
-            // refractory filter (Sec. 3.4) in order along each pixel's crossings: each owner
-            // walks its items of this chunk; t_last carries over to the next chunk
-            S.rt[warp][lane] = t;
-            __syncwarp();
-            const int lo = max(excl, c0), hi = min(incl, c0 + 32);
-            for (int cc = lo; cc < hi; ++cc) {
-              const int64_t tt = S.rt[warp][cc - c0];
-              const bool keep = refr <= 0 || tlast[j][c] == kNoEvent || tt - tlast[j][c] >= refr;
-              if (keep) tlast[j][c] = tt;
-              S.rkeep[warp][cc - c0] = keep ? 1 : 0;
+            // refractory filter (Sec. 3.4): greedy along each pixel's crossings, t_last
+            // carried over chunks.  Fast path: if every item clears the last kept time of
+            // its pixel under the assumption that its predecessors in the chunk were kept
+            // (a pixel's first item here against t_last, the others against the item just
+            // before them), then by induction the greedy filter keeps them all.
+            const int64_t t_before = __shfl_up_sync(kFull, t, 1);
+            const int64_t otl = __shfl_sync(kFull, tlast[j][c], own);
+            const bool first = k == 1 || lane == 0;  // no earlier item of its pixel in the chunk
+            const bool ok = it >= total || refr <= 0 || (first && otl == kNoEvent) ||
+                            t - (first ? otl : t_before) >= refr;
+            if (__all_sync(kFull, ok)) {
+              // all kept: each pixel's t_last is its last item's time in this chunk
+              const int last = min(incl, c0 + 32) - 1 - c0;
+              const int64_t tl_new = __shfl_sync(kFull, t, min(max(last, 0), 31));
+              if (n > 0 && incl > c0 && excl < c0 + 32) tlast[j][c] = tl_new;
+            } else {
+              // each owner walks its items of this chunk in order
+              S.rt[warp][lane] = t;
+              __syncwarp();
+              const int lo = max(excl, c0), hi = min(incl, c0 + 32);
+              for (int cc = lo; cc < hi; ++cc) {
+                const int64_t tt = S.rt[warp][cc - c0];
+                const bool keep = refr <= 0 || tlast[j][c] == kNoEvent || tt - tlast[j][c] >= refr;
+                if (keep) tlast[j][c] = tt;
+                S.rkeep[warp][cc - c0] = keep ? 1 : 0;
+              }
+              __syncwarp();
+              emit = emit && S.rkeep[warp][lane] != 0;
             }
-            __syncwarp();
-            emit = emit && S.rkeep[warp][lane] != 0;
           }
           const unsigned m = __ballot_sync(kFull, emit);
           if (m == 0) continue;
