@@ -119,16 +119,19 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
 }
 
 // True when no source of a row segment [xs, xs+31] x {ys}, displaced by an amount in
-// [dxl, dxh] x [dyl, dyh], can put a footprint pixel into the TX x TY tile at (x0, y0).  The
-// 2-pixel margin covers the footprint (1 pixel) and the rounding of the exact target
-// computation; NaN bounds never count as a miss.
+// [dxl, dxh] x [dyl, dyh], can put a footprint pixel into the TX x TY tile at (x0, y0).  A
+// source lands a footprint pixel in the tile only if its target q has x0 - 1 < q_x <
+// x0 + TX (the pixel floor(q) + 1 needs a positive weight) and likewise in y.  The bounds
+// enclose the rounded displacements and rounding is monotone, so fl(xs + 31 + dxh) bounds
+// every q_x of the segment from above and fl(xs + dxl) from below: fl(that + 1) < x0 or
+// fl(xs + dxl) >= x0 + TX excludes the tile exactly.  NaN bounds never count as a miss.
 template <int TX, int TY>
 __device__ __forceinline__ bool seg_misses(float xs, float ys, float dxl, float dxh, float dyl,
                                            float dyh, int x0, int y0) {
-  return (xs + 31.0f + dxh + 2.0f < static_cast<float>(x0)) ||
-         (xs + dxl - 2.0f > static_cast<float>(x0 + TX - 1)) ||
-         (ys + dyh + 2.0f < static_cast<float>(y0)) ||
-         (ys + dyl - 2.0f > static_cast<float>(y0 + TY - 1));
+  return (xs + 31.0f + dxh + 1.0f < static_cast<float>(x0)) ||
+         (xs + dxl >= static_cast<float>(x0 + TX)) ||
+         (ys + dyh + 1.0f < static_cast<float>(y0)) ||
+         (ys + dyl >= static_cast<float>(y0 + TY));
 }
 
 // t_prev + llrint(fr * (t_i - t_prev)) with the product taken in binary64 and rounded half to
@@ -444,11 +447,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           const float xsf = small_int_to_float(xs);
           if (!seg_misses<TX, TY>(xsf, small_int_to_float(static_cast<int>(xy >> 16)), dxl, dxh,
                                   dyl, dyh, tl.x0, tl.y0)) {
-            // a source x can reach only if x + dxh >= x0 - 1 and x + dxl < x0 + TX (its
-            // footprint spans floor(q) and floor(q) + 1); half a pixel more on each side
-            // covers rounding.  NaN bounds keep every lane.
-            const float flo = ceilf(static_cast<float>(tl.x0) - 1.5f - dxh - xsf);
-            const float fhi = ceilf(static_cast<float>(tl.x0 + TX) + 0.5f - dxl - xsf);
+            // a source x can reach only if x + dxh > x0 - 1 and x + dxl < x0 + TX (its
+            // footprint spans floor(q) and floor(q) + 1); a quarter pixel more on each side
+            // covers the rounding of these sums.  NaN bounds keep every lane.
+            const float flo = ceilf(static_cast<float>(tl.x0) - 1.25f - dxh - xsf);
+            const float fhi = ceilf(static_cast<float>(tl.x0 + TX) + 0.25f - dxl - xsf);
             lo = flo > 0.0f ? (flo < 32.0f ? static_cast<int>(flo) : 32) : 0;
             int hi = fhi < 32.0f ? (fhi > 0.0f ? static_cast<int>(fhi) : 0) : 32;
             hi = min(hi, W - xs);
