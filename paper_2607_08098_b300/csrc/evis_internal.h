@@ -17,7 +17,7 @@ constexpr int kThreads = 256;               // threads per step CTA (8 warps)
 constexpr int kEventStage = 512;            // events staged in shared memory per CTA
 constexpr int kSegW = 32;                   // motion bounds are kept per 32-pixel row segment
 constexpr int kCandidates = 512;            // candidate segments per direction per tile
-constexpr int kSplatItems = 2560;           // sources listed for one sub-frame's splat
+constexpr int kSplatItems = 1536;           // sources of partial segments listed for a splat
 constexpr int kSplatOverflow = 128;         // segments beyond that list, one warp each
 
 // Per-environment constants, resident in device memory.

@@ -215,7 +215,8 @@ struct StepSmem {
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
-  unsigned short items[kSplatItems];       // sources to splat this sub-frame: candidate | lane << 10
+  unsigned short full[2 * kCandidates];    // segments splat whole this sub-frame (candidate)
+  unsigned short items[kSplatItems];       // other sources to splat: candidate | lane << 10
   unsigned ovf[kSplatOverflow];            // candidates beyond the item list: c | lo << 16 | hi << 24
   int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
   unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
@@ -269,7 +270,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
-  __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_arrive;
+  __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_arrive;
   __shared__ unsigned long long s_base;
   __shared__ int s_nc[2], s_over, s_ovf_full[2];
 
@@ -332,6 +333,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     s_base = 0;
     s_nitems[0] = s_nitems[1] = 0;
     s_novf[0] = s_novf[1] = 0;
+    s_nfull[0] = s_nfull[1] = 0;
     s_ovf_full[0] = s_ovf_full[1] = 0;
     s_arrive = 0;
     s_nc[0] = s_nc[1] = 0;
@@ -458,6 +460,19 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
             cnt = max(0, hi - lo);
           }
         }
+        // a segment whose 32 sources all may land goes to the list of whole segments (one
+        // warp each in phase 2); the sources of the others are listed one by one
+        const bool whole = cnt == 32;
+        {
+          const unsigned wm = __ballot_sync(kFull, whole);
+          if (wm) {
+            unsigned fb = 0;
+            if (lane == 0) fb = atomicAdd(&s_nfull[par], static_cast<unsigned>(__popc(wm)));
+            fb = __shfl_sync(kFull, fb, 0);
+            if (whole) S.full[fb + __popc(wm & lanes_below)] = static_cast<unsigned short>(c);
+          }
+        }
+        if (whole) cnt = 0;
         // allocate the warp's items (a scan of the counts, one atomic) and write them
         // cooperatively; what does not fit goes to the overflow list, one entry per segment
         int incl = cnt;
@@ -509,6 +524,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     if (tid == 0) {
       s_nitems[par ^ 1] = 0;
       s_novf[par ^ 1] = 0;
+      s_nfull[par ^ 1] = 0;
       s_ovf_full[par ^ 1] = 0;
     }
     {
@@ -520,10 +536,20 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       }
     }
     if (!over && !s_ovf_full[par]) {
-      const unsigned ni = min(s_nitems[par], static_cast<unsigned>(kSplatItems));
-      for (unsigned it = tid; it < ni; it += kThreads) {  // one source per lane
-        const unsigned v = S.items[it];
-        const int c = static_cast<int>(v & 1023u), l = static_cast<int>(v >> 10);
+      // one flat index space, one source per thread: the whole segments' sources first
+      // (item it -> segment it / 32, lane it % 32), then the listed sources
+      const unsigned nwh = s_nfull[par] * 32u;
+      const unsigned ni = nwh + min(s_nitems[par], static_cast<unsigned>(kSplatItems));
+      for (unsigned it = tid; it < ni; it += kThreads) {
+        int c, l;
+        if (it < nwh) {
+          c = static_cast<int>(S.full[it >> 5]);
+          l = static_cast<int>(it & 31u);
+        } else {
+          const unsigned v = S.items[it - nwh];
+          c = static_cast<int>(v & 1023u);
+          l = static_cast<int>(v >> 10);
+        }
         const int dir = c >= nA ? 1 : 0;
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + l, sy = static_cast<int>(xy >> 16);
