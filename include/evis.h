@@ -154,11 +154,26 @@ evis_status evis_events_device(evis_ctx *ctx, evis_event **events, uint64_t **co
 /* Asynchronously empties the event buffer (stream-ordered, no synchronisation). */
 evis_status evis_clear_events(evis_ctx *ctx);
 
-/* Synchronises and copies the per-pixel reference levels [total px] and last emitted event
- * times [total px] (INT64_MIN = none) and the per-environment keyframe times [n_envs] to
- * host memory (any pointer may be null).  Last-event times are tracked only when some
- * environment of the context has a refractory period; otherwise all read INT64_MIN. */
+/* Synchronises and copies the per-pixel reference levels [nc][total px] and last emitted
+ * event times [nc][total px] (INT64_MIN = none; nc = 3 in colour mode, else 1) and the
+ * per-environment keyframe times [n_envs] to host memory (any pointer may be null).
+ * Last-event times are tracked only when some environment of the context has a refractory
+ * period; otherwise all read INT64_MIN. */
 evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t *clocks);
+
+/* Synchronises and copies the per-environment count of keyframe gaps processed (the noise
+ * generator's gap counter) [n_envs] to host memory. */
+evis_status evis_get_gaps(evis_ctx *ctx, uint32_t *gaps);
+
+/* Restores state read by evis_get_state and evis_get_gaps: checkpoint and resume.  To
+ * resume, create a context with the same environments and configuration, feed the last
+ * keyframe before the checkpoint as its first keyframe (evis_step), then call this.  The
+ * following gaps then produce what the uninterrupted context would have.  Arrays are laid
+ * out as evis_get_state's (host or device memory); a null pointer keeps that part.  t_last
+ * is ignored when the context tracks no refractory times.  EVIS_ERR_STATE before the first
+ * keyframe.  Synchronises; a captured graph stays valid. */
+evis_status evis_set_state(evis_ctx *ctx, const float *Lref, const int64_t *t_last,
+                           const int64_t *clocks, const uint32_t *gaps);
 
 /* Sensor non-idealities of one environment (Sec. 3.4).  The paper lists leak events, shot
  * noise and hot pixels without fixing their distributions; this library draws each as at most

@@ -70,6 +70,8 @@ _SIGS = {
     "evis_events_device": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "evis_clear_events": (ctypes.c_int, [ctypes.c_void_p]),
     "evis_get_state": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "evis_get_gaps": (ctypes.c_int, [ctypes.c_void_p] * 2),
+    "evis_set_state": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "evis_set_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -375,6 +377,22 @@ class Context:
         n = ctypes.c_int32()
         _check(lib().evis_profile_read(self._h, buf.ctypes.data, 4096, ctypes.byref(n)), self._h)
         return buf[:2 * n.value].reshape(-1, 2)
+
+    def gaps(self):
+        """Keyframe gaps processed per environment (the noise generator's gap counter)."""
+        g = np.empty(len(self.envs), dtype=np.uint32)
+        _check(lib().evis_get_gaps(self._h, g.ctypes.data), self._h)
+        return g
+
+    def set_state(self, Lref=None, t_last=None, clocks=None, gaps=None):
+        """Restore a checkpoint (host arrays as returned by state() and gaps()); feed the
+        last keyframe before the checkpoint first."""
+        def arr(a, dt):
+            return None if a is None else np.ascontiguousarray(a, dtype=dt)
+        keep = [arr(Lref, np.float32), arr(t_last, np.int64), arr(clocks, np.int64),
+                arr(gaps, np.uint32)]
+        ptrs = [None if a is None else a.ctypes.data for a in keep]
+        _check(lib().evis_set_state(self._h, *ptrs), self._h)
 
     def state(self):
         """(Lref, t_last, clocks); Lref and t_last hold nc planes of total pixels."""

@@ -579,6 +579,34 @@ evis_status evis_get_state(evis_ctx *c, float *Lref, int64_t *t_last, int64_t *c
   return EVIS_OK;
 }
 
+evis_status evis_get_gaps(evis_ctx *c, uint32_t *gaps) {
+  if (!c || !gaps) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(gaps, c->d_gap + c->clk * c->n, sizeof(uint32_t) * c->n, cudaMemcpyDefault);
+  return e == cudaSuccess ? EVIS_OK : cuda_fail(c, e, "copy gap counters");
+}
+
+evis_status evis_set_state(evis_ctx *c, const float *Lref, const int64_t *t_last,
+                           const int64_t *clocks, const uint32_t *gaps) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (!c->have_A) return fail(c, EVIS_ERR_STATE, "set_state needs the retained keyframe (step once first)");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "state sync");
+  const size_t px = static_cast<size_t>(c->nc) * c->total;
+  if (Lref && (e = cudaMemcpy(c->d_Lref, Lref, sizeof(float) * px, cudaMemcpyDefault)))
+    return cuda_fail(c, e, "restore Lref");
+  if (t_last && c->d_tlast && (e = cudaMemcpy(c->d_tlast, t_last, sizeof(int64_t) * px, cudaMemcpyDefault)))
+    return cuda_fail(c, e, "restore t_last");
+  if (clocks && (e = cudaMemcpy(c->d_clock + c->clk * c->n, clocks, sizeof(int64_t) * c->n,
+                                cudaMemcpyDefault)))
+    return cuda_fail(c, e, "restore clocks");
+  if (gaps && (e = cudaMemcpy(c->d_gap + c->clk * c->n, gaps, sizeof(uint32_t) * c->n,
+                              cudaMemcpyDefault)))
+    return cuda_fail(c, e, "restore gap counters");
+  return EVIS_OK;
+}
+
 evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float eps, float *out,
                                evis_stream_t stream) {
   if (n < 0 || (n > 0 && (!in || !out)) || (mode != EVIS_IN_LUM && mode != EVIS_IN_RGB) ||

@@ -120,3 +120,9 @@ def test_voxel_arguments_checked_without_a_gpu(evis, seg, bins):
 def test_voxel_workspace_size(evis):
     n = evis.voxel_workspace_size([(640, 480, 0, 500_000_000), (3, 2, 5, 9)], 128)
     assert n >= 4 * 2 * 128 * (640 * 480 + 6) and n < 4 * 2 * 128 * (640 * 480 + 6) + 4096
+
+
+def test_state_calls_reject_a_null_context_without_a_gpu(evis):
+    L = evis.lib()
+    assert L.evis_set_state(None, None, None, None, None) == evis.ERR_INVALID_ARG
+    assert L.evis_get_gaps(None, None) == evis.ERR_INVALID_ARG

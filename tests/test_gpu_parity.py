@@ -702,3 +702,46 @@ def test_colour_linear_rgb_and_defocus(ev, oracle_mod, scenes_mod):
             _per_pixel_close(eo[np.abs(eo["p"]) == c + 1], ga[np.abs(ga["p"]) == c + 1])
     with pytest.raises(ev.EvisError):
         ev.Context(envs, flags=ev.IN_LUM | ev.COLOR)
+
+
+@pytest.mark.parametrize("flags", [0x0, 0x200])
+def test_checkpoint_resume(ev, oracle_mod, scenes_mod, flags):
+    """State get/set: a context resumed from a checkpoint (state, clocks and noise gap
+    counters, after re-feeding the retained keyframe) continues exactly like the
+    uninterrupted one, in mono and colour mode, with noise and refractory periods."""
+    envs = _tint(_ragged_envs(scenes_mod))
+    kfs = [scenes_mod.render(envs, k, want=("L", "rgb", "mv", "Z")) for k in range(6)]
+    noise = [dict(leak_hz=30.0, hot_hz=200.0, hot_fraction=0.05, shot_hz=50.0, seed=4)] * len(envs)
+    dt = 16_666_667
+
+    def fr(kf):   # log-intensity input: one plane, or three in colour mode
+        return _dev(_frames(kf, 0, 3 if flags & 0x200 else 1))
+
+    full = ev.Context(envs, flags=flags, capacity=1 << 22)
+    full.set_noise(noise)
+    for kf in kfs[:3]:
+        full.step(fr(kf), _dev(kf.mv), _dev(kf.Z), dt)
+    full.read_events()
+    Lref, tl, clk = full.state()
+    gaps = full.gaps()
+    assert np.all(gaps == 2)
+    for kf in kfs[3:]:
+        full.step(fr(kf), _dev(kf.mv), _dev(kf.Z), dt)
+    want = ev.sort_events(full.read_events())
+    want_state = full.state()
+    res = ev.Context(envs, flags=flags, capacity=1 << 22)
+    res.set_noise(noise)
+    with pytest.raises(ev.EvisError):
+        res.set_state(Lref=Lref)            # no retained keyframe yet
+    res.step(fr(kfs[2]), _dev(kfs[2].mv), _dev(kfs[2].Z), dt)
+    res.read_events()
+    res.set_state(Lref=Lref, t_last=tl, clocks=clk, gaps=gaps)
+    for kf in kfs[3:]:
+        res.step(fr(kf), _dev(kf.mv), _dev(kf.Z), dt)
+    got = ev.sort_events(res.read_events())
+    assert len(want) > 1000
+    np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+    for a, b in zip(res.state(), want_state):
+        np.testing.assert_array_equal(a, b)
+    full.close()
+    res.close()
