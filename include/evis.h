@@ -161,6 +161,13 @@ evis_status evis_clear_events(evis_ctx *ctx);
  * period; otherwise all read INT64_MIN. */
 evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t *clocks);
 
+/* Statistics since creation (any pointer may be null): keyframes fed and keyframe gaps
+ * synthesised (as counted by the gap counter, which evis_set_state can restore), and per
+ * environment [n_envs] the sources, summed over all keyframes, that cannot splat: depth
+ * not finite and > 0, or a motion vector that is not finite.  Synchronises. */
+evis_status evis_get_stats(evis_ctx *ctx, uint64_t *keyframes, uint64_t *gaps,
+                           uint64_t *invalid_sources);
+
 /* Synchronises and copies the per-environment count of keyframe gaps processed (the noise
  * generator's gap counter) [n_envs] to host memory. */
 evis_status evis_get_gaps(evis_ctx *ctx, uint32_t *gaps);

@@ -71,6 +71,7 @@ _SIGS = {
     "evis_clear_events": (ctypes.c_int, [ctypes.c_void_p]),
     "evis_get_state": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "evis_get_gaps": (ctypes.c_int, [ctypes.c_void_p] * 2),
+    "evis_get_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "evis_set_state": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
@@ -377,6 +378,15 @@ class Context:
         n = ctypes.c_int32()
         _check(lib().evis_profile_read(self._h, buf.ctypes.data, 4096, ctypes.byref(n)), self._h)
         return buf[:2 * n.value].reshape(-1, 2)
+
+    def stats(self):
+        """{'keyframes', 'gaps', 'invalid_sources' [n_envs]} since creation."""
+        kf = ctypes.c_uint64()
+        gp = ctypes.c_uint64()
+        inv = np.zeros(len(self.envs), dtype=np.uint64)
+        _check(lib().evis_get_stats(self._h, ctypes.byref(kf), ctypes.byref(gp), inv.ctypes.data),
+               self._h)
+        return {"keyframes": kf.value, "gaps": gp.value, "invalid_sources": inv}
 
     def gaps(self):
         """Keyframe gaps processed per environment (the noise generator's gap counter)."""

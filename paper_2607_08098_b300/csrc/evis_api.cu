@@ -56,6 +56,7 @@ struct evis_ctx {
   float4 *d_pack[2] = {nullptr, nullptr}; // per-source packs of A and B for the current gap
   int64_t *d_clock = nullptr;  // [2][n]
   uint32_t *d_gap = nullptr;   // [2][n]: keyframe gaps processed, alternating like d_clock
+  unsigned long long *d_invalid = nullptr;  // [n]: sources that could not splat, all keyframes
   ulonglong2 *d_events = nullptr;
   unsigned long long *d_count = nullptr;
   int64_t *d_tr_off = nullptr; // [2][n]: key offsets, then L offsets
@@ -269,6 +270,7 @@ cudaError_t enqueue_prep(evis_ctx *c, const float *frames, const float *mv, cons
   pa.mode = mode;
   pa.nc = c->nc;
   pa.plane = c->total;
+  pa.invalid = c->d_invalid;
   pa.max_segs = c->max_segs;
   if ((e = evis::launch_prep(pa, c->n, c->stream)) != cudaSuccess) return e;
   out->L = c->need_L ? c->d_L[b] : frames;
@@ -450,6 +452,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
     if ((e = dalloc(c, &c->d_pack[s], c->total)) != cudaSuccess) return bail(e, "alloc source packs");
   if ((e = dalloc(c, &c->d_clock, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc clock");
   if ((e = dalloc(c, &c->d_gap, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc gap counters");
+  if ((e = dalloc(c, &c->d_invalid, n_envs)) != cudaSuccess) return bail(e, "alloc statistics");
   if ((e = dalloc(c, &c->d_events, cfg->event_capacity)) != cudaSuccess) return bail(e, "alloc events");
   if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");
   if ((e = dalloc(c, &c->d_tr_off, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc trace offsets");
@@ -468,6 +471,7 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
       (e = cudaMemcpyAsync(c->d_tr_off, troff.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s)) ||
       (e = cudaMemsetAsync(c->d_gap, 0, sizeof(uint32_t) * 2 * n_envs, s)) ||
+      (e = cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long) * n_envs, s)) ||
       // packing pads of the L slots are never written by a step: zero them once
       (c->d_L[0] && (e = cudaMemsetAsync(c->d_L[0], 0, sizeof(float) * c->nc * c->total, s))) ||
       (c->d_L[1] && (e = cudaMemsetAsync(c->d_L[1], 0, sizeof(float) * c->nc * c->total, s))) ||
@@ -585,6 +589,22 @@ evis_status evis_get_gaps(evis_ctx *c, uint32_t *gaps) {
   if (e == cudaSuccess)
     e = cudaMemcpy(gaps, c->d_gap + c->clk * c->n, sizeof(uint32_t) * c->n, cudaMemcpyDefault);
   return e == cudaSuccess ? EVIS_OK : cuda_fail(c, e, "copy gap counters");
+}
+
+evis_status evis_get_stats(evis_ctx *c, uint64_t *keyframes, uint64_t *gaps,
+                           uint64_t *invalid_sources) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stats sync");
+  uint32_t g0 = 0;
+  if ((e = cudaMemcpy(&g0, c->d_gap + c->clk * c->n, sizeof g0, cudaMemcpyDeviceToHost)))
+    return cuda_fail(c, e, "copy gap counter");
+  if (gaps) *gaps = g0;
+  if (keyframes) *keyframes = c->have_A ? static_cast<uint64_t>(g0) + 1 : 0;
+  if (invalid_sources &&
+      (e = cudaMemcpy(invalid_sources, c->d_invalid, sizeof(uint64_t) * c->n, cudaMemcpyDefault)))
+    return cuda_fail(c, e, "copy statistics");
+  return EVIS_OK;
 }
 
 evis_status evis_set_state(evis_ctx *c, const float *Lref, const int64_t *t_last,
@@ -786,7 +806,11 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
                                      cudaMemcpyDeviceToDevice))))
     return cuda_fail(c, e, "autotune save");
   KeyframeB B{};
-  if ((e = enqueue_prep(c, frames, mv, depth, &B)) != cudaSuccess) return cuda_fail(c, e, "autotune prep");
+  unsigned long long *stats = c->d_invalid;  // the trial keyframe is not counted
+  c->d_invalid = nullptr;
+  e = enqueue_prep(c, frames, mv, depth, &B);
+  c->d_invalid = stats;
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune prep");
   evis::StepArgs base = step_args(c, B, dt_ns);
   const int shapes[5][2] = {{32, 16}, {32, 32}, {64, 16}, {64, 32}, {128, 16}};
   cudaEvent_t ev0, ev1;

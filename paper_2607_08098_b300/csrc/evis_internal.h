@@ -91,6 +91,7 @@ struct PrepArgs {
   int nc;                        // planes of L_out: 1, or 3 in colour mode (0 reads as 1)
   int64_t plane;                 // channel stride of frames (planar) and L_out
   int max_segs;                  // largest environment (row segments)
+  unsigned long long *invalid;   // per environment: sources that cannot splat, accumulated (or null)
 };
 
 constexpr int kMaxBlurR = 24;                 // defocus radius limit (sigma <= 8 px)

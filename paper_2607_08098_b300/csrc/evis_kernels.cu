@@ -29,6 +29,7 @@ __global__ void prep_kernel(const PrepArgs a) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   float mx = 0.0f;
+  unsigned bad = 0;  // this lane's sources that cannot splat (the statistics)
   for (int sg = blockIdx.x * wpb + (threadIdx.x >> 5); sg < nseg; sg += gridDim.x * wpb) {
     const int y = sg / E.segs_x;
     const int x = (sg - y * E.segs_x) * kSegW + lane;
@@ -41,6 +42,8 @@ __global__ void prep_kernel(const PrepArgs a) {
         lox = hix = m.x;
         loy = hiy = m.y;
         mx = fmaxf(mx, fmaxf(fabsf(m.x), fabsf(m.y)));
+      } else {
+        ++bad;
       }
       if (a.mv_out) reinterpret_cast<float2 *>(a.mv_out)[p] = m;
       if (a.Z_out) a.Z_out[p] = z;
@@ -91,8 +94,17 @@ __global__ void prep_kernel(const PrepArgs a) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, d));
   __shared__ float sm[32];
+  __shared__ unsigned s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
   if (lane == 0) sm[threadIdx.x >> 5] = mx;
   __syncthreads();
+  if (a.invalid) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) bad += __shfl_xor_sync(kFull, bad, d);
+    if (lane == 0 && bad) atomicAdd(&s_bad, bad);
+  }
+  __syncthreads();
+  if (a.invalid && threadIdx.x == 0 && s_bad) atomicAdd(a.invalid + e, static_cast<unsigned long long>(s_bad));
   if (threadIdx.x < 32) {
     mx = threadIdx.x < wpb ? sm[threadIdx.x] : 0.0f;
 #pragma unroll

@@ -126,3 +126,4 @@ def test_state_calls_reject_a_null_context_without_a_gpu(evis):
     L = evis.lib()
     assert L.evis_set_state(None, None, None, None, None) == evis.ERR_INVALID_ARG
     assert L.evis_get_gaps(None, None) == evis.ERR_INVALID_ARG
+    assert L.evis_get_stats(None, None, None, None) == evis.ERR_INVALID_ARG

@@ -192,6 +192,34 @@ def test_adversarial_motion_and_depth(ev, oracle_mod):
     run_both(ev, oracle_mod, envs, kfs, 5_000_000, trace_steps=(1, 2))
 
 
+def test_statistics_count_sources_that_cannot_splat(ev, scenes_mod):
+    """evis_get_stats: keyframes, gaps, and per environment the sources with depth not finite
+    and > 0 or a non-finite motion vector, summed over the keyframes fed."""
+    rng = np.random.default_rng(5)
+    envs = [TinyEnv(W=40, H=30, K=2), TinyEnv(W=17, H=9, K=3)]
+    n = packed_total(envs)
+    ctx = ev.Context(envs, flags=ev.IN_LOG, capacity=1 << 16)
+    assert ctx.stats()["keyframes"] == 0
+    want = np.zeros(2, np.uint64)
+    offs = [0, (40 * 30 + 3) // 4 * 4]
+    for k in range(3):
+        L = rng.normal(0, 1, n).astype(np.float32)
+        mv = rng.normal(0, 2, (n, 2)).astype(np.float32)
+        Z = rng.uniform(1, 5, n).astype(np.float32)
+        bad = rng.random(n) < 0.1
+        Z[bad] = rng.choice([0.0, -1.0, np.nan, np.inf], bad.sum())
+        mvbad = rng.random(n) < 0.05
+        mv[mvbad, 0] = np.nan
+        for e, o in zip(envs, offs):
+            m = slice(o, o + e.W * e.H)
+            want[envs.index(e)] += np.sum(bad[m] | mvbad[m])
+        ctx.step(_dev(L), _dev(mv), _dev(Z), 1_000_000)
+    st = ctx.stats()
+    assert st["keyframes"] == 3 and st["gaps"] == 2
+    np.testing.assert_array_equal(st["invalid_sources"], want)
+    ctx.close()
+
+
 def test_wild_motion_overflows_candidate_lists(ev, oracle_mod):
     """Motion of up to +-300 px in every row segment: each tile's list of candidate source
     segments overflows and the kernel scans its whole source region instead."""
