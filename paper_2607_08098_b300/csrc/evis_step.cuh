@@ -8,18 +8,17 @@
 // splat winners, event counts, pixels and polarities are then reproducible bit for bit on
 // any IEEE host.
 //
-// step_kernel: per keyframe gap: one CTA owns a TX x TY target tile of one environment
-//   and keeps, for all K sub-frames, its pixels' event state in registers.
-//   Once per gap it lists the row segments whose motion bounds let them reach
-//   the tile; per sub-frame all threads re-test the listed segments at once,
-//   and each warp splats the sources of one reaching segment of A (forward)
-//   or B (backward) into two shared-memory
-//   z-buffers with 64-bit atomicMin on (depth, weight, source) keys
-//   (Eqs. 5-7).  It then resolves the winners,
-//   blends in time with hole filling, runs the event model (Eq. 4, Eq. 8,
-//   refractory period) and compacts the events: a warp-wide reservation per
-//   crossing index in a shared staging buffer, one global atomic per CTA per
-//   sub-frame and a coalesced 16-byte-per-thread flush.
+// step_kernel: per keyframe gap, one CTA owns a TX x TY target tile of one environment and
+//   keeps, for all K sub-frames, its pixels' event state in registers.  Once per gap it
+//   lists the row segments whose motion bounds let them reach the tile.  Per sub-frame:
+//   phase 1 re-tests the listed segments and lists the sources that may land in the tile
+//   (whole segments, and lane intervals of the others); phase 2 gives every thread one
+//   listed source and splats A forward and B backward into two shared-memory z-buffers with
+//   64-bit atomicMin on (depth, weight, source) keys (Eqs. 5-7); phase 3 resolves the
+//   winners, blends in time with hole filling, runs the event model (Eq. 4, Eq. 8,
+//   refractory period) and compacts the events: a warp-wide reservation per chunk of
+//   crossings in a shared staging buffer, one global atomic per CTA per sub-frame, and a
+//   coalesced 16-byte-per-thread flush during the next sub-frame.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -283,7 +282,6 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const float *__restrict__ LB = a.LB + o;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lanes_below = (1u << lane) - 1u;
-  const float lane_f = small_int_to_float(lane);
   const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
   const bool joint = (a.flags & EVIS_MODE_JOINT) != 0;
   const int64_t T0 = a.clock_in[tl.env];
@@ -462,8 +460,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
             cnt = max(0, hi - lo);
           }
         }
-        // a segment whose 32 sources all may land goes to the list of whole segments (one
-        // warp each in phase 2); the sources of the others are listed one by one
+        // a segment whose 32 sources all may land goes to the list of whole segments (32
+        // consecutive slots of phase 2's flat index); the sources of the others are listed
+        // one by one
         const bool whole = cnt == 32;
         {
           const unsigned wm = __ballot_sync(kFull, whole);
