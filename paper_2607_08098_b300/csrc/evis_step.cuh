@@ -271,7 +271,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
-  __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_arrive;
+  __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_p1[2], s_arrive;
   __shared__ unsigned long long s_base;
   __shared__ int s_nc[2], s_over, s_ovf_full[2];
 
@@ -334,6 +334,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     s_nitems[0] = s_nitems[1] = 0;
     s_novf[0] = s_novf[1] = 0;
     s_nfull[0] = s_nfull[1] = 0;
+    s_p1[0] = s_p1[1] = 0;
     s_ovf_full[0] = s_ovf_full[1] = 0;
     s_arrive = 0;
     s_nc[0] = s_nc[1] = 0;
@@ -428,8 +429,14 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     // displaced position can put a footprint pixel into the tile; the sources go into one
     // flat list so that every lane of phase 2 splats a source that may land ----
     if (!over) {
-      for (int c0 = 0; c0 < nAB; c0 += kThreads) {
-        const int c = c0 + tid;
+      // warps take chunks of 32 candidates from a counter: those that finish the previous
+      // sub-frame's emission first do more of this phase
+      for (;;) {
+        unsigned cb = 0;
+        if (lane == 0) cb = atomicAdd(&s_p1[par], 32u);
+        cb = __shfl_sync(kFull, cb, 0);
+        if (cb >= static_cast<unsigned>(nAB)) break;
+        const int c = static_cast<int>(cb) + lane;
         int lo = 0, cnt = 0;
         if (c < nAB) {
           const int dir = c >= nA ? 1 : 0;
@@ -526,6 +533,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       s_nitems[par ^ 1] = 0;
       s_novf[par ^ 1] = 0;
       s_nfull[par ^ 1] = 0;
+      s_p1[par ^ 1] = 0;
       s_ovf_full[par ^ 1] = 0;
     }
     {
