@@ -773,3 +773,31 @@ def test_checkpoint_resume(ev, oracle_mod, scenes_mod, flags):
         np.testing.assert_array_equal(a, b)
     full.close()
     res.close()
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (128, 16)])
+def test_extreme_shapes_and_long_k(ev, oracle_mod, tile):
+    """The size limits: a 65535-pixel-wide strip, a 65535-pixel-tall column (16-bit event
+    coordinates, 2048 row segments per row, a tile column at x0 = 65504), one pixel with
+    K = 700 sub-frames and a 4x3 image with K = 257, with motion, holes and refractory."""
+    rng = np.random.default_rng(42)
+    envs = [TinyEnv(W=65535, H=2, K=2, c_on=0.15, c_off=0.15, refractory_ns=1000),
+            TinyEnv(W=3, H=65535, K=3, c_on=0.15, c_off=0.15),
+            TinyEnv(W=1, H=1, K=700, c_on=0.01, c_off=0.01),
+            TinyEnv(W=4, H=3, K=257, c_on=0.05, c_off=0.05, refractory_ns=30_000)]
+    n = packed_total(envs)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(3):
+        k = KF()
+        k.mv = rng.uniform(-2.5, 2.5, size=(n, 2)).astype(np.float32)
+        k.Z = rng.uniform(1, 5, size=n).astype(np.float32)
+        k.Z[rng.random(n) < 0.02] = 0.0
+        k.L = rng.normal(0, 1, size=n).astype(np.float32)
+        kfs.append(k)
+    evs = run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(2,), tile=tile,
+                   capacity=1 << 23)
+    assert evs["x"].max() >= 65000 and evs["y"].max() >= 65000
