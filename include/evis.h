@@ -277,7 +277,7 @@ evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float 
                                evis_stream_t stream);
 
 /* Selects the target tile of the synthesis kernel: tile_w x tile_h pixels per CTA, one of
- * 32x16 (default), 32x32, 64x16, 64x32, 128x16.  Results do not depend on the shape, only
+ * 32x8, 32x16 (default), 32x32, 64x16, 64x32, 128x16.  Results do not depend on the shape, only
  * speed does.  Synchronises the stream; EVIS_ERR_INVALID_ARG for another shape. */
 evis_status evis_set_tile_shape(evis_ctx *ctx, int32_t tile_w, int32_t tile_h);
 

@@ -316,7 +316,7 @@ class Context:
         ev, cnt = self.events_device()
         return voxel_grid(ev, cnt, self.capacity, segments, bins, workspace, self._stream)
 
-    TILE_SHAPES = ((32, 16), (32, 32), (64, 16), (64, 32), (128, 16))
+    TILE_SHAPES = ((32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 16))
 
     def set_tile_shape(self, tile_w: int, tile_h: int):
         """Target tile of the synthesis kernel (speed only; results are identical)."""

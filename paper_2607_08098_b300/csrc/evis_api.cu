@@ -185,7 +185,7 @@ std::vector<Tile> tiles_for(const evis_ctx *c, int tw, int th, Pred take) {
 // Tile count of the smallest supported tile (the capacity of the device tile table).
 int64_t max_tiles(const evis_ctx *c) {
   int64_t n = 0;
-  for (const evis_env_desc &d : c->envs) n += int64_t((d.width + 31) / 32) * ((d.height + 15) / 16);
+  for (const evis_env_desc &d : c->envs) n += int64_t((d.width + 31) / 32) * ((d.height + 7) / 8);
   return n;
 }
 
@@ -812,7 +812,7 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
   c->d_invalid = stats;
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune prep");
   evis::StepArgs base = step_args(c, B, dt_ns);
-  const int shapes[5][2] = {{32, 16}, {32, 32}, {64, 16}, {64, 32}, {128, 16}};
+  const int shapes[6][2] = {{32, 16}, {32, 8}, {32, 32}, {64, 16}, {64, 32}, {128, 16}};
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);

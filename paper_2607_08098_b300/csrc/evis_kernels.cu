@@ -314,7 +314,7 @@ cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, flo
 }
 
 bool tile_shape_supported(int tw, int th) {
-  return (tw == 32 && (th == 16 || th == 32)) || (tw == 64 && (th == 16 || th == 32)) ||
+  return (tw == 32 && (th == 8 || th == 16 || th == 32)) || (tw == 64 && (th == 16 || th == 32)) ||
          (tw == 128 && th == 16);
 }
 
@@ -338,6 +338,7 @@ cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, i
                : (trace ? launch_shape<TX, TY, true, true, true, 1>(a, n_tiles, grid_cap, s) \
                         : (a.noise ? launch_shape<TX, TY, false, true, true, 1>(a, n_tiles, grid_cap, s) \
                                    : launch_shape<TX, TY, false, true, false, 1>(a, n_tiles, grid_cap, s)));
+  EVIS_SHAPE(32, 8)
   EVIS_SHAPE(32, 16)
   EVIS_SHAPE(32, 32)
   EVIS_SHAPE(64, 16)

@@ -4,6 +4,7 @@
 
 namespace evis {
 
+template cudaError_t launch_shape<32, 8, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
 template cudaError_t launch_shape<32, 16, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
 template cudaError_t launch_shape<32, 32, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);
 template cudaError_t launch_shape<64, 16, true, true, true, 3>(const StepArgs &, int, int, cudaStream_t);

@@ -136,7 +136,7 @@ def _ragged_envs(scenes_mod):
     return envs
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
 def test_ragged_multi_env(ev, oracle_mod, scenes_mod, tile):
     """Uneven sizes (1x1, single rows/columns, ragged tiles), per-env K, refractory, maps,
     for every tile shape of the synthesis kernel."""
@@ -491,7 +491,7 @@ def _noise_specs(n):
     return out
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
 def test_noise_ragged_multi_env(ev, oracle_mod, scenes_mod, tile):
     """Leak, shot and hot-pixel events (Sec. 3.4) with the signal events, refractory periods
     and threshold maps of the ragged set, through the production and the trace kernels."""
@@ -663,7 +663,7 @@ def _tint(envs, seed=31):
     return envs
 
 
-@pytest.mark.parametrize("tile", [(32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
+@pytest.mark.parametrize("tile", [(32, 8), (32, 16), (32, 32), (64, 16), (64, 32), (128, 16)])
 def test_colour_planes_exact(ev, oracle_mod, scenes_mod, tile):
     """Colour events (Sec. 3.2) from three log-intensity planes: bit-exact events, traced
     winners and per-channel log-intensity, per-channel reference levels and refractory
