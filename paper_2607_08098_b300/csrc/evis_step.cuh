@@ -224,10 +224,11 @@ struct StepSmem {
 // Resident CTAs per SM each tile shape is compiled for (bounded by its shared memory); it
 // sets the register budget.  Colour (NC = 3) triples the per-pixel state held in registers;
 // it runs best with more resident CTAs and some spills than with fewer and none (measured:
-// four CTAs of 32 x 16 beat three, five and six).
+// four CTAs of 32 x 16 beat three, five and six; six of 32 x 8 beat four, five ties).
 template <int TX, int TY, int NC>
 constexpr int step_min_blocks() {
-  return NC == 1 ? (TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3)) : (TX * TY <= 512 ? 4 : 3);
+  return NC == 1 ? (TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3))
+                 : (TX * TY <= 256 ? 6 : (TX * TY <= 512 ? 4 : 3));
 }
 
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
