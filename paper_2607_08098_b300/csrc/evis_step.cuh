@@ -293,7 +293,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 
   // per-pixel event state of this thread's targets (rows ty0 + ROWS j), in registers for
   // the whole keyframe gap
-  float Lref[NT][NC], Lprev[NT][NC], thon[NT], thoff[NT];
+  float Lref[NT][NC], Lprev[NT][NC];  // thresholds are read at use (constants or the maps)
   int64_t tprev[NT], tlast[NT][NC];
   bool act[NT];
 #pragma unroll
@@ -302,8 +302,6 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     const int pix = ty * W + tx;
     act[j] = tx < W - E.margin && ty < H - E.margin;  // tiles start inside the margin
     tprev[j] = T0;
-    thon[j] = E.c_on;
-    thoff[j] = E.c_off;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       tlast[j][c] = kNoEvent;
@@ -313,12 +311,6 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         Lref[j][c] = a.Lref[c * a.plane + o + pix];
         Lprev[j][c] = LA[c * a.plane + pix];
         if (a.tlast) tlast[j][c] = a.tlast[c * a.plane + o + pix];
-      }
-    }
-    if (act[j]) {
-      if (E.con_map) {
-        thon[j] = E.con_map[pix];
-        thoff[j] = E.coff_map[pix];
       }
     }
   }
@@ -600,7 +592,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         bool has = false;
-        float L = 0.0f, th = thon[j], nf = 0.0f;
+        float L = 0.0f, th = E.c_on, nf = 0.0f;
         int n = 0, pol = 1;
         if (act[j]) {
           if (c == 0) {
@@ -633,7 +625,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           if (has) {
             const float d = __fsub_rn(L, Lref[j][c]);
             pol = d > 0.0f ? 1 : -1;
-            th = pol > 0 ? thon[j] : thoff[j];
+            // Eq. 8 thresholds: the environment's, or its per-pixel maps (read through L1)
+            th = E.con_map ? __ldg((pol > 0 ? E.con_map : E.coff_map) + pix)
+                           : (pol > 0 ? E.c_on : E.c_off);
             const float q = __fdiv_rn(fabsf(d), th);
             if (q >= 1.0f) {
               if (q >= static_cast<float>(kMaxCrossings)) {
