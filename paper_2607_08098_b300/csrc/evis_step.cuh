@@ -383,8 +383,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const int nA = min(s_nc[0], kCandidates);
   const int nAB = nA + min(s_nc[1], kCandidates);
   // t_i = T0 + floor(i dt / K), stepped with a quotient and a remainder
-  const int64_t dq = a.dt / K, dr = a.dt % K;
-  int64_t tq = 0, trem = 0;
+  const int64_t dq = a.dt / K;
+  const int dr = static_cast<int>(a.dt % K);  // remainders stay below K <= 4096
+  int64_t tq = 0;
+  int trem = 0;
   // noise: this gap's counter and the hot pixels among this thread's targets (bit j NC + c)
   const bool noisy = NOISE && E.noise != 0;
   const unsigned gap = noisy ? a.gap_in[tl.env] : 0u;
