@@ -43,6 +43,11 @@ __device__ __forceinline__ float small_int_to_float(int i) {
   return __fsub_rn(__int_as_float(0x4B000000 + i), 8388608.0f);
 }
 
+// The target tile clipped to the image: pixels [x0, x0 + nx) x [y0, y0 + ny).
+struct TileBox {
+  int x0, y0, nx, ny;
+};
+
 // Splat of one source into the tile's z-buffer (Sec. 3.3).  Direction 0 moves a source of A
 // forward to q = p - f m_A with depth (1-f) Z_A(p) + f Z_B(p - m_A); direction 1 moves a source
 // of B backward to q = p + (1-f) m_B with depth (1-f) Z_A(p + m_B) + f Z_B(p) (Eqs. 5, 7).
@@ -53,7 +58,7 @@ __device__ __forceinline__ float small_int_to_float(int i) {
 // for sources that reach the tile.
 template <int TX, int TY, bool PACKED>
 __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, int sx, int sy,
-                                             float fx, float fy, int W, int H, int x0, int y0,
+                                             float fx, float fy, int W, int H, TileBox bx,
                                              float f, float g, const StepArgs &a, int64_t o) {
   const int p = sy * W + sx;
   float mx, my, zs, zo = 0.0f;
@@ -79,12 +84,14 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
     qx = __fadd_rn(fx, __fmul_rn(g, mx));
     qy = __fadd_rn(fy, __fmul_rn(g, my));
   }
-  // No footprint pixel can be inside unless -1 < q < size; this also rejects NaN.
-  if (!(qx > -1.0f && qx < static_cast<float>(W) && qy > -1.0f && qy < static_cast<float>(H)))
+  // A footprint pixel lies in the box only if x0 - 1 < q_x < x0 + nx (floor(q_x) + 1 needs
+  // a positive weight) and likewise in y.  The box lies inside the image, so this also
+  // rejects targets that leave it, and NaN.
+  if (!(qx > static_cast<float>(bx.x0 - 1) && qx < static_cast<float>(bx.x0 + bx.nx) &&
+        qy > static_cast<float>(bx.y0 - 1) && qy < static_cast<float>(bx.y0 + bx.ny)))
     return;
   float fx0, fy0;
-  const int lx0 = floor_small(qx, &fx0) - x0, ly0 = floor_small(qy, &fy0) - y0;
-  if (lx0 < -1 || lx0 >= TX || ly0 < -1 || ly0 >= TY) return;
+  const int lx0 = floor_small(qx, &fx0) - bx.x0, ly0 = floor_small(qy, &fy0) - bx.y0;  // >= -1
   if (!PACKED) {
     zo = dir == 0 ? other_depth(a.ZB + o, W, H, __fsub_rn(fx, mx), __fsub_rn(fy, my), zs)
                   : other_depth(a.ZA + o, W, H, __fadd_rn(fx, mx), __fadd_rn(fy, my), zs);
@@ -94,25 +101,29 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
   const float ax = __fsub_rn(qx, fx0), ay = __fsub_rn(qy, fy0);
   const float wx[2] = {__fsub_rn(1.0f, ax), ax};
   const float wy[2] = {__fsub_rn(1.0f, ay), ay};
-  const unsigned long long hi = (static_cast<unsigned long long>(__float_as_uint(zt)) << 32) |
-                                static_cast<unsigned>(p);
+  const bool in_x[2] = {lx0 >= 0, lx0 + 1 < bx.nx};
+  const bool in_y[2] = {ly0 >= 0, ly0 + 1 < bx.ny};
+  const unsigned long long hi = static_cast<unsigned long long>(__float_as_uint(zt)) << 32;
+  const int c00 = ly0 * TX + lx0;
   const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy) {
-    const int ly = ly0 + dy;
-    if (ly < 0 || ly >= TY || y0 + ly >= H) continue;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-      const int lx = lx0 + dx;
-      if (lx < 0 || lx >= TX || x0 + lx >= W) continue;
+      if (!(in_x[dx] && in_y[dy])) continue;
       const float w = __fmul_rn(wx[dx], wy[dy]);
-      if (!(w > 0.0f)) continue;
-      unsigned wq = 0;
+      // Inside the box the pixel floor(q) has q >= 0, so a = q - floor(q) < 1 is exact and
+      // 1 - a >= 2^-24: its weight is at least 2^-48.  The others may round to 0.
+      if ((dx | dy) && !(w > 0.0f)) continue;
+      unsigned low = static_cast<unsigned>(p);
       if (!tie_index) {
-        float unused;  // truncation of (1 - w) * 256 in [0, 256]
-        wq = min(static_cast<unsigned>(floor_small(__fmul_rn(__fsub_rn(1.0f, w), 256.0f), &unused)), 255u);
+        // (1 - w) 256 in [0, 256], rounded once (256 w is exact), clamped below 256 and
+        // truncated by a rounding-down add onto the integer grid of 1.5 x 2^23: the low byte
+        // of the sum's bits is the integer min(floor((1 - w) 256), 255)
+        const float t = fminf(__fmaf_rn(-256.0f, w, 256.0f), 255.5f);
+        low += __float_as_uint(__fadd_rd(t, 12582912.0f)) << 24;
       }
-      atomicMin(&zb[ly * TX + lx], hi | (static_cast<unsigned long long>(wq) << 24));
+      atomicMin(&zb[c00 + dy * TX + dx], hi | low);
     }
   }
 }
@@ -290,6 +301,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const int tx = tl.x0 + tid % TX;
   const int ty0 = tl.y0 + tid / TX;
   const int64_t HW = static_cast<int64_t>(W) * H;
+  const TileBox box = {tl.x0, tl.y0, min(TX, W - tl.x0), min(TY, H - tl.y0)};
 
   // per-pixel event state of this thread's targets (rows ty0 + ROWS j), in registers for
   // the whole keyframe gap
@@ -558,7 +570,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + l, sy = static_cast<int>(xy >> 16);
         splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy, small_int_to_float(sx),
-                                     small_int_to_float(sy), W, H, tl.x0, tl.y0, f, g, a, o);
+                                     small_int_to_float(sy), W, H, box, f, g, a, o);
       }
       const unsigned no = min(s_novf[par], static_cast<unsigned>(kSplatOverflow));
       for (unsigned e = warp; e < no; e += NW) {  // overflow: one warp per segment
@@ -570,15 +582,15 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + lane, sy = static_cast<int>(xy >> 16);
         if (lane >= lo && lane < hi)
           splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy, small_int_to_float(sx),
-                                       small_int_to_float(sy), W, H, tl.x0, tl.y0, f, g, a, o);
+                                       small_int_to_float(sy), W, H, box, f, g, a, o);
       }
     } else {  // the candidate or overflow lists were full: every source of the region
       for (int sy = sy0 + warp; sy < sy1; sy += NW) {
         const float fy = small_int_to_float(sy);
         for (int sx = sx0 + lane; sx < sx1; sx += 32) {
           const float fx = small_int_to_float(sx);
-          splat_source<TX, TY, PACKED>(S.zb[0], 0, sx, sy, fx, fy, W, H, tl.x0, tl.y0, f, g, a, o);
-          splat_source<TX, TY, PACKED>(S.zb[1], 1, sx, sy, fx, fy, W, H, tl.x0, tl.y0, f, g, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[0], 0, sx, sy, fx, fy, W, H, box, f, g, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[1], 1, sx, sy, fx, fy, W, H, box, f, g, a, o);
         }
       }
     }
