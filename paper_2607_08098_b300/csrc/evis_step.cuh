@@ -217,29 +217,48 @@ __device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d)
   return t0 + static_cast<int64_t>(static_cast<unsigned long long>(u) * (du >> 32) + lo);
 }
 
+// Threads of one step CTA for a tile shape: one target per thread for 32 x 16 and 64 x 16,
+// two for 32 x 32 (measured on 64 environments of 346 x 260: 3.59 ms per gap for 32 x 16 at
+// 512 threads and four CTAs per SM, against 3.75 ms at 256 threads and six), 256 threads
+// for the other shapes.
+template <int TX, int TY>
+__host__ __device__ constexpr int step_threads() {
+  return (TX == 32 && (TY == 16 || TY == 32)) ? 512 : ((TX == 64 && TY == 16) ? 1024 : kThreads);
+}
+
+// Events staged in shared memory per CTA and sub-frame (more overflow to global memory).
+template <int TX, int TY>
+__host__ __device__ constexpr int step_stage() {
+  return step_threads<TX, TY>() > kEventStage ? step_threads<TX, TY>() : kEventStage;
+}
+
 // Dynamic shared memory of one step CTA.
 template <int TX, int TY>
 struct StepSmem {
   unsigned long long zb[2][TX * TY];       // z-buffers, A forward and B backward
-  ulonglong2 stage[kEventStage];           // events of this sub-frame before the flush
+  ulonglong2 stage[step_stage<TX, TY>()];  // events of this sub-frame before the flush
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
   unsigned short full[2 * kCandidates];    // segments splat whole this sub-frame (candidate)
   unsigned short items[kSplatItems];       // other sources to splat: candidate | lane << 10
   unsigned ovf[kSplatOverflow];            // candidates beyond the item list: c | lo << 16 | hi << 24
-  int64_t rt[kThreads / 32][32];           // per warp: crossing times of one chunk
-  unsigned char rkeep[kThreads / 32][32];  // per warp: refractory decisions of one chunk
+  int64_t rt[step_threads<TX, TY>() / 32][32];           // per warp: crossing times of one chunk
+  unsigned char rkeep[step_threads<TX, TY>() / 32][32];  // per warp: refractory decisions of one chunk
 };
 
 // Resident CTAs per SM each tile shape is compiled for (bounded by its shared memory); it
-// sets the register budget.  Colour (NC = 3) triples the per-pixel state held in registers;
-// it runs best with more resident CTAs and some spills than with fewer and none (measured:
-// four CTAs of 32 x 16 beat three, five and six; six of 32 x 8 beat four, five ties).
+// sets the register budget.  Targets per thread NT decide the resident threads: 2048 (64
+// warps, 32 registers) for one target per thread in CTAs of 512 or more threads, 1536 (48
+// warps, 40 registers) for one or two otherwise, 1024 for four, 768 for more.  Colour
+// (NC = 3) triples the per-pixel state held in registers; it runs best with more resident
+// threads and some spills than with fewer and none (measured: four CTAs of 32 x 16 at 256
+// threads beat three, five and six; six of 32 x 8 beat four, five ties).
 template <int TX, int TY, int NC>
-constexpr int step_min_blocks() {
-  return NC == 1 ? (TX * TY <= 512 ? 6 : (TX * TY <= 1024 ? 4 : 3))
-                 : (TX * TY <= 256 ? 6 : (TX * TY <= 512 ? 4 : 3));
+__host__ __device__ constexpr int step_min_blocks() {
+  constexpr int nth = step_threads<TX, TY>(), nt = TX * TY / nth;
+  return (NC == 1 ? (nt == 1 && nth >= 512 ? 2048 : (nt <= 2 ? 1536 : (nt <= 4 ? 1024 : 768)))
+                  : (nt <= 1 ? 1536 : (nt <= 2 ? 1024 : 768))) / nth;
 }
 
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
@@ -255,18 +274,18 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, c
   unsigned long long gb = 0;
   if (lane == 0) {
     base = atomicAdd(s_n, cnt);
-    if (base + cnt > static_cast<unsigned>(kEventStage))
+    if (base + cnt > static_cast<unsigned>(step_stage<TX, TY>()))
       gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
-                                     base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+                                     base + cnt - max(base, static_cast<unsigned>(step_stage<TX, TY>()))));
   }
   base = __shfl_sync(kFull, base, 0);
   gb = __shfl_sync(kFull, gb, 0);
   if (emit) {
     const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
-    if (idx < static_cast<unsigned>(kEventStage)) {
+    if (idx < static_cast<unsigned>(step_stage<TX, TY>())) {
       S.stage[idx] = rec;
     } else {
-      const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
+      const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(step_stage<TX, TY>())));
       if (gi < a.capacity) a.events[gi] = rec;
     }
   }
@@ -277,10 +296,12 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, c
 // model on the R, G and B planes (Sec. 3.2), NC = 1 on the one log-intensity plane.
 template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
 __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
-  constexpr int NT = TX * TY / kThreads;   // targets per thread
-  constexpr int NW = kThreads / 32;
-  constexpr int ROWS = kThreads / TX;      // tile rows covered by one pass of the block
-  static_assert(TX % 32 == 0 && kThreads % TX == 0 && NT * kThreads == TX * TY, "tile shape");
+  constexpr int NTH = step_threads<TX, TY>();
+  constexpr int NT = TX * TY / NTH;        // targets per thread
+  constexpr int NW = NTH / 32;
+  constexpr int ROWS = NTH / TX;           // tile rows covered by one pass of the block
+  constexpr unsigned NSTAGE = step_stage<TX, TY>();
+  static_assert(TX % 32 == 0 && NTH % TX == 0 && NT * NTH == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
   __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_p1[2], s_arrive;
@@ -348,8 +369,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   // z-buffers start empty; afterwards each thread clears its own slots once it has read them
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
-    S.zb[0][tid + kThreads * j] = kEmptyKey;
-    S.zb[1][tid + kThreads * j] = kEmptyKey;
+    S.zb[0][tid + NTH * j] = kEmptyKey;
+    S.zb[1][tid + NTH * j] = kEmptyKey;
   }
   __syncthreads();
 
@@ -359,7 +380,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     const int cx_lo = sx0 / kSegW, cx_hi = (sx1 - 1) / kSegW;
     const int ncx = cx_hi - cx_lo + 1;
     const int nreg = ncx * (sy1 - sy0);
-    for (int r = tid; r < 2 * nreg; r += kThreads) {
+    for (int r = tid; r < 2 * nreg; r += NTH) {
       const int dir = r >= nreg ? 1 : 0;
       const int rr = r - dir * nreg;
       const int row = rr / ncx;
@@ -546,7 +567,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     {
       const unsigned nf = s_flush;
       const unsigned long long gbs = s_base;
-      for (unsigned r = tid; r < nf; r += kThreads) {
+      for (unsigned r = tid; r < nf; r += NTH) {
         const unsigned long long gi = gbs + r;
         if (gi < a.capacity) a.events[gi] = S.stage[r];
       }
@@ -556,7 +577,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       // (item it -> segment it / 32, lane it % 32), then the listed sources
       const unsigned nwh = s_nfull[par] * 32u;
       const unsigned ni = nwh + min(s_nitems[par], static_cast<unsigned>(kSplatItems));
-      for (unsigned it = tid; it < ni; it += kThreads) {
+      for (unsigned it = tid; it < ni; it += NTH) {
         int c, l;
         if (it < nwh) {
           c = static_cast<int>(S.full[it >> 5]);
@@ -610,10 +631,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         int n = 0, pol = 1;
         if (act[j]) {
           if (c == 0) {
-            kA = S.zb[0][tid + kThreads * j];
-            kB = S.zb[1][tid + kThreads * j];
-            S.zb[0][tid + kThreads * j] = kEmptyKey;  // ready for the next sub-frame
-            S.zb[1][tid + kThreads * j] = kEmptyKey;
+            kA = S.zb[0][tid + NTH * j];
+            kB = S.zb[1][tid + NTH * j];
+            S.zb[0][tid + NTH * j] = kEmptyKey;  // ready for the next sub-frame
+            S.zb[1][tid + NTH * j] = kEmptyKey;
           }
           const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
           const float la = hasA ? __ldg(LA + c * a.plane + (kA & 0xFFFFFFull)) : 0.0f;
@@ -724,9 +745,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           unsigned long long gb = 0;
           if (lane == 0) {
             base = atomicAdd(&s_n, cnt);
-            if (base + cnt > static_cast<unsigned>(kEventStage))  // staging full: go global
+            if (base + cnt > NSTAGE)  // staging full: go global
               gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
-                                             base + cnt - max(base, static_cast<unsigned>(kEventStage))));
+                                             base + cnt - max(base, NSTAGE)));
           }
           base = __shfl_sync(kFull, base, 0);
           gb = __shfl_sync(kFull, gb, 0);
@@ -736,11 +757,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
             const ulonglong2 rec = make_event(t, tl.x0 - E.margin + otid % TX,
                                               tl.y0 - E.margin + otid / TX + ROWS * j, tl.env,
                                               opol * (1 + c));
-            if (idx < static_cast<unsigned>(kEventStage)) {
+            if (idx < NSTAGE) {
               S.stage[idx] = rec;
             } else {
               const unsigned long long gi =
-                  gb + (idx - max(base, static_cast<unsigned>(kEventStage)));
+                  gb + (idx - max(base, NSTAGE));
               if (gi < a.capacity) a.events[gi] = rec;
             }
           }
@@ -791,7 +812,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     if (lane == 0) {
       __threadfence_block();
       if (atomicAdd(&s_arrive, 1u) == static_cast<unsigned>(NW - 1)) {
-        const unsigned nn = min(s_n, static_cast<unsigned>(kEventStage));
+        const unsigned nn = min(s_n, NSTAGE);
         s_flush = nn;
         s_base = nn ? atomicAdd(a.ev_count, static_cast<unsigned long long>(nn)) : 0ull;
         s_n = 0;
@@ -803,7 +824,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   {
     const unsigned nf = s_flush;
     const unsigned long long gbs = s_base;
-    for (unsigned r = tid; r < nf; r += kThreads) {
+    for (unsigned r = tid; r < nf; r += NTH) {
       const unsigned long long gi = gbs + r;
       if (gi < a.capacity) a.events[gi] = S.stage[r];
     }
@@ -828,7 +849,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 // One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
 // first one by block index, the next ones from a work counter that starts at 0.
 template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
-__global__ void __launch_bounds__(kThreads, step_min_blocks<TX, TY, NC>()) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY, NC>())
+    step_kernel(const StepArgs a) {
   __shared__ int s_tile;
   int t = blockIdx.x;
   while (t < a.n_tiles) {
@@ -855,13 +877,14 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>, kThreads, smem)) != cudaSuccess)
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>, step_threads<TX, TY>(),
+             smem)) != cudaSuccess)
       return e;
     resident = max(1, per_sm) * sms;
   }
   int grid = n_tiles;
   if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
-  step_kernel<TX, TY, TRACE, PACKED, NOISE, NC><<<grid, kThreads, smem, s>>>(a);
+  step_kernel<TX, TY, TRACE, PACKED, NOISE, NC><<<grid, step_threads<TX, TY>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 
