@@ -68,7 +68,6 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
     my = v.y;
     zs = v.z;
     zo = v.w;
-    if (!valid_depth(zs)) return;
   } else {
     zs = __ldg((dir ? a.ZB : a.ZA) + o + p);
     if (!valid_depth(zs)) return;
@@ -86,9 +85,10 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
   }
   // A footprint pixel lies in the box only if x0 - 1 < q_x < x0 + nx (floor(q_x) + 1 needs
   // a positive weight) and likewise in y.  The box lies inside the image, so this also
-  // rejects targets that leave it, and NaN.
-  if (!(qx > static_cast<float>(bx.x0 - 1) && qx < static_cast<float>(bx.x0 + bx.nx) &&
-        qy > static_cast<float>(bx.y0 - 1) && qy < static_cast<float>(bx.y0 + bx.ny)))
+  // rejects targets that leave it, and NaN.  (Packed sources check their depth here too.)
+  if (!((!PACKED || valid_depth(zs)) && qx > static_cast<float>(bx.x0 - 1) &&
+        qx < static_cast<float>(bx.x0 + bx.nx) && qy > static_cast<float>(bx.y0 - 1) &&
+        qy < static_cast<float>(bx.y0 + bx.ny)))
     return;
   float fx0, fy0;
   const int lx0 = floor_small(qx, &fx0) - bx.x0, ly0 = floor_small(qy, &fy0) - bx.y0;  // >= -1
@@ -106,24 +106,22 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
   const unsigned long long hi = static_cast<unsigned long long>(__float_as_uint(zt)) << 32;
   const int c00 = ly0 * TX + lx0;
   const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
+  // Straight-line code: every cell's key is formed, only the atomic is predicated.
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy) {
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-      if (!(in_x[dx] && in_y[dy])) continue;
       const float w = __fmul_rn(wx[dx], wy[dy]);
       // Inside the box the pixel floor(q) has q >= 0, so a = q - floor(q) < 1 is exact and
       // 1 - a >= 2^-24: its weight is at least 2^-48.  The others may round to 0.
-      if ((dx | dy) && !(w > 0.0f)) continue;
-      unsigned low = static_cast<unsigned>(p);
-      if (!tie_index) {
-        // (1 - w) 256 in [0, 256], rounded once (256 w is exact), clamped below 256 and
-        // truncated by a rounding-down add onto the integer grid of 1.5 x 2^23: the low byte
-        // of the sum's bits is the integer min(floor((1 - w) 256), 255)
-        const float t = fminf(__fmaf_rn(-256.0f, w, 256.0f), 255.5f);
-        low += __float_as_uint(__fadd_rd(t, 12582912.0f)) << 24;
-      }
-      atomicMin(&zb[c00 + dy * TX + dx], hi | low);
+      const bool ok = in_x[dx] && in_y[dy] && ((dx | dy) == 0 || w > 0.0f);
+      // (1 - w) 256 in [0, 256], rounded once (256 w is exact), clamped below 256 and
+      // truncated by a rounding-down add onto the integer grid of 1.5 x 2^23: the low byte
+      // of the sum's bits is the integer min(floor((1 - w) 256), 255)
+      const float t = fminf(__fmaf_rn(-256.0f, w, 256.0f), 255.5f);
+      const unsigned low = static_cast<unsigned>(p) +
+                           (tie_index ? 0u : __float_as_uint(__fadd_rd(t, 12582912.0f)) << 24);
+      if (ok) atomicMin(&zb[c00 + dy * TX + dx], hi | low);
     }
   }
 }
@@ -226,10 +224,14 @@ __host__ __device__ constexpr int step_threads() {
   return (TX == 32 && (TY == 16 || TY == 32)) ? 512 : ((TX == 64 && TY == 16) ? 1024 : kThreads);
 }
 
-// Events staged in shared memory per CTA and sub-frame (more overflow to global memory).
+// Events staged in shared memory per CTA and sub-frame (more go to global memory one warp
+// reservation at a time): two per target up to 2048, 1024 for the largest tiles, whose
+// shared memory would otherwise cost resident CTAs.  On 32 x 346x260 environments (K=16,
+// 0.72 events per pixel-substep) 1 % of the emission chunks of 32 x 16 tiles then overflow
+// the stage, against 16 % with 512 events.
 template <int TX, int TY>
 __host__ __device__ constexpr int step_stage() {
-  return step_threads<TX, TY>() > kEventStage ? step_threads<TX, TY>() : kEventStage;
+  return TX * TY >= 2048 ? 1024 : (2 * TX * TY < kEventStage ? kEventStage : 2 * TX * TY);
 }
 
 // Dynamic shared memory of one step CTA.
@@ -623,6 +625,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     for (int j = 0; j < NT; ++j) {
       const int ty = ty0 + ROWS * j;
       const int pix = ty * W + tx;
+      // sensor (x | y << 16) of the warp's first target; its lanes add their index
+      const unsigned ev_xy = static_cast<unsigned>(tl.x0 - E.margin + (warp * 32) % TX) |
+                             (static_cast<unsigned>(ty - E.margin) << 16);
       unsigned long long kA = kEmptyKey, kB = kEmptyKey;  // read at channel 0
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
@@ -742,27 +747,32 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           if (m == 0) continue;
           const unsigned cnt = static_cast<unsigned>(__popc(m));
           unsigned base = 0;
-          unsigned long long gb = 0;
-          if (lane == 0) {
-            base = atomicAdd(&s_n, cnt);
-            if (base + cnt > NSTAGE)  // staging full: go global
-              gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
-                                             base + cnt - max(base, NSTAGE)));
-          }
+          if (lane == 0) base = atomicAdd(&s_n, cnt);
           base = __shfl_sync(kFull, base, 0);
-          gb = __shfl_sync(kFull, gb, 0);
-          if (emit) {
-            const int otid = warp * 32 + own;
-            const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
-            const ulonglong2 rec = make_event(t, tl.x0 - E.margin + otid % TX,
-                                              tl.y0 - E.margin + otid / TX + ROWS * j, tl.env,
-                                              opol * (1 + c));
-            if (idx < NSTAGE) {
-              S.stage[idx] = rec;
-            } else {
-              const unsigned long long gi =
-                  gb + (idx - max(base, NSTAGE));
-              if (gi < a.capacity) a.events[gi] = rec;
+          const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
+          // the warp's 32 targets are consecutive pixels of one row: the owner's sensor x
+          // is the warp's first x plus its lane (below 2^16, so the add stays in its field)
+          ulonglong2 rec;
+          rec.x = static_cast<unsigned long long>(t);
+          rec.y = static_cast<unsigned long long>(ev_xy + static_cast<unsigned>(own)) |
+                  (static_cast<unsigned long long>(
+                       (static_cast<unsigned>(tl.env) & 0xFFFFu) |
+                       (static_cast<unsigned>(static_cast<uint16_t>(static_cast<int16_t>(opol * (1 + c)))) << 16))
+                   << 32);
+          if (base + cnt <= NSTAGE) {  // (uniform) the chunk fits in the stage
+            if (emit) S.stage[idx] = rec;
+          } else {  // staging full: what does not fit goes to global memory directly
+            unsigned long long gb = 0;
+            if (lane == 0)
+              gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(base + cnt - max(base, NSTAGE)));
+            gb = __shfl_sync(kFull, gb, 0);
+            if (emit) {
+              if (idx < NSTAGE) {
+                S.stage[idx] = rec;
+              } else {
+                const unsigned long long gi = gb + (idx - max(base, NSTAGE));
+                if (gi < a.capacity) a.events[gi] = rec;
+              }
             }
           }
           __syncwarp();  // the next chunk reuses this warp's refractory scratch
