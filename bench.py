@@ -562,8 +562,9 @@ def batched_arm(args):
 
 
 def _timed_gaps(ev, envs, dev, dt, steps, warmup, flags, setup=None):
-    """ms per keyframe gap (CUDA events on the context's stream, L2 flushed between gaps) and
-    events per gap of a context over dev[k] = (frames, mv, depth) device tensors."""
+    """ms per keyframe gap (CUDA events on the context's stream, L2 flushed between gaps),
+    events per gap and the autotuned tile shape of a context over dev[k] = (frames, mv, depth)
+    device tensors."""
     import torch
     probe = ev.Context(envs, eps=1e-4, flags=flags, capacity=1 << 27)
     if setup:
@@ -592,8 +593,9 @@ def _timed_gaps(ev, envs, dev, dt, steps, warmup, flags, setup=None):
         b.synchronize()
         ms += a.elapsed_time(b)
     n = ctx.event_count()
+    sh = ctx.tile_shapes()[0]
     ctx.close()
-    return ms / steps, n / steps
+    return ms / steps, n / steps, f"{sh[0]}x{sh[1]}"
 
 
 def stages_arm(args):
@@ -630,22 +632,23 @@ def _stage_synthesis(ev, scenes, w, args):
     units = w.pixel_substeps
     kfs = [scenes.render(w.envs, k, want=("I", "rgb", "mv", "Z")) for k in range(n_kf)]
     mono = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)) for kf in kfs]
-    base_ms, base_ev = _timed_gaps(ev, w.envs, mono, w.dt_ns, steps, warmup, ev.IN_LUM | ev.KEEP_INPUTS)
+    base_ms, base_ev, sh = _timed_gaps(ev, w.envs, mono, w.dt_ns, steps, warmup,
+                                       ev.IN_LUM | ev.KEEP_INPUTS)
     out["plain"] = {"ms_per_gap": base_ms, "mpx_substeps_per_s": units / base_ms / 1e3,
-                    "events_per_gap": base_ev}
+                    "events_per_gap": base_ev, "tile_shape": sh}
     noise = [dict(leak_hz=0.1, shot_hz=5.0, hot_hz=100.0, hot_fraction=1e-3, lo=-3.0, hi=3.0,
                   seed=11)] * len(w.envs)
-    nz_ms, nz_ev = _timed_gaps(ev, w.envs, mono, w.dt_ns, steps, warmup, ev.IN_LUM | ev.KEEP_INPUTS,
-                               setup=lambda c: c.set_noise(noise))
+    nz_ms, nz_ev, sh = _timed_gaps(ev, w.envs, mono, w.dt_ns, steps, warmup,
+                                   ev.IN_LUM | ev.KEEP_INPUTS, setup=lambda c: c.set_noise(noise))
     out["noise"] = {"rates": "leak 0.1 Hz, shot 5 Hz (dark), hot 100 Hz on 0.1 % of pixels",
                     "ms_per_gap": nz_ms, "mpx_substeps_per_s": units / nz_ms / 1e3,
-                    "events_per_gap": nz_ev, "cost_vs_plain": nz_ms / base_ms}
+                    "events_per_gap": nz_ev, "cost_vs_plain": nz_ms / base_ms, "tile_shape": sh}
     del mono
     colour = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.rgb, kf.mv, kf.Z)) for kf in kfs]
-    c_ms, c_ev = _timed_gaps(ev, w.envs, colour, w.dt_ns, steps, warmup,
-                             ev.IN_RGB | ev.COLOR | ev.KEEP_INPUTS)
+    c_ms, c_ev, sh = _timed_gaps(ev, w.envs, colour, w.dt_ns, steps, warmup,
+                                 ev.IN_RGB | ev.COLOR | ev.KEEP_INPUTS)
     out["colour"] = {"ms_per_gap": c_ms, "mpx_substeps_per_s": units / c_ms / 1e3,
-                     "events_per_gap": c_ev, "cost_vs_plain": c_ms / base_ms,
+                     "events_per_gap": c_ev, "cost_vs_plain": c_ms / base_ms, "tile_shape": sh,
                      "note": "three event models per pixel-substep over one splat"}
     del colour, kfs
     # margin: the same scenes rendered 8 pixels larger on each side, the sensor unchanged
@@ -655,8 +658,9 @@ def _stage_synthesis(ev, scenes, w, args):
         e.W, e.H, e.margin = e.W + 2 * m, e.H + 2 * m, m
     kfm = [scenes.render(wm.envs, k, want=("I", "mv", "Z")) for k in range(n_kf)]
     devm = [tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)) for kf in kfm]
-    m_ms, m_ev = _timed_gaps(ev, wm.envs, devm, wm.dt_ns, steps, warmup, ev.IN_LUM | ev.KEEP_INPUTS)
-    out["margin"] = {"margin_px": m, "ms_per_gap": m_ms,
+    m_ms, m_ev, sh = _timed_gaps(ev, wm.envs, devm, wm.dt_ns, steps, warmup,
+                                 ev.IN_LUM | ev.KEEP_INPUTS)
+    out["margin"] = {"margin_px": m, "ms_per_gap": m_ms, "tile_shape": sh,
                      "sensor_mpx_substeps_per_s": units / m_ms / 1e3, "cost_vs_plain": m_ms / base_ms}
     del devm, kfm
     return out

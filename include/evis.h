@@ -244,7 +244,8 @@ typedef struct {
   int64_t t0_ns, t1_ns;    /* segment, 0 < t1_ns - t0_ns < 2^32 */
 } evis_voxel_env;
 
-/* Device workspace bytes of evis_voxel_grid (a descriptor table and one uint32 per voxel). */
+/* Device workspace bytes of evis_voxel_grid (a descriptor table, one uint32 per plane for
+ * its maximum and one uint32 per voxel). */
 evis_status evis_voxel_workspace_size(const evis_voxel_env *envs, int32_t n_envs, int32_t bins,
                                       int64_t *bytes);
 

@@ -1,6 +1,7 @@
 """The event voxel grid on the GPU against the oracle, bit for bit (needs a B300): random
-records with skips and colour polarities, the device-side count, and the grid of a
-synthesis step read in place from the library's event buffer."""
+records with skips and colour polarities, the device-side count, planes on both sides of the
+cluster normalisation's size limit, and the grid of a synthesis step read in place from the
+library's event buffer."""
 import numpy as np
 import pytest
 
@@ -47,6 +48,18 @@ def test_voxel_grid_random_records(ev, oracle_mod, bins):
     _, want2 = oracle_mod.voxel_grid(rec[:250_000], segs, bins=bins)
     got2 = ev.voxel_grid(d.data_ptr(), cnt.data_ptr(), rec.size, segs, bins).cpu().numpy()
     np.testing.assert_array_equal(got2, want2)
+
+
+def test_voxel_grid_large_planes(ev, oracle_mod):
+    """A plane above 327,680 voxels (1280 x 720) sends the whole call to the one-CTA-per-plane
+    normalisation; the smaller planes of the same call must come out the same."""
+    rng = np.random.default_rng(5)
+    segs = [(1280, 720, 0, 50_000_000), (64, 48, 1_000, 2_001_000), (640, 480, 7, 99_999)]
+    rec = _records(rng, 300_000, segs)
+    _, want = oracle_mod.voxel_grid(rec, segs, bins=3)
+    d = torch.from_numpy(rec.view(np.int64).reshape(-1)).cuda()
+    got = ev.voxel_grid(d.data_ptr(), None, rec.size, segs, 3).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
 
 
 def test_voxel_grid_of_a_synthesis_step(ev, oracle_mod, scenes_mod):
