@@ -144,11 +144,26 @@ evis_status evis_step_host(evis_ctx *ctx, const float *frames, const float *mv,
  * events are delivered and the per-pixel state has advanced as if none were lost. */
 evis_status evis_read_events(evis_ctx *ctx, evis_event *dst, int64_t cap, int64_t *n_out);
 
+/* Pipelined read-back: waits until the stream has passed every step enqueued so far (and
+ * for the previous call's copy), starts copying the buffered events (in no particular
+ * order, up to cap) to dst on the library's own copy stream, and switches the context to
+ * its second event buffer, so that the steps enqueued next run while the copy proceeds.
+ * *n_out and EVIS_ERR_OVERFLOW as for evis_read_events.  dst (host memory should be
+ * pinned) is complete once the next evis_read_events_async or evis_read_wait returns, and
+ * must stay valid until then.  The first call allocates the second buffer (event_capacity
+ * records) and the copy stream.  Captured graphs are discarded (they hold the other
+ * buffer's address). */
+evis_status evis_read_events_async(evis_ctx *ctx, evis_event *dst, int64_t cap, int64_t *n_out);
+
+/* Waits for the copy started by the last evis_read_events_async (no-op if none). */
+evis_status evis_read_wait(evis_ctx *ctx);
+
 /* Synchronises and reports the number of events produced since the last read. */
 evis_status evis_event_count(evis_ctx *ctx, int64_t *n_out);
 
 /* Device-side view of the event buffer for consumers on the GPU: *events points to the
- * capacity-sized array, *count to the 64-bit produced-event counter.  Valid until destroy. */
+ * capacity-sized array, *count to the 64-bit produced-event counter.  Valid until destroy
+ * or the next evis_read_events_async (which switches buffers). */
 evis_status evis_events_device(evis_ctx *ctx, evis_event **events, uint64_t **count);
 
 /* Asynchronously empties the event buffer (stream-ordered, no synchronisation). */

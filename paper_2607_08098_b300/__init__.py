@@ -66,6 +66,9 @@ _SIGS = {
                         [ctypes.c_void_p] * 2),
     "evis_read_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p]),
+    "evis_read_events_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_void_p]),
+    "evis_read_wait": (ctypes.c_int, [ctypes.c_void_p]),
     "evis_event_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "evis_events_device": (ctypes.c_int, [ctypes.c_void_p] * 3),
     "evis_clear_events": (ctypes.c_int, [ctypes.c_void_p]),
@@ -267,6 +270,19 @@ class Context:
             return out[:min(n.value, cap)], n.value
         _check(st, self._h)
         return (out[:n.value], n.value) if allow_overflow else out[:n.value]
+
+    def read_events_async(self, dst_ptr: int, cap: int) -> int:
+        """Start copying the buffered events to dst_ptr (pinned host or device memory, room
+        for cap records) while the next steps fill the context's other buffer; returns the
+        number of events produced since the last read.  dst is complete once the next
+        read_events_async or read_wait returns."""
+        n = ctypes.c_int64()
+        _check(lib().evis_read_events_async(self._h, dst_ptr, int(cap), ctypes.byref(n)), self._h)
+        return n.value
+
+    def read_wait(self):
+        """Wait for the copy started by the last read_events_async."""
+        _check(lib().evis_read_wait(self._h), self._h)
 
     def event_count(self) -> int:
         n = ctypes.c_int64()

@@ -57,8 +57,14 @@ struct evis_ctx {
   int64_t *d_clock = nullptr;  // [2][n]
   uint32_t *d_gap = nullptr;   // [2][n]: keyframe gaps processed, alternating like d_clock
   unsigned long long *d_invalid = nullptr;  // [n]: sources that could not splat, all keyframes
-  ulonglong2 *d_events = nullptr;
+  ulonglong2 *d_events = nullptr;          // the buffer the steps append to
   unsigned long long *d_count = nullptr;
+  // pipelined read-back: the second buffer, and the copy of the other one in flight
+  ulonglong2 *d_events_alt = nullptr;
+  unsigned long long *d_count_alt = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done = nullptr;
+  bool copy_pending = false;
   int64_t *d_tr_off = nullptr; // [2][n]: key offsets, then L offsets
   float *d_in[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   int in_slot = 0;
@@ -146,6 +152,12 @@ cudaError_t dalloc(evis_ctx *c, T **p, size_t count) {
 }
 
 void release(evis_ctx *c) {
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);  // a read-back may be in flight
+  if (c->copy_done) cudaEventDestroy(c->copy_done);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  c->copy_done = nullptr;
+  c->copy_stream = nullptr;
+  c->copy_pending = false;
   for (auto &g : c->graph) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
@@ -537,6 +549,57 @@ evis_status evis_read_events(evis_ctx *c, evis_event *dst, int64_t cap, int64_t 
     return cuda_fail(c, e, "reset count");
   *n_out = produced;
   return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+}
+
+evis_status evis_read_events_async(evis_ctx *c, evis_event *dst, int64_t cap, int64_t *n_out) {
+  if (!c || !n_out || cap < 0 || (cap > 0 && !dst)) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e;
+  if (!c->copy_stream) {  // first call: the copy stream, its event and the second buffer
+    if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(c, e, "copy stream");
+    if ((e = cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(c, e, "copy event");
+    if ((e = dalloc(c, &c->d_events_alt, c->cfg.event_capacity)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_count_alt, 1)) != cudaSuccess)
+      return cuda_fail(c, e, "alloc second event buffer");
+  }
+  // every step enqueued so far has finished, and so has the previous read-back, whose
+  // buffer the next steps will fill
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "read sync");
+  if (c->copy_pending) {
+    if ((e = cudaEventSynchronize(c->copy_done)) != cudaSuccess) return cuda_fail(c, e, "copy wait");
+    c->copy_pending = false;
+  }
+  unsigned long long cnt = 0;
+  if ((e = cudaMemcpy(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "read count");
+  const int64_t produced = static_cast<int64_t>(cnt);
+  const int64_t n = std::min<int64_t>(produced, std::min<int64_t>(c->cfg.event_capacity, cap));
+  if (n > 0 && (e = cudaMemcpyAsync(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault,
+                                    c->copy_stream)) != cudaSuccess)
+    return cuda_fail(c, e, "copy events");
+  if ((e = cudaEventRecord(c->copy_done, c->copy_stream)) != cudaSuccess)
+    return cuda_fail(c, e, "copy record");
+  c->copy_pending = true;
+  // the next steps append to the other buffer, its count zeroed first in stream order;
+  // captured graphs hold the old buffer's address
+  std::swap(c->d_events, c->d_events_alt);
+  std::swap(c->d_count, c->d_count_alt);
+  if ((e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "reset count");
+  drop_graphs(c);
+  *n_out = produced;
+  return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+}
+
+evis_status evis_read_wait(evis_ctx *c) {
+  if (!c) return EVIS_ERR_INVALID_ARG;
+  if (c->copy_pending) {
+    cudaError_t e = cudaEventSynchronize(c->copy_done);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy wait");
+    c->copy_pending = false;
+  }
+  return EVIS_OK;
 }
 
 evis_status evis_event_count(evis_ctx *c, int64_t *n_out) {

@@ -127,3 +127,10 @@ def test_state_calls_reject_a_null_context_without_a_gpu(evis):
     assert L.evis_set_state(None, None, None, None, None) == evis.ERR_INVALID_ARG
     assert L.evis_get_gaps(None, None) == evis.ERR_INVALID_ARG
     assert L.evis_get_stats(None, None, None, None) == evis.ERR_INVALID_ARG
+
+
+def test_pipelined_readback_rejects_a_null_context_without_a_gpu(evis):
+    L = evis.lib()
+    n = ctypes.c_int64()
+    assert L.evis_read_events_async(None, None, 0, ctypes.byref(n)) == evis.ERR_INVALID_ARG
+    assert L.evis_read_wait(None) == evis.ERR_INVALID_ARG

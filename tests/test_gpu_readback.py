@@ -1,0 +1,58 @@
+"""Pipelined event read-back on the GPU (needs a B300): events copied by
+evis_read_events_async while the next keyframe gaps run are the same records, gap by gap,
+as a context read synchronously after every gap."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_08098_b300 import build
+    build.build()
+    import paper_2607_08098_b300 as m
+    return m
+
+
+def _gaps(scenes_mod, n_kf):
+    w = scenes_mod.config2(n_envs=4)
+    kfs = [scenes_mod.render(w.envs, k) for k in range(n_kf)]
+    dev = [(torch.from_numpy(kf.L).cuda(), torch.from_numpy(kf.mv.reshape(-1)).cuda(),
+            torch.from_numpy(kf.Z).cuda()) for kf in kfs]
+    return w, dev
+
+
+def test_pipelined_readback_matches_synchronous_reads(ev, scenes_mod):
+    w, dev = _gaps(scenes_mod, 7)
+    cap = 1 << 22
+    a = ev.Context(w.envs, flags=ev.IN_LOG, capacity=cap)
+    want = []
+    for d in dev:
+        a.step(*d, w.dt_ns)
+        want.append(np.sort(a.read_events()))
+    a.close()
+    assert sum(len(x) for x in want) > 100_000
+    b = ev.Context(w.envs, flags=ev.IN_LOG, capacity=cap)
+    bufs = [torch.empty(cap * 16, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    counts = []
+
+    def got(k):
+        return np.sort(bufs[k % 2].numpy().view(ev.EVENT_DTYPE)[:counts[k]])
+
+    for k, d in enumerate(dev[:-1]):
+        b.step(*d, w.dt_ns)
+        counts.append(b.read_events_async(bufs[k % 2].data_ptr(), cap))
+        if k > 0:  # the previous gap's copy is complete now
+            np.testing.assert_array_equal(got(k - 1), want[k - 1])
+    b.read_wait()
+    np.testing.assert_array_equal(got(len(dev) - 2), want[-2])
+    assert counts == [len(x) for x in want[:-1]]
+    # a synchronous read after the switch drains the buffer the steps now fill
+    b.step(*dev[-1], w.dt_ns)
+    np.testing.assert_array_equal(np.sort(b.read_events()), want[-1])
+    b.close()
