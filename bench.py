@@ -784,6 +784,7 @@ def highspeed_arm(args):
     clocks = ClockSampler(0)
     ctx.step(*dev[0], w.dt_ns)
     tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=1)
+    shape = "x".join(str(v) for v in ctx.tile_shapes()[0])
     for k in range(1, 1 + args.warmup):
         ctx.clear_events()
         ctx.step(*dev[k], w.dt_ns)
@@ -813,7 +814,7 @@ def highspeed_arm(args):
             "events_per_s": n_events / (total / 1e3),
             "config": {"workload": f"{args.hs_envs} envs at 640x480, K=32, C=0.15, 5 layers, "
                                    "flows up to 40 px/frame (~10 % holes), log inputs",
-                       "autotune_best_ms": tuned_ms,
+                       "autotune_best_ms": tuned_ms, "tile_shape": shape,
                        "l2": "flushed between timed steps; inputs far larger than L2"},
             "clocks": clk, "data": "synthetic"}
     print(json.dumps(line), flush=True)

@@ -898,7 +898,11 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
       s.work_counter = c->d_work + kMaxGroups - 1;
       float t_min = 1e30f;
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // r = 0 warms up
-        if ((e = cudaMemcpyAsync(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->nc * c->total,
+        // every trial starts from the saved state and event count, so each one writes its
+        // events to the same part of the buffer (none is timed past a full buffer)
+        if ((e = cudaMemcpyAsync(c->d_count, &count0, sizeof count0, cudaMemcpyHostToDevice,
+                                 c->stream)) ||
+            (e = cudaMemcpyAsync(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->nc * c->total,
                                  cudaMemcpyDeviceToDevice, c->stream)) ||
             (c->d_tlast && (e = cudaMemcpyAsync(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->nc * c->total,
                                                 cudaMemcpyDeviceToDevice, c->stream))) ||
