@@ -21,7 +21,7 @@ namespace {
 
 // One warp per 32-pixel row segment: log-intensity, optional copies, and the segment's
 // motion bounds over the sources that can splat (valid depth, finite motion).
-__global__ void prep_kernel(const PrepArgs a) {
+__global__ void __launch_bounds__(256, 8) prep_kernel(const PrepArgs a) {
   const int e = blockIdx.y;
   const DevEnv E = a.envs[e];
   const int nseg = E.segs_x * E.H;
