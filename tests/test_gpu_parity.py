@@ -282,6 +282,31 @@ def test_static_scene_is_per_pixel_linear_esim(ev, oracle_mod):
     run_both(ev, oracle_mod, envs, kfs, 10_000_000, trace_steps=(1, 3))
 
 
+@pytest.mark.parametrize("tile", [(32, 16), (64, 16), (64, 32)])
+def test_dense_crossings_overflow_the_event_stage(ev, oracle_mod, tile):
+    """About 35 crossings per pixel and sub-frame (threshold 0.01 against unit-variance jumps):
+    every tile-sub-frame stages far more events than the CTA's shared buffer holds, so most
+    chunks go to global memory one warp reservation at a time, each warp's row needs many
+    chunks, and the refractory period (100 us against crossings about 70 us apart) sends
+    chunks to the per-pixel walk."""
+    envs = [TinyEnv(W=70, H=35, K=4, c_on=0.01, c_off=0.012, refractory_ns=100_000)]
+    n = packed_total(envs)
+    rng = np.random.default_rng(11)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(4):
+        k = KF()
+        k.L = rng.normal(0, 1, size=n).astype(np.float32)
+        k.mv = np.zeros((n, 2), dtype=np.float32)
+        k.Z = np.ones(n, dtype=np.float32)
+        kfs.append(k)
+    evs = run_both(ev, oracle_mod, envs, kfs, 10_000_000, trace_steps=(2,), tile=tile)
+    assert len(evs) > 200_000
+
+
 def test_constant_image_emits_nothing(ev, scenes_mod):
     w = scenes_mod.config2(n_envs=4)
     kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
