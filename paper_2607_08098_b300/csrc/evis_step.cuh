@@ -253,14 +253,16 @@ struct StepSmem {
 // sets the register budget.  Targets per thread NT decide the resident threads: 2048 (64
 // warps, 32 registers) for one target per thread in CTAs of 512 or more threads, 1536 (48
 // warps, 40 registers) for one or two otherwise, 1024 for four, 768 for more.  Colour
-// (NC = 3) triples the per-pixel state held in registers; it runs best with more resident
-// threads and some spills than with fewer and none (measured: four CTAs of 32 x 16 at 256
-// threads beat three, five and six; six of 32 x 8 beat four, five ties).
+// (NC = 3) triples the per-pixel state held in registers; it too runs best with more
+// resident threads and some spills than with fewer and none (measured on 64 environments of
+// 346 x 260: 64 x 16 tiles at 2048 threads 8.15 ms per gap, 32 x 16 at 1536 threads 8.63 ms;
+// before the CTA size followed the tile, six CTAs of 32 x 8 beat four, five tied).
 template <int TX, int TY, int NC>
 __host__ __device__ constexpr int step_min_blocks() {
   constexpr int nth = step_threads<TX, TY>(), nt = TX * TY / nth;
-  return (NC == 1 ? (nt == 1 && nth >= 512 ? 2048 : (nt <= 2 ? 1536 : (nt <= 4 ? 1024 : 768)))
-                  : (nt <= 1 ? 1536 : (nt <= 2 ? 1024 : 768))) / nth;
+  return (nt == 1 && nth >= 512 ? 2048
+                                : (NC == 1 ? (nt <= 2 ? 1536 : (nt <= 4 ? 1024 : 768))
+                                           : (nt <= 1 ? 1536 : (nt <= 2 ? 1024 : 768)))) / nth;
 }
 
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
