@@ -56,3 +56,25 @@ def test_pipelined_readback_matches_synchronous_reads(ev, scenes_mod):
     b.step(*dev[-1], w.dt_ns)
     np.testing.assert_array_equal(np.sort(b.read_events()), want[-1])
     b.close()
+
+
+def test_pipelined_readback_overflow(ev, scenes_mod):
+    """A gap that produces more events than the buffer holds: the asynchronous read reports
+    the total with EVIS_ERR_OVERFLOW and delivers the stored ones; the next gap fills the
+    other buffer from empty."""
+    import ctypes
+    w, dev = _gaps(scenes_mod, 3)
+    cap = 1000
+    c = ev.Context(w.envs, flags=ev.IN_LOG, capacity=cap)
+    buf = torch.empty(cap * 16, dtype=torch.uint8).pin_memory()
+    n = ctypes.c_int64()
+    c.step(*dev[0], w.dt_ns)
+    c.step(*dev[1], w.dt_ns)
+    st = ev.lib().evis_read_events_async(c.handle, buf.data_ptr(), cap, ctypes.byref(n))
+    assert st == ev.ERR_OVERFLOW and n.value > cap
+    c.read_wait()
+    recs = buf.numpy().view(ev.EVENT_DTYPE)[:cap]
+    assert np.all(recs["env"] < len(w.envs)) and np.all(np.abs(recs["p"]) == 1)
+    c.step(*dev[2], w.dt_ns)
+    assert c.event_count() > cap   # counted from zero in the other buffer, beyond capacity again
+    c.close()
