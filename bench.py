@@ -154,6 +154,19 @@ def oracle_sample_rate(n_envs, n_steps, rank=0):
             f"refractory), single-threaded C++ oracle")
 
 
+def oracle_gap_seconds(envs, dt_ns, frame_key, log_inputs):
+    """Seconds the oracle (single thread) takes for one keyframe gap of envs, after their
+    first keyframe: the sample behind an extrapolated CPU baseline."""
+    import oracle
+    import scenes
+    kfs = [scenes.render(envs, k, want=(frame_key, "mv", "Z")) for k in range(2)]
+    o = oracle.Oracle(envs, eps=1e-4, flags=oracle.IN_LOG if log_inputs else oracle.IN_LUM)
+    o.step(getattr(kfs[0], frame_key), kfs[0].mv, kfs[0].Z, dt_ns)
+    t0 = time.perf_counter()
+    o.step(getattr(kfs[1], frame_key), kfs[1].mv, kfs[1].Z, dt_ns)
+    return time.perf_counter() - t0
+
+
 def oracle_parallel_rate(envs_per_thread, n_steps, threads):
     """The env-parallel CPU baseline: one oracle per thread, each over its own slice of
     environments, stepping at the same time (the oracle's C calls release the GIL).
@@ -575,6 +588,22 @@ def batched_arm(args):
             "events_last_step": n_events, "event_buffer_overflow": n_events > sum(cap_env),
             "autotuned_tile_shapes": classes,
             "autotune_best_ms": best}
+    if not args.no_cpu_baseline:
+        # one environment per resolution class, one gap each; the whole batch's CPU time is
+        # extrapolated from each class's seconds per pixel-substep
+        first = {}
+        for e in w.envs:
+            first.setdefault((e.W, e.H), e)
+        per_unit = {}
+        for key, e in first.items():
+            per_unit[key] = oracle_gap_seconds([e], w.dt_ns, "I", False) / (e.W * e.H * e.K)
+        sec = sum(e.W * e.H * e.K * per_unit[(e.W, e.H)] for e in w.envs)
+        line["cpu_baseline"] = {
+            "value": units / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "extrapolated: one environment of each resolution class (128x128, 346x260, "
+                      "640x480, 1280x720, their own K and threshold maps) for one keyframe gap, "
+                      "single-threaded C++ oracle, scaled by each class's pixel-substeps in the batch",
+            "seconds_sampled": sum(per_unit[(e.W, e.H)] * e.W * e.H * e.K for e in first.values())}
     print(json.dumps(line), flush=True)
 
 
@@ -817,6 +846,14 @@ def highspeed_arm(args):
                        "autotune_best_ms": tuned_ms, "tile_shape": shape,
                        "l2": "flushed between timed steps; inputs far larger than L2"},
             "clocks": clk, "data": "synthetic"}
+    if not args.no_cpu_baseline:
+        e = w.envs[0]
+        sec = oracle_gap_seconds([e], w.dt_ns, "L", True)
+        line["cpu_baseline"] = {
+            "value": e.W * e.H * e.K / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "extrapolated: the first environment (640x480, K=32, same scenes) for one "
+                      "keyframe gap, single-threaded C++ oracle; every environment of the batch "
+                      "has the same size and K", "seconds_sampled": sec}
     print(json.dumps(line), flush=True)
 
 
