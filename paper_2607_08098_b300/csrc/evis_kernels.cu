@@ -13,6 +13,8 @@
 //   defocus_kernel, log_kernel, init_ref_kernel: the per-keyframe stages around it.
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "evis_device.cuh"
 #include "evis_internal.h"
 
@@ -290,13 +292,20 @@ cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStr
   if (a.max_r < 0 || a.max_r > kMaxBlurR || n_envs < 1 || max_tiles < 1) return cudaErrorInvalidValue;
   const int R = a.max_r;
   const size_t smem = sizeof(float) * (static_cast<size_t>(kBlurTY + 2 * R) * (kBlurTX + 2 * R + kBlurTX) + 4);
-  static bool attr = false;  // up to 56 KB of shared memory at the largest radius
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(defocus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(sizeof(float) * ((kBlurTY + 2 * kMaxBlurR) *
-                                                          (2 * kBlurTX + 2 * kMaxBlurR) + 4)));
+  // up to 56 KB of shared memory at the largest radius, allowed once per device (the
+  // attribute belongs to the device's context)
+  constexpr int kMaxDevices = 64;
+  static std::atomic<bool> attr[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!attr[dev].load(std::memory_order_relaxed)) {
+    e = cudaFuncSetAttribute(defocus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(float) * ((kBlurTY + 2 * kMaxBlurR) *
+                                              (2 * kBlurTX + 2 * kMaxBlurR) + 4)));
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr[dev].store(true, std::memory_order_relaxed);
   }
   defocus_kernel<<<dim3(max_tiles, n_envs, a.nc == 3 ? 3 : 1), kBlurThreads, smem, s>>>(a);
   return cudaGetLastError();

@@ -23,6 +23,8 @@
 
 #include <cuda_fp16.h>
 
+#include <atomic>
+
 #include "evis_device.cuh"
 #include "evis_internal.h"
 
@@ -878,14 +880,21 @@ __global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY
 
 template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
-  static int resident = 0;  // CTAs per SM x SMs, looked up once per instantiation
+  // per device (the shared-memory attribute belongs to the device's context): resident CTAs
+  // per SM x SMs, looked up at the first launch of this instantiation on that device
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> resident_of[kMaxDevices];
   const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int resident = resident_of[dev].load(std::memory_order_relaxed);
   if (!resident) {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return e;
+    int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -893,6 +902,7 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
              smem)) != cudaSuccess)
       return e;
     resident = max(1, per_sm) * sms;
+    resident_of[dev].store(resident, std::memory_order_relaxed);
   }
   int grid = n_tiles;
   if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
