@@ -13,8 +13,8 @@ namespace evis {
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxCrossings = 4096;         // crossings per pixel per sub-frame
 constexpr int64_t kNoEvent = INT64_MIN;     // t_last of a pixel that never fired
-constexpr int kThreads = 256;               // threads per step CTA (8 warps)
-constexpr int kEventStage = 512;            // events staged in shared memory per CTA
+constexpr int kThreads = 256;               // threads per step CTA unless its tile shape sets more
+constexpr int kEventStage = 512;            // fewest events staged in shared memory per CTA
 constexpr int kSegW = 32;                   // motion bounds are kept per 32-pixel row segment
 constexpr int kCandidates = 512;            // candidate segments per direction per tile
 constexpr int kSplatItems = 1536;           // sources of partial segments listed for a splat
