@@ -25,6 +25,7 @@ MODE_B_PRIMARY = 0x10
 TIE_INDEX = 0x20
 MODE_JOINT = 0x40
 COLOR = 0x200          # Sec. 3.2: events of the R, G and B channels (polarity field +-(1 + c))
+MAX_CROSSINGS = 4096   # events one pixel may emit in one sub-frame (per channel)
 
 EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2"), ("p", "<i2")])
 
@@ -159,6 +160,7 @@ class Oracle:
         if not self._h:
             raise ValueError("oracle rejected the environment table")
         self.envs = list(envs)
+        self.last_over_limit = False
         self.nc = 3 if flags & COLOR else 1   # planes of L, Lref and t_last
         self.total = 0
         self.offsets = []
@@ -187,9 +189,20 @@ class Oracle:
             lint = np.empty(nl, dtype=np.float32)
         rc = _lib.orc_step(self._h, _ptr(frames), _ptr(mv), _ptr(depth), int(dt_ns), _ptr(keys),
                            _ptr(lint))
-        if rc != 0:
+        if rc == 1:
             raise ValueError("oracle step rejected its arguments")
+        # 2: some pixel-sub-frame of this gap had more crossings than a pixel may emit
+        self.last_over_limit = rc == 2
         return (keys, lint) if trace else None
+
+    def over_limit(self) -> np.ndarray:
+        """Per environment: pixel-sub-frames (per channel) since creation whose crossing
+        count n of Eq. 4 exceeded the emission limit (none of their crossings was emitted)."""
+        lib = _load()
+        lib.orc_over_limit.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        out = np.zeros(len(self.envs), dtype=np.uint64)
+        lib.orc_over_limit(self._h, out.ctypes.data)
+        return out
 
     def events(self) -> np.ndarray:
         n = _lib.orc_num_events(self._h)

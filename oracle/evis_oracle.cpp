@@ -32,7 +32,10 @@ constexpr uint32_t TIE_INDEX = 0x20u;       // key = (depth, source index), no w
 constexpr uint32_t COLOR = 0x200u;          // Sec. 3.2: the event model on R, G and B apart
 
 constexpr uint64_t EMPTY = ~0ull;
-constexpr int MAX_CROSSINGS = 4096;          // per pixel per substep
+// Events one pixel may emit in one sub-frame (per channel).  Eq. 4 bounds n only by the
+// input; a pixel-sub-frame with n above this limit emits none of its crossings, still moves
+// its reference level by the whole p n C of Eq. 4, and is counted (status 2 of orc_step).
+constexpr int MAX_CROSSINGS = 4096;
 constexpr int64_t NO_EVENT = std::numeric_limits<int64_t>::min();
 
 struct Env {
@@ -75,6 +78,8 @@ struct Ctx {
   std::vector<float> con, coff;            // per-pixel thresholds (Eq. 8), if any env has them
   std::vector<int64_t> clock;              // time of keyframe A per env
   std::vector<Event> events;
+  std::vector<uint64_t> over_limit;        // per env: pixel-sub-frames with n > MAX_CROSSINGS
+  bool gap_over_limit = false;             // some pixel-sub-frame of the last gap had one
 };
 
 inline bool valid_depth(float z) { return z > 0.0f && z < INFINITY; }
@@ -194,9 +199,18 @@ void cross_pixel(Ctx& c, int env, int x, int y, int ch, float L, float& Lref, fl
   int pol = d > 0.0f ? 1 : -1;
   float th = pol > 0 ? th_on : th_off;
   float q = std::fabs(d) / th;
-  int n = 0;
-  if (q >= 1.0f) n = q >= static_cast<float>(MAX_CROSSINGS) ? MAX_CROSSINGS
-                                                            : static_cast<int>(std::floor(q));
+  float nf = q >= 1.0f ? std::floor(q) : 0.0f;  // n of Eq. 4 (NaN compares false: n = 0)
+  if (nf > static_cast<float>(MAX_CROSSINGS)) {
+    // beyond the emission limit: no crossing of this pixel-sub-frame is emitted (none is
+    // truncated either); the reference update of Eq. 4 is the exact one
+    ++c.over_limit[env];
+    c.gap_over_limit = true;
+    Lref = Lref + (pol > 0 ? nf : -nf) * th;
+    Lprev = L;
+    tprev = ti;
+    return;
+  }
+  int n = static_cast<int>(nf);
   float lev = Lref;
   for (int k = 1; k <= n; ++k) {
     lev = Lref + static_cast<float>(pol * k) * th;
@@ -493,6 +507,7 @@ void* orc_create(const orc_env* envs, int32_t n_envs, float eps, uint32_t flags)
   c->Lref.assign(c->nc * c->total, 0.0f);
   c->t_last.assign(c->nc * c->total, NO_EVENT);
   for (int i = 0; i < n_envs; ++i) c->clock.push_back(envs[i].t0_ns);
+  c->over_limit.assign(n_envs, 0);
   return c;
 }
 
@@ -501,7 +516,9 @@ void orc_destroy(void* h) { delete static_cast<Ctx*>(h); }
 // One keyframe (host arrays in the packed layout).  The first call only sets the reference
 // level to the keyframe's log-intensity; each later call synthesises the K substeps between
 // the retained keyframe and this one and appends the events.  Trace pointers (optional)
-// receive, per env in order, K*2*H*W keys and K*H*W interpolated values.
+// receive, per env in order, K*2*H*W keys and K*H*W interpolated values.  Returns 0, 1 for
+// rejected arguments, or 2 when some pixel-sub-frame of this gap had more crossings than a
+// pixel may emit (the gap is otherwise complete; see cross_pixel).
 int32_t orc_step(void* h, const float* frames, const float* mv, const float* depth,
                  int64_t dt_ns, uint64_t* trace_keys, float* trace_L) {
   Ctx& c = *static_cast<Ctx*>(h);
@@ -517,6 +534,7 @@ int32_t orc_step(void* h, const float* frames, const float* mv, const float* dep
     return 0;
   }
   size_t tk = 0, tl = 0;
+  c.gap_over_limit = false;
   for (size_t e = 0; e < c.envs.size(); ++e) {
     size_t o = static_cast<size_t>(c.off[e]);
     size_t HW = static_cast<size_t>(c.envs[e].W) * c.envs[e].H;
@@ -530,7 +548,7 @@ int32_t orc_step(void* h, const float* frames, const float* mv, const float* dep
   c.LA = LB;
   c.mvA.assign(mv, mv + 2 * c.total);
   c.ZA.assign(depth, depth + c.total);
-  return 0;
+  return c.gap_over_limit ? 2 : 0;
 }
 
 typedef struct {
@@ -654,6 +672,13 @@ int64_t orc_take_events(void* h, void* dst, int64_t cap) {
   std::memcpy(dst, c.events.data(), static_cast<size_t>(n) * sizeof(Event));
   c.events.erase(c.events.begin(), c.events.begin() + n);
   return n;
+}
+
+// Per environment: pixel-sub-frames (per channel) since creation whose crossing count
+// exceeded the emission limit.
+void orc_over_limit(void* h, uint64_t* out) {
+  Ctx& c = *static_cast<Ctx*>(h);
+  std::memcpy(out, c.over_limit.data(), c.over_limit.size() * 8);
 }
 
 // Copies the per-pixel state out (any pointer may be null).
@@ -806,9 +831,9 @@ void soft_env(int W, int H, int K, float Con, float Coff, double Cd, double tau,
       const int pol = dd > 0.0f ? 1 : -1;
       const float th = pol > 0 ? Con : Coff;
       const float q = std::fabs(dd) / th;
-      int n = 0;
-      if (q >= 1.0f) n = q >= static_cast<float>(MAX_CROSSINGS) ? MAX_CROSSINGS : static_cast<int>(std::floor(q));
-      if (n > 0) Lref[t] = Lref[t] + static_cast<float>(pol * n) * th;
+      // n of Eq. 4 without bound: the trajectory emits nothing, so no emission limit applies
+      const float nf = q >= 1.0f ? std::floor(q) : 0.0f;
+      if (nf > 0.0f) Lref[t] = Lref[t] + (pol > 0 ? nf : -nf) * th;
     }
     if (gcounts) {
       for (int d = 0; d < 2; ++d) {

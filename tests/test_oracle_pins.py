@@ -304,6 +304,52 @@ def test_single_pixel_ramp_closed_form(oracle_mod, n_ev, C, K, sign):
     assert np.all(np.abs(ev["t"] - want) <= 1.0), (ev["t"], want)
 
 
+def test_emission_limit_is_reported_and_keeps_eq4_state(oracle_mod):
+    """Eq. 4 sets n = floor(|dL| / C) with no bound; a pixel may emit at most MAX_CROSSINGS
+    (4096) events per sub-frame.  At the limit every crossing is emitted; above it none is
+    (nothing truncated), the step reports it, and the reference still moves by the whole
+    p n C of Eq. 4 (closed forms with C = 1/4, K = 1 so that the sub-frame is keyframe B)."""
+    C = 0.25
+    env = TinyEnv(W=6, H=1, K=1, c_on=C, c_off=C, t0_ns=0)
+    npx = packed_total([env])
+    mv, z = _static(npx)
+    L0 = np.zeros(npx, dtype=np.float32)
+    L1 = np.zeros(npx, dtype=np.float32)
+    lim = oracle_mod.MAX_CROSSINGS
+    L1[0] = (lim + 0.5) * C          # n = 4096: all emitted
+    L1[1] = (lim + 1.5) * C          # n = 4097: over the limit
+    L1[2] = -(5000 + 0.5) * C        # n = 5000, OFF
+    L1[3] = 2.5 * C                  # n = 2
+    L1[4] = np.float32(3e38)         # |dL| / C overflows to inf: n = inf
+    dt = 1_000_000
+    o = oracle_mod.Oracle([env], flags=oracle_mod.IN_LOG)
+    o.step(L0, mv, z, dt)
+    assert not o.last_over_limit
+    o.step(L1, mv, z, dt)
+    assert o.last_over_limit
+    assert o.over_limit().tolist() == [3]
+    ev = o.events()
+    per_x = np.bincount(ev["x"], minlength=6)
+    assert per_x.tolist() == [lim, 0, 0, 2, 0, 0]
+    assert np.all(ev["p"][ev["x"] == 0] == 1)
+    Lref = o.state()[0][:env.W]
+    want = np.array([lim * C, (lim + 1) * C, -5000 * C, 2 * C, np.inf, 0], dtype=np.float32)
+    np.testing.assert_array_equal(Lref, want)
+    # the next gap starts from the exact Eq. 4 state: 0.75 above the reference gives 3 events
+    L2 = L1.copy()
+    L2[1] = np.float32((lim + 1) * C + 0.75)
+    o.step(L2, mv, z, dt)
+    # pixel 4's infinite reference stays out of range (inf - L), and Eq. 4 makes it NaN
+    assert o.last_over_limit and o.over_limit().tolist() == [4]
+    assert np.isnan(o.state()[0][4])
+    ev2 = o.events()
+    assert np.bincount(ev2["x"], minlength=6).tolist() == [0, 3, 0, 0, 0, 0]
+    # levels (lim + 2, lim + 3, lim + 4) C between L = (lim + 1.5) C at t0 + dt and
+    # (lim + 4) C at t0 + 2 dt
+    want_t = dt + dt * (np.array([0.5, 1.5, 2.5]) / 2.5)
+    assert np.all(np.abs(np.sort(ev2["t"]) - want_t) <= 1.0)
+
+
 def _linear_esim(L_seq, C, t0, dt):
     """Per-pixel textbook ESIM on a piecewise-linear log-intensity signal (fp64).
 
