@@ -133,12 +133,16 @@ def render(envs, k: int, want=("L", "I", "mv", "Z"), threads: int | None = None)
     lay = np.concatenate([l.as_array() for e in envs for l in e.layers]) if nl.sum() else \
         np.zeros(len(_FIELDS))
     out = {}
+    # padding pixels between environments (each environment's H*W rounded up to 4): zero
+    # motion, unit depth and linear radiance, zero log-radiance; the renderer's threads write
+    # every other pixel (and so touch the pages of the large arrays in parallel)
+    pads = [np.arange(o + e.H * e.W, o + (e.H * e.W + 3) // 4 * 4) for e, o in zip(envs, off)]
+    pads = np.concatenate(pads) if pads else np.zeros(0, np.int64)
     for name, width in (("L", 1), ("I", 1), ("rgb", 3), ("mv", 2), ("Z", 1)):
         if name in want:
-            # padding pixels: zero motion, unit depth, zero log-radiance
-            a = np.zeros(total * width, dtype=np.float32)
-            if name in ("Z", "I"):
-                a[:] = 1.0
+            a = np.empty(total * width, dtype=np.float32)
+            v = a.reshape(total, width)
+            v[pads] = 1.0 if name in ("Z", "I") else 0.0
             out[name] = a
         else:
             out[name] = None

@@ -64,12 +64,31 @@ inline double lattice(uint64_t seed, int64_t i, int64_t j) {
 
 inline double smooth(double t) { return t * t * (3.0 - 2.0 * t); }
 
-inline double value_noise(uint64_t seed, double x, double y) {
+// A small direct-mapped memo of lattice values: neighbouring pixels share lattice points, and
+// a memoised value is the same double that lattice() returns, so the output is unchanged.
+struct LatticeMemo {
+  struct Slot { uint64_t seed; int64_t i, j; double v; bool ok; };
+  Slot slot[512] = {};
+  double get(uint64_t seed, int64_t i, int64_t j) {
+    Slot& s = slot[(static_cast<uint64_t>(i) * 0x9E37u + static_cast<uint64_t>(j) * 0x85EBu +
+                    (seed & 0xFFu) * 0x27u) & 511u];
+    if (!(s.ok && s.seed == seed && s.i == i && s.j == j)) {
+      s.seed = seed;
+      s.i = i;
+      s.j = j;
+      s.v = lattice(seed, i, j);
+      s.ok = true;
+    }
+    return s.v;
+  }
+};
+
+inline double value_noise(LatticeMemo& m, uint64_t seed, double x, double y) {
   double fx = std::floor(x), fy = std::floor(y);
   int64_t i = static_cast<int64_t>(fx), j = static_cast<int64_t>(fy);
   double sx = smooth(x - fx), sy = smooth(y - fy);
-  double a = lattice(seed, i, j), b = lattice(seed, i + 1, j);
-  double c = lattice(seed, i, j + 1), d = lattice(seed, i + 1, j + 1);
+  double a = m.get(seed, i, j), b = m.get(seed, i + 1, j);
+  double c = m.get(seed, i, j + 1), d = m.get(seed, i + 1, j + 1);
   double top = a + (b - a) * sx, bot = c + (d - c) * sx;
   return top + (bot - top) * sy;
 }
@@ -105,6 +124,7 @@ void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return ls[x].depth < ls[y].depth; });
   const double ln10 = 2.302585092994046;
+  LatticeMemo memo;
   for (int y = row0; y < row1; ++y) {
     for (int x = 0; x < W; ++x) {
       const LayerAt* hit = nullptr;
@@ -134,8 +154,8 @@ void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int
       if (p[F_TEX_KIND] == 0.0) {
         uint64_t seed = static_cast<uint64_t>(p[F_SEED]);
         double cell = p[F_CELL];
-        double n1 = value_noise(splitmix64(seed), ux / cell, uy / cell);
-        double n2 = value_noise(splitmix64(seed ^ 0xA5A5A5A5ull), 2.0 * ux / cell, 2.0 * uy / cell);
+        double n1 = value_noise(memo, splitmix64(seed), ux / cell, uy / cell);
+        double n2 = value_noise(memo, splitmix64(seed ^ 0xA5A5A5A5ull), 2.0 * ux / cell, 2.0 * uy / cell);
         z = (n1 + 0.5 * n2) * 1.35;  // ~unit variance for smoothstep value noise
       } else if (p[F_TEX_KIND] == 2.0) {
         z = ux;
@@ -144,7 +164,7 @@ void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int
       }
       double l10 = p[F_MU] + p[F_SIGMA] * z + p[F_BRIGHT_RATE] * k;
       l10 = std::min(std::max(l10, p[F_LO]), p[F_HI]);
-      double inten = std::pow(10.0, l10);
+      const double inten = (I || rgb) ? std::pow(10.0, l10) : 0.0;
       if (L) L[px] = static_cast<float>(ln10 * l10);
       if (I) I[px] = static_cast<float>(inten);
       if (rgb) {
