@@ -24,9 +24,15 @@
  *    point in the previous keyframe.
  *  - Depth: a source pixel takes part in the splat iff its depth is finite and > 0.
  *  - All work is enqueued on the context's stream; nothing blocks unless stated.
- *  - Errors detected on the host return immediately and change nothing.  Errors detected
- *    on the device (event buffer overflow) are latched and returned by the next call that
- *    synchronises (evis_read_events, evis_event_count).
+ *  - Errors detected on the host return immediately and change nothing.  Conditions detected
+ *    on the device (event buffer overflow, pixels beyond the crossing limit) are latched and
+ *    returned by the next call that synchronises (evis_read_events, evis_event_count).
+ *  - Crossing limit: Eq. 4 gives a pixel n = floor(|L - L_ref| / C) crossings in one
+ *    sub-frame, without bound.  A pixel emits at most EVIS_MAX_CROSSINGS of them per
+ *    sub-frame (per channel in colour mode).  A pixel-sub-frame whose n is larger emits none
+ *    of its crossings (no truncated stream), still moves its reference level by the whole
+ *    p n C of Eq. 4, and is counted: the next read returns EVIS_ERR_RANGE and
+ *    evis_get_env_stats reports the count per environment.
  *  - One context must not be used by two host threads at the same time.
  */
 #ifndef EVIS_H
@@ -49,8 +55,15 @@ typedef enum {
   EVIS_ERR_OOM = 3,         /* device allocation failed */
   EVIS_ERR_OVERFLOW = 4,    /* more events than the buffer (or the caller's array) holds */
   EVIS_ERR_STATE = 5,       /* call not valid in the context's current state */
-  EVIS_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+  EVIS_ERR_TIMEOUT = 6,     /* reserved: no kernel of the library waits on another CTA, a
+                             * flag or a peer, so no call returns it */
+  EVIS_ERR_RANGE = 7        /* some pixel-sub-frame had more crossings than a pixel may emit
+                             * (EVIS_MAX_CROSSINGS); its crossings were withheld, the state
+                             * follows Eq. 4 exactly, everything else was delivered */
 } evis_status;
+
+/* Crossings one pixel may emit in one sub-frame (per channel). */
+#define EVIS_MAX_CROSSINGS 4096
 
 /* One event (16 bytes): time in ns, pixel, environment index, polarity +1 / -1. */
 typedef struct {
@@ -89,6 +102,11 @@ typedef struct {
  * Threshold maps serve all channels; each channel draws its own noise streams (the last
  * counter word is stream + 4 c); defocus blurs each channel. */
 #define EVIS_COLOR 0x200u
+/* Collect the per-environment statistics of evis_get_env_stats that cost kernel work (holes
+ * per warp direction, ON / OFF and noise event counts): about 3 to 4 % of the synthesis
+ * kernel's time.  Without it those counts read 0; target-sub-frames and the crossing-limit
+ * count are always kept. */
+#define EVIS_STATS 0x400u
 
 typedef struct {
   int32_t width, height; /* rendered frame, 1..65535 each, width * height <= 2^24 */
@@ -108,7 +126,7 @@ typedef struct {
 typedef struct {
   float eps;              /* added before the log (Sec. 3.2), finite and >= 0 */
   uint32_t flags;         /* EVIS_IN_* | EVIS_MODE_* (one) | EVIS_TIE_* | EVIS_KEEP_INPUTS |
-                           * EVIS_COLOR */
+                           * EVIS_COLOR | EVIS_STATS */
   int64_t event_capacity; /* events the device buffer holds between two reads, >= 1 */
 } evis_config;
 
@@ -139,8 +157,10 @@ evis_status evis_step_host(evis_ctx *ctx, const float *frames, const float *mv,
 
 /* Synchronises the stream, copies the buffered events (in no particular order) to dst
  * (host or device, up to cap events), empties the buffer and clears latched errors.
- * *n_out = number of events produced since the last read.  Returns EVIS_ERR_OVERFLOW when
- * that number exceeds the buffer capacity or cap: the first min(capacity, cap) stored
+ * *n_out = number of events produced since the last read.  Returns EVIS_ERR_RANGE when
+ * some pixel-sub-frame since the last read exceeded the crossing limit (see the
+ * conventions above; the events are delivered as usual), else EVIS_ERR_OVERFLOW when the
+ * number produced exceeds the buffer capacity or cap: the first min(capacity, cap) stored
  * events are delivered and the per-pixel state has advanced as if none were lost. */
 evis_status evis_read_events(evis_ctx *ctx, evis_event *dst, int64_t cap, int64_t *n_out);
 
@@ -158,15 +178,18 @@ evis_status evis_read_events_async(evis_ctx *ctx, evis_event *dst, int64_t cap, 
 /* Waits for the copy started by the last evis_read_events_async (no-op if none). */
 evis_status evis_read_wait(evis_ctx *ctx);
 
-/* Synchronises and reports the number of events produced since the last read. */
+/* Synchronises and reports the number of events produced since the last read (status as
+ * for evis_read_events; nothing is cleared). */
 evis_status evis_event_count(evis_ctx *ctx, int64_t *n_out);
 
 /* Device-side view of the event buffer for consumers on the GPU: *events points to the
- * capacity-sized array, *count to the 64-bit produced-event counter.  Valid until destroy
- * or the next evis_read_events_async (which switches buffers). */
+ * capacity-sized array, *count to the 64-bit produced-event counter (followed by the
+ * counter of pixel-sub-frames beyond the crossing limit).  Valid until destroy or the next
+ * evis_read_events_async (which switches buffers). */
 evis_status evis_events_device(evis_ctx *ctx, evis_event **events, uint64_t **count);
 
-/* Asynchronously empties the event buffer (stream-ordered, no synchronisation). */
+/* Asynchronously empties the event buffer and clears the latched crossing-limit condition
+ * (stream-ordered, no synchronisation; evis_get_env_stats keeps its counts). */
 evis_status evis_clear_events(evis_ctx *ctx);
 
 /* Synchronises and copies the per-pixel reference levels [nc][total px] and last emitted
@@ -182,6 +205,26 @@ evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t 
  * not finite and > 0, or a motion vector that is not finite.  Synchronises. */
 evis_status evis_get_stats(evis_ctx *ctx, uint64_t *keyframes, uint64_t *gaps,
                            uint64_t *invalid_sources);
+
+/* Per-environment statistics since creation (the survey's counters: event count, ON/OFF
+ * split, hole fraction per warp direction; Sec. 3.3 fills the holes of one direction from
+ * the other).  A target-sub-frame is one sensor pixel at one sub-frame i = 1..K. */
+typedef struct {
+  uint64_t target_subframes; /* sensor pixels x K x keyframe gaps synthesised */
+  uint64_t holes_a;          /* target-sub-frames that no source of A (forward warp) reached */
+  uint64_t holes_b;          /* ... that no source of B (backward warp) reached */
+  uint64_t holes_both;       /* ... that neither reached: no sample, the pixel held its state */
+  uint64_t events_on;        /* events emitted with positive polarity (crossings and noise) */
+  uint64_t events_off;       /* ... with negative polarity */
+  uint64_t noise_events;     /* of those, sensor noise events (evis_set_noise) */
+  uint64_t over_limit;       /* pixel-sub-frames (per channel) beyond EVIS_MAX_CROSSINGS */
+} evis_env_stats;
+
+/* Copies the statistics of every environment to out (host array of n_envs).  Holes, ON /
+ * OFF and noise counts need EVIS_STATS (else 0).  Events past the buffer's capacity are
+ * counted too (they were produced).  The autotuner's trial gaps are not counted.
+ * Synchronises. */
+evis_status evis_get_env_stats(evis_ctx *ctx, evis_env_stats *out);
 
 /* Synchronises and copies the per-environment count of keyframe gaps processed (the noise
  * generator's gap counter) [n_envs] to host memory. */
@@ -387,10 +430,13 @@ evis_status evis_profile_read(evis_ctx *ctx, float *ms, int32_t cap, int32_t *n_
  * and depth in the single-environment layout; the reference levels Lref [H*W] (set them to
  * the first keyframe's log-intensity before the first call) and, when refractory_ns > 0,
  * the last-event times t_last [H*W] (INT64_MIN = none), both updated in place; the event
- * array (capacity entries) and its 64-bit event counter *count, to which the events of this
- * gap are added exactly as evis_step adds them to a context's buffer (the caller resets it).
+ * array (capacity entries) and two 64-bit counters count[0..1]: count[0] receives the number
+ * of events of this gap exactly as evis_step adds them to a context's buffer, count[1] the
+ * number of pixel-sub-frames beyond the crossing limit (the caller resets both).
  * Sub-frame i is at t_a_ns + (i * dt_ns) / K.  The results equal those of evis_step.
  * flags may hold EVIS_MODE_B_PRIMARY and EVIS_TIE_INDEX only.
+ *
+ * Invalid arguments return EVIS_ERR_INVALID_ARG before any work.
  *
  * Limits: width, height <= 4096 and width * height <= 1048576, set by a static scratch
  * array of about 1.3 MB that every GPU loading the library holds until the process exits

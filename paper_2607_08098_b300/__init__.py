@@ -20,8 +20,14 @@ MODE_BLEND, MODE_B_PRIMARY, MODE_JOINT = 0x0, 0x10, 0x40
 TIE_WEIGHT, TIE_INDEX = 0x0, 0x20
 KEEP_INPUTS = 0x100
 COLOR = 0x200   # R, G, B events (Sec. 3.2); polarity field +-(1 + channel)
+STATS = 0x400   # collect holes, ON / OFF and noise counts for env_stats()
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_STATE, ERR_TIMEOUT = range(7)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_OVERFLOW, ERR_STATE, ERR_TIMEOUT, ERR_RANGE = range(8)
+MAX_CROSSINGS = 4096   # crossings one pixel may emit per sub-frame (EVIS_MAX_CROSSINGS)
+
+ENV_STATS_DTYPE = np.dtype([("target_subframes", "<u8"), ("holes_a", "<u8"), ("holes_b", "<u8"),
+                            ("holes_both", "<u8"), ("events_on", "<u8"), ("events_off", "<u8"),
+                            ("noise_events", "<u8"), ("over_limit", "<u8")])
 
 EVENT_DTYPE = np.dtype([("t", "<i8"), ("x", "<u2"), ("y", "<u2"), ("env", "<u2"), ("p", "<i2")])
 
@@ -50,8 +56,9 @@ class VoxelEnv(ctypes.Structure):
 
 
 class EvisError(RuntimeError):
-    def __init__(self, status: int, msg: str = ""):
+    def __init__(self, status: int, msg: str = "", events=None):
         self.status = status
+        self.events = events   # what a read delivered before reporting the status
         super().__init__(f"{status_string(status)} ({status}){': ' + msg if msg else ''}")
 
 
@@ -75,6 +82,7 @@ _SIGS = {
     "evis_get_state": (ctypes.c_int, [ctypes.c_void_p] * 4),
     "evis_get_gaps": (ctypes.c_int, [ctypes.c_void_p] * 2),
     "evis_get_stats": (ctypes.c_int, [ctypes.c_void_p] * 4),
+    "evis_get_env_stats": (ctypes.c_int, [ctypes.c_void_p] * 2),
     "evis_set_state": (ctypes.c_int, [ctypes.c_void_p] * 5),
     "evis_log_intensity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32,
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
@@ -257,8 +265,13 @@ class Context:
         _check(lib().evis_step_host(self._h, hp(frames, self.n_frame), hp(mv, 2 * self.total),
                                     hp(depth, self.total), int(dt_ns)), self._h)
 
-    def read_events(self, cap: int | None = None, allow_overflow: bool = False):
-        """Drain the event buffer to a numpy structured array (EVENT_DTYPE)."""
+    def read_events(self, cap: int | None = None, allow_overflow: bool = False,
+                    allow_over_limit: bool = False):
+        """Drain the event buffer to a numpy structured array (EVENT_DTYPE).
+
+        A pixel-sub-frame beyond the crossing limit since the last read raises EvisError
+        (ERR_RANGE, the delivered events in .events) unless allow_over_limit is set; its
+        count per environment is in env_stats()."""
         n = ctypes.c_int64()
         cnt = self.event_count()
         if cap is None:
@@ -266,10 +279,16 @@ class Context:
         out = np.empty(max(cap, 0), dtype=EVENT_DTYPE)
         st = lib().evis_read_events(self._h, out.ctypes.data if cap else None, int(cap),
                                     ctypes.byref(n))
+        got = out[:min(n.value, cap)]
+        over = n.value > min(cap, self.capacity)
+        if st == ERR_RANGE:
+            if not allow_over_limit:
+                raise EvisError(st, "a pixel-sub-frame exceeded the crossing limit", events=got)
+            st = ERR_OVERFLOW if over else OK
         if st == ERR_OVERFLOW and allow_overflow:
-            return out[:min(n.value, cap)], n.value
+            return got, n.value
         _check(st, self._h)
-        return (out[:n.value], n.value) if allow_overflow else out[:n.value]
+        return (got, n.value) if allow_overflow else got
 
     def read_events_async(self, dst_ptr: int, cap: int) -> int:
         """Start copying the buffered events to dst_ptr (pinned host or device memory, room
@@ -287,7 +306,7 @@ class Context:
     def event_count(self) -> int:
         n = ctypes.c_int64()
         st = lib().evis_event_count(self._h, ctypes.byref(n))
-        if st not in (OK, ERR_OVERFLOW):
+        if st not in (OK, ERR_OVERFLOW, ERR_RANGE):
             _check(st, self._h)
         return n.value
 
@@ -403,6 +422,14 @@ class Context:
         _check(lib().evis_get_stats(self._h, ctypes.byref(kf), ctypes.byref(gp), inv.ctypes.data),
                self._h)
         return {"keyframes": kf.value, "gaps": gp.value, "invalid_sources": inv}
+
+    def env_stats(self) -> np.ndarray:
+        """Per-environment statistics since creation (ENV_STATS_DTYPE): target-sub-frames,
+        holes of each warp direction and of both, ON / OFF events, noise events and
+        pixel-sub-frames beyond the crossing limit."""
+        out = np.zeros(len(self.envs), dtype=ENV_STATS_DTYPE)
+        _check(lib().evis_get_env_stats(self._h, out.ctypes.data), self._h)
+        return out
 
     def gaps(self):
         """Keyframe gaps processed per environment (the noise generator's gap counter)."""

@@ -58,12 +58,14 @@ struct evis_ctx {
   uint32_t *d_gap = nullptr;   // [2][n]: keyframe gaps processed, alternating like d_clock
   unsigned long long *d_invalid = nullptr;  // [n]: sources that could not splat, all keyframes
   ulonglong2 *d_events = nullptr;          // the buffer the steps append to
-  unsigned long long *d_count = nullptr;
+  unsigned long long *d_count = nullptr;   // [0] events produced, [1] pixel-sub-frames over the limit
+  unsigned long long *d_stats = nullptr;   // [n][kStatWords] statistics since creation
   // pipelined read-back: the second buffer, and the copy of the other one in flight
   ulonglong2 *d_events_alt = nullptr;
   unsigned long long *d_count_alt = nullptr;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
+  bool copy_ready = false;   // the second buffer, the copy stream and its event all exist
   bool copy_pending = false;
   int64_t *d_tr_off = nullptr; // [2][n]: key offsets, then L offsets
   float *d_in[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -113,7 +115,7 @@ std::string validate(const evis_env_desc *envs, int32_t n, const evis_config *cf
   if (n < 1 || n > 65535) return "n_envs must be in 1..65535";
   if (!std::isfinite(cfg->eps) || cfg->eps < 0.0f) return "eps must be finite and >= 0";
   const uint32_t known = 0x3u | EVIS_MODE_B_PRIMARY | EVIS_MODE_JOINT | EVIS_TIE_INDEX |
-                         EVIS_KEEP_INPUTS | EVIS_COLOR;
+                         EVIS_KEEP_INPUTS | EVIS_COLOR | EVIS_STATS;
   if (cfg->flags & ~known) return "unknown flag bits";
   if ((cfg->flags & EVIS_COLOR) && (cfg->flags & 0x3u) == EVIS_IN_LUM)
     return "EVIS_COLOR needs EVIS_IN_RGB (linear RGB) or EVIS_IN_LOG (three log-intensity planes)";
@@ -157,6 +159,7 @@ void release(evis_ctx *c) {
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   c->copy_done = nullptr;
   c->copy_stream = nullptr;
+  c->copy_ready = false;
   c->copy_pending = false;
   for (auto &g : c->graph) {
     if (g) cudaGraphExecDestroy(g);
@@ -318,6 +321,8 @@ evis::StepArgs step_args(const evis_ctx *c, const KeyframeB &B, int64_t dt) {
   s.events = c->d_events;
   s.ev_count = c->d_count;
   s.capacity = static_cast<unsigned long long>(c->cfg.event_capacity);
+  s.env_stats = c->d_stats;
+  s.stats = (c->cfg.flags & EVIS_STATS) != 0;
   s.dt = dt;
   s.flags = c->cfg.flags;
   s.nc = c->nc;
@@ -466,7 +471,9 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if ((e = dalloc(c, &c->d_gap, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc gap counters");
   if ((e = dalloc(c, &c->d_invalid, n_envs)) != cudaSuccess) return bail(e, "alloc statistics");
   if ((e = dalloc(c, &c->d_events, cfg->event_capacity)) != cudaSuccess) return bail(e, "alloc events");
-  if ((e = dalloc(c, &c->d_count, 1)) != cudaSuccess) return bail(e, "alloc count");
+  if ((e = dalloc(c, &c->d_count, 2)) != cudaSuccess) return bail(e, "alloc count");
+  if ((e = dalloc(c, &c->d_stats, static_cast<size_t>(evis::kStatWords) * n_envs)) != cudaSuccess)
+    return bail(e, "alloc statistics");
   if ((e = dalloc(c, &c->d_tr_off, 2 * n_envs)) != cudaSuccess) return bail(e, "alloc trace offsets");
   for (int s = 0; s < 2; ++s) {
     if (c->need_L && (e = dalloc(c, &c->d_L[s], c->nc * c->total)) != cudaSuccess) return bail(e, "alloc L");
@@ -481,7 +488,8 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
   if ((e = cudaMemcpyAsync(c->d_envs, denv.data(), sizeof(DevEnv) * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(c->d_clock, clocks.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(c->d_tr_off, troff.data(), sizeof(int64_t) * 2 * n_envs, cudaMemcpyHostToDevice, s)) ||
-      (e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s)) ||
+      (e = cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), s)) ||
+      (e = cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * evis::kStatWords * n_envs, s)) ||
       (e = cudaMemsetAsync(c->d_gap, 0, sizeof(uint32_t) * 2 * n_envs, s)) ||
       (e = cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long) * n_envs, s)) ||
       // packing pads of the L slots are never written by a step: zero them once
@@ -534,34 +542,46 @@ evis_status evis_step_host(evis_ctx *c, const float *frames, const float *mv,
   return st;
 }
 
+// Status of a read: pixel-sub-frames beyond the emission limit first, then overflow.
+static evis_status read_status(const evis_ctx *c, const unsigned long long cnt[2], int64_t cap) {
+  const int64_t produced = static_cast<int64_t>(cnt[0]);
+  if (cnt[1] != 0) return EVIS_ERR_RANGE;
+  return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+}
+
 evis_status evis_read_events(evis_ctx *c, evis_event *dst, int64_t cap, int64_t *n_out) {
   if (!c || !n_out || cap < 0 || (cap > 0 && !dst)) return EVIS_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "read sync");
-  unsigned long long cnt = 0;
-  if ((e = cudaMemcpy(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  unsigned long long cnt[2] = {0, 0};
+  if ((e = cudaMemcpy(cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "read count");
-  const int64_t produced = static_cast<int64_t>(cnt);
+  const int64_t produced = static_cast<int64_t>(cnt[0]);
   const int64_t n = std::min<int64_t>(produced, std::min<int64_t>(c->cfg.event_capacity, cap));
   if (n > 0 && (e = cudaMemcpy(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault)) != cudaSuccess)
     return cuda_fail(c, e, "copy events");
-  if ((e = cudaMemset(c->d_count, 0, sizeof(unsigned long long))) != cudaSuccess)
+  if ((e = cudaMemset(c->d_count, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
     return cuda_fail(c, e, "reset count");
   *n_out = produced;
-  return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+  return read_status(c, cnt, cap);
 }
 
 evis_status evis_read_events_async(evis_ctx *c, evis_event *dst, int64_t cap, int64_t *n_out) {
   if (!c || !n_out || cap < 0 || (cap > 0 && !dst)) return EVIS_ERR_INVALID_ARG;
   cudaError_t e;
-  if (!c->copy_stream) {  // first call: the copy stream, its event and the second buffer
-    if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+  if (!c->copy_ready) {  // first call: the copy stream, its event and the second buffer
+    // a set-up that failed part way is retried whole: whatever exists is used, the rest made
+    if (!c->copy_stream &&
+        (e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail(c, e, "copy stream");
-    if ((e = cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming)) != cudaSuccess)
+    if (!c->copy_done &&
+        (e = cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(c, e, "copy event");
-    if ((e = dalloc(c, &c->d_events_alt, c->cfg.event_capacity)) != cudaSuccess ||
-        (e = dalloc(c, &c->d_count_alt, 1)) != cudaSuccess)
+    if (!c->d_events_alt && (e = dalloc(c, &c->d_events_alt, c->cfg.event_capacity)) != cudaSuccess)
       return cuda_fail(c, e, "alloc second event buffer");
+    if (!c->d_count_alt && (e = dalloc(c, &c->d_count_alt, 2)) != cudaSuccess)
+      return cuda_fail(c, e, "alloc second event counter");
+    c->copy_ready = true;
   }
   // every step enqueued so far has finished, and so has the previous read-back, whose
   // buffer the next steps will fill
@@ -570,10 +590,10 @@ evis_status evis_read_events_async(evis_ctx *c, evis_event *dst, int64_t cap, in
     if ((e = cudaEventSynchronize(c->copy_done)) != cudaSuccess) return cuda_fail(c, e, "copy wait");
     c->copy_pending = false;
   }
-  unsigned long long cnt = 0;
-  if ((e = cudaMemcpy(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  unsigned long long cnt[2] = {0, 0};
+  if ((e = cudaMemcpy(cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "read count");
-  const int64_t produced = static_cast<int64_t>(cnt);
+  const int64_t produced = static_cast<int64_t>(cnt[0]);
   const int64_t n = std::min<int64_t>(produced, std::min<int64_t>(c->cfg.event_capacity, cap));
   if (n > 0 && (e = cudaMemcpyAsync(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault,
                                     c->copy_stream)) != cudaSuccess)
@@ -585,11 +605,11 @@ evis_status evis_read_events_async(evis_ctx *c, evis_event *dst, int64_t cap, in
   // captured graphs hold the old buffer's address
   std::swap(c->d_events, c->d_events_alt);
   std::swap(c->d_count, c->d_count_alt);
-  if ((e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "reset count");
   drop_graphs(c);
   *n_out = produced;
-  return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+  return read_status(c, cnt, cap);
 }
 
 evis_status evis_read_wait(evis_ctx *c) {
@@ -606,11 +626,11 @@ evis_status evis_event_count(evis_ctx *c, int64_t *n_out) {
   if (!c || !n_out) return EVIS_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "count sync");
-  unsigned long long cnt = 0;
-  if ((e = cudaMemcpy(&cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
+  unsigned long long cnt[2] = {0, 0};
+  if ((e = cudaMemcpy(cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "read count");
-  *n_out = static_cast<int64_t>(cnt);
-  return cnt > static_cast<unsigned long long>(c->cfg.event_capacity) ? EVIS_ERR_OVERFLOW : EVIS_OK;
+  *n_out = static_cast<int64_t>(cnt[0]);
+  return read_status(c, cnt, INT64_MAX);
 }
 
 evis_status evis_events_device(evis_ctx *c, evis_event **events, uint64_t **count) {
@@ -622,7 +642,7 @@ evis_status evis_events_device(evis_ctx *c, evis_event **events, uint64_t **coun
 
 evis_status evis_clear_events(evis_ctx *c) {
   if (!c) return EVIS_ERR_INVALID_ARG;
-  cudaError_t e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->stream);
+  cudaError_t e = cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), c->stream);
   return e == cudaSuccess ? EVIS_OK : cuda_fail(c, e, "clear events");
 }
 
@@ -667,6 +687,32 @@ evis_status evis_get_stats(evis_ctx *c, uint64_t *keyframes, uint64_t *gaps,
   if (invalid_sources &&
       (e = cudaMemcpy(invalid_sources, c->d_invalid, sizeof(uint64_t) * c->n, cudaMemcpyDefault)))
     return cuda_fail(c, e, "copy statistics");
+  return EVIS_OK;
+}
+
+evis_status evis_get_env_stats(evis_ctx *c, evis_env_stats *out) {
+  if (!c || !out) return EVIS_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stats sync");
+  std::vector<unsigned long long> w(static_cast<size_t>(evis::kStatWords) * c->n);
+  uint32_t gaps = 0;
+  if ((e = cudaMemcpy(w.data(), c->d_stats, sizeof(unsigned long long) * w.size(), cudaMemcpyDeviceToHost)) ||
+      (e = cudaMemcpy(&gaps, c->d_gap + c->clk * c->n, sizeof gaps, cudaMemcpyDeviceToHost)))
+    return cuda_fail(c, e, "copy statistics");
+  for (int i = 0; i < c->n; ++i) {
+    const evis_env_desc &d = c->envs[i];
+    const unsigned long long *v = w.data() + static_cast<size_t>(evis::kStatWords) * i;
+    evis_env_stats &o = out[i];
+    o.target_subframes = static_cast<uint64_t>(d.width - 2 * d.margin) * (d.height - 2 * d.margin) *
+                         static_cast<uint64_t>(d.K) * gaps;
+    o.holes_a = v[evis::kStatHolesA];
+    o.holes_b = v[evis::kStatHolesB];
+    o.holes_both = v[evis::kStatHolesBoth];
+    o.events_on = v[evis::kStatEventsOn];
+    o.events_off = v[evis::kStatEventsOff];
+    o.noise_events = v[evis::kStatNoise];
+    o.over_limit = v[evis::kStatOverLimit];
+  }
   return EVIS_OK;
 }
 
@@ -862,8 +908,8 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
       return cuda_fail(c, e, "alloc autotune scratch");
   }
   // save the per-pixel state and the event counter; every trial starts from them
-  unsigned long long count0 = 0;
-  if ((e = cudaMemcpy(&count0, c->d_count, sizeof count0, cudaMemcpyDeviceToHost)) ||
+  unsigned long long count0[2] = {0, 0};
+  if ((e = cudaMemcpy(count0, c->d_count, sizeof count0, cudaMemcpyDeviceToHost)) ||
       (e = cudaMemcpy(c->d_tune_Lref, c->d_Lref, sizeof(float) * c->nc * c->total, cudaMemcpyDeviceToDevice)) ||
       (c->d_tlast && (e = cudaMemcpy(c->d_tune_tlast, c->d_tlast, sizeof(int64_t) * c->nc * c->total,
                                      cudaMemcpyDeviceToDevice))))
@@ -875,6 +921,8 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
   c->d_invalid = stats;
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune prep");
   evis::StepArgs base = step_args(c, B, dt_ns);
+  base.env_stats = nullptr;  // trials are not counted
+  base.stats = false;
   const int shapes[6][2] = {{32, 16}, {32, 8}, {32, 32}, {64, 16}, {64, 32}, {128, 16}};
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
@@ -900,7 +948,7 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // r = 0 warms up
         // every trial starts from the saved state and event count, so each one writes its
         // events to the same part of the buffer (none is timed past a full buffer)
-        if ((e = cudaMemcpyAsync(c->d_count, &count0, sizeof count0, cudaMemcpyHostToDevice,
+        if ((e = cudaMemcpyAsync(c->d_count, count0, sizeof count0, cudaMemcpyHostToDevice,
                                  c->stream)) ||
             (e = cudaMemcpyAsync(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->nc * c->total,
                                  cudaMemcpyDeviceToDevice, c->stream)) ||
@@ -932,7 +980,7 @@ evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, con
   if (r == cudaSuccess) r = cudaMemcpy(c->d_Lref, c->d_tune_Lref, sizeof(float) * c->nc * c->total, cudaMemcpyDeviceToDevice);
   if (r == cudaSuccess && c->d_tlast)
     r = cudaMemcpy(c->d_tlast, c->d_tune_tlast, sizeof(int64_t) * c->nc * c->total, cudaMemcpyDeviceToDevice);
-  if (r == cudaSuccess) r = cudaMemcpy(c->d_count, &count0, sizeof count0, cudaMemcpyHostToDevice);
+  if (r == cudaSuccess) r = cudaMemcpy(c->d_count, count0, sizeof count0, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = r;
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
   if (best_ms) *best_ms = total_best;
@@ -1060,7 +1108,8 @@ const char *evis_status_string(evis_status s) {
     case EVIS_ERR_OOM: return "out of device memory";
     case EVIS_ERR_OVERFLOW: return "event buffer overflow";
     case EVIS_ERR_STATE: return "invalid state";
-    case EVIS_ERR_TIMEOUT: return "device wait timed out";
+    case EVIS_ERR_TIMEOUT: return "device wait timed out (reserved)";
+    case EVIS_ERR_RANGE: return "a pixel exceeded the per-sub-frame crossing limit";
   }
   return "unknown status";
 }

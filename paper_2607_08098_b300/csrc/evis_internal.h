@@ -11,7 +11,21 @@
 namespace evis {
 
 constexpr uint64_t kEmptyKey = ~0ull;
-constexpr int kMaxCrossings = 4096;         // crossings per pixel per sub-frame
+// Crossings one pixel may emit per sub-frame (per channel).  A pixel-sub-frame whose Eq. 4
+// count n is larger emits none of them, still moves its reference level by the whole p n C,
+// and is counted (ev_count[1] and the environment's kStatOverLimit word).
+constexpr int kMaxCrossings = 4096;
+// Per-environment statistics words (64-bit counters, accumulated by the step kernel).
+enum StatWord {
+  kStatHolesA = 0,      // target-sub-frames with no source of A (forward warp)
+  kStatHolesB = 1,      // ... with no source of B (backward warp)
+  kStatHolesBoth = 2,   // ... with neither (no sample)
+  kStatEventsOn = 3,    // crossing events emitted with positive polarity
+  kStatEventsOff = 4,   // ... negative polarity
+  kStatNoise = 5,       // sensor noise events emitted
+  kStatOverLimit = 6,   // pixel-sub-frames (per channel) beyond the emission limit
+  kStatWords = 8
+};
 constexpr int64_t kNoEvent = INT64_MIN;     // t_last of a pixel that never fired
 constexpr int kThreads = 256;               // threads per step CTA unless its tile shape sets more
 constexpr int kEventStage = 512;            // fewest events staged in shared memory per CTA
@@ -63,8 +77,10 @@ struct StepArgs {
   const float4 *segA, *segB;   // per row segment: (min dx, max dx, min dy, max dy)
   const float4 *packA, *packB; // per source: (mx, my, Z, Z at the other endpoint), or null
   ulonglong2 *events;
-  unsigned long long *ev_count;
+  unsigned long long *ev_count;    // [0] events produced, [1] pixel-sub-frames beyond the limit
   unsigned long long capacity;
+  unsigned long long *env_stats;   // per environment kStatWords counters, or null
+  bool stats;                      // collect holes, polarity and noise counts (EVIS_STATS)
   int64_t dt;
   uint32_t flags;
   bool noise;                // some environment of the launch has noise on (needs gap_in)
@@ -117,7 +133,9 @@ cudaError_t launch_defocus(const BlurArgs &a, int n_envs, int max_tiles, cudaStr
 cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t s);
 // One tile shape and variant of the synthesis kernel (defined in evis_step.cuh and
 // instantiated in the evis_step_*.cu translation units).
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
+// STATS compiles the statistics code (EVIS_STATS, checked at run time); the plain production
+// variant is also built without it.
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s);
 
 // grid_cap > 0: persistent launch of at most grid_cap x (resident CTAs) blocks that take

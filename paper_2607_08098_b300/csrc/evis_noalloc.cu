@@ -105,24 +105,17 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
   if ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))
     return reject("give both threshold maps or neither");
   if (d.refractory_ns < 0) return reject("refractory_ns must be >= 0");
-  if (d.margin < 0 || 2 * d.margin >= d.width || 2 * d.margin >= d.height)
+  if (d.margin < 0 || 2 * int64_t(d.margin) >= d.width || 2 * int64_t(d.margin) >= d.height)
     return reject("margin must satisfy 0 <= 2 * margin < min(width, height)");
   if (flags & ~(EVIS_MODE_B_PRIMARY | EVIS_TIE_INDEX))
     return reject("only EVIS_MODE_B_PRIMARY and EVIS_TIE_INDEX are accepted (inputs are log-intensity)");
   if (!L_A || !mv_A || !Z_A || !L_B || !mv_B || !Z_B || !Lref || !count)
-    return reject("null buffer");
+    return reject("null buffer");  // count: two 64-bit words (events, pixels over the limit)
   if (d.refractory_ns > 0 && !t_last) return reject("t_last is required with a refractory period");
   if (dt_ns <= 0 || dt_ns > (int64_t(1) << 40)) return reject("dt_ns must be in 1..2^40");
   if (capacity < 0 || capacity > (int64_t(1) << 40) || (capacity > 0 && !events))
     return reject("capacity must be in 0..2^40 with a non-null event buffer");
 
-  unsigned char *scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
-  if (e != cudaSuccess) {
-    evis::set_detached_error(std::string("evis_step_noalloc: scratch address: ") +
-                             cudaGetErrorString(e));
-    return EVIS_ERR_CUDA;
-  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   DevEnv de{};
   de.W = d.width;
@@ -141,6 +134,17 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
   const int tiles_x = (d.width - 2 * d.margin + kNaTileW - 1) / kNaTileW;  // sensor tiles
   const int n_tiles = tiles_x * ((d.height - 2 * d.margin + kNaTileH - 1) / kNaTileH);
   const int n_segs = de.segs_x * d.height;
+  // the size checks above keep both tables inside the scratch array; this guards them
+  if (n_tiles < 1 || n_tiles > kNaMaxTiles || n_segs < 1 || n_segs > kNaMaxSegs)
+    return reject("the tile or segment table would not fit the scratch array");
+
+  unsigned char *scratch = nullptr;
+  cudaError_t e = scratch_for_current_device(&scratch);
+  if (e != cudaSuccess) {
+    evis::set_detached_error(std::string("evis_step_noalloc: scratch address: ") +
+                             cudaGetErrorString(e));
+    return EVIS_ERR_CUDA;
+  }
 
   DevEnv *s_env = reinterpret_cast<DevEnv *>(scratch + kOffEnv);
   int64_t *s_clock = reinterpret_cast<int64_t *>(scratch + kOffClock);

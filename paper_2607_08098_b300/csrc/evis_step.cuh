@@ -267,10 +267,71 @@ __host__ __device__ constexpr int step_min_blocks() {
                                            : (nt <= 1 ? 1536 : (nt <= 2 ? 1024 : 768)))) / nth;
 }
 
+// Statistics of one tile in shared memory (the environment's kStat* words).  Warps add
+// their counts of a sub-frame to 32-bit words with one atomic each (every count of a
+// sub-frame stays below 2^16); the warp that closes the sub-frame folds them into the tile's
+// 64-bit totals, which go to the environment's words once per tile.
+struct TileStats {
+  unsigned holes_ab;     // target-sub-frames without a source of A | without one of B << 16
+  unsigned holes_both;   // ... without either
+  unsigned pol;          // staged events copied out since the last fold: ON | OFF << 16
+  unsigned noise;        // noise events staged in this sub-frame
+  unsigned long long tot[kStatOverLimit];
+};
+
+// Folds the per-sub-frame words into the totals (one thread; no warp is between its
+// staging or flush and the end of the sub-frame).
+__device__ __forceinline__ void fold_stats(TileStats &st) {
+  st.tot[kStatHolesA] += st.holes_ab & 0xFFFFu;
+  st.tot[kStatHolesB] += st.holes_ab >> 16;
+  st.tot[kStatHolesBoth] += st.holes_both;
+  st.tot[kStatEventsOn] += st.pol & 0xFFFFu;
+  st.tot[kStatEventsOff] += st.pol >> 16;
+  st.tot[kStatNoise] += st.noise;
+  st.holes_ab = st.holes_both = st.pol = st.noise = 0;
+}
+
+// A record written to global memory without the stage (the stage was full) counts at once.
+__device__ __forceinline__ void count_polarity(TileStats &st, const ulonglong2 &rec) {
+  atomicAdd(&st.tot[static_cast<long long>(rec.y) < 0 ? kStatEventsOff : kStatEventsOn], 1ull);
+}
+
+// Copies staged records [0, n) to the event buffer from position gbs; with statistics on,
+// counts them by polarity (one shared atomic per warp; every lane of a warp then runs the
+// same iterations).
+template <int TX, int TY>
+__device__ __forceinline__ void flush_stage(const StepSmem<TX, TY> &S, unsigned n,
+                                            unsigned long long gbs, const StepArgs &a,
+                                            TileStats &st, bool stats, int tid, int nth) {
+  if (!stats) {
+    for (unsigned r = tid; r < n; r += nth) {
+      const unsigned long long gi = gbs + r;
+      if (gi < a.capacity) a.events[gi] = S.stage[r];
+    }
+    return;
+  }
+  for (unsigned r0 = tid & ~31u; r0 < n; r0 += nth) {
+    const unsigned r = r0 + (tid & 31);
+    bool off = false;
+    if (r < n) {
+      const ulonglong2 rec = S.stage[r];
+      const unsigned long long gi = gbs + r;
+      if (gi < a.capacity) a.events[gi] = rec;
+      off = static_cast<long long>(rec.y) < 0;
+    }
+    const unsigned moff = __ballot_sync(kFull, off);
+    if ((tid & 31) == 0) {
+      const unsigned k = min(32u, n - r0), koff = static_cast<unsigned>(__popc(moff));
+      atomicAdd(&st.pol, (k - koff) | (koff << 16));
+    }
+  }
+}
+
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
 // shared-memory reservation per warp; past the stage's capacity, one global reservation.
 template <int TX, int TY>
-__device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, const StepArgs &a,
+__device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n,
+                                           TileStats &st, bool stats, const StepArgs &a,
                                            bool emit, const ulonglong2 &rec, unsigned lanes_below,
                                            int lane) {
   const unsigned m = __ballot_sync(kFull, emit);
@@ -279,6 +340,7 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, c
   unsigned base = 0;
   unsigned long long gb = 0;
   if (lane == 0) {
+    if (stats) atomicAdd(&st.noise, cnt);
     base = atomicAdd(s_n, cnt);
     if (base + cnt > static_cast<unsigned>(step_stage<TX, TY>()))
       gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
@@ -293,6 +355,7 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, c
     } else {
       const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(step_stage<TX, TY>())));
       if (gi < a.capacity) a.events[gi] = rec;
+      if (stats) count_polarity(st, rec);
     }
   }
 }
@@ -300,7 +363,7 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n, c
 // All K sub-frames of one target tile (the body of step_kernel).  NOISE compiles the sensor
 // noise of Sec. 3.4 in (environments with it off skip it at run time); NC = 3 runs the event
 // model on the R, G and B planes (Sec. 3.2), NC = 1 on the one log-intensity plane.
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
 __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NTH = step_threads<TX, TY>();
   constexpr int NT = TX * TY / NTH;        // targets per thread
@@ -312,6 +375,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
   __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_p1[2], s_arrive;
   __shared__ unsigned long long s_base;
+  __shared__ TileStats tstat;  // this tile's statistics
   __shared__ int s_nc[2], s_over, s_ovf_full[2];
 
   const DevEnv E = a.envs[tl.env];
@@ -323,6 +387,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const unsigned lanes_below = (1u << lane) - 1u;
   const bool b_primary = (a.flags & EVIS_MODE_B_PRIMARY) != 0;
   const bool joint = (a.flags & EVIS_MODE_JOINT) != 0;
+  const bool stats = STATS && a.stats;  // the plain variant compiles no statistics code
   const int64_t T0 = a.clock_in[tl.env];
   const int64_t refr = E.refractory_ns;
   const int tx = tl.x0 + tid % TX;
@@ -372,6 +437,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     s_nc[0] = s_nc[1] = 0;
     s_over = 0;
   }
+  if (tid < kStatOverLimit) tstat.tot[tid] = 0;
+  if (tid == 0) tstat.holes_ab = tstat.holes_both = tstat.pol = tstat.noise = 0;
   // z-buffers start empty; afterwards each thread clears its own slots once it has read them
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
@@ -570,14 +637,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       s_p1[par ^ 1] = 0;
       s_ovf_full[par ^ 1] = 0;
     }
-    {
-      const unsigned nf = s_flush;
-      const unsigned long long gbs = s_base;
-      for (unsigned r = tid; r < nf; r += NTH) {
-        const unsigned long long gi = gbs + r;
-        if (gi < a.capacity) a.events[gi] = S.stage[r];
-      }
-    }
+    flush_stage(S, s_flush, s_base, a, tstat, stats, tid, NTH);
     if (!over && !s_ovf_full[par]) {
       // one flat index space, one source per thread: the whole segments' sources first
       // (item it -> segment it / 32, lane it % 32), then the listed sources
@@ -674,13 +734,24 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
                            : (pol > 0 ? E.c_on : E.c_off);
             const float q = __fdiv_rn(fabsf(d), th);
             if (q >= 1.0f) {
-              if (q >= static_cast<float>(kMaxCrossings)) {
-                n = kMaxCrossings;
-                nf = static_cast<float>(kMaxCrossings);
-              } else {
+              if (q < static_cast<float>(kMaxCrossings + 1)) {
                 n = floor_small(q, &nf);
+              } else {  // n of Eq. 4 above the emission limit: none emitted, counted
+                nf = floorf(q);
+                atomicAdd(a.ev_count + 1, 1ull);
+                if (a.env_stats)
+                  atomicAdd(a.env_stats + static_cast<int64_t>(tl.env) * kStatWords + kStatOverLimit, 1ull);
               }
             }
+          }
+        }
+        if (c == 0 && stats) {  // holes per warp direction (statistics)
+          const unsigned ha = __ballot_sync(kFull, act[j] && kA == kEmptyKey);
+          const unsigned hb = __ballot_sync(kFull, act[j] && kB == kEmptyKey);
+          if (lane == 0 && (ha | hb)) {
+            atomicAdd(&tstat.holes_ab, static_cast<unsigned>(__popc(ha)) |
+                                        (static_cast<unsigned>(__popc(hb)) << 16));
+            if (ha & hb) atomicAdd(&tstat.holes_both, static_cast<unsigned>(__popc(ha & hb)));
           }
         }
         // ---- crossings k = 1..n of the warp's 32 pixels, spread over its lanes ----
@@ -776,6 +847,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
               } else {
                 const unsigned long long gi = gb + (idx - max(base, NSTAGE));
                 if (gi < a.capacity) a.events[gi] = rec;
+                if (stats) count_polarity(tstat, rec);
               }
             }
           }
@@ -803,17 +875,17 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
             if (fl || fs || fh)
               rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u + cw), E.key0, E.key1);
             const int cp = 1 + c;
-            stage_warp(S, &s_n, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, cp),
+            stage_warp(S, &s_n, tstat, stats, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, cp),
                        lanes_below, lane);
-            stage_warp(S, &s_n, a, fs,
+            stage_warp(S, &s_n, tstat, stats, a, fs,
                        make_event(noise_time(rt.y, tim1, d), ex, ey, tl.env, (rt.w & 1u) ? cp : -cp),
                        lanes_below, lane);
-            stage_warp(S, &s_n, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, cp),
+            stage_warp(S, &s_n, tstat, stats, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, cp),
                        lanes_below, lane);
           }
         }
         if (has) {
-          if (n > 0) Lref[j][c] = __fadd_rn(Lref[j][c], __fmul_rn(pol > 0 ? nf : -nf, th));
+          if (nf > 0.0f) Lref[j][c] = __fadd_rn(Lref[j][c], __fmul_rn(pol > 0 ? nf : -nf, th));
           Lprev[j][c] = L;
           if (c == NC - 1) tprev[j] = ti;  // after every channel's crossings used it
         }
@@ -831,18 +903,13 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         s_base = nn ? atomicAdd(a.ev_count, static_cast<unsigned long long>(nn)) : 0ull;
         s_n = 0;
         s_arrive = 0;
+        if (stats) fold_stats(tstat);
       }
     }
   }
   __syncthreads();
-  {
-    const unsigned nf = s_flush;
-    const unsigned long long gbs = s_base;
-    for (unsigned r = tid; r < nf; r += NTH) {
-      const unsigned long long gi = gbs + r;
-      if (gi < a.capacity) a.events[gi] = S.stage[r];
-    }
-  }
+  flush_stage(S, s_flush, s_base, a, tstat, stats, tid, NTH);
+  __syncthreads();  // the statistics words are complete
 
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
@@ -854,6 +921,12 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       if (a.tlast) a.tlast[c * a.plane + o + pix] = tlast[j][c];
     }
   }
+  if (tid == 0 && stats) {
+    fold_stats(tstat);  // the last stage's copy
+    for (int w = 0; w < kStatOverLimit; ++w)
+      if (tstat.tot[w])
+        atomicAdd(a.env_stats + static_cast<int64_t>(tl.env) * kStatWords + w, tstat.tot[w]);
+  }
   if (tid == 0 && tl.x0 == E.margin && tl.y0 == E.margin) {  // the environment's first tile
     a.clock_out[tl.env] = T0 + a.dt;
     if (a.gap_out) a.gap_out[tl.env] = a.gap_in[tl.env] + 1u;
@@ -862,13 +935,13 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 
 // One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
 // first one by block index, the next ones from a work counter that starts at 0.
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
 __global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY, NC>())
     step_kernel(const StepArgs a) {
   __shared__ int s_tile;
   int t = blockIdx.x;
   while (t < a.n_tiles) {
-    run_tile<TX, TY, TRACE, PACKED, NOISE, NC>(a, a.tiles[t]);
+    run_tile<TX, TY, TRACE, PACKED, NOISE, NC, STATS>(a, a.tiles[t]);
     __syncthreads();  // the tile's shared memory is free again
     if (threadIdx.x == 0) s_tile = static_cast<int>(gridDim.x + atomicAdd(a.work_counter, 1u));
     __syncthreads();
@@ -878,7 +951,7 @@ __global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY
 
 }  // namespace
 
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC>
+template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
   // per device (the shared-memory attribute belongs to the device's context): resident CTAs
   // per SM x SMs, looked up at the first launch of this instantiation on that device
@@ -891,14 +964,14 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   int resident = resident_of[dev].load(std::memory_order_relaxed);
   if (!resident) {
-    if ((e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>,
+    if ((e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE, NC, STATS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return e;
     int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE, NC>, step_threads<TX, TY>(),
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE, NC, STATS>, step_threads<TX, TY>(),
              smem)) != cudaSuccess)
       return e;
     resident = max(1, per_sm) * sms;
@@ -906,7 +979,7 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
   }
   int grid = n_tiles;
   if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
-  step_kernel<TX, TY, TRACE, PACKED, NOISE, NC><<<grid, step_threads<TX, TY>(), smem, s>>>(a);
+  step_kernel<TX, TY, TRACE, PACKED, NOISE, NC, STATS><<<grid, step_threads<TX, TY>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 

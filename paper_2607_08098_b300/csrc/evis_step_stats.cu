@@ -1,0 +1,14 @@
+// Explicit instantiations of the synthesis kernel: production variants without sensor noise that
+// collect the statistics of EVIS_STATS, every tile shape.
+#include "evis_step.cuh"
+
+namespace evis {
+
+template cudaError_t launch_shape<32, 8, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 16, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+
+}  // namespace evis

@@ -826,3 +826,121 @@ def test_extreme_shapes_and_long_k(ev, oracle_mod, tile):
     evs = run_both(ev, oracle_mod, envs, kfs, 16_666_667, trace_steps=(2,), tile=tile,
                    capacity=1 << 23)
     assert evs["x"].max() >= 65000 and evs["y"].max() >= 65000
+
+
+@pytest.mark.parametrize("tile", [(32, 16), (64, 16), (32, 8)])
+def test_crossing_limit_is_reported(ev, oracle_mod, tile):
+    """Pixel-sub-frames whose Eq. 4 count n exceeds the per-pixel emission limit (4096):
+    none of their crossings is emitted, the reference still moves by the whole p n C, the
+    read reports ERR_RANGE (with every other event delivered), env_stats counts them per
+    environment, and all of it equals the oracle bit for bit (refractory period on, an
+    infinite and a NaN outcome included)."""
+    C = 0.25
+    envs = [TinyEnv(W=70, H=37, K=3, c_on=C, c_off=0.3, refractory_ns=30_000),
+            TinyEnv(W=33, H=20, K=2, c_on=C, c_off=C)]
+    n = packed_total(envs)
+    rng = np.random.default_rng(21)
+    lim = ev.MAX_CROSSINGS
+
+    class KF:
+        pass
+
+    kfs = []
+    for s in range(3):
+        k = KF()
+        k.L = rng.normal(0, 1, n).astype(np.float32)
+        big = rng.random(n) < 0.04
+        k.L[big] = np.float32((3 * (lim + 1) + 1.5) * C) * rng.choice([-1, 1], big.sum())
+        k.L[rng.random(n) < 0.002] = np.float32(3e38)
+        k.mv = np.zeros((n, 2), np.float32)
+        k.Z = np.ones(n, np.float32)
+        kfs.append(k)
+    o = oracle_mod.Oracle(envs, flags=oracle_mod.IN_LOG)
+    ctx = ev.Context(envs, flags=ev.IN_LOG | (ev.STATS if tile == (32, 16) else 0),
+                     capacity=1 << 22)
+    ctx.set_tile_shape(*tile)
+    for s, k in enumerate(kfs):
+        o.step(k.L, k.mv, k.Z, 1_000_000)
+        ctx.step(_dev(k.L), _dev(k.mv), _dev(k.Z), 1_000_000)
+        if s == 0:
+            continue
+        assert o.last_over_limit
+        with pytest.raises(ev.EvisError) as ei:
+            ctx.read_events()
+        assert ei.value.status == ev.ERR_RANGE
+        got = ev.sort_events(ei.value.events)
+        want = oracle_mod.sort_events(o.events())
+        assert len(got) == len(want) > 1000
+        np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+        np.testing.assert_array_equal(ctx.env_stats()["over_limit"], o.over_limit())
+    so, sg = o.state(), ctx.state()
+    np.testing.assert_array_equal(sg[0], so[0])      # NaN where Eq. 4 met inf - inf
+    np.testing.assert_array_equal(sg[1], so[1])
+    # a gap without such pixels reads OK again
+    k = kfs[-1]
+    o.step(k.L, k.mv, k.Z, 1_000_000)
+    ctx.step(_dev(k.L), _dev(k.mv), _dev(k.Z), 1_000_000)
+    if not o.last_over_limit:
+        assert len(ctx.read_events()) == len(o.events())
+    ctx.close()
+
+
+def test_env_stats_holes_polarity_and_noise(ev, oracle_mod, scenes_mod):
+    """evis_get_env_stats against counts taken from the oracle: holes per warp direction and
+    of both from its traced z-buffers (sensor pixels inside a margin), ON / OFF events from
+    its stream, noise events as the difference to a noise-free oracle run."""
+    w = scenes_mod.config4(n_envs=3, W=200, H=150)
+    for e in w.envs:
+        e.K, e.margin = 8, 5
+    kfs = [scenes_mod.render(w.envs, k) for k in range(3)]
+    noise = [dict(leak_hz=60.0, shot_hz=90.0, hot_hz=200.0, hot_fraction=0.02, lo=-3.0, hi=3.0,
+                  seed=77 + i) for i in range(len(w.envs))]
+    o = oracle_mod.Oracle(w.envs, flags=oracle_mod.IN_LOG)
+    o.set_noise(noise)
+    quiet = oracle_mod.Oracle(w.envs, flags=oracle_mod.IN_LOG)
+    ctx = ev.Context(w.envs, flags=ev.IN_LOG | ev.STATS, capacity=1 << 23)
+    ctx.set_noise(noise)
+    plain = ev.Context(w.envs, flags=ev.IN_LOG, capacity=1 << 23)   # statistics off
+    plain.set_noise(noise)
+    holes = np.zeros((len(w.envs), 3), np.uint64)
+    for s, kf in enumerate(kfs):
+        tr = o.step(kf.L, kf.mv, kf.Z, w.dt_ns, trace=s > 0)
+        quiet.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+        ctx.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+        plain.step(_dev(kf.L), _dev(kf.mv), _dev(kf.Z), w.dt_ns)
+        if s == 0:
+            continue
+        keys = tr[0]
+        ko = 0
+        for i, e in enumerate(w.envs):
+            k = keys[ko:ko + e.K * 2 * e.H * e.W].reshape(e.K, 2, e.H, e.W)
+            ko += e.K * 2 * e.H * e.W
+            m = e.margin
+            emp = k[:, :, m:e.H - m, m:e.W - m] == np.uint64(0xFFFFFFFFFFFFFFFF)
+            holes[i] += np.array([emp[:, 0].sum(), emp[:, 1].sum(), (emp[:, 0] & emp[:, 1]).sum()],
+                                 dtype=np.uint64)
+    evs = o.events()
+    n_quiet = np.bincount(quiet.events()["env"], minlength=len(w.envs))
+    st = ctx.env_stats()
+    got = ev.sort_events(ctx.read_events())
+    np.testing.assert_array_equal(got.view(np.uint8), oracle_mod.sort_events(evs).view(np.uint8))
+    for i, e in enumerate(w.envs):
+        mine = evs[evs["env"] == i]
+        assert st["target_subframes"][i] == (e.W - 2 * e.margin) * (e.H - 2 * e.margin) * e.K * 2
+        assert [st["holes_a"][i], st["holes_b"][i], st["holes_both"][i]] == holes[i].tolist()
+        assert st["events_on"][i] == np.sum(mine["p"] > 0)
+        assert st["events_off"][i] == np.sum(mine["p"] < 0)
+        assert st["noise_events"][i] == len(mine) - n_quiet[i] > 0
+        assert st["over_limit"][i] == 0
+    # the high-speed scenes leave holes in both directions (Sec. 3.3 fills one from the other)
+    assert np.all(st["holes_a"] > 0) and np.all(st["holes_b"] > 0)
+    ctx.close()
+    # without EVIS_STATS: the same events, only the always-kept counts
+    sp = plain.env_stats()
+    got_p = ev.sort_events(plain.read_events())
+    np.testing.assert_array_equal(got_p.view(np.uint8), got.view(np.uint8))
+    np.testing.assert_array_equal(sp["target_subframes"], st["target_subframes"])
+    for f in ("holes_a", "holes_b", "holes_both", "events_on", "events_off", "noise_events",
+              "over_limit"):
+        assert np.all(sp[f] == 0), f
+    plain.close()
