@@ -64,31 +64,38 @@ inline double lattice(uint64_t seed, int64_t i, int64_t j) {
 
 inline double smooth(double t) { return t * t * (3.0 - 2.0 * t); }
 
-// A small direct-mapped memo of lattice values: neighbouring pixels share lattice points, and
-// a memoised value is the same double that lattice() returns, so the output is unchanged.
-struct LatticeMemo {
-  struct Slot { uint64_t seed; int64_t i, j; double v; bool ok; };
-  Slot slot[512] = {};
-  double get(uint64_t seed, int64_t i, int64_t j) {
-    Slot& s = slot[(static_cast<uint64_t>(i) * 0x9E37u + static_cast<uint64_t>(j) * 0x85EBu +
-                    (seed & 0xFFu) * 0x27u) & 511u];
-    if (!(s.ok && s.seed == seed && s.i == i && s.j == j)) {
-      s.seed = seed;
-      s.i = i;
-      s.j = j;
-      s.v = lattice(seed, i, j);
-      s.ok = true;
-    }
-    return s.v;
+// Lattice values of one octave of one layer over a rectangle of lattice points, filled once
+// per render job: a table entry is the very double lattice() returns, so the output does not
+// depend on the table (points outside it are computed directly).
+struct LatticeTable {
+  uint64_t seed = 0;
+  int64_t i0 = 0, j0 = 0;
+  int64_t ni = 0, nj = 0;
+  std::vector<double> v;
+  void fill(uint64_t s, int64_t ilo, int64_t ihi, int64_t jlo, int64_t jhi) {
+    seed = s;
+    i0 = ilo;
+    j0 = jlo;
+    ni = std::max<int64_t>(0, ihi - ilo + 1);
+    nj = std::max<int64_t>(0, jhi - jlo + 1);
+    if (ni * nj > (int64_t(1) << 22)) ni = nj = 0;  // too large: compute every point
+    v.resize(static_cast<size_t>(ni * nj));
+    for (int64_t j = 0; j < nj; ++j)
+      for (int64_t i = 0; i < ni; ++i) v[static_cast<size_t>(j * ni + i)] = lattice(s, i0 + i, j0 + j);
+  }
+  double get(int64_t i, int64_t j) const {
+    const int64_t a = i - i0, b = j - j0;
+    if (a >= 0 && a < ni && b >= 0 && b < nj) return v[static_cast<size_t>(b * ni + a)];
+    return lattice(seed, i, j);
   }
 };
 
-inline double value_noise(LatticeMemo& m, uint64_t seed, double x, double y) {
+inline double value_noise(const LatticeTable& m, double x, double y) {
   double fx = std::floor(x), fy = std::floor(y);
   int64_t i = static_cast<int64_t>(fx), j = static_cast<int64_t>(fy);
   double sx = smooth(x - fx), sy = smooth(y - fy);
-  double a = m.get(seed, i, j), b = m.get(seed, i + 1, j);
-  double c = m.get(seed, i, j + 1), d = m.get(seed, i + 1, j + 1);
+  double a = m.get(i, j), b = m.get(i + 1, j);
+  double c = m.get(i, j + 1), d = m.get(i + 1, j + 1);
   double top = a + (b - a) * sx, bot = c + (d - c) * sx;
   return top + (bot - top) * sy;
 }
@@ -97,7 +104,30 @@ struct LayerAt {  // a layer evaluated at one keyframe
   const double* p;
   double depth, cx, cy, ca, sa;         // at keyframe k
   double pcx, pcy, pca, psa;            // at keyframe k-1
+  LatticeTable oct[2];                  // value-noise lattice of both octaves over this job
 };
+
+// Lattice points that texture coordinates (u / cell) * scale of the job's pixels can reach:
+// the layer-local images of the rectangle's corners, widened by two points on each side.
+void lattice_range(const LayerAt& a, double scale, int W, int row0, int row1, int64_t* ilo,
+                   int64_t* ihi, int64_t* jlo, int64_t* jhi) {
+  double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+  const double xs[2] = {0.0, static_cast<double>(W - 1)};
+  const double ys[2] = {static_cast<double>(row0), static_cast<double>(row1 - 1)};
+  for (double x : xs)
+    for (double y : ys) {
+      const double dx = x - a.cx, dy = y - a.cy;
+      const double ux = (a.ca * dx + a.sa * dy) * scale, uy = (-a.sa * dx + a.ca * dy) * scale;
+      xmin = std::min(xmin, ux);
+      xmax = std::max(xmax, ux);
+      ymin = std::min(ymin, uy);
+      ymax = std::max(ymax, uy);
+    }
+  *ilo = static_cast<int64_t>(std::floor(xmin)) - 2;
+  *ihi = static_cast<int64_t>(std::floor(xmax)) + 2;
+  *jlo = static_cast<int64_t>(std::floor(ymin)) - 2;
+  *jhi = static_cast<int64_t>(std::floor(ymax)) + 2;
+}
 
 void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int row0, int row1,
                 float* L, float* I, float* rgb, float* mv, float* Z) {
@@ -117,6 +147,14 @@ void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int
     double pang = p[F_ANGLE0] + p[F_OMEGA] * (k - 1);
     a.pca = std::cos(pang);
     a.psa = std::sin(pang);
+    if (p[F_TEX_KIND] == 0.0) {
+      const uint64_t seed = static_cast<uint64_t>(p[F_SEED]);
+      for (int o = 0; o < 2; ++o) {
+        int64_t ilo, ihi, jlo, jhi;
+        lattice_range(a, (o ? 2.0 : 1.0) / p[F_CELL], W, row0, row1, &ilo, &ihi, &jlo, &jhi);
+        a.oct[o].fill(o ? splitmix64(seed ^ 0xA5A5A5A5ull) : splitmix64(seed), ilo, ihi, jlo, jhi);
+      }
+    }
   }
   // nearest layer first; equal depths keep layer order
   std::vector<int> order(n_layers);
@@ -124,7 +162,6 @@ void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return ls[x].depth < ls[y].depth; });
   const double ln10 = 2.302585092994046;
-  LatticeMemo memo;
   for (int y = row0; y < row1; ++y) {
     for (int x = 0; x < W; ++x) {
       const LayerAt* hit = nullptr;
@@ -152,10 +189,9 @@ void render_env(int W, int H, int n_layers, const double* layers, int32_t k, int
       double uy = -hit->sa * dx + hit->ca * dy;
       double z;
       if (p[F_TEX_KIND] == 0.0) {
-        uint64_t seed = static_cast<uint64_t>(p[F_SEED]);
         double cell = p[F_CELL];
-        double n1 = value_noise(memo, splitmix64(seed), ux / cell, uy / cell);
-        double n2 = value_noise(memo, splitmix64(seed ^ 0xA5A5A5A5ull), 2.0 * ux / cell, 2.0 * uy / cell);
+        double n1 = value_noise(hit->oct[0], ux / cell, uy / cell);
+        double n2 = value_noise(hit->oct[1], 2.0 * ux / cell, 2.0 * uy / cell);
         z = (n1 + 0.5 * n2) * 1.35;  // ~unit variance for smoothstep value noise
       } else if (p[F_TEX_KIND] == 2.0) {
         z = ux;
@@ -204,7 +240,8 @@ int scenes_render(int32_t n_envs, const int32_t* W, const int32_t* H, const int6
   std::vector<Job> jobs;
   for (int e = 0; e < n_envs; ++e) {
     if (W[e] <= 0 || H[e] <= 0 || n_layers[e] < 0) return -1;
-    for (int r = 0; r < H[e]; r += 16) jobs.push_back({e, r, std::min(H[e], r + 16)});
+    const int rows = n_envs >= 4 * std::max(1, n_threads) ? 64 : 16;  // fewer lattice fills
+    for (int r = 0; r < H[e]; r += rows) jobs.push_back({e, r, std::min(H[e], r + rows)});
   }
   auto run = [&](size_t j) {
     const Job& jb = jobs[j];
