@@ -1,24 +1,32 @@
 #!/usr/bin/env python3
 """Throughput of the EVIS event-synthesis hot path on B300.
 
-Workload (default): 64 environments at 346x260, K = 16 sub-frames per keyframe gap,
-C = 0.25, refractory period 100 us, fp32, three depth layers per environment with seeded
-random rigid motions (synthetic scenes; no dataset).  Inputs are linear radiance, motion
-vectors and depth, resident in HBM, so the log conversion is part of the timed path.
+Headline workload (default): the high-speed batch, the largest configuration that fits one
+GPU.  1024 environments at 640x480, K = 32 sub-frames per keyframe gap (8 ms), C = 0.15, five
+depth layers of seeded textured disks moving up to 40 px per keyframe (about 10 % of the
+target-sub-frames are disocclusion holes of one warp direction), fp32 log-intensity inputs,
+no refractory period.  Synthetic scenes, no dataset.
 
-One step = one keyframe gap of every environment: the input-preparation kernel (log,
-motion bound) and the synthesis kernel (bidirectional splat, z-buffer, blend, threshold
-crossings, event compaction).  Metric: Mpixel-substeps/s (sum over environments of
-H * W * K per step / time); events/s is reported beside it.
+One step = one keyframe gap of every environment: the input-preparation kernel (motion
+bounds, per-source packs) and the synthesis kernel (bidirectional splat, z-buffer, blend,
+threshold crossings, event compaction), on keyframes already resident in HBM.  Metric:
+Mpixel-substeps/s (sum over environments of H * W * K per step / time); events/s beside it.
+
+The same JSON line carries, as extra keys: the 64-environment 346x260 workload with linear
+inputs and a refractory period ("config2"), the uneven 256-environment batch run as one
+context per environment, as one batched step and as an autotuned graph replay ("config3"),
+and the differentiable surrogate ("soft_surrogate").
 
     python bench.py [--steps K] [--warmup W] [--gpus N] [--impl evis|reference]
 
-Under torchrun each rank runs its own 64 environments (disjoint seeds, no data exchange:
+Under torchrun each rank runs its own 1024 environments (disjoint seeds, no data exchange:
 weak scaling); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
+import hashlib
 import json
 import os
 import statistics
@@ -40,24 +48,26 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["evis", "reference"], default="evis")
-    ap.add_argument("--envs", type=int, default=64)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--workload", choices=["highspeed", "envs64", "batched", "stages"],
+                    default="highspeed",
+                    help="highspeed: the headline line (1024 envs at 640x480, K=32) with the "
+                         "other workloads as extra keys; envs64: the 64-env 346x260 line alone; "
+                         "batched: the uneven 256-env batch alone; stages: sensor noise, colour, "
+                         "margin, defocus and the voxel grid")
+    ap.add_argument("--hs-envs", type=int, default=1024,
+                    help="environments of the high-speed workload (640x480, K=32)")
+    ap.add_argument("--envs", type=int, default=64, help="environments of the 346x260 workload")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only (no config2 / config3 / soft_surrogate keys)")
     ap.add_argument("--stage", choices=["all", "synthesis", "defocus", "voxel"], default="all",
                     help="with --workload stages: the part to run")
     ap.add_argument("--voxel-envs", type=int, default=8,
                     help="environments (640x480) of the voxel-grid stage")
-    ap.add_argument("--hs-envs", type=int, default=1024,
-                    help="environments of --workload highspeed (640x480, K=32)")
-    ap.add_argument("--cpu-envs", type=int, default=6, help="oracle sample size (environments)")
-    ap.add_argument("--workload", choices=["envs64", "batched", "stages", "highspeed"], default="envs64",
-                    help="envs64: the benchmarked 64-env workload; batched: the uneven 256-env "
-                         "batch, per-environment launches vs one batched context vs graph replay; "
-                         "stages: sensor noise, colour, margin, defocus and the voxel grid; "
-                         "highspeed: 1024 envs at 640x480, K=32, flows up to 40 px (full size)")
     return ap.parse_args()
 
 
@@ -68,18 +78,55 @@ def dist_info():
     return world, rank, local
 
 
-def workload(n_envs, rank):
+# ------------------------------------------------------------------------------------------
+# workloads and their byte models
+# ------------------------------------------------------------------------------------------
+
+def highspeed_workload(n_envs, rank=0):
+    import scenes
+    return scenes.config4(n_envs=n_envs, first_env=rank * n_envs)
+
+
+def highspeed_config(w, n_envs):
+    e = w.envs[0]
+    return {"workload": f"high-speed batch: {n_envs} envs at {e.W}x{e.H}, K={e.K}, C={e.c_on}, "
+                        "5 depth layers, flows up to 40 px per keyframe (~10 % holes), "
+                        "log-intensity inputs, no refractory period",
+            "envs": n_envs, "width": e.W, "height": e.H, "K": e.K, "C": e.c_on,
+            "refractory_ns": 0, "dt_ns": w.dt_ns, "input": "log intensity, fp32",
+            "pixel_substeps_per_step": w.pixel_substeps,
+            "l2": "each step reads a fresh 5 GB keyframe (inputs far larger than the 126 MB L2); "
+                  "a 256 MB L2 flush runs between timed steps as well"}
+
+
+def config2_workload(n_envs, rank=0):
     import scenes
     return scenes.config2(n_envs=n_envs, first_env=rank * n_envs)
 
 
-def config_block(w, n_envs):
+def config2_config(w, n_envs):
     return {"workload": f"{n_envs} envs at 346x260, K=16, C=0.25, refractory 100us, "
                         "3 depth layers, linear-radiance inputs",
             "envs": n_envs, "width": 346, "height": 260, "K": 16, "C": 0.25,
             "refractory_ns": 100_000, "dt_ns": w.dt_ns, "input": "linear luminance (log on path)",
             "pixel_substeps_per_step": w.pixel_substeps,
             "l2": "flushed between timed steps (256 MB write); each step also reads a fresh keyframe"}
+
+
+def algorithmic_bytes(envs, n_events):
+    """Bytes the method must move for one keyframe gap of envs (per pixel: keyframes A and B,
+    2 x (4 L + 8 mv + 4 Z) = 32 B; the reference level read and written, 8 B; the last-event
+    time read and written, 16 B, where a refractory period is set; the two threshold maps,
+    8 B, where they are per pixel) plus 16 B per event written."""
+    b = 0
+    for e in envs:
+        per_px = 32 + 8
+        if e.refractory_ns > 0:
+            per_px += 16
+        if getattr(e, "c_on_map", None) is not None:
+            per_px += 8
+        b += e.W * e.H * per_px
+    return b + 16 * n_events
 
 
 # ------------------------------------------------------------------------------------------
@@ -132,108 +179,140 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-# CPU baseline and reference arm: the oracle on a bounded sample
+# peaks and committed profile records
 # ------------------------------------------------------------------------------------------
 
-def oracle_sample_rate(n_envs, n_steps, rank=0):
-    """Times the oracle (single thread) on n_envs environments for n_steps keyframe gaps.
-    Returns (Mpx-substeps/s, events/s, seconds, description)."""
-    import oracle
-    import scenes
-    w = scenes.config2(n_envs=n_envs, first_env=rank * n_envs)
-    kfs = [scenes.render(w.envs, k) for k in range(n_steps + 1)]
-    o = oracle.Oracle(w.envs, eps=1e-4, flags=oracle.IN_LUM)
-    o.step(kfs[0].I, kfs[0].mv, kfs[0].Z, w.dt_ns)
-    t0 = time.perf_counter()
-    for kf in kfs[1:]:
-        o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
-    sec = time.perf_counter() - t0
-    nev = len(o.events())
-    return (w.pixel_substeps * n_steps / sec / 1e6, nev / sec, sec,
-            f"{n_envs} of the environments x {n_steps} keyframe gaps (same scenes, same K, C, "
-            f"refractory), single-threaded C++ oracle")
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
 
 
-def oracle_gap_seconds(envs, dt_ns, frame_key, log_inputs):
-    """Seconds the oracle (single thread) takes for one keyframe gap of envs, after their
-    first keyframe: the sample behind an extrapolated CPU baseline."""
-    import oracle
-    import scenes
-    kfs = [scenes.render(envs, k, want=(frame_key, "mv", "Z")) for k in range(2)]
-    o = oracle.Oracle(envs, eps=1e-4, flags=oracle.IN_LOG if log_inputs else oracle.IN_LUM)
-    o.step(getattr(kfs[0], frame_key), kfs[0].mv, kfs[0].Z, dt_ns)
-    t0 = time.perf_counter()
-    o.step(getattr(kfs[1], frame_key), kfs[1].mv, kfs[1].Z, dt_ns)
-    return time.perf_counter() - t0
+def traffic_record(workload_key):
+    """ncu figures per launch of the synthesis kernel for one workload (DRAM bytes, warp
+    instructions), if profiles/step_kernel_traffic.json holds a capture of the current kernel
+    source, else None."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2607_08098_b300", "csrc", "evis_step.cuh")
+    try:
+        rec = json.load(open(p))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("kernel_sha256") == h:
+            return rec.get("workloads", {}).get(workload_key)
+    except (OSError, ValueError):
+        pass
+    return None
 
 
-def oracle_parallel_rate(envs_per_thread, n_steps, threads):
-    """The env-parallel CPU baseline: one oracle per thread, each over its own slice of
-    environments, stepping at the same time (the oracle's C calls release the GIL).
-    Returns (Mpx-substeps/s, events/s, seconds, description)."""
-    from concurrent.futures import ThreadPoolExecutor
-    import oracle
-    import scenes
-    work = []
-    for t in range(threads):
-        w = scenes.config2(n_envs=envs_per_thread, first_env=t * envs_per_thread)
-        kfs = [scenes.render(w.envs, k) for k in range(n_steps + 1)]
-        o = oracle.Oracle(w.envs, eps=1e-4, flags=oracle.IN_LUM)
-        o.step(kfs[0].I, kfs[0].mv, kfs[0].Z, w.dt_ns)
-        work.append((o, kfs[1:], w))
-
-    def run(item):
-        o, kfs, w = item
-        for kf in kfs:
-            o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
-
-    with ThreadPoolExecutor(max_workers=threads) as pool:
-        t0 = time.perf_counter()
-        list(pool.map(run, work))
-        sec = time.perf_counter() - t0
-    units = sum(w.pixel_substeps for _, _, w in work) * n_steps
-    nev = sum(len(o.events()) for o, _, _ in work)
-    return (units / sec / 1e6, nev / sec, sec,
-            f"{threads} threads x {envs_per_thread} environments x {n_steps} keyframe gaps, one "
-            f"single-threaded C++ oracle per thread on its own environments")
-
-
-def reference_arm(args, world, rank):
-    if rank != 0:
-        return
-    per_step_envs = 2
-    import oracle
-    import scenes
-    w = scenes.config2(n_envs=per_step_envs)
-    n_kf = args.warmup + args.steps + 1
-    kfs = [scenes.render(w.envs, k) for k in range(n_kf)]
-    o = oracle.Oracle(w.envs, eps=1e-4, flags=oracle.IN_LUM)
-    o.step(kfs[0].I, kfs[0].mv, kfs[0].Z, w.dt_ns)
-    for kf in kfs[1:1 + args.warmup]:
-        o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
-    o.events()
-    t0 = time.perf_counter()
-    for kf in kfs[1 + args.warmup:]:
-        o.step(kf.I, kf.mv, kf.Z, w.dt_ns)
-    sec = time.perf_counter() - t0
-    nev = len(o.events())
-    value = w.pixel_substeps * args.steps / sec / 1e6
-    sample = (f"each step: {per_step_envs} of the 64 environments (346x260, K=16) for one "
-              f"keyframe gap, single-threaded C++ oracle")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": config_block(scenes.config2(), 64),
-            "events_per_s": nev / sec,
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
-                             "unit": UNIT},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def roofline_block(envs, n_events_per_step, syn_ms, prep_ms, shapes, tuned_ms, workload_key,
+                   clk, sms):
+    """The synthesis kernel against HBM (algorithmic bytes / its mean CUDA-event duration)
+    and against instruction issue (its captured warp instructions / duration)."""
+    peak, peak_kind = measured_peak()
+    alg = algorithmic_bytes(envs, n_events_per_step)
+    achieved = alg / (syn_ms / 1e3) / 1e9
+    tr = traffic_record(workload_key)
+    r = {"kernel": "step_kernel (splat + z-buffer + blend + crossings + compaction)",
+         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+         "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+         "traffic": None if tr is None else tr["dram_bytes_per_launch"],
+         "algorithmic_bytes_per_launch": alg, "kernel_ms": syn_ms, "prep_ms": prep_ms,
+         "tile_shape": shapes, "autotune_best_ms": tuned_ms,
+         "nominal_peak": 7700.0, "frac_of_nominal": achieved / 7700.0}
+    if tr is not None:
+        dram = tr["dram_bytes_per_launch"] / (syn_ms / 1e3) / 1e9
+        r["dram"] = {"achieved": dram, "frac": dram / peak, "unit": "GB/s",
+                     "source": tr.get("source", "ncu dram__bytes_read.sum + dram__bytes_write.sum")}
+        if "warp_instructions_per_launch" in tr:
+            # the kernel's real ceiling: instruction issue, 4 schedulers per SM, one warp
+            # instruction per clock each, at the SM clock sampled during the timed region
+            mhz = clk.get("sm_mhz") or 2032.0
+            peak_issue = sms * 4 * mhz * 1e6
+            ach = tr["warp_instructions_per_launch"] / (syn_ms / 1e3)
+            r["issue"] = {"bound": "instruction issue", "achieved_warp_inst_per_s": ach,
+                          "peak_warp_inst_per_s": peak_issue, "frac": ach / peak_issue,
+                          "sm_mhz": mhz, "nominal_peak_warp_inst_per_s": sms * 4 * 2.032e9,
+                          "warp_instructions_per_pixel_substep":
+                              tr.get("warp_instructions_per_pixel_substep"),
+                          "source": "ncu smsp__inst_executed.sum of the committed capture"}
+    return r
 
 
 # ------------------------------------------------------------------------------------------
-# the CUDA path
+# device-timed keyframe gaps
 # ------------------------------------------------------------------------------------------
+
+def upload_keyframes(w, n_kf, frame_key):
+    """Renders keyframes 0..n_kf-1 (host) and keeps them on the device: (frames, mv, depth)."""
+    import scenes
+    import torch
+    dev = []
+    for k in range(n_kf):
+        kf = scenes.render(w.envs, k, want=(frame_key, "mv", "Z"))
+        dev.append(tuple(torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
+                         for a in (getattr(kf, frame_key), kf.mv, kf.Z)))
+        del kf
+    return dev
+
+
+def timed_gaps(ev, w, dev, flags, steps, warmup, dist=None, clocks=None, reps_autotune=1):
+    """Context over w.envs fed dev[0] (reference levels), autotuned on dev[1], warmed up on
+    dev[1..warmup], then `steps` timed gaps dev[warmup+1..], each bracketed by CUDA events on
+    the context's stream after an L2 flush and an event-buffer clear (the events of a gap
+    stay in the buffer until the next gap).  Returns the per-step figures."""
+    import torch
+    probe = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=1 << 20)
+    probe.step(*dev[0], w.dt_ns)
+    probe.step(*dev[1], w.dt_ns)
+    per_gap = probe.event_count()          # counted beyond the buffer too
+    probe.close()
+    # later gaps of the moving scenes carry more events than the first (up to ~1.4x over 25
+    # gaps of the high-speed batch): room for twice the first gap's
+    capacity = int(per_gap * 2.0) + (1 << 20)
+    ctx = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=capacity)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ctx.step(*dev[0], w.dt_ns)
+    tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=reps_autotune)
+    shapes = ctx.tile_shapes()
+    for k in range(1, 1 + warmup):
+        ctx.clear_events()
+        ctx.step(*dev[k], w.dt_ns)
+    torch.cuda.synchronize()
+    ctx.profile(steps)
+    st = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, events = [], []
+    wall0 = time.perf_counter()
+    for s_ in range(steps):
+        ctx.clear_events()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ctx.step(*dev[1 + warmup + s_], w.dt_ns)
+        b.record(st)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+        n = ctx.event_count()
+        if n > capacity:
+            raise RuntimeError("event buffer overflow in the timed region")
+        events.append(n)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    prof = ctx.profile_read()
+    ctx.close()
+    classes = {}
+    for e, sh in zip(w.envs, shapes):
+        classes.setdefault(f"{e.W}x{e.H}", f"{sh[0]}x{sh[1]}")
+    return {"step_ms": ms, "events": events, "syn_ms": float(prof[:, 1].mean()),
+            "prep_ms": float(prof[:, 0].mean()), "shapes": classes, "tuned_ms": tuned_ms,
+            "capacity": capacity, "per_gap_probe": per_gap, "wall_s": wall}
+
 
 def reduce_over_ranks(total_ms, units, events, device):
     """Whole-job figures of a weak-scaling run: the slowest rank's time and the units and
@@ -249,31 +328,208 @@ def reduce_over_ranks(total_ms, units, events, device):
     return float(mx[0]), float(sm[1]), float(sm[2])
 
 
-def measured_peak():
+def host_mem_available():
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"]), "measured"
-    except (OSError, KeyError, ValueError):
-        return 6400.0, "fallback"
-
-
-def traffic_record():
-    """ncu DRAM bytes per launch of the synthesis kernel, if a capture of the current kernel
-    source was committed (profiles/step_kernel_traffic.json), else None."""
-    import hashlib
-    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2607_08098_b300", "csrc", "evis_step.cuh")
-    try:
-        rec = json.load(open(p))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("kernel_sha256") == h:
-            return rec
-    except (OSError, ValueError):
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
         pass
     return None
 
 
-def evis_arm(args, world, rank, local):
+def e2e_leg(ev, w, dev, n_steps, capacity, flags_host):
+    """Host buffers in, events out, through the public API: pinned host keyframes copied by
+    evis_step_host, every gap's events copied to pinned host memory by
+    evis_read_events_async (while the next gap runs), all inside the timed region.  The
+    copy of a gap completes before the next one starts, so one destination buffer serves."""
+    import torch
+    n = n_steps
+    need = sum(t.numel() * 4 for t in dev[0]) * (n + 1) + capacity * 16
+    avail = host_mem_available()
+    if avail is not None and need > 0.6 * avail:
+        return {"skipped": f"needs {need / 2**30:.0f} GiB of pinned host memory, "
+                           f"{avail / 2**30:.0f} GiB available"}
+    host = [tuple(t.cpu().pin_memory() for t in dev[k]) for k in range(n + 1)]
+    out = torch.empty(capacity * 16, dtype=torch.uint8).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host[0])
+    cnt = ctypes.c_int64()
+    L = ev.lib()
+    ctx = ev.Context(w.envs, eps=1e-4, flags=flags_host, capacity=capacity)
+    ctx.step_host(*host[0], w.dt_ns)
+    torch.cuda.synchronize()
+    d2h = 0
+    t0 = time.perf_counter()
+    for k in range(1, n + 1):
+        ctx.step_host(*host[k], w.dt_ns)
+        st = L.evis_read_events_async(ctx.handle, out.data_ptr(), capacity, ctypes.byref(cnt))
+        if st != ev.OK:
+            raise RuntimeError(f"event read-back: {ev.status_string(st)}")
+        d2h += cnt.value * 16 + 16
+    ctx.read_wait()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ctx.close()
+    del host, out
+    return {"value": w.pixel_substeps * n / sec / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h // n, "steps": n,
+            "path": "evis_step_host (pinned host keyframe -> device) + evis_read_events_async "
+                    "(every event -> pinned host, copied while the next gap runs), host wall "
+                    "clock over the steps"}
+
+
+# ------------------------------------------------------------------------------------------
+# the oracle: CPU baseline, reference arm, and the parity sample of the benchmarked launch
+# ------------------------------------------------------------------------------------------
+
+def _events_of_envs_on_device(ev, ctx, env_ids):
+    """Drains the context's events into device memory and returns, on the host, those of
+    the given environments (the filter runs on the device)."""
+    import torch
+    n = ctx.event_count()
+    buf = torch.empty((max(n, 1), 2), dtype=torch.int64, device="cuda")
+    cnt = ctypes.c_int64()
+    st = ev.lib().evis_read_events(ctx.handle, buf.data_ptr(), n, ctypes.byref(cnt))
+    if st != ev.OK:
+        raise RuntimeError(f"read: {ev.status_string(st)}")
+    words = buf[:cnt.value]
+    env = (words[:, 1] >> 32) & 0xFFFF
+    keep = torch.isin(env, torch.tensor(env_ids, device="cuda"))
+    sel = words[keep].cpu().numpy()
+    del buf
+    return sel.view(ev.EVENT_DTYPE).reshape(-1), cnt.value
+
+
+def parity_and_cpu_baseline(ev, w, dev, shapes, sample_ids, gaps):
+    """The oracle (single thread) on a bounded sample of the benchmarked workload: the
+    environments sample_ids for `gaps` keyframe gaps.  Its time is the CPU baseline; its
+    events and reference levels are compared bit for bit with those environments' share of
+    a full launch of the library over every environment (the autotuned tile shapes)."""
+    import oracle
+    import scenes
+    import torch
+    sub = [w.envs[i] for i in sample_ids]
+    o = oracle.Oracle(sub, eps=1e-4, flags=oracle.IN_LOG)
+    kfs = [scenes.render(sub, k, want=("L", "mv", "Z")) for k in range(gaps + 1)]
+    o.step(kfs[0].L, kfs[0].mv, kfs[0].Z, w.dt_ns)
+    t0 = time.perf_counter()
+    for kf in kfs[1:]:
+        o.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+    sec = time.perf_counter() - t0
+    want = oracle.sort_events(o.events())
+    Lref_o = o.state()[0]
+
+    cap = int(w.pixel_substeps * 0.15) + (1 << 20)
+    ctx = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LOG | ev.KEEP_INPUTS, capacity=cap)
+    tw = [int(shapes[f"{e.W}x{e.H}"].split("x")[0]) for e in w.envs]
+    th = [int(shapes[f"{e.W}x{e.H}"].split("x")[1]) for e in w.envs]
+    ctx.set_env_tile_shapes(list(zip(tw, th)))
+    ctx.step(*dev[0], w.dt_ns)
+    got, total = [], 0
+    for k in range(1, gaps + 1):
+        ctx.step(*dev[k], w.dt_ns)
+        sel, n = _events_of_envs_on_device(ev, ctx, sample_ids)
+        got.append(sel)
+        total += n
+    Lref_g = ctx.state()[0]
+    ctx.close()
+    torch.cuda.synchronize()
+    got = np.concatenate(got)
+    remap = np.zeros(max(sample_ids) + 1, dtype=np.uint16)
+    remap[sample_ids] = np.arange(len(sample_ids), dtype=np.uint16)
+    got["env"] = remap[got["env"]]
+    got = oracle.sort_events(got)
+    same_events = len(got) == len(want) and np.array_equal(got.view(np.uint8), want.view(np.uint8))
+    off_g = np.concatenate([[0], np.cumsum([(e.W * e.H + 3) // 4 * 4 for e in w.envs])])
+    same_lref = True
+    oo = 0
+    for i, e in zip(sample_ids, sub):
+        n = e.W * e.H
+        same_lref &= np.array_equal(Lref_g[off_g[i]:off_g[i] + n], Lref_o[oo:oo + n])
+        oo += (n + 3) // 4 * 4
+    units = sum(e.W * e.H * e.K for e in sub) * gaps
+    cpu = {"value": units / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"environments {sample_ids} of the {len(w.envs)} (their own scenes, "
+                     f"{sub[0].W}x{sub[0].H}, K={sub[0].K}) for {gaps} keyframe gaps, "
+                     "single-threaded C++ oracle", "seconds": sec,
+           "events_per_s": len(want) / sec}
+    parity = {"envs": list(sample_ids), "gaps": gaps, "launch": f"all {len(w.envs)} environments",
+              "events_compared": int(len(want)), "events_in_launch": int(total),
+              "events_bit_exact": bool(same_events), "lref_bit_exact": bool(same_lref)}
+    return cpu, parity
+
+
+def oracle_parallel_rate(w, threads):
+    """Env-parallel CPU baseline: one single-threaded oracle per host thread, each on its own
+    environment of w for one keyframe gap, all at the same time (the oracle's C calls release
+    the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+    import scenes
+    work = []
+    for t in range(threads):
+        e = w.envs[t % len(w.envs)]
+        kfs = [scenes.render([e], k, want=("L", "mv", "Z")) for k in range(2)]
+        o = oracle.Oracle([e], eps=1e-4, flags=oracle.IN_LOG)
+        o.step(kfs[0].L, kfs[0].mv, kfs[0].Z, w.dt_ns)
+        work.append((o, kfs[1], e))
+
+    def run(item):
+        o, kf, _ = item
+        o.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+
+    with ThreadPoolExecutor(max_workers=threads) as pool:
+        t0 = time.perf_counter()
+        list(pool.map(run, work))
+        sec = time.perf_counter() - t0
+    units = sum(e.W * e.H * e.K for _, _, e in work)
+    return {"value": units / sec / 1e6, "unit": UNIT, "cores": threads,
+            "kind": "oracle, env-parallel", "seconds": sec,
+            "sample": f"{threads} threads, each the single-threaded C++ oracle on one "
+                      "environment for one keyframe gap"}
+
+
+def reference_arm(args, world, rank):
+    """The oracle as it stands, on the host cores, for the headline workload: each step is
+    one keyframe gap of one environment (a bounded sample: environment 0, gap after gap)."""
+    if rank != 0:
+        return
+    import oracle
+    import scenes
+    w = highspeed_workload(args.hs_envs)
+    n_kf = args.warmup + args.steps + 1
+    e = w.envs[0]
+    kfs = [scenes.render([e], k, want=("L", "mv", "Z")) for k in range(n_kf)]
+    o = oracle.Oracle([e], eps=1e-4, flags=oracle.IN_LOG)
+    o.step(kfs[0].L, kfs[0].mv, kfs[0].Z, w.dt_ns)
+    for kf in kfs[1:1 + args.warmup]:
+        o.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+    o.events()
+    t0 = time.perf_counter()
+    for kf in kfs[1 + args.warmup:]:
+        o.step(kf.L, kf.mv, kf.Z, w.dt_ns)
+    sec = time.perf_counter() - t0
+    nev = len(o.events())
+    units = e.W * e.H * e.K * args.steps
+    value = units / sec / 1e6
+    sample = (f"each step: environment 0 of the {args.hs_envs} ({e.W}x{e.H}, K={e.K}) for its next "
+              "keyframe gap, single-threaded C++ oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": highspeed_config(w, args.hs_envs),
+            "events_per_s": nev / sec,
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# the CUDA path
+# ------------------------------------------------------------------------------------------
+
+def headline_arm(args, world, rank, local):
     import torch
     import paper_2607_08098_b300 as ev
 
@@ -282,135 +538,214 @@ def evis_arm(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = workload(args.envs, rank)
-    n_kf = args.warmup + args.steps + 1
-    kfs = [None] * n_kf
-
-    import scenes
-    dev = []
-    for k in range(n_kf):
-        kf = scenes.render(w.envs, k, want=("I", "mv", "Z"))
-        dev.append(tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)))
-        kfs[k] = kf if k < 2 else None
-    flags = ev.IN_LUM | ev.KEEP_INPUTS
-    # size the event buffer from one keyframe gap
-    probe = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=1 << 27)
-    probe.step(*dev[0], w.dt_ns)
-    probe.step(*dev[1], w.dt_ns)
-    per_step = probe.event_count()
-    probe.close()
-    capacity = int(per_step * 1.5 * (args.steps + 1)) + (1 << 20)
-    ctx = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=capacity)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    clocks = ClockSampler(local)                    # sampled from the warm-up on (under load)
-    ctx.step(*dev[0], w.dt_ns)                      # first keyframe: reference levels only
-    tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=2)  # tile shape per resolution class
-    shapes = ctx.tile_shapes()
-    for k in range(1, 1 + args.warmup):
-        flush.zero_()
-        ctx.step(*dev[k], w.dt_ns)
-    ctx.clear_events()
-    ctx.profile(args.steps)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for s in range(args.steps):
-        flush.zero_()                               # L2 flush between timed steps
-        starts[s].record(stream)
-        ctx.step(*dev[1 + args.warmup + s], w.dt_ns)
-        ends[s].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    wall = time.perf_counter() - wall0
+    w = highspeed_workload(args.hs_envs, rank)
+    n_kf = max(args.warmup + args.steps + 1, 4)
+    dev = upload_keyframes(w, n_kf, "L")
+    flags = ev.IN_LOG | ev.KEEP_INPUTS
+    clocks = ClockSampler(local)            # sampled from the autotuner and warm-up on
+    r = timed_gaps(ev, w, dev, flags, args.steps, args.warmup, dist=dist)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    n_events = ctx.event_count()
-    if n_events > capacity:
-        raise RuntimeError("event buffer overflow in the timed region")
-    prof = ctx.profile_read()
-    syn_ms = float(prof[:, 1].mean())
-    prep_ms = float(prof[:, 0].mean())
-    ctx.close()
-
-    total_units = w.pixel_substeps * args.steps
+    total_ms = float(sum(r["step_ms"]))
+    n_events = int(sum(r["events"]))
+    units = w.pixel_substeps * args.steps
     if dist:
-        total_ms, total_units, n_events = reduce_over_ranks(total_ms, total_units, n_events,
-                                                            "cuda")
-    value = total_units / (total_ms / 1e3) / 1e6
-    events_per_s = n_events / (total_ms / 1e3)
-
-    # roofline of the synthesis kernel: algorithmic bytes per launch / its mean duration
-    px = w.pixels
-    ev_per_step = n_events / args.steps / max(world, 1)
-    alg_bytes = px * (32 + 8 + 16) + ev_per_step * 16
-    peak, peak_kind = measured_peak()
-    achieved = alg_bytes / (syn_ms / 1e3) / 1e9
-    tr = traffic_record()
-    roofline = {"kernel": "step_kernel (splat + z-buffer + blend + crossings + compaction)",
-                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "traffic": None if tr is None else tr["dram_bytes_per_launch_scaled"],
-                "kernel_ms": syn_ms, "prep_ms": prep_ms,
-                "tile_shape": f"{shapes[0][0]}x{shapes[0][1]} (autotuned, {tuned_ms:.2f} ms in the trial)"}
-    roofline["nominal_peak"] = 7700.0          # HBM3e, for context (the fraction uses the measured)
-    roofline["frac_of_nominal"] = achieved / 7700.0
-    if tr is not None:
-        dram = tr["dram_bytes_per_launch_scaled"] / (syn_ms / 1e3) / 1e9
-        roofline["dram"] = {"achieved": dram, "frac": dram / peak, "unit": "GB/s",
-                            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
-                                      "committed capture over this run's kernel time"}
-    if tr is not None and "warp_instructions_per_launch_scaled" in tr and world == 1:
-        # the kernel's real ceiling: instruction issue (4 schedulers per SM, one warp
-        # instruction per clock each, at the maximum SM clock)
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        peak_issue = sms * 4 * 2.032e9
-        ach = tr["warp_instructions_per_launch_scaled"] / (syn_ms / 1e3)
-        roofline["issue"] = {"bound": "instruction issue", "achieved_warp_inst_per_s": ach,
-                             "peak_warp_inst_per_s": peak_issue, "frac": ach / peak_issue,
-                             "source": "ncu smsp__inst_executed.sum of the committed capture"}
-
+        total_ms, units, n_events = reduce_over_ranks(total_ms, units, n_events, "cuda")
+    value = units / (total_ms / 1e3) / 1e6
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = roofline_block(w.envs, sum(r["events"]) / args.steps, r["syn_ms"], r["prep_ms"],
+                          r["shapes"], r["tuned_ms"], "highspeed_1024x640x480_K32"
+                          if args.hs_envs == 1024 else f"highspeed_{args.hs_envs}x640x480_K32",
+                          clk, sms)
+    keep = max(4, args.e2e_steps + 1)
+    del dev[keep:]                          # the legs below need the first keyframes only
+    torch.cuda.empty_cache()
     e2e = None
     if args.e2e_steps > 0:
-        e2e = e2e_leg(ev, w, dev, args, capacity=int(per_step * 1.5) + (1 << 20))
+        e2e = e2e_leg(ev, w, dev, args.e2e_steps, r["capacity"], ev.IN_LOG)
+    cpu = cpu_par = parity = None
+    if world == 1 and not args.no_cpu_baseline:
+        n = len(w.envs)
+        ids = sorted({0, max(0, n // 2 - 1), n - 1})
+        cpu, parity = parity_and_cpu_baseline(ev, w, dev, r["shapes"], ids, gaps=3)
+        cpu_par = oracle_parallel_rate(w, os.cpu_count() or 1)
+    del dev
+    torch.cuda.empty_cache()
     if dist:
         dist.destroy_process_group()
     if rank != 0:
         return
-    soft = soft_leg() if rank == 0 else None
-    cpu = cpu_par = None
-    if world == 1 and not args.no_cpu_baseline:
-        r, evs, sec, desc = oracle_sample_rate(args.cpu_envs, 2)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": sec, "events_per_s": evs}
-        nthreads = os.cpu_count() or 1
-        rp, evp, secp, descp = oracle_parallel_rate(2, 2, nthreads)
-        cpu_par = {"value": rp, "unit": UNIT, "cores": nthreads, "kind": "oracle, env-parallel",
-                   "sample": descp, "seconds": secp, "events_per_s": evp}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded layered scenes; the paper's scenes are not available)",
-            "config": config_block(w, args.envs), "events_per_s": events_per_s,
-            "events_per_step": n_events / args.steps, "step_ms": step_ms,
-            "wall_s": wall, "roofline": roofline, "cpu_baseline": cpu,
-            "cpu_baseline_parallel": cpu_par, "e2e": e2e,
-            "gpu_launches": 2 * args.steps, "clocks": clk, "soft_surrogate": soft,
+            "config": highspeed_config(w, args.hs_envs), "events_per_s": n_events / (total_ms / 1e3),
+            "events_per_step": n_events / args.steps / max(world, 1), "step_ms": r["step_ms"],
+            "wall_s": r["wall_s"], "roofline": roof, "cpu_baseline": cpu,
+            "cpu_baseline_parallel": cpu_par, "parity": parity, "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "clocks": clk,
             "parallelism": f"env shards x{world}, no collective on the data path"}
+    if world == 1 and not args.no_extras:
+        line["config2"] = config2_leg(ev, args)
+        line["config3"] = config3_leg(ev, args)
+        line["soft_surrogate"] = soft_leg()
     print(json.dumps(line), flush=True)
+
+
+def config2_leg(ev, args, world=1, rank=0, dist=None):
+    """The 64-environment 346x260 workload (K=16, refractory 100 us, linear luminance with
+    the log on the path): device-timed gaps and the roofline of its synthesis kernel."""
+    import torch
+    w = config2_workload(args.envs, rank)
+    steps = args.steps
+    dev = upload_keyframes(w, args.warmup + steps + 1, "I")
+    clocks = ClockSampler(torch.cuda.current_device())
+    r = timed_gaps(ev, w, dev, ev.IN_LUM | ev.KEEP_INPUTS, steps, args.warmup, dist=dist,
+                   reps_autotune=2)
+    clk = clocks.stop()
+    del dev
+    torch.cuda.empty_cache()
+    total_ms = float(sum(r["step_ms"]))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {"config": config2_config(w, args.envs), "metric": METRIC, "unit": UNIT,
+           "value": w.pixel_substeps * steps / (total_ms / 1e3) / 1e6,
+           "ms_per_step": total_ms / steps, "events_per_step": sum(r["events"]) / steps,
+           "events_per_s": sum(r["events"]) / (total_ms / 1e3), "steps": steps,
+           "roofline": roofline_block(w.envs, sum(r["events"]) / steps, r["syn_ms"], r["prep_ms"],
+                                      r["shapes"], r["tuned_ms"], f"config2_{args.envs}x346x260_K16",
+                                      clk, sms),
+           "clocks": clk}
+    return out
+
+
+def config3_leg(ev, args):
+    """The uneven 256-environment batch (128x128, 346x260, 640x480, 1280x720 in 4:2:1:1, K ~
+    U{4..32}, per-pixel thresholds, linear inputs): the same keyframe gaps run (a) as one
+    context per environment, (b) as one batched context with evis_step, (c) autotuned and
+    replayed from a captured CUDA graph.  Device time of the timed steps."""
+    import torch
+    import scenes
+    w = scenes.config3()
+    steps = min(args.steps, 5)
+    warmup = args.warmup
+    n_kf = warmup + steps + 1
+    off, total = scenes.pixel_offsets(w.envs)
+    dev = upload_keyframes(w, n_kf, "I")
+    units = w.pixel_substeps
+    cap_env = [int(e.H * e.W * e.K * 1.7) + 4096 for e in w.envs]  # ~1.4 events per px-substep
+    stream = torch.cuda.Stream()
+    res = {}
+    with torch.cuda.stream(stream):
+        ctxs = [ev.Context([e], eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS, capacity=c,
+                           stream=stream) for e, c in zip(w.envs, cap_env)]
+
+        def views(k, i):
+            e, o = w.envs[i], int(off[i])
+            n = e.H * e.W
+            I, mv, Z = dev[k]
+            return I[o:o + n], mv[2 * o:2 * (o + n)], Z[o:o + n]
+
+        def run_per_env(k):
+            for i, c in enumerate(ctxs):
+                c.clear_events()
+                c.step(*views(k, i), w.dt_ns)
+
+        def timed(fn, first):
+            t = 0.0
+            for k in range(first, first + steps):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                fn(k, prepare=True)
+                a_.record(stream)
+                fn(k, prepare=False)
+                b_.record(stream)
+                b_.synchronize()
+                t += a_.elapsed_time(b_)
+            return t
+
+        run_per_env(0)
+        for k in range(1, 1 + warmup):
+            run_per_env(k)
+        res["per_env_contexts"] = timed(lambda k, prepare: None if prepare else run_per_env(k),
+                                        1 + warmup)
+        for c in ctxs:
+            c.close()
+        big = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS,
+                         capacity=sum(cap_env), stream=stream)
+
+        def run_big(k, prepare):
+            if prepare:
+                big.clear_events()
+            else:
+                big.step(*dev[k], w.dt_ns)
+
+        big.step(*dev[0], w.dt_ns)
+        for k in range(1, 1 + warmup):
+            run_big(k, True)
+            run_big(k, False)
+        res["batched_step"] = timed(run_big, 1 + warmup)
+        big.close()
+        graph = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM, capacity=sum(cap_env), stream=stream)
+        graph.step(*dev[0], w.dt_ns)
+        best = graph.autotune(*dev[1], w.dt_ns, reps=2)
+        shapes = graph.tile_shapes()
+        for k in range(1, 1 + warmup):
+            graph.step(*dev[k], w.dt_ns)
+        graph.capture(w.dt_ns)
+
+        def run_graph(k, prepare):
+            if prepare:
+                graph.clear_events()
+                graph.write_inputs(*dev[k])
+            else:
+                graph.replay()
+
+        res["batched_graph_autotuned"] = timed(run_graph, 1 + warmup)
+        n_events = graph.event_count()
+        graph.close()
+    del dev
+    torch.cuda.empty_cache()
+    classes = {}
+    for e, sh in zip(w.envs, shapes):
+        classes[f"{e.W}x{e.H}"] = f"{sh[0]}x{sh[1]}"
+    vals = {k: units * steps / (v / 1e3) / 1e6 for k, v in res.items()}
+    return {"workload": "batched uneven: 256 envs (128x128, 346x260, 640x480, 1280x720 in "
+                        "4:2:1:1), K~U{4..32}, per-pixel C, linear inputs",
+            "metric": METRIC, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "pixel_substeps_per_step": units, "value": vals,
+            "ms_per_step": {k: v / steps for k, v in res.items()},
+            "batched_over_per_env": vals["batched_step"] / vals["per_env_contexts"],
+            "graph_over_per_env": vals["batched_graph_autotuned"] / vals["per_env_contexts"],
+            "events_last_step": n_events, "event_buffer_overflow": n_events > sum(cap_env),
+            "autotuned_tile_shapes": classes, "autotune_best_ms": best}
+
+
+def envs64_arm(args, world, rank, local):
+    """The 346x260 workload as a line of its own (N ranks: disjoint environments)."""
+    import torch
+    import paper_2607_08098_b300 as ev
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = config2_leg(ev, args, world, rank, dist)
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def batched_arm(args):
+    import torch
+    import paper_2607_08098_b300 as ev
+    torch.cuda.set_device(0)
+    print(json.dumps(config3_leg(ev, args)), flush=True)
 
 
 def soft_leg(reps=10):
     """Differentiable workload (16 envs at 346x260, K=8, tau=0.02): device time of the soft
-    forward and of the backward under a random cotangent, and their ratio."""
-    import numpy as np
+    forward and of the backward under a random cotangent, their ratio, and the forward's
+    HBM roofline (per pixel: L_A, L_B, both motion fields, both depths and the start
+    reference level read, 36 B; the ON / OFF counts written, 8 B)."""
     import torch
     import paper_2607_08098_b300 as ev
     import scenes
@@ -434,177 +769,18 @@ def soft_leg(reps=10):
         e2.synchronize()
         tf += e0.elapsed_time(e1)
         tb += e1.elapsed_time(e2)
+    fwd_ms, bwd_ms = tf / reps, tb / reps
+    peak, peak_kind = measured_peak()
+    alg = w.pixels * (36 + 8)
+    ach = alg / (fwd_ms / 1e3) / 1e9
     return {"workload": "16 envs at 346x260, K=8, tau=0.02, delta=1e-3, random cotangent",
-            "fwd_ms": tf / reps, "bwd_ms": tb / reps, "bwd_fwd_ratio": tb / tf,
-            "pixel_substeps": w.pixel_substeps}
-
-
-def e2e_leg(ev, w, dev, args, capacity):
-    """Host buffers in, events out: pinned host keyframes copied by evis_step_host, each
-    gap's events read back to pinned host memory, all inside the timed region.  The value
-    is the pipelined read-back (evis_read_events_async: a gap's events copy out while the
-    next gap runs); the synchronous read after every gap (evis_read_events) is reported
-    beside it."""
-    import ctypes
-    import torch
-    n = args.e2e_steps
-    host = []
-    for k in range(n + 1):
-        host.append(tuple(t.cpu().pin_memory() for t in dev[k]))
-    outs = [torch.empty(capacity * 16, dtype=torch.uint8).pin_memory() for _ in range(2)]
-    h2d = sum(t.numel() * 4 for t in host[0])
-    cnt = ctypes.c_int64()
-    L = ev.lib()
-
-    def run(pipelined):
-        ctx = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM, capacity=capacity)
-        ctx.step_host(*host[0], w.dt_ns)
-        d2h = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(1, n + 1):
-            ctx.step_host(*host[k], w.dt_ns)
-            if pipelined:
-                st = L.evis_read_events_async(ctx.handle, outs[k % 2].data_ptr(), capacity,
-                                              ctypes.byref(cnt))
-            else:
-                st = L.evis_read_events(ctx.handle, outs[0].data_ptr(), capacity, ctypes.byref(cnt))
-            if st != ev.OK:
-                raise RuntimeError(f"event read-back: {ev.status_string(st)}")
-            d2h += cnt.value * 16 + 8
-        if pipelined:
-            ctx.read_wait()
-        torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        ctx.close()
-        return w.pixel_substeps * n / sec / 1e6, d2h // n
-
-    sync_value, _ = run(False)
-    value, d2h = run(True)
-    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "steps": n, "sync_readback_value": sync_value,
-            "path": "evis_step_host (pinned host keyframe -> device) + evis_read_events_async "
-                    "(all events -> pinned host, copied while the next gap runs); "
-                    "sync_readback_value: evis_read_events after every gap"}
-
-
-def batched_arm(args):
-    """Uneven batch (256 envs: 128x128, 346x260, 640x480, 1280x720 in a 4:2:1:1 mix, K ~ U{4..32},
-    per-pixel thresholds): the same keyframe gaps run (a) as one context per environment,
-    (b) as one batched context with evis_step, (c) autotuned and replayed from a CUDA graph.
-    Prints one JSON line with the three rates (device time of the timed steps)."""
-    import torch
-    import paper_2607_08098_b300 as ev
-    import scenes
-    torch.cuda.set_device(0)
-    w = scenes.config3()
-    n_kf = args.warmup + args.steps + 1
-    off, total = scenes.pixel_offsets(w.envs)
-    dev = []
-    for k in range(n_kf):
-        kf = scenes.render(w.envs, k, want=("I", "mv", "Z"))
-        dev.append(tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.I, kf.mv, kf.Z)))
-    units = w.pixel_substeps
-    cap_env = [int(e.H * e.W * e.K * 1.7) + 4096 for e in w.envs]  # ~1.4 events per px-substep
-    stream = torch.cuda.Stream()
-    res = {}
-    with torch.cuda.stream(stream):
-        # (a) one context per environment, stepped one after the other on one stream
-        ctxs = [ev.Context([e], eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS, capacity=c,
-                           stream=stream) for e, c in zip(w.envs, cap_env)]
-
-        def views(k, i):
-            e, o = w.envs[i], int(off[i])
-            n = e.H * e.W
-            I, mv, Z = dev[k]
-            return I[o:o + n], mv[2 * o:2 * (o + n)], Z[o:o + n]
-
-        def run_per_env(k):
-            for i, c in enumerate(ctxs):
-                c.clear_events()
-                c.step(*views(k, i), w.dt_ns)
-
-        # (b) one batched context, (c) the same autotuned and captured
-        big = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS,
-                         capacity=sum(cap_env), stream=stream)
-        graph = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM, capacity=sum(cap_env), stream=stream)
-
-        def timed(fn, first):
-            t = 0.0
-            for k in range(first, first + args.steps):
-                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                pre = fn(k, prepare=True)
-                a_.record(stream)
-                fn(k, prepare=False)
-                b_.record(stream)
-                b_.synchronize()
-                t += a_.elapsed_time(b_)
-                del pre
-            return t
-
-        run_per_env(0)
-        for k in range(1, 1 + args.warmup):
-            run_per_env(k)
-        res["per_env_contexts"] = timed(lambda k, prepare: None if prepare else run_per_env(k),
-                                        1 + args.warmup)
-
-        def run_big(k, prepare):
-            if prepare:
-                big.clear_events()
-            else:
-                big.step(*dev[k], w.dt_ns)
-
-        big.step(*dev[0], w.dt_ns)
-        for k in range(1, 1 + args.warmup):
-            run_big(k, True)
-            run_big(k, False)
-        res["batched_step"] = timed(run_big, 1 + args.warmup)
-
-        graph.step(*dev[0], w.dt_ns)
-        best = graph.autotune(*dev[1], w.dt_ns, reps=2)
-        shapes = graph.tile_shapes()
-        for k in range(1, 1 + args.warmup):
-            graph.step(*dev[k], w.dt_ns)
-        graph.capture(w.dt_ns)
-
-        def run_graph(k, prepare):
-            if prepare:
-                graph.clear_events()
-                graph.write_inputs(*dev[k])
-            else:
-                graph.replay()
-
-        res["batched_graph_autotuned"] = timed(run_graph, 1 + args.warmup)
-        n_events = graph.event_count()
-    classes = {}
-    for e, sh in zip(w.envs, shapes):
-        classes[f"{e.W}x{e.H}"] = f"{sh[0]}x{sh[1]}"
-    line = {"bench": "batched uneven: 256 envs (128x128, 346x260, 640x480, 1280x720 in 4:2:1:1), "
-                     "K~U{4..32}, per-pixel C, linear inputs",
-            "metric": METRIC, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
-            "pixel_substeps_per_step": units,
-            "value": {k: units * args.steps / (v / 1e3) / 1e6 for k, v in res.items()},
-            "ms_per_step": {k: v / args.steps for k, v in res.items()},
-            "events_last_step": n_events, "event_buffer_overflow": n_events > sum(cap_env),
-            "autotuned_tile_shapes": classes,
-            "autotune_best_ms": best}
-    if not args.no_cpu_baseline:
-        # one environment per resolution class, one gap each; the whole batch's CPU time is
-        # extrapolated from each class's seconds per pixel-substep
-        first = {}
-        for e in w.envs:
-            first.setdefault((e.W, e.H), e)
-        per_unit = {}
-        for key, e in first.items():
-            per_unit[key] = oracle_gap_seconds([e], w.dt_ns, "I", False) / (e.W * e.H * e.K)
-        sec = sum(e.W * e.H * e.K * per_unit[(e.W, e.H)] for e in w.envs)
-        line["cpu_baseline"] = {
-            "value": units / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "extrapolated: one environment of each resolution class (128x128, 346x260, "
-                      "640x480, 1280x720, their own K and threshold maps) for one keyframe gap, "
-                      "single-threaded C++ oracle, scaled by each class's pixel-substeps in the batch",
-            "seconds_sampled": sum(per_unit[(e.W, e.H)] * e.W * e.H * e.K for e in first.values())}
-    print(json.dumps(line), flush=True)
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "bwd_fwd_ratio": bwd_ms / fwd_ms,
+            "pixel_substeps": w.pixel_substeps,
+            "fwd_mpx_substeps_per_s": w.pixel_substeps / fwd_ms / 1e3,
+            "roofline": {"kernel": "soft forward (winners, surface sums, per-target counts)",
+                         "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak, "algorithmic_bytes_per_launch": alg,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}}
 
 
 def _timed_gaps(ev, envs, dev, dt, steps, warmup, flags, setup=None):
@@ -786,93 +962,19 @@ def _stage_voxel(ev, scenes, peak, peak_src, n_envs=8):
     return res
 
 
-def highspeed_arm(args):
-    """The high-speed batch at full size: 1024 environments at 640x480, K=32, C=0.15, five
-    layers with flows up to 40 px per frame (about 10 % holes).  Keyframes are rendered once
-    and resident on the device; the event buffer holds one gap and is cleared before each
-    timed gap; L2 is flushed between gaps."""
-    import numpy as np
-    import torch
-    import paper_2607_08098_b300 as ev
-    import scenes
-    w = scenes.config4(n_envs=args.hs_envs)
-    n_kf = args.warmup + args.steps + 1
-    dev = []
-    for k in range(n_kf):
-        kf = scenes.render(w.envs, k, want=("L", "mv", "Z"))
-        dev.append(tuple(torch.from_numpy(a.reshape(-1)).cuda() for a in (kf.L, kf.mv, kf.Z)))
-        del kf
-    flags = ev.IN_LOG | ev.KEEP_INPUTS
-    probe = ev.Context(w.envs, flags=flags, capacity=1 << 20)
-    probe.step(*dev[0], w.dt_ns)
-    probe.step(*dev[1], w.dt_ns)
-    per_gap = probe.event_count()   # counted even beyond the buffer
-    probe.close()
-    ctx = ev.Context(w.envs, flags=flags, capacity=int(per_gap * 1.3) + (1 << 20))
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    clocks = ClockSampler(0)
-    ctx.step(*dev[0], w.dt_ns)
-    tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=1)
-    shape = "x".join(str(v) for v in ctx.tile_shapes()[0])
-    for k in range(1, 1 + args.warmup):
-        ctx.clear_events()
-        ctx.step(*dev[k], w.dt_ns)
-    st = torch.cuda.current_stream()
-    ms, n_events = [], 0
-    for s_ in range(args.steps):
-        ctx.clear_events()
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        ctx.step(*dev[1 + args.warmup + s_], w.dt_ns)
-        b.record(st)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
-        n = ctx.event_count()
-        if n > int(per_gap * 1.3) + (1 << 20):
-            raise RuntimeError("event buffer overflow in the timed region")
-        n_events += n
-    clk = clocks.stop()
-    ctx.close()
-    total = float(sum(ms))
-    units = w.pixel_substeps * args.steps
-    line = {"bench": "highspeed", "metric": METRIC, "unit": UNIT,
-            "value": units / (total / 1e3) / 1e6, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total / args.steps, "step_ms": ms,
-            "pixel_substeps_per_step": w.pixel_substeps, "events_per_step": n_events / args.steps,
-            "events_per_s": n_events / (total / 1e3),
-            "config": {"workload": f"{args.hs_envs} envs at 640x480, K=32, C=0.15, 5 layers, "
-                                   "flows up to 40 px/frame (~10 % holes), log inputs",
-                       "autotune_best_ms": tuned_ms, "tile_shape": shape,
-                       "l2": "flushed between timed steps; inputs far larger than L2"},
-            "clocks": clk, "data": "synthetic"}
-    if not args.no_cpu_baseline:
-        e = w.envs[0]
-        sec = oracle_gap_seconds([e], w.dt_ns, "L", True)
-        line["cpu_baseline"] = {
-            "value": e.W * e.H * e.K / sec / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "extrapolated: the first environment (640x480, K=32, same scenes) for one "
-                      "keyframe gap, single-threaded C++ oracle; every environment of the batch "
-                      "has the same size and K", "seconds_sampled": sec}
-    print(json.dumps(line), flush=True)
-
-
 def main():
     args = parse()
     world, rank, local = dist_info()
-    if args.workload == "batched":
-        batched_arm(args)
-        return
-    if args.workload == "stages":
-        stages_arm(args)
-        return
-    if args.workload == "highspeed":
-        highspeed_arm(args)
-        return
     if args.impl == "reference":
         reference_arm(args, world, rank)
+    elif args.workload == "batched":
+        batched_arm(args)
+    elif args.workload == "stages":
+        stages_arm(args)
+    elif args.workload == "envs64":
+        envs64_arm(args, world, rank, local)
     else:
-        evis_arm(args, world, rank, local)
+        headline_arm(args, world, rank, local)
 
 
 if __name__ == "__main__":

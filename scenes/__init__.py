@@ -277,15 +277,16 @@ def config3(n_envs: int = 256, scale: float = 1.0) -> Workload:
                     16_666_667, 8)
 
 
-def config4(n_envs: int = 1024, W: int = 640, H: int = 480) -> Workload:
+def config4(n_envs: int = 1024, W: int = 640, H: int = 480, first_env: int = 0) -> Workload:
     """High-speed: 640x480, K=32, flows up to 40 px/frame, five depth layers, C=0.15.
 
     Disks of radius 0.2-0.4 x 480 moving up to 40 px/frame leave about 10 % of the
     pixel-substeps without a source in one warp direction (disocclusion holes); textures are
     smoother (64 px cells, sigma 0.3) so that the output stays event-dense but bounded
-    (about 0.11 events per pixel-substep)."""
+    (about 0.11 events per pixel-substep).  ``first_env`` shifts the seeds (environment e
+    uses seed index first_env + e)."""
     envs = []
-    for e in range(n_envs):
+    for e in range(first_env, first_env + n_envs):
         rng = _rng(4, e)
         lay = _random_layers(rng, W, H, 5, vmax=40.0, wmax=0.1, rmin=0.2, rmax=0.4)
         for layer in lay:
