@@ -21,8 +21,10 @@ def _rank(rank, world, port, q):
     import torch.distributed as dist
     import bench
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = bench.workload(4, rank)
-    seeds = [l.seed for e in w.envs for l in e.layers]
+    seeds = []
+    for make in (bench.highspeed_workload, bench.config2_workload):   # both sharded lines
+        w = make(4, rank)
+        seeds.append([l.seed for e in w.envs for l in e.layers])
     t, units, events = bench.reduce_over_ranks(10.0 + rank, 1000 * (rank + 1), 7, "cpu")
     q.put((rank, seeds, t, units, events))
     dist.destroy_process_group()
@@ -40,6 +42,7 @@ def test_two_rank_sharding_and_reduction():
         p.join(timeout=60)
         assert p.exitcode == 0
     (r0, s0, t0, u0, e0), (r1, s1, t1, u1, e1) = out
-    assert not set(s0) & set(s1)                # disjoint scenes per rank
+    for a, b in zip(s0, s1):
+        assert not set(a) & set(b)              # disjoint scenes per rank
     assert t0 == t1 == 11.0                     # slowest rank's time
     assert u0 == u1 == 3000 and e0 == e1 == 14  # work summed over ranks
