@@ -61,6 +61,8 @@ def parse():
                     help="environments of the high-speed workload (640x480, K=32)")
     ap.add_argument("--envs", type=int, default=64, help="environments of the 346x260 workload")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--tile", default=None,
+                    help="WxH: fixed tile shape instead of the autotuner's (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="headline line only (no config2 / config3 / soft_surrogate keys)")
@@ -257,7 +259,7 @@ def upload_keyframes(w, n_kf, frame_key):
     return dev
 
 
-def timed_gaps(ev, w, dev, flags, steps, warmup, dist=None, clocks=None, reps_autotune=1):
+def timed_gaps(ev, w, dev, flags, steps, warmup, dist=None, reps_autotune=1, tile=None):
     """Context over w.envs fed dev[0] (reference levels), autotuned on dev[1], warmed up on
     dev[1..warmup], then `steps` timed gaps dev[warmup+1..], each bracketed by CUDA events on
     the context's stream after an L2 flush and an event-buffer clear (the events of a gap
@@ -274,7 +276,11 @@ def timed_gaps(ev, w, dev, flags, steps, warmup, dist=None, clocks=None, reps_au
     ctx = ev.Context(w.envs, eps=1e-4, flags=flags, capacity=capacity)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ctx.step(*dev[0], w.dt_ns)
-    tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=reps_autotune)
+    if tile:
+        ctx.set_tile_shape(*(int(v) for v in tile.split("x")))
+        tuned_ms = None
+    else:
+        tuned_ms = ctx.autotune(*dev[1], w.dt_ns, reps=reps_autotune)
     shapes = ctx.tile_shapes()
     for k in range(1, 1 + warmup):
         ctx.clear_events()
@@ -543,7 +549,7 @@ def headline_arm(args, world, rank, local):
     dev = upload_keyframes(w, n_kf, "L")
     flags = ev.IN_LOG | ev.KEEP_INPUTS
     clocks = ClockSampler(local)            # sampled from the autotuner and warm-up on
-    r = timed_gaps(ev, w, dev, flags, args.steps, args.warmup, dist=dist)
+    r = timed_gaps(ev, w, dev, flags, args.steps, args.warmup, dist=dist, tile=args.tile)
     clk = clocks.stop()
     total_ms = float(sum(r["step_ms"]))
     n_events = int(sum(r["events"]))
@@ -600,7 +606,7 @@ def config2_leg(ev, args, world=1, rank=0, dist=None):
     dev = upload_keyframes(w, args.warmup + steps + 1, "I")
     clocks = ClockSampler(torch.cuda.current_device())
     r = timed_gaps(ev, w, dev, ev.IN_LUM | ev.KEEP_INPUTS, steps, args.warmup, dist=dist,
-                   reps_autotune=2)
+                   reps_autotune=2, tile=args.tile)
     clk = clocks.stop()
     del dev
     torch.cuda.empty_cache()
