@@ -50,33 +50,17 @@ struct TileBox {
   int x0, y0, nx, ny;
 };
 
-// Splat of one source into the tile's z-buffer (Sec. 3.3).  Direction 0 moves a source of A
-// forward to q = p - f m_A with depth (1-f) Z_A(p) + f Z_B(p - m_A); direction 1 moves a source
-// of B backward to q = p + (1-f) m_B with depth (1-f) Z_A(p + m_B) + f Z_B(p) (Eqs. 5, 7).
-// Every integer pixel of the bilinear footprint of q with weight > 0, inside the image and
-// inside the tile, keeps the minimum key [depth bits | quantised (1 - w) | source index]
-// (Eq. 6).  PACKED reads (mx, my, Z, Z at the other endpoint) prepared once per keyframe gap;
-// otherwise the motion and depth maps are read and the other endpoint's depth is gathered
-// for sources that reach the tile.
-template <int TX, int TY, bool PACKED>
-__device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, int sx, int sy,
-                                             float fx, float fy, int W, int H, TileBox bx,
-                                             float f, float g, const StepArgs &a, int64_t o) {
-  const int p = sy * W + sx;
-  float mx, my, zs, zo = 0.0f;
-  if (PACKED) {
-    const float4 v = __ldg((dir ? a.packB : a.packA) + o + p);
-    mx = v.x;
-    my = v.y;
-    zs = v.z;
-    zo = v.w;
-  } else {
-    zs = __ldg((dir ? a.ZB : a.ZA) + o + p);
-    if (!valid_depth(zs)) return;
-    const float2 m = __ldg(reinterpret_cast<const float2 *>(dir ? a.mvB : a.mvA) + o + p);
-    mx = m.x;
-    my = m.y;
-  }
+// Splat of one source at one sub-frame into the tile's z-buffer of that sub-frame
+// (Sec. 3.3).  Direction 0 moves a source of A forward to q = p - f m_A with depth
+// (1-f) Z_A(p) + f Z_B(p - m_A); direction 1 moves a source of B backward to
+// q = p + (1-f) m_B with depth (1-f) Z_A(p + m_B) + f Z_B(p) (Eqs. 5, 7): zs is the source's
+// own depth, zo the other keyframe's at the correspondence endpoint.  Every integer pixel of
+// the bilinear footprint of q with weight > 0, inside the image and inside the tile, keeps
+// the minimum key [depth bits | quantised (1 - w) | source index] (Eq. 6).
+template <int TX, int TY>
+__device__ __forceinline__ void splat_at(unsigned long long *zb, int dir, int p, float fx,
+                                         float fy, float mx, float my, float zs, float zo,
+                                         float f, float g, TileBox bx, bool tie_index) {
   float qx, qy;
   if (dir == 0) {
     qx = __fsub_rn(fx, __fmul_rn(f, mx));
@@ -87,17 +71,12 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
   }
   // A footprint pixel lies in the box only if x0 - 1 < q_x < x0 + nx (floor(q_x) + 1 needs
   // a positive weight) and likewise in y.  The box lies inside the image, so this also
-  // rejects targets that leave it, and NaN.  (Packed sources check their depth here too.)
-  if (!((!PACKED || valid_depth(zs)) && qx > static_cast<float>(bx.x0 - 1) &&
-        qx < static_cast<float>(bx.x0 + bx.nx) && qy > static_cast<float>(bx.y0 - 1) &&
-        qy < static_cast<float>(bx.y0 + bx.ny)))
+  // rejects targets that leave it, and NaN.
+  if (!(qx > static_cast<float>(bx.x0 - 1) && qx < static_cast<float>(bx.x0 + bx.nx) &&
+        qy > static_cast<float>(bx.y0 - 1) && qy < static_cast<float>(bx.y0 + bx.ny)))
     return;
   float fx0, fy0;
   const int lx0 = floor_small(qx, &fx0) - bx.x0, ly0 = floor_small(qy, &fy0) - bx.y0;  // >= -1
-  if (!PACKED) {
-    zo = dir == 0 ? other_depth(a.ZB + o, W, H, __fsub_rn(fx, mx), __fsub_rn(fy, my), zs)
-                  : other_depth(a.ZA + o, W, H, __fadd_rn(fx, mx), __fadd_rn(fy, my), zs);
-  }
   const float zt = dir == 0 ? __fadd_rn(__fmul_rn(g, zs), __fmul_rn(f, zo))
                             : __fadd_rn(__fmul_rn(g, zo), __fmul_rn(f, zs));
   const float ax = __fsub_rn(qx, fx0), ay = __fsub_rn(qy, fy0);
@@ -107,7 +86,6 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
   const bool in_y[2] = {ly0 >= 0, ly0 + 1 < bx.ny};
   const unsigned long long hi = static_cast<unsigned long long>(__float_as_uint(zt)) << 32;
   const int c00 = ly0 * TX + lx0;
-  const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
   // Straight-line code: every cell's key is formed, only the atomic is predicated.
 #pragma unroll
   for (int dy = 0; dy < 2; ++dy) {
@@ -126,6 +104,38 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb, int dir, in
       if (ok) atomicMin(&zb[c00 + dy * TX + dx], hi | low);
     }
   }
+}
+
+// One source of direction dir splat at the pass's sub-frames: f1 into zb1 and, when two is
+// set, f2 into zb2.  PACKED reads (mx, my, Z, Z at the other endpoint) prepared once per
+// keyframe gap; otherwise the motion and depth maps are read and the other endpoint's depth
+// is gathered.  Only sources with a valid depth splat.
+template <int TX, int TY, bool PACKED>
+__device__ __forceinline__ void splat_source(unsigned long long *zb1, unsigned long long *zb2,
+                                             int dir, int sx, int sy, float fx, float fy, int W,
+                                             int H, TileBox bx, float f1, float g1, float f2,
+                                             float g2, bool two, const StepArgs &a, int64_t o) {
+  const int p = sy * W + sx;
+  float mx, my, zs, zo;
+  if (PACKED) {
+    const float4 v = __ldg((dir ? a.packB : a.packA) + o + p);
+    mx = v.x;
+    my = v.y;
+    zs = v.z;
+    zo = v.w;
+    if (!valid_depth(zs)) return;
+  } else {
+    zs = __ldg((dir ? a.ZB : a.ZA) + o + p);
+    if (!valid_depth(zs)) return;
+    const float2 m = __ldg(reinterpret_cast<const float2 *>(dir ? a.mvB : a.mvA) + o + p);
+    mx = m.x;
+    my = m.y;
+    zo = dir == 0 ? other_depth(a.ZB + o, W, H, __fsub_rn(fx, mx), __fsub_rn(fy, my), zs)
+                  : other_depth(a.ZA + o, W, H, __fadd_rn(fx, mx), __fadd_rn(fy, my), zs);
+  }
+  const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
+  splat_at<TX, TY>(zb1, dir, p, fx, fy, mx, my, zs, zo, f1, g1, bx, tie_index);
+  if (two) splat_at<TX, TY>(zb2, dir, p, fx, fy, mx, my, zs, zo, f2, g2, bx, tie_index);
 }
 
 // True when no source of a row segment [xs, xs+31] x {ys}, displaced by an amount in
@@ -239,7 +249,7 @@ __host__ __device__ constexpr int step_stage() {
 // Dynamic shared memory of one step CTA.
 template <int TX, int TY>
 struct StepSmem {
-  unsigned long long zb[2][TX * TY];       // z-buffers, A forward and B backward
+  unsigned long long zb[2][2][TX * TY];    // z-buffers per sub-frame of a pass: A forward, B backward
   ulonglong2 stage[step_stage<TX, TY>()];  // events of this sub-frame before the flush
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
@@ -442,8 +452,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   // z-buffers start empty; afterwards each thread clears its own slots once it has read them
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
-    S.zb[0][tid + NTH * j] = kEmptyKey;
-    S.zb[1][tid + NTH * j] = kEmptyKey;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      S.zb[u][0][tid + NTH * j] = kEmptyKey;
+      S.zb[u][1][tid + NTH * j] = kEmptyKey;
+    }
   }
   __syncthreads();
 
@@ -510,25 +523,24 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     }
   }
 
-  for (int i = 1; i <= K; ++i) {
-    const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
-    const float g = __fsub_rn(1.0f, f);
-    const int64_t tim1 = T0 + tq;  // t_{i-1}
-    tq += dq;
-    trem += dr;
-    if (trem >= K) {
-      trem -= K;
-      ++tq;
-    }
-    const int64_t ti = T0 + tq;
+  // Sub-frames are processed in passes of two (i0 and i0 + 1; the last pass of an odd K has
+  // one): one source list serves both, each listed source is read once and splat at both
+  // f into the pass's two pairs of z-buffers, and the pass has two barriers.
+  for (int i0 = 1; i0 <= K; i0 += 2) {
+    const bool two = i0 < K;
+    const float f1 = __fdiv_rn(static_cast<float>(i0), static_cast<float>(K));
+    const float g1 = __fsub_rn(1.0f, f1);
+    const float f2 = two ? __fdiv_rn(static_cast<float>(i0 + 1), static_cast<float>(K)) : f1;
+    const float g2 = __fsub_rn(1.0f, f2);
 
-    // Two barriers per sub-frame.  Phase 1 (list reaching candidates) may overlap other
-    // warps' phase 3 of the previous sub-frame; the hit list is double-buffered by parity.
-    const int par = i & 1;
-    // ---- phase 1: list the sources that can reach the tile at this f: for each candidate
-    // segment whose motion bounds reach the tile, the interval of its lanes (sources) whose
-    // displaced position can put a footprint pixel into the tile; the sources go into one
-    // flat list so that every lane of phase 2 splats a source that may land ----
+    // Phase 1 (list reaching candidates) may overlap other warps' phase 3 of the previous
+    // pass; the hit list is double-buffered by parity.
+    const int par = (i0 >> 1) & 1;
+    // ---- phase 1: list the sources that can reach the tile at f1 or f2: for each
+    // candidate segment whose motion bounds reach the tile, the interval of its lanes
+    // (sources) whose displaced position can put a footprint pixel into the tile; the
+    // sources go into one flat list so that every lane of phase 2 splats a source that may
+    // land ----
     if (!over) {
       // warps take chunks of 32 candidates from a counter: those that finish the previous
       // sub-frame's emission first do more of this phase
@@ -547,11 +559,16 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           const float2 by = __half22float2(*reinterpret_cast<const __half2 *>(&hb.y));
           const float4 b = make_float4(bx.x, bx.y, by.x, by.y);
           const unsigned xy = S.cand_xy[dir][idx];
+          // displacement bounds at f1 and f2 (the products are monotone in f and in the
+          // motion, so the corners enclose every rounded displacement; an infinite bound
+          // times g = 0 is NaN and leaves the other corner, itself infinite)
           float dxl, dxh, dyl, dyh;
           if (dir == 0) {
-            dxl = -f * b.y; dxh = -f * b.x; dyl = -f * b.w; dyh = -f * b.z;
+            dxl = fminf(-f1 * b.y, -f2 * b.y); dxh = fmaxf(-f1 * b.x, -f2 * b.x);
+            dyl = fminf(-f1 * b.w, -f2 * b.w); dyh = fmaxf(-f1 * b.z, -f2 * b.z);
           } else {
-            dxl = g * b.x; dxh = g * b.y; dyl = g * b.z; dyh = g * b.w;
+            dxl = fminf(g1 * b.x, g2 * b.x); dxh = fmaxf(g1 * b.y, g2 * b.y);
+            dyl = fminf(g1 * b.z, g2 * b.z); dyh = fmaxf(g1 * b.w, g2 * b.w);
           }
           const int xs = static_cast<int>(xy & 0xFFFFu) * kSegW;
           const float xsf = small_int_to_float(xs);
@@ -628,8 +645,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     }
     __syncthreads();
 
-    // ---- phase 2: flush the previous sub-frame's staged events (reserved by the last warp
-    // to finish it), then splat both directions (Eq. 5 targets, Eq. 7 depth, Eq. 6 z-test) ----
+    // ---- phase 2: flush the previous pass's staged events (reserved by the last warp to
+    // finish it), then splat both directions at both sub-frames (Eq. 5 targets, Eq. 7 depth,
+    // Eq. 6 z-test) ----
     if (tid == 0) {
       s_nitems[par ^ 1] = 0;
       s_novf[par ^ 1] = 0;
@@ -656,8 +674,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const int dir = c >= nA ? 1 : 0;
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + l, sy = static_cast<int>(xy >> 16);
-        splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy, small_int_to_float(sx),
-                                     small_int_to_float(sy), W, H, box, f, g, a, o);
+        splat_source<TX, TY, PACKED>(S.zb[0][dir], S.zb[1][dir], dir, sx, sy,
+                                     small_int_to_float(sx), small_int_to_float(sy), W, H, box,
+                                     f1, g1, f2, g2, two, a, o);
       }
       const unsigned no = min(s_novf[par], static_cast<unsigned>(kSplatOverflow));
       for (unsigned e = warp; e < no; e += NW) {  // overflow: one warp per segment
@@ -668,23 +687,40 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + lane, sy = static_cast<int>(xy >> 16);
         if (lane >= lo && lane < hi)
-          splat_source<TX, TY, PACKED>(S.zb[dir], dir, sx, sy, small_int_to_float(sx),
-                                       small_int_to_float(sy), W, H, box, f, g, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[0][dir], S.zb[1][dir], dir, sx, sy,
+                                       small_int_to_float(sx), small_int_to_float(sy), W, H,
+                                       box, f1, g1, f2, g2, two, a, o);
       }
     } else {  // the candidate or overflow lists were full: every source of the region
       for (int sy = sy0 + warp; sy < sy1; sy += NW) {
         const float fy = small_int_to_float(sy);
         for (int sx = sx0 + lane; sx < sx1; sx += 32) {
           const float fx = small_int_to_float(sx);
-          splat_source<TX, TY, PACKED>(S.zb[0], 0, sx, sy, fx, fy, W, H, box, f, g, a, o);
-          splat_source<TX, TY, PACKED>(S.zb[1], 1, sx, sy, fx, fy, W, H, box, f, g, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[0][0], S.zb[1][0], 0, sx, sy, fx, fy, W, H, box,
+                                       f1, g1, f2, g2, two, a, o);
+          splat_source<TX, TY, PACKED>(S.zb[0][1], S.zb[1][1], 1, sx, sy, fx, fy, W, H, box,
+                                       f1, g1, f2, g2, two, a, o);
         }
       }
     }
     __syncthreads();
 
-    // ---- phase 3: resolve, blend, threshold crossings, emission (per channel: the winners
-    // depend on motion and depth only, so one resolve serves all NC channels) ----
+    // ---- phase 3, per sub-frame of the pass: resolve, blend, threshold crossings, emission
+    // (per channel: the winners depend on motion and depth only, so one resolve serves all
+    // NC channels) ----
+#pragma unroll 1
+    for (int u = 0; u < (two ? 2 : 1); ++u) {
+    const int i = i0 + u;
+    const float f = u ? f2 : f1;
+    const float g = u ? g2 : g1;
+    const int64_t tim1 = T0 + tq;  // t_{i-1}
+    tq += dq;
+    trem += dr;
+    if (trem >= K) {
+      trem -= K;
+      ++tq;
+    }
+    const int64_t ti = T0 + tq;
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
       const int ty = ty0 + ROWS * j;
@@ -700,10 +736,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         int n = 0, pol = 1;
         if (act[j]) {
           if (c == 0) {
-            kA = S.zb[0][tid + NTH * j];
-            kB = S.zb[1][tid + NTH * j];
-            S.zb[0][tid + NTH * j] = kEmptyKey;  // ready for the next sub-frame
-            S.zb[1][tid + NTH * j] = kEmptyKey;
+            kA = S.zb[u][0][tid + NTH * j];
+            kB = S.zb[u][1][tid + NTH * j];
+            S.zb[u][0][tid + NTH * j] = kEmptyKey;  // ready for the next pass
+            S.zb[u][1][tid + NTH * j] = kEmptyKey;
           }
           const bool hasA = kA != kEmptyKey, hasB = kB != kEmptyKey;
           const float la = hasA ? __ldg(LA + c * a.plane + (kA & 0xFFFFFFull)) : 0.0f;
@@ -891,9 +927,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         }
       }
     }
+    }  // sub-frames of the pass
     // ---- end of phase 3: the last warp to finish reserves the global range of this
-    // sub-frame's staged events (one atomic per CTA); they are copied out in phase 2 of the
-    // next sub-frame, or after the loop ----
+    // pass's staged events (one atomic per CTA); they are copied out in phase 2 of the next
+    // pass, or after the loop ----
     __syncwarp();
     if (lane == 0) {
       __threadfence_block();
