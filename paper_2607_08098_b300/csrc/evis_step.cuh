@@ -106,15 +106,16 @@ __device__ __forceinline__ void splat_at(unsigned long long *zb, int dir, int p,
   }
 }
 
-// One source of direction dir splat at the pass's sub-frames: f1 into zb1 and, when two is
-// set, f2 into zb2.  PACKED reads (mx, my, Z, Z at the other endpoint) prepared once per
-// keyframe gap; otherwise the motion and depth maps are read and the other endpoint's depth
-// is gathered.  Only sources with a valid depth splat.
-template <int TX, int TY, bool PACKED>
-__device__ __forceinline__ void splat_source(unsigned long long *zb1, unsigned long long *zb2,
-                                             int dir, int sx, int sy, float fx, float fy, int W,
-                                             int H, TileBox bx, float f1, float g1, float f2,
-                                             float g2, bool two, const StepArgs &a, int64_t o) {
+// One source of direction dir splat at the first ns sub-frames of a pass (fractions fs,
+// 1 - fs) into their z-buffers.  PACKED reads (mx, my, Z, Z at the other endpoint) prepared
+// once per keyframe gap; otherwise the motion and depth maps are read and the other
+// endpoint's depth is gathered.  Only sources with a valid depth splat.
+template <int TX, int TY, int NP, bool PACKED>
+__device__ __forceinline__ void splat_source(unsigned long long (&zb)[NP][2][TX * TY], int dir,
+                                             int sx, int sy, float fx, float fy, int W, int H,
+                                             TileBox bx, const float (&fs)[NP],
+                                             const float (&gs)[NP], int ns, const StepArgs &a,
+                                             int64_t o) {
   const int p = sy * W + sx;
   float mx, my, zs, zo;
   if (PACKED) {
@@ -134,8 +135,9 @@ __device__ __forceinline__ void splat_source(unsigned long long *zb1, unsigned l
                   : other_depth(a.ZA + o, W, H, __fadd_rn(fx, mx), __fadd_rn(fy, my), zs);
   }
   const bool tie_index = (a.flags & EVIS_TIE_INDEX) != 0;
-  splat_at<TX, TY>(zb1, dir, p, fx, fy, mx, my, zs, zo, f1, g1, bx, tie_index);
-  if (two) splat_at<TX, TY>(zb2, dir, p, fx, fy, mx, my, zs, zo, f2, g2, bx, tie_index);
+#pragma unroll
+  for (int u = 0; u < NP; ++u)
+    if (u < ns) splat_at<TX, TY>(zb[u][dir], dir, p, fx, fy, mx, my, zs, zo, fs[u], gs[u], bx, tie_index);
 }
 
 // True when no source of a row segment [xs, xs+31] x {ys}, displaced by an amount in
@@ -227,6 +229,16 @@ __device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d)
   return t0 + static_cast<int64_t>(static_cast<unsigned long long>(u) * (du >> 32) + lo);
 }
 
+// Sub-frames per pass of the step kernel for a tile shape: each pass lists the sources
+// once, reads each listed source once and has two barriers, and holds a pair of z-buffers
+// per sub-frame in shared memory.  Three where the third pair still leaves the shape's
+// resident CTAs their shared memory (96 environments of 640 x 480, K = 32, 64 x 16 tiles:
+// 28.99 ms per gap one sub-frame at a time, 23.87 ms in pairs, 22.12 ms in threes).
+template <int TX, int TY>
+__host__ __device__ constexpr int step_pass() {
+  return ((TX == 64 && TY == 16) || (TX == 32 && TY == 32)) ? 3 : 2;
+}
+
 // Threads of one step CTA for a tile shape: one target per thread for 32 x 16 and 64 x 16,
 // two for 32 x 32 (measured on 64 environments of 346 x 260: 3.59 ms per gap for 32 x 16 at
 // 512 threads and four CTAs per SM, against 3.75 ms at 256 threads and six), 256 threads
@@ -249,7 +261,7 @@ __host__ __device__ constexpr int step_stage() {
 // Dynamic shared memory of one step CTA.
 template <int TX, int TY>
 struct StepSmem {
-  unsigned long long zb[2][2][TX * TY];    // z-buffers per sub-frame of a pass: A forward, B backward
+  unsigned long long zb[step_pass<TX, TY>()][2][TX * TY];  // per sub-frame of a pass: A forward, B backward
   ulonglong2 stage[step_stage<TX, TY>()];  // events of this sub-frame before the flush
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
@@ -380,6 +392,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NW = NTH / 32;
   constexpr int ROWS = NTH / TX;           // tile rows covered by one pass of the block
   constexpr unsigned NSTAGE = step_stage<TX, TY>();
+  constexpr int NP = step_pass<TX, TY>();  // sub-frames per pass
   static_assert(TX % 32 == 0 && NTH % TX == 0 && NT * NTH == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
@@ -453,7 +466,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < NP; ++u) {
       S.zb[u][0][tid + NTH * j] = kEmptyKey;
       S.zb[u][1][tid + NTH * j] = kEmptyKey;
     }
@@ -523,21 +536,25 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     }
   }
 
-  // Sub-frames are processed in passes of two (i0 and i0 + 1; the last pass of an odd K has
-  // one): one source list serves both, each listed source is read once and splat at both
-  // f into the pass's two pairs of z-buffers, and the pass has two barriers.
-  for (int i0 = 1; i0 <= K; i0 += 2) {
-    const bool two = i0 < K;
-    const float f1 = __fdiv_rn(static_cast<float>(i0), static_cast<float>(K));
-    const float g1 = __fsub_rn(1.0f, f1);
-    const float f2 = two ? __fdiv_rn(static_cast<float>(i0 + 1), static_cast<float>(K)) : f1;
-    const float g2 = __fsub_rn(1.0f, f2);
+  // Sub-frames are processed in passes of NP (i0 .. i0 + ns - 1; the last pass may hold
+  // fewer): one source list serves them all, each listed source is read once and splat at
+  // every f of the pass into that sub-frame's pair of z-buffers, and the pass has two
+  // barriers.
+  for (int i0 = 1; i0 <= K; i0 += NP) {
+    const int ns = min(NP, K - i0 + 1);
+    float fs[NP], gs[NP];  // past ns: the last sub-frame's again (extends no bound)
+#pragma unroll
+    for (int u = 0; u < NP; ++u) {
+      fs[u] = __fdiv_rn(static_cast<float>(min(i0 + u, K)), static_cast<float>(K));
+      gs[u] = __fsub_rn(1.0f, fs[u]);
+    }
+    const float f1 = fs[0], g1 = gs[0], f2 = fs[NP - 1], g2 = gs[NP - 1];
 
     // Phase 1 (list reaching candidates) may overlap other warps' phase 3 of the previous
     // pass; the hit list is double-buffered by parity.
-    const int par = (i0 >> 1) & 1;
-    // ---- phase 1: list the sources that can reach the tile at f1 or f2: for each
-    // candidate segment whose motion bounds reach the tile, the interval of its lanes
+    const int par = ((i0 - 1) / NP) & 1;
+    // ---- phase 1: list the sources that can reach the tile at some f of the pass (f1 to f2):
+    // for each candidate segment whose motion bounds reach the tile, the interval of its lanes
     // (sources) whose displaced position can put a footprint pixel into the tile; the
     // sources go into one flat list so that every lane of phase 2 splats a source that may
     // land ----
@@ -559,9 +576,9 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           const float2 by = __half22float2(*reinterpret_cast<const __half2 *>(&hb.y));
           const float4 b = make_float4(bx.x, bx.y, by.x, by.y);
           const unsigned xy = S.cand_xy[dir][idx];
-          // displacement bounds at f1 and f2 (the products are monotone in f and in the
-          // motion, so the corners enclose every rounded displacement; an infinite bound
-          // times g = 0 is NaN and leaves the other corner, itself infinite)
+          // displacement bounds at the pass's first and last f (the products are monotone in
+          // f and in the motion, so the corners enclose every rounded displacement; an
+          // infinite bound times g = 0 is NaN and leaves the other corner, itself infinite)
           float dxl, dxh, dyl, dyh;
           if (dir == 0) {
             dxl = fminf(-f1 * b.y, -f2 * b.y); dxh = fmaxf(-f1 * b.x, -f2 * b.x);
@@ -646,8 +663,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     __syncthreads();
 
     // ---- phase 2: flush the previous pass's staged events (reserved by the last warp to
-    // finish it), then splat both directions at both sub-frames (Eq. 5 targets, Eq. 7 depth,
-    // Eq. 6 z-test) ----
+    // finish it), then splat both directions at every sub-frame of the pass (Eq. 5 targets,
+    // Eq. 7 depth, Eq. 6 z-test) ----
     if (tid == 0) {
       s_nitems[par ^ 1] = 0;
       s_novf[par ^ 1] = 0;
@@ -674,9 +691,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const int dir = c >= nA ? 1 : 0;
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + l, sy = static_cast<int>(xy >> 16);
-        splat_source<TX, TY, PACKED>(S.zb[0][dir], S.zb[1][dir], dir, sx, sy,
-                                     small_int_to_float(sx), small_int_to_float(sy), W, H, box,
-                                     f1, g1, f2, g2, two, a, o);
+        splat_source<TX, TY, NP, PACKED>(S.zb, dir, sx, sy, small_int_to_float(sx),
+                                         small_int_to_float(sy), W, H, box, fs, gs, ns, a, o);
       }
       const unsigned no = min(s_novf[par], static_cast<unsigned>(kSplatOverflow));
       for (unsigned e = warp; e < no; e += NW) {  // overflow: one warp per segment
@@ -687,19 +703,16 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
         const unsigned xy = S.cand_xy[dir][c - dir * nA];
         const int sx = static_cast<int>(xy & 0xFFFFu) * kSegW + lane, sy = static_cast<int>(xy >> 16);
         if (lane >= lo && lane < hi)
-          splat_source<TX, TY, PACKED>(S.zb[0][dir], S.zb[1][dir], dir, sx, sy,
-                                       small_int_to_float(sx), small_int_to_float(sy), W, H,
-                                       box, f1, g1, f2, g2, two, a, o);
+          splat_source<TX, TY, NP, PACKED>(S.zb, dir, sx, sy, small_int_to_float(sx),
+                                           small_int_to_float(sy), W, H, box, fs, gs, ns, a, o);
       }
     } else {  // the candidate or overflow lists were full: every source of the region
       for (int sy = sy0 + warp; sy < sy1; sy += NW) {
         const float fy = small_int_to_float(sy);
         for (int sx = sx0 + lane; sx < sx1; sx += 32) {
           const float fx = small_int_to_float(sx);
-          splat_source<TX, TY, PACKED>(S.zb[0][0], S.zb[1][0], 0, sx, sy, fx, fy, W, H, box,
-                                       f1, g1, f2, g2, two, a, o);
-          splat_source<TX, TY, PACKED>(S.zb[0][1], S.zb[1][1], 1, sx, sy, fx, fy, W, H, box,
-                                       f1, g1, f2, g2, two, a, o);
+          splat_source<TX, TY, NP, PACKED>(S.zb, 0, sx, sy, fx, fy, W, H, box, fs, gs, ns, a, o);
+          splat_source<TX, TY, NP, PACKED>(S.zb, 1, sx, sy, fx, fy, W, H, box, fs, gs, ns, a, o);
         }
       }
     }
@@ -709,10 +722,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     // (per channel: the winners depend on motion and depth only, so one resolve serves all
     // NC channels) ----
 #pragma unroll 1
-    for (int u = 0; u < (two ? 2 : 1); ++u) {
+    for (int u = 0; u < ns; ++u) {
     const int i = i0 + u;
-    const float f = u ? f2 : f1;
-    const float g = u ? g2 : g1;
+    const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
+    const float g = __fsub_rn(1.0f, f);
     const int64_t tim1 = T0 + tq;  // t_{i-1}
     tq += dq;
     trem += dr;
