@@ -48,6 +48,7 @@ __device__ __forceinline__ float small_int_to_float(int i) {
 // The target tile clipped to the image: pixels [x0, x0 + nx) x [y0, y0 + ny).
 struct TileBox {
   int x0, y0, nx, ny;
+  float qxl, qxh, qyl, qyh;  // x0 - 1, x0 + nx, y0 - 1, y0 + ny as floats
 };
 
 // Splat of one source at one sub-frame into the tile's z-buffer of that sub-frame
@@ -72,9 +73,7 @@ __device__ __forceinline__ void splat_at(unsigned long long *zb, int dir, int p,
   // A footprint pixel lies in the box only if x0 - 1 < q_x < x0 + nx (floor(q_x) + 1 needs
   // a positive weight) and likewise in y.  The box lies inside the image, so this also
   // rejects targets that leave it, and NaN.
-  if (!(qx > static_cast<float>(bx.x0 - 1) && qx < static_cast<float>(bx.x0 + bx.nx) &&
-        qy > static_cast<float>(bx.y0 - 1) && qy < static_cast<float>(bx.y0 + bx.ny)))
-    return;
+  if (!(qx > bx.qxl && qx < bx.qxh && qy > bx.qyl && qy < bx.qyh)) return;
   float fx0, fy0;
   const int lx0 = floor_small(qx, &fx0) - bx.x0, ly0 = floor_small(qy, &fy0) - bx.y0;  // >= -1
   const float zt = dir == 0 ? __fadd_rn(__fmul_rn(g, zs), __fmul_rn(f, zo))
@@ -171,9 +170,11 @@ __device__ __forceinline__ int64_t interp_time(float fr, int64_t tprev, int64_t 
     const unsigned long long P = static_cast<unsigned long long>(m) *
                                  static_cast<unsigned>(d);   // 24 x 29 bits: < 2^53
     if (sh >= 64) return tprev;                      // fr * d < 2^-11
-    unsigned long long q = P >> sh;
-    const unsigned long long r = P & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    if (r > half || (r == half && (q & 1ull))) ++q;
+    // round half to even: adding 2^(sh-1) - 1 and the parity of the truncated quotient
+    // carries into bit sh exactly when the discarded part exceeds the half, or equals it
+    // with an odd quotient (the sum stays below 2^63)
+    const unsigned long long q =
+        (P + ((1ull << (sh - 1)) - 1ull) + ((P >> sh) & 1ull)) >> sh;
     return tprev + static_cast<int64_t>(q);
   }
   return tprev + __double2ll_rn(__dmul_rn(static_cast<double>(fr), static_cast<double>(d)));
@@ -416,7 +417,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const int tx = tl.x0 + tid % TX;
   const int ty0 = tl.y0 + tid / TX;
   const int64_t HW = static_cast<int64_t>(W) * H;
-  const TileBox box = {tl.x0, tl.y0, min(TX, W - tl.x0), min(TY, H - tl.y0)};
+  TileBox box = {tl.x0, tl.y0, min(TX, W - tl.x0), min(TY, H - tl.y0), 0.0f, 0.0f, 0.0f, 0.0f};
+  box.qxl = static_cast<float>(box.x0 - 1);
+  box.qxh = static_cast<float>(box.x0 + box.nx);
+  box.qyl = static_cast<float>(box.y0 - 1);
+  box.qyh = static_cast<float>(box.y0 + box.ny);
 
   // per-pixel event state of this thread's targets (rows ty0 + ROWS j), in registers for
   // the whole keyframe gap
