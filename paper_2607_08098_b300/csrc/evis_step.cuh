@@ -234,10 +234,12 @@ __device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d)
 // once, reads each listed source once and has two barriers, and holds a pair of z-buffers
 // per sub-frame in shared memory.  Three where the third pair still leaves the shape's
 // resident CTAs their shared memory (96 environments of 640 x 480, K = 32, 64 x 16 tiles:
-// 28.99 ms per gap one sub-frame at a time, 23.87 ms in pairs, 22.12 ms in threes).
-template <int TX, int TY>
+// 28.99 ms per gap one sub-frame at a time, 23.87 ms in pairs, 22.12 ms in threes).  Colour
+// (three channels' state in registers) runs one sub-frame per pass: 64 environments of
+// 346 x 260, 64 x 16 tiles, 8.20 ms per gap against 8.88 in pairs and 9.13 in threes.
+template <int TX, int TY, bool NOISE, int NC>
 __host__ __device__ constexpr int step_pass() {
-  return ((TX == 64 && TY == 16) || (TX == 32 && TY == 32)) ? 3 : 2;
+  return NC == 3 ? 1 : (((TX == 64 && TY == 16) || (TX == 32 && TY == 32)) ? 3 : 2);
 }
 
 // Threads of one step CTA for a tile shape: one target per thread for 32 x 16 and 64 x 16,
@@ -259,10 +261,10 @@ __host__ __device__ constexpr int step_stage() {
   return TX * TY >= 2048 ? 1024 : (2 * TX * TY < kEventStage ? kEventStage : 2 * TX * TY);
 }
 
-// Dynamic shared memory of one step CTA.
-template <int TX, int TY>
+// Dynamic shared memory of one step CTA with passes of NP sub-frames.
+template <int TX, int TY, int NP>
 struct StepSmem {
-  unsigned long long zb[step_pass<TX, TY>()][2][TX * TY];  // per sub-frame of a pass: A forward, B backward
+  unsigned long long zb[NP][2][TX * TY];   // per sub-frame of a pass: A forward, B backward
   ulonglong2 stage[step_stage<TX, TY>()];  // events of this sub-frame before the flush
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
@@ -282,7 +284,7 @@ struct StepSmem {
 // resident threads and some spills than with fewer and none (measured on 64 environments of
 // 346 x 260: 64 x 16 tiles at 2048 threads 8.15 ms per gap, 32 x 16 at 1536 threads 8.63 ms;
 // before the CTA size followed the tile, six CTAs of 32 x 8 beat four, five tied).
-template <int TX, int TY, int NC>
+template <int TX, int TY, bool NOISE, int NC>
 __host__ __device__ constexpr int step_min_blocks() {
   constexpr int nth = step_threads<TX, TY>(), nt = TX * TY / nth;
   return (nt == 1 && nth >= 512 ? 2048
@@ -322,8 +324,8 @@ __device__ __forceinline__ void count_polarity(TileStats &st, const ulonglong2 &
 // Copies staged records [0, n) to the event buffer from position gbs; with statistics on,
 // counts them by polarity (one shared atomic per warp; every lane of a warp then runs the
 // same iterations).
-template <int TX, int TY>
-__device__ __forceinline__ void flush_stage(const StepSmem<TX, TY> &S, unsigned n,
+template <int TX, int TY, int NP>
+__device__ __forceinline__ void flush_stage(const StepSmem<TX, TY, NP> &S, unsigned n,
                                             unsigned long long gbs, const StepArgs &a,
                                             TileStats &st, bool stats, int tid, int nth) {
   if (!stats) {
@@ -352,8 +354,8 @@ __device__ __forceinline__ void flush_stage(const StepSmem<TX, TY> &S, unsigned 
 
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
 // shared-memory reservation per warp; past the stage's capacity, one global reservation.
-template <int TX, int TY, bool NOISE_EVENTS = true>
-__device__ __forceinline__ void stage_warp(StepSmem<TX, TY> &S, unsigned *s_n,
+template <int TX, int TY, int NP, bool NOISE_EVENTS = true>
+__device__ __forceinline__ void stage_warp(StepSmem<TX, TY, NP> &S, unsigned *s_n,
                                            TileStats &st, bool stats, const StepArgs &a,
                                            bool emit, const ulonglong2 &rec, unsigned lanes_below,
                                            int lane) {
@@ -393,10 +395,10 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NW = NTH / 32;
   constexpr int ROWS = NTH / TX;           // tile rows covered by one pass of the block
   constexpr unsigned NSTAGE = step_stage<TX, TY>();
-  constexpr int NP = step_pass<TX, TY>();  // sub-frames per pass
+  constexpr int NP = step_pass<TX, TY, NOISE, NC>();  // sub-frames per pass
   static_assert(TX % 32 == 0 && NTH % TX == 0 && NT * NTH == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StepSmem<TX, TY> &S = *reinterpret_cast<StepSmem<TX, TY> *>(smem_raw);
+  StepSmem<TX, TY, NP> &S = *reinterpret_cast<StepSmem<TX, TY, NP> *>(smem_raw);
   __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_p1[2], s_arrive;
   __shared__ unsigned long long s_base;
   __shared__ TileStats tstat;  // this tile's statistics
@@ -831,7 +833,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
                          (static_cast<unsigned>(tl.env) & 0xFFFFu) |
                          (static_cast<unsigned>(static_cast<uint16_t>(static_cast<int16_t>(pol * (1 + c)))) << 16))
                      << 32);
-            stage_warp<TX, TY, false>(S, &s_n, tstat, stats, a, emit, rec, lanes_below, lane);
+            stage_warp<TX, TY, NP, false>(S, &s_n, tstat, stats, a, emit, rec, lanes_below, lane);
           }
         } else {
         // Otherwise item c of the warp (pixels in lane order, k ascending) is computed by lane
@@ -1018,7 +1020,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 // One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
 // first one by block index, the next ones from a work counter that starts at 0.
 template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
-__global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY, NC>())
+__global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY, NOISE, NC>())
     step_kernel(const StepArgs a) {
   __shared__ int s_tile;
   int t = blockIdx.x;
@@ -1039,7 +1041,7 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
   // per SM x SMs, looked up at the first launch of this instantiation on that device
   constexpr int kMaxDevices = 64;
   static std::atomic<int> resident_of[kMaxDevices];
-  const int smem = static_cast<int>(sizeof(StepSmem<TX, TY>));
+  const int smem = static_cast<int>(sizeof(StepSmem<TX, TY, step_pass<TX, TY, NOISE, NC>()>));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
