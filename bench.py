@@ -51,12 +51,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["evis", "reference"], default="evis")
-    ap.add_argument("--workload", choices=["highspeed", "envs64", "batched", "stages"],
+    ap.add_argument("--workload", choices=["highspeed", "envs64", "batched", "stages", "soft"],
                     default="highspeed",
                     help="highspeed: the headline line (1024 envs at 640x480, K=32) with the "
                          "other workloads as extra keys; envs64: the 64-env 346x260 line alone; "
                          "batched: the uneven 256-env batch alone; stages: sensor noise, colour, "
-                         "margin, defocus and the voxel grid")
+                         "margin, defocus and the voxel grid; soft: the differentiable surrogate")
     ap.add_argument("--hs-envs", type=int, default=1024,
                     help="environments of the high-speed workload (640x480, K=32)")
     ap.add_argument("--envs", type=int, default=64, help="environments of the 346x260 workload")
@@ -979,6 +979,10 @@ def main():
         stages_arm(args)
     elif args.workload == "envs64":
         envs64_arm(args, world, rank, local)
+    elif args.workload == "soft":
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(soft_leg()), flush=True)
     else:
         headline_arm(args, world, rank, local)
 

@@ -24,7 +24,6 @@ using evis::other_depth;
 using evis::valid_depth;
 
 constexpr unsigned long long kEmpty = ~0ull;
-constexpr int kMaxN = 4096;
 
 struct SoftEnv {
   int32_t W, H, K;
@@ -191,14 +190,43 @@ __global__ void soft_winners(const SoftArgs a) {
   }
 }
 
-constexpr double kFix = 1099511627776.0;  // 2^40
+// Fixed point in units of 2^-40.  This part runs binary64 at a small fraction of the
+// binary32 rate, so the conversions are integer or binary32 operations that give the same
+// integers as rounding the exact binary64 values half to even.
 
-__device__ __forceinline__ long long to_fixed(double v) { return __double2ll_rn(v * kFix); }
+// w in (0, 1]: w 2^40 is exact in binary32 (a power-of-two scaling), then rounded.
+__device__ __forceinline__ long long fixed_of_weight(float w) {
+  return __float2ll_rn(__fmul_rn(w, 1099511627776.0f));
+}
+
+// w L (w in (0, 1], L finite): the exact 48-bit product of the significands, scaled by
+// 2^(e_w + e_L + 40) with the shift rounding half to even; saturates at +-2^62.
+__device__ __forceinline__ long long fixed_of_product(float w, float L) {
+  const unsigned bw = __float_as_uint(w), bl = __float_as_uint(L);
+  const int ew = static_cast<int>(bw >> 23), el = static_cast<int>((bl >> 23) & 0xFFu);
+  if ((bl & 0x7FFFFFFFu) == 0u || el == 255) return 0;  // zero (or a non-finite L)
+  const unsigned long long mw = (bw & 0x7FFFFFu) | 0x800000u;  // w is normal (>= 2^-48)
+  const unsigned long long ml = el ? ((bl & 0x7FFFFFu) | 0x800000u) : (bl & 0x7FFFFFu);
+  const unsigned long long prod = mw * ml;                       // < 2^48
+  const int sh = ew + (el ? el : 1) - 300 + 40;                 // value = prod 2^sh
+  unsigned long long q;
+  if (sh >= 0) {
+    q = sh >= 14 ? (1ull << 62) : min(prod << sh, 1ull << 62);
+  } else if (sh <= -64) {
+    q = 0;
+  } else {
+    const int r = -sh;
+    q = (prod + ((1ull << (r - 1)) - 1ull) + ((prod >> r) & 1ull)) >> r;
+  }
+  const long long v = static_cast<long long>(q);
+  return (bl >> 31) ? -v : v;
+}
+
 __device__ __forceinline__ float fixed_ratio(long long num, long long den) {
-  return static_cast<float>(static_cast<double>(num) / static_cast<double>(den));
+  return __fdiv_rn(__ll2float_rn(num), __ll2float_rn(den));
 }
 __device__ __forceinline__ float from_fixed(long long v) {
-  return static_cast<float>(static_cast<double>(v) / kFix);
+  return __fmul_rn(__ll2float_rn(v), 9.094947017729282e-13f);  // 2^-40
 }
 
 // Pass 2: sums of w and w L over each target's winner surface.
@@ -223,10 +251,9 @@ __global__ void soft_sums(const SoftArgs a) {
           // fixed-point sums: integer addition is exact and order-independent, so the
           // forward pass is deterministic (finite differences can resolve single inputs)
           atomicAdd(reinterpret_cast<unsigned long long *>(&a.sw[u]),
-                    static_cast<unsigned long long>(to_fixed(static_cast<double>(w))));
+                    static_cast<unsigned long long>(fixed_of_weight(w)));
           atomicAdd(reinterpret_cast<unsigned long long *>(&a.swl[u]),
-                    static_cast<unsigned long long>(
-                        to_fixed(static_cast<double>(w) * static_cast<double>(dir ? LBp : LAp))));
+                    static_cast<unsigned long long>(fixed_of_product(w, dir ? LBp : LAp)));
         }
     }
   }
@@ -263,9 +290,9 @@ __global__ void soft_targets(const SoftArgs a) {
     const int pol = d > 0.0f ? 1 : -1;
     const float th = pol > 0 ? E.c_on : E.c_off;
     const float qn = __fdiv_rn(fabsf(d), th);
-    int n = 0;
-    if (qn >= 1.0f) n = qn >= static_cast<float>(kMaxN) ? kMaxN : static_cast<int>(floorf(qn));
-    if (n > 0) Lref = __fadd_rn(Lref, __fmul_rn(static_cast<float>(pol * n), th));
+    // n of Eq. 4 without bound: the trajectory emits nothing, so no emission limit applies
+    const float nf = qn >= 1.0f ? floorf(qn) : 0.0f;
+    if (nf > 0.0f) Lref = __fadd_rn(Lref, __fmul_rn(pol > 0 ? nf : -nf, th));
   }
   a.counts[2 * o + pix] = non;
   a.counts[2 * o + HW + pix] = noff;
@@ -374,7 +401,7 @@ evis_status soft_prepare(const evis_env_desc *envs, int32_t n, void *ws, int64_t
     if (e == cudaSuccess) e = cudaMemsetAsync(a->keys, 0xFF, 8 * 2 * size_t(L.U), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a->sw, 0, 8 * 2 * size_t(L.U), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a->swl, 0, 8 * 2 * size_t(L.U), st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table is a local
+    // (a copy from pageable memory returns once the table is staged, so the local may go)
     if (e != cudaSuccess) return EVIS_ERR_CUDA;
   }
   return EVIS_OK;
