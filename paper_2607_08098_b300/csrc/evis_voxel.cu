@@ -7,8 +7,8 @@
 //                    three blocks per SM, so that the events in flight touch a part of the
 //                    accumulator that L2 holds, and evict-first loads of the records; each
 //                    event adds w_b and w_next to two uint32 accumulators (global atomics).
-//                    (8 x 640x480, 128 bins, 130 M events: 2.44 ms with sixteen blocks per
-//                    SM, 1.6 ms with three.)
+//                    (8 x 640x480, 128 bins, 130 M events: the whole grid in 3.88 ms with
+//                    sixteen blocks per SM, 3.14 ms with three.)
 //   voxel_plane_max  chunks of 8192 voxels of every (environment, polarity, bin) plane: a
 //                    block reduction, then one atomicMax into the plane's maximum.
 //   voxel_divide     the same chunks: each voxel divided by its plane's maximum.
