@@ -232,14 +232,18 @@ __device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d)
 
 // Sub-frames per pass of the step kernel for a tile shape: each pass lists the sources
 // once, reads each listed source once and has two barriers, and holds a pair of z-buffers
-// per sub-frame in shared memory.  Three where the third pair still leaves the shape's
-// resident CTAs their shared memory (96 environments of 640 x 480, K = 32, 64 x 16 tiles:
-// 28.99 ms per gap one sub-frame at a time, 23.87 ms in pairs, 22.12 ms in threes).  Colour
+// per sub-frame in shared memory.  More where the extra pairs still leave the shape's
+// resident CTAs their shared memory: four for 64 x 16 tiles (with a smaller event stage),
+// three for 32 x 32 and for 32 x 16 without noise (with a 512-event stage, keeping four CTAs
+// per SM); 96 environments of 640 x 480, K = 32, 64 x 16 tiles: 28.99 ms per gap one
+// sub-frame at a time, 23.87 ms in pairs, 22.12 ms in threes; with the later emission and
+// timestamp changes 20.91 ms in threes and 19.82 ms in fours.  64 environments of 346 x 260,
+// K = 16, 32 x 16 tiles: 2.87 ms in pairs, 2.81 ms in threes.  Colour
 // (three channels' state in registers) runs one sub-frame per pass: 64 environments of
 // 346 x 260, 64 x 16 tiles, 8.20 ms per gap against 8.88 in pairs and 9.13 in threes.
 template <int TX, int TY, bool NOISE, int NC>
 __host__ __device__ constexpr int step_pass() {
-  return NC == 3 ? 1 : (((TX == 64 && TY == 16) || (TX == 32 && TY == 32)) ? 3 : 2);
+  return NC == 3 ? 1 : ((TX == 64 && TY == 16) ? 4 : ((TX == 32 && (TY == 32 || (TY == 16 && !NOISE))) ? 3 : 2));
 }
 
 // Threads of one step CTA for a tile shape: one target per thread for 32 x 16 and 64 x 16,
@@ -251,21 +255,22 @@ __host__ __device__ constexpr int step_threads() {
   return (TX == 32 && (TY == 16 || TY == 32)) ? 512 : ((TX == 64 && TY == 16) ? 1024 : kThreads);
 }
 
-// Events staged in shared memory per CTA and sub-frame (more go to global memory one warp
-// reservation at a time): two per target up to 2048, 1024 for the largest tiles, whose
-// shared memory would otherwise cost resident CTAs.  On 32 x 346x260 environments (K=16,
+// Events staged in shared memory per CTA and pass (more go to global memory one warp
+// reservation at a time): two per target up to 2048, 1024 for the largest tiles and for
+// passes of four sub-frames, 512 for 32 x 16 tiles in passes of three, whose shared memory
+// would otherwise cost resident CTAs.  On 32 x 346x260 environments (K=16,
 // 0.72 events per pixel-substep) 1 % of the emission chunks of 32 x 16 tiles then overflow
 // the stage, against 16 % with 512 events.
-template <int TX, int TY>
+template <int TX, int TY, int NP>
 __host__ __device__ constexpr int step_stage() {
-  return TX * TY >= 2048 ? 1024 : (2 * TX * TY < kEventStage ? kEventStage : 2 * TX * TY);
+  return (TX == 32 && TY == 16 && NP == 3) ? 512 : ((TX * TY >= 2048 || NP >= 4) ? 1024 : (2 * TX * TY < kEventStage ? kEventStage : 2 * TX * TY));
 }
 
 // Dynamic shared memory of one step CTA with passes of NP sub-frames.
 template <int TX, int TY, int NP>
 struct StepSmem {
   unsigned long long zb[NP][2][TX * TY];   // per sub-frame of a pass: A forward, B backward
-  ulonglong2 stage[step_stage<TX, TY>()];  // events of this sub-frame before the flush
+  ulonglong2 stage[step_stage<TX, TY, NP>()];  // events of this pass before the flush
   uint2 cand_b[2][kCandidates];            // candidate segments' motion bounds, as half2 pairs
                                            // (min dx, max dx), (min dy, max dy) rounded outward
   unsigned cand_xy[2][kCandidates];        // candidate segments (row << 16 | column)
@@ -367,18 +372,18 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY, NP> &S, unsigned *s_
   if (lane == 0) {
     if (NOISE_EVENTS && stats) atomicAdd(&st.noise, cnt);
     base = atomicAdd(s_n, cnt);
-    if (base + cnt > static_cast<unsigned>(step_stage<TX, TY>()))
+    if (base + cnt > static_cast<unsigned>(step_stage<TX, TY, NP>()))
       gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
-                                     base + cnt - max(base, static_cast<unsigned>(step_stage<TX, TY>()))));
+                                     base + cnt - max(base, static_cast<unsigned>(step_stage<TX, TY, NP>()))));
   }
   base = __shfl_sync(kFull, base, 0);
   gb = __shfl_sync(kFull, gb, 0);
   if (emit) {
     const unsigned idx = base + static_cast<unsigned>(__popc(m & lanes_below));
-    if (idx < static_cast<unsigned>(step_stage<TX, TY>())) {
+    if (idx < static_cast<unsigned>(step_stage<TX, TY, NP>())) {
       S.stage[idx] = rec;
     } else {
-      const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(step_stage<TX, TY>())));
+      const unsigned long long gi = gb + (idx - max(base, static_cast<unsigned>(step_stage<TX, TY, NP>())));
       if (gi < a.capacity) a.events[gi] = rec;
       if (stats) count_polarity(st, rec);
     }
@@ -394,8 +399,8 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NT = TX * TY / NTH;        // targets per thread
   constexpr int NW = NTH / 32;
   constexpr int ROWS = NTH / TX;           // tile rows covered by one pass of the block
-  constexpr unsigned NSTAGE = step_stage<TX, TY>();
   constexpr int NP = step_pass<TX, TY, NOISE, NC>();  // sub-frames per pass
+  constexpr unsigned NSTAGE = step_stage<TX, TY, NP>();
   static_assert(TX % 32 == 0 && NTH % TX == 0 && NT * NTH == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepSmem<TX, TY, NP> &S = *reinterpret_cast<StepSmem<TX, TY, NP> *>(smem_raw);
