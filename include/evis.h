@@ -302,17 +302,19 @@ typedef struct {
   int64_t t0_ns, t1_ns;    /* segment, 0 < t1_ns - t0_ns < 2^32 */
 } evis_voxel_env;
 
-/* Device workspace bytes of evis_voxel_grid (a descriptor table, one uint32 per plane for
- * its maximum and one uint32 per voxel). */
+/* Device workspace bytes of evis_voxel_grid for up to max_events records (a descriptor
+ * table, one uint32 per plane for its maximum, two uint64 per region of 32 pixels of a row
+ * across 256 planes, and one uint32 per record, two when bins > 128). */
 evis_status evis_voxel_workspace_size(const evis_voxel_env *envs, int32_t n_envs, int32_t bins,
-                                      int64_t *bytes);
+                                      int64_t max_events, int64_t *bytes);
 
 /* Builds the grid of every environment (host array envs of n_envs, bins in 1..1024) from
  * the device event records events[0 .. n), n = min(*count, max_events) with count a device
  * pointer (for example evis_events_device's, so no host synchronisation is needed) or
  * max_events when count is NULL.  grid is a device float array, per environment in order
- * [2][bins][height][width].  workspace is device memory of evis_voxel_workspace_size bytes
- * (its contents need not be initialised).  Asynchronous on stream; EVIS_ERR_INVALID_ARG
+ * [2][bins][height][width].  workspace is device memory of evis_voxel_workspace_size(...,
+ * max_events, ...) bytes (its contents need not be initialised).  events and workspace must
+ * be 16-byte aligned, grid 4-byte aligned.  Asynchronous on stream; EVIS_ERR_INVALID_ARG
  * (evis_last_error(NULL) says why) before any work for a bad argument. */
 evis_status evis_voxel_grid(const evis_event *events, const uint64_t *count, int64_t max_events,
                             const evis_voxel_env *envs, int32_t n_envs, int32_t bins,

@@ -88,7 +88,7 @@ _SIGS = {
                                           ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "evis_set_noise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "evis_voxel_workspace_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                                 ctypes.c_void_p]),
+                                                 ctypes.c_int64, ctypes.c_void_p]),
     "evis_voxel_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
@@ -489,11 +489,12 @@ def _voxel_envs(segments):
     return arr
 
 
-def voxel_workspace_size(segments, bins: int = 128) -> int:
+def voxel_workspace_size(segments, bins: int = 128, max_events: int = 0) -> int:
+    """Device workspace bytes of voxel_grid for up to max_events records."""
     n = ctypes.c_int64()
     arr = _voxel_envs(segments)
     _check(lib().evis_voxel_workspace_size(ctypes.addressof(arr), len(segments), int(bins),
-                                           ctypes.byref(n)))
+                                           int(max_events), ctypes.byref(n)))
     return n.value
 
 
@@ -505,7 +506,7 @@ def voxel_grid(events_ptr: int, count_ptr, max_events: int, segments, bins: int 
     tensor, per environment [2][bins][H][W] concatenated."""
     import torch
     arr = _voxel_envs(segments)
-    wsb = voxel_workspace_size(segments, bins)
+    wsb = voxel_workspace_size(segments, bins, max_events)
     if workspace is None or workspace.numel() < wsb:
         workspace = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     n_vox = sum(2 * bins * int(W) * int(H) for W, H, _, _ in segments)

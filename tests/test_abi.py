@@ -118,8 +118,16 @@ def test_voxel_arguments_checked_without_a_gpu(evis, seg, bins):
 
 
 def test_voxel_workspace_size(evis):
-    n = evis.voxel_workspace_size([(640, 480, 0, 500_000_000), (3, 2, 5, 9)], 128)
-    assert n >= 4 * 2 * 128 * (640 * 480 + 6) and n < 4 * 2 * 128 * (640 * 480 + 6) + 4096
+    """Two uint64 per region (a row segment of 32 pixels across 256 planes), one uint32 entry
+    per record, two once the planes of an environment span two groups (bins > 128)."""
+    segs = [(640, 480, 0, 500_000_000), (3, 2, 5, 9)]
+    regions = 480 * 20 + 2 * 1
+    n0 = evis.voxel_workspace_size(segs, 128)
+    assert 16 * regions <= n0 < 16 * regions + 4096 + 4 * 2 * 128 * 2
+    assert evis.voxel_workspace_size(segs, 128, 1_000_000) - n0 == 4 * 1_000_000
+    m0 = evis.voxel_workspace_size(segs, 129)
+    assert 32 * regions <= m0 < 32 * regions + 4096 + 4 * 2 * 129 * 2
+    assert evis.voxel_workspace_size(segs, 129, 1_000_000) - m0 == 8 * 1_000_000
 
 
 def test_state_calls_reject_a_null_context_without_a_gpu(evis):

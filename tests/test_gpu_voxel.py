@@ -1,7 +1,8 @@
 """The event voxel grid on the GPU against the oracle, bit for bit (needs a B300): random
-records with skips and colour polarities, the device-side count, planes on both sides of the
-cluster normalisation's size limit, and the grid of a synthesis step read in place from the
-library's event buffer."""
+records with skips and colour polarities, the device-side count, bin counts whose planes fill
+one, two and eight groups of 256 planes (events whose two bins straddle a group boundary), a
+1280-pixel-wide sensor next to small ones, and the grid of a synthesis step read in place
+from the library's event buffer."""
 import numpy as np
 import pytest
 
@@ -34,7 +35,7 @@ def _records(rng, n, segs, junk_env=True):
     return e
 
 
-@pytest.mark.parametrize("bins", [1, 7, 128])
+@pytest.mark.parametrize("bins", [1, 7, 128, 129, 1024])
 def test_voxel_grid_random_records(ev, oracle_mod, bins):
     rng = np.random.default_rng(bins)
     segs = [(64, 48, 1_000, 500_001_000), (37, 23, 0, 123_456_789), (1, 1, 5, 9), (346, 260, 0, 16_666_667)]
@@ -51,8 +52,8 @@ def test_voxel_grid_random_records(ev, oracle_mod, bins):
 
 
 def test_voxel_grid_large_planes(ev, oracle_mod):
-    """A plane above 327,680 voxels (1280 x 720) sends the whole call to the one-CTA-per-plane
-    normalisation; the smaller planes of the same call must come out the same."""
+    """A 1280 x 720 sensor (40 row segments per row) beside a small and a VGA one, in one
+    call."""
     rng = np.random.default_rng(5)
     segs = [(1280, 720, 0, 50_000_000), (64, 48, 1_000, 2_001_000), (640, 480, 7, 99_999)]
     rec = _records(rng, 300_000, segs)
