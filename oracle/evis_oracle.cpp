@@ -255,40 +255,77 @@ void philox4x32_10(uint32_t ctr[4], uint32_t k0, uint32_t k1) {
 // Bernoulli draw with probability p from a 32-bit uniform (24 bits used, binary32 compare).
 inline bool fires(uint32_t u, float p) { return static_cast<float>(u >> 8) < p * 16777216.0f; }
 
-// Leak, shot and hot-pixel events of one pixel (and channel ch) in sub-frame i (Sec. 3.4).
-// Each fires at most once per sub-frame with the stated probability over the interval
-// [t0, t1); its time is uniform in the interval.  Noise events bypass the refractory filter
-// and leave the reference level untouched.  Shot noise needs the sub-frame's sample (has).
-// Channels draw independent streams: the last counter word is stream + 4 ch.
-void noise_pixel(Ctx& c, int env, int x, int y, int ch, uint32_t pix, uint32_t i, int64_t t0,
-                 int64_t t1, bool has, float L) {
-  const Noise& nz = c.noise[env];
+// Leak, shot and hot-pixel events of one keyframe gap of environment e (Sec. 3.4).  They
+// pass no refractory filter, leave the reference levels unchanged and depend only on the
+// gap's two keyframes.  Per sensor pixel, channel ch and sub-frame i, over [t_{i-1}, t_i)
+// with d = t_i - t_{i-1} ns and dts = d 1e-9 s, the sources compete:
+//   leak  p_leak = leak_hz dts;
+//   shot  p_shot = shot_hz dts (1 - clamp((L_i - lo) / (hi - lo), 0, 1)), where
+//         L_i = (1 - f) LA + f LB (f = i / K) is the pixel's own log intensity between the
+//         keyframes, so darker pixels fire more;
+//   hot   p_hot = hot_hz dts for the fixed hot subset, 0 elsewhere.
+// One uniform word u picks at most one of them: with x = (float)(u >> 8), leak when
+// x < p_leak 2^24, else shot when x < (p_leak + p_shot) 2^24, else hot when
+// x < (p_leak + p_shot + p_hot) 2^24 (probabilities and sums in binary32, left to right).
+// Words: Philox4x32-10 at (pixel, gap, floor((i - 1) / 4), 4 ch), word (i - 1) mod 4.  A
+// fired event takes its time t_{i-1} + floor(v d / 2^32) from word 0 of (pixel, gap, i,
+// 1 + 4 ch) and, for shot noise, its polarity from bit 0 of word 3 (1: ON); leak and hot
+// events are ON.  The hot subset: word 0 of (pixel, 2^32 - 1, 0, 2 + 4 ch) fires with
+// probability hot_fraction.  The pixel index is the sensor's, y * W + x inside the margin.
+void noise_gap(Ctx& c, int e, const float* LB, int64_t dt) {
+  const Noise& nz = c.noise[e];
   if (!(nz.leak_hz > 0.0f || nz.shot_hz > 0.0f || nz.hot_hz > 0.0f)) return;
+  const Env& en = c.envs[e];
+  const int W = en.W, K = en.K, m = en.margin, SW = en.W - 2 * m, SH = en.H - 2 * m;
+  const size_t o = static_cast<size_t>(c.off[e]), plane = static_cast<size_t>(c.total);
   const uint32_t k0 = static_cast<uint32_t>(nz.seed);
-  const uint32_t k1 = static_cast<uint32_t>(nz.seed >> 32) ^ static_cast<uint32_t>(env);
-  const uint32_t cw = 4u * static_cast<uint32_t>(ch);
-  uint32_t r[4] = {pix, c.gap, i, cw}, rt[4] = {pix, c.gap, i, 1u + cw},
-           rh[4] = {pix, 0xFFFFFFFFu, 0u, 2u + cw};
-  philox4x32_10(r, k0, k1);
-  philox4x32_10(rt, k0, k1);
-  philox4x32_10(rh, k0, k1);
-  const int64_t d = t1 - t0;
-  const float dts = static_cast<float>(d) * 1e-9f;
-  auto at = [&](uint32_t u) {  // t0 + floor(u d / 2^32); d reaches 2^40, so 128-bit product
-    return t0 + static_cast<int64_t>((static_cast<unsigned __int128>(u) * static_cast<uint64_t>(d)) >> 32);
-  };
-  auto emit = [&](int64_t t, int p) {
-    c.events.push_back(Event{t, static_cast<uint16_t>(x), static_cast<uint16_t>(y),
-                             static_cast<uint16_t>(env), static_cast<int16_t>(p * (1 + ch))});
-  };
-  if (nz.leak_hz > 0.0f && fires(r[0], nz.leak_hz * dts)) emit(at(rt[0]), 1);
-  if (nz.shot_hz > 0.0f && has) {
-    float ib = (L - nz.lo) / (nz.hi - nz.lo);
-    ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
-    if (fires(r[1], nz.shot_hz * dts * (1.0f - ib))) emit(at(rt[1]), (rt[3] & 1u) ? 1 : -1);
+  const uint32_t k1 = static_cast<uint32_t>(nz.seed >> 32) ^ static_cast<uint32_t>(e);
+  const int64_t T0 = c.clock[e];
+  const float inv_range = 1.0f / (nz.hi - nz.lo);
+  for (int ch = 0; ch < c.nc; ++ch) {
+    const uint32_t cw = 4u * static_cast<uint32_t>(ch);
+    for (int sy = 0; sy < SH; ++sy) {
+      for (int sx = 0; sx < SW; ++sx) {
+        const uint32_t pix = static_cast<uint32_t>(sy * SW + sx);
+        const size_t t = static_cast<size_t>(sy + m) * W + (sx + m);
+        const float la = c.LA[ch * plane + o + t], lb = LB[ch * plane + t];
+        uint32_t rh[4] = {pix, 0xFFFFFFFFu, 0u, 2u + cw};
+        philox4x32_10(rh, k0, k1);
+        const bool hot = nz.hot_hz > 0.0f && fires(rh[0], nz.hot_fraction);
+        uint32_t r[4] = {0u, 0u, 0u, 0u};
+        for (int i = 1; i <= K; ++i) {
+          const int64_t t0 = T0 + (static_cast<int64_t>(i - 1) * dt) / K;
+          const int64_t d = T0 + (static_cast<int64_t>(i) * dt) / K - t0;
+          if ((i - 1) % 4 == 0) {
+            r[0] = pix;
+            r[1] = c.gap;
+            r[2] = static_cast<uint32_t>((i - 1) / 4);
+            r[3] = cw;
+            philox4x32_10(r, k0, k1);
+          }
+          const uint32_t u = r[(i - 1) % 4];
+          const float dts = static_cast<float>(d) * 1e-9f;
+          const float f = static_cast<float>(i) / static_cast<float>(K);
+          const float L = (1.0f - f) * la + f * lb;
+          float ib = (L - nz.lo) * inv_range;
+          ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
+          const float s1 = nz.leak_hz * dts;
+          const float s2 = s1 + nz.shot_hz * dts * (1.0f - ib);
+          const float s3 = hot ? s2 + nz.hot_hz * dts : s2;
+          const float x = static_cast<float>(u >> 8);
+          if (!(x < s3 * 16777216.0f)) continue;
+          uint32_t rt[4] = {pix, c.gap, static_cast<uint32_t>(i), 1u + cw};
+          philox4x32_10(rt, k0, k1);
+          const bool leak = x < s1 * 16777216.0f, shot = !leak && x < s2 * 16777216.0f;
+          const int p = (shot && !(rt[3] & 1u)) ? -1 : 1;
+          const int64_t te = t0 + static_cast<int64_t>((static_cast<unsigned __int128>(rt[0]) *
+                                                        static_cast<uint64_t>(d)) >> 32);
+          c.events.push_back(Event{te, static_cast<uint16_t>(sx), static_cast<uint16_t>(sy),
+                                   static_cast<uint16_t>(e), static_cast<int16_t>(p * (1 + ch))});
+        }
+      }
+    }
   }
-  if (nz.hot_hz > 0.0f && fires(rh[0], nz.hot_fraction) && fires(r[2], nz.hot_hz * dts))
-    emit(at(rt[2]), 1);
 }
 
 // One keyframe gap of one environment: K substeps f = i/K (Sec. 3.3), each a bidirectional
@@ -328,7 +365,7 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
     }
     // targets: the sensor, i.e. the rendered frame without its margin (Appendix B); every
     // rendered pixel splats, and events carry sensor coordinates
-    const int m = en.margin, SW = W - 2 * m;
+    const int m = en.margin;
     for (int y = m; y < H - m; ++y) {
       for (int x = m; x < W - m; ++x) {
         size_t t = static_cast<size_t>(y) * W + x;
@@ -358,8 +395,6 @@ void run_pair(Ctx& c, int e, const float* LB, const float* mvB, const float* ZB,
             else L = NAN;
           }
           if (Lint) Lint[(static_cast<size_t>(i - 1) * nc + ch) * HW + t] = L;
-          noise_pixel(c, e, sx, sy, ch, static_cast<uint32_t>(sy * SW + sx), static_cast<uint32_t>(i),
-                      T0 + (static_cast<int64_t>(i - 1) * dt) / K, ti, hasA || hasB, L);
           if (!hasA && !hasB) continue;  // no sample this substep: the pixel holds its state
           float th_on = en.c_on, th_off = en.c_off;
           if (en.has_map) {  // one threshold map for all channels
@@ -538,6 +573,7 @@ int32_t orc_step(void* h, const float* frames, const float* mv, const float* dep
   for (size_t e = 0; e < c.envs.size(); ++e) {
     size_t o = static_cast<size_t>(c.off[e]);
     size_t HW = static_cast<size_t>(c.envs[e].W) * c.envs[e].H;
+    noise_gap(c, static_cast<int>(e), LB.data() + o, dt_ns);
     run_pair(c, static_cast<int>(e), LB.data() + o, mv + 2 * o, depth + o, dt_ns,
              trace_keys ? trace_keys + tk : nullptr, trace_L ? trace_L + tl : nullptr);
     tk += static_cast<size_t>(c.envs[e].K) * 2 * HW;

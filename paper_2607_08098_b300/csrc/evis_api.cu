@@ -40,6 +40,7 @@ struct evis_ctx {
 
   std::vector<DevEnv> h_envs;  // host copy of d_envs (noise and defocus parameters change it)
   bool any_noise = false;
+  int noise_max_px = 0;        // largest sensor (pixels) among the environments with noise on
   int blur_r_max = -1;         // largest defocus radius; -1: no defocus pass
   float *d_blur = nullptr;     // [total] blurred luminance of the keyframe being prepared
   float *d_blur_w = nullptr;   // [n][2 kMaxBlurR + 1] defocus weights
@@ -222,7 +223,7 @@ cudaError_t rebuild_groups(evis_ctx *c) {
   return cudaMemcpy(c->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice);
 }
 
-// Launches the synthesis kernel for every tile group.
+// Launches the synthesis kernel for every tile group, then the sensor noise of the gap.
 cudaError_t launch_groups(evis_ctx *c, evis::StepArgs s, bool trace) {
   for (size_t gi = 0; gi < c->groups.size(); ++gi) {
     const auto &g = c->groups[gi];
@@ -232,7 +233,7 @@ cudaError_t launch_groups(evis_ctx *c, evis::StepArgs s, bool trace) {
     cudaError_t e = evis::launch_step(s, g.tw, g.th, trace, c->grid_cap, c->stream);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return evis::launch_noise(s, c->n, c->noise_max_px, c->stream);
 }
 
 // The new keyframe B as the synthesis kernel reads it.
@@ -834,6 +835,7 @@ evis_status evis_set_noise(evis_ctx *c, const evis_noise_desc *nz) {
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   drop_graphs(c);
   bool any = false;
+  int max_px = 0;
   for (int i = 0; i < c->n; ++i) {
     DevEnv &v = c->h_envs[i];
     const evis_noise_desc d = nz ? nz[i] : evis_noise_desc{0, 0, 0, 0, 0, 1, 0};
@@ -847,12 +849,14 @@ evis_status evis_set_noise(evis_ctx *c, const evis_noise_desc *nz) {
     v.key1 = static_cast<uint32_t>(d.seed >> 32) ^ static_cast<uint32_t>(i);
     v.noise = (d.leak_hz > 0.0f || d.shot_hz > 0.0f || d.hot_hz > 0.0f) ? 1 : 0;
     any |= v.noise != 0;
+    if (v.noise) max_px = std::max(max_px, (v.W - 2 * v.margin) * (v.H - 2 * v.margin));
   }
   // pageable source: the call returns once the table is staged, so h_envs may change after
   if ((e = cudaMemcpyAsync(c->d_envs, c->h_envs.data(), sizeof(DevEnv) * c->n,
                            cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "upload noise parameters");
   c->any_noise = any;
+  c->noise_max_px = max_px;
   return EVIS_OK;
 }
 

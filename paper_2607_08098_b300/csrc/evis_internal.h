@@ -83,7 +83,7 @@ struct StepArgs {
   bool stats;                      // collect holes, polarity and noise counts (EVIS_STATS)
   int64_t dt;
   uint32_t flags;
-  bool noise;                // some environment of the launch has noise on (needs gap_in)
+  bool noise;                // some environment of the launch has noise on (launch_noise)
   int nc;                    // event channels: 1, or 3 in colour mode (0 reads as 1)
   int64_t plane;             // channel stride of LA, LB, Lref, tlast (packed pixels)
   uint64_t *tr_keys;         // debug trace (null in the production path)
@@ -135,7 +135,7 @@ cudaError_t launch_init_ref(const float *L, float *Lref, int64_t n, cudaStream_t
 // instantiated in the evis_step_*.cu translation units).
 // STATS compiles the statistics code (EVIS_STATS, checked at run time); the plain production
 // variant is also built without it.
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
+template <int TX, int TY, bool TRACE, bool PACKED, int NC, bool STATS>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s);
 
 // grid_cap > 0: persistent launch of at most grid_cap x (resident CTAs) blocks that take
@@ -143,6 +143,11 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
 cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, int grid_cap,
                         cudaStream_t s);
 bool tile_shape_supported(int tile_w, int tile_h);
+// Sensor noise of one keyframe gap (Sec. 3.4) of every environment with noise on, appended
+// to the event buffer.  Reads a.envs, a.LA and a.LB (the gap's prepared log-intensity
+// planes), a.clock_in, a.gap_in, a.dt, a.nc, a.plane and writes a.events, a.ev_count and,
+// with a.stats, a.env_stats.  max_px: the largest sensor (pixels) of those environments.
+cudaError_t launch_noise(const StepArgs &a, int n_envs, int max_px, cudaStream_t s);
 // Error text reported by evis_last_error(NULL) for calls made without a context.
 void set_detached_error(const std::string &msg);
 cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, float *out,

@@ -332,22 +332,19 @@ cudaError_t launch_step(const StepArgs &a, int tile_w, int tile_h, bool trace, i
   const int n_tiles = a.n_tiles;
   if (n_tiles <= 0) return cudaSuccess;
   if (!a.packA) {  // unpacked sources: 64x16 tiles only
-    if (tile_w != 64 || tile_h != 16 || trace || a.noise) return cudaErrorInvalidValue;
+    if (tile_w != 64 || tile_h != 16 || trace) return cudaErrorInvalidValue;
     if (a.nc == 3) return cudaErrorInvalidValue;
-    return launch_shape<64, 16, false, false, false, 1, false>(a, n_tiles, grid_cap, s);
+    return launch_shape<64, 16, false, false, 1, false>(a, n_tiles, grid_cap, s);
   }
-  if (a.noise && !a.gap_in) return cudaErrorInvalidValue;
-  // the trace and colour variants always carry the noise and statistics code; the mono
-  // production one only when asked
+  // the trace and colour variants always carry the statistics code; the mono production one
+  // only when asked
 #define EVIS_SHAPE(TX, TY)                                                                      \
   if (tile_w == TX && tile_h == TY)                                                             \
-    return a.nc == 3                                                                            \
-               ? (trace ? launch_shape<TX, TY, true, true, true, 3, true>(a, n_tiles, grid_cap, s) \
-                        : launch_shape<TX, TY, false, true, true, 3, true>(a, n_tiles, grid_cap, s)) \
-               : (trace ? launch_shape<TX, TY, true, true, true, 1, true>(a, n_tiles, grid_cap, s) \
-                        : (a.noise ? launch_shape<TX, TY, false, true, true, 1, true>(a, n_tiles, grid_cap, s) \
-                                   : (a.stats ? launch_shape<TX, TY, false, true, false, 1, true>(a, n_tiles, grid_cap, s) \
-                                              : launch_shape<TX, TY, false, true, false, 1, false>(a, n_tiles, grid_cap, s))));
+    return a.nc == 3 ? (trace ? launch_shape<TX, TY, true, true, 3, true>(a, n_tiles, grid_cap, s)  \
+                              : launch_shape<TX, TY, false, true, 3, true>(a, n_tiles, grid_cap, s)) \
+                     : (trace ? launch_shape<TX, TY, true, true, 1, true>(a, n_tiles, grid_cap, s)   \
+                              : (a.stats ? launch_shape<TX, TY, false, true, 1, true>(a, n_tiles, grid_cap, s) \
+                                         : launch_shape<TX, TY, false, true, 1, false>(a, n_tiles, grid_cap, s)));
   EVIS_SHAPE(32, 8)
   EVIS_SHAPE(32, 16)
   EVIS_SHAPE(32, 32)

@@ -1,6 +1,6 @@
 // The synthesis kernel of the EVIS event path (sm_103a), as templates: the translation
-// units evis_step_*.cu instantiate its variants (tile shapes, trace, noise), so that they
-// compile in parallel.
+// units evis_step_*.cu instantiate its variants (tile shapes, trace, colour, statistics), so
+// that they compile in parallel.  Sensor noise has its own kernel (evis_noise.cu).
 //
 // Compiled with -fmad=false and written with explicit round-to-nearest intrinsics so that
 // every floating-point step that decides a z-buffer winner or an event count is the same
@@ -193,57 +193,20 @@ __device__ __forceinline__ int64_t crossing_time(float Lref, float pk, float th,
   return interp_time(fr, tprev, ti);
 }
 
-__device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int env, int p) {
-  ulonglong2 r;
-  r.x = static_cast<unsigned long long>(t);
-  r.y = static_cast<unsigned long long>(x & 0xFFFF) |
-        (static_cast<unsigned long long>(y & 0xFFFF) << 16) |
-        (static_cast<unsigned long long>(env & 0xFFFF) << 32) |
-        (static_cast<unsigned long long>(static_cast<uint16_t>(static_cast<int16_t>(p))) << 48);
-  return r;
-}
-
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
-// SC 2011): ten rounds, each two 32 x 32 -> 64-bit products of the counter's even words
-// mixed into the odd words with the round key; the key advances by the Weyl increments.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c;
-}
-
-// Bernoulli draw with probability q from a 32-bit uniform word (24 bits, binary32 compare).
-__device__ __forceinline__ bool fires(unsigned u, float q) {
-  return __uint2float_rn(u >> 8) < __fmul_rn(q, 16777216.0f);
-}
-
-// t0 + floor(u d / 2^32) for d < 2^41: the product split at bit 32 of d.
-__device__ __forceinline__ int64_t noise_time(unsigned u, int64_t t0, int64_t d) {
-  const unsigned long long du = static_cast<unsigned long long>(d);
-  const unsigned long long lo = (static_cast<unsigned long long>(u) * (du & 0xFFFFFFFFull)) >> 32;
-  return t0 + static_cast<int64_t>(static_cast<unsigned long long>(u) * (du >> 32) + lo);
-}
-
 // Sub-frames per pass of the step kernel for a tile shape: each pass lists the sources
 // once, reads each listed source once and has two barriers, and holds a pair of z-buffers
 // per sub-frame in shared memory.  More where the extra pairs still leave the shape's
 // resident CTAs their shared memory: four for 64 x 16 tiles (with a smaller event stage),
-// three for 32 x 32 and for 32 x 16 without noise (with a 512-event stage, keeping four CTAs
-// per SM); 96 environments of 640 x 480, K = 32, 64 x 16 tiles: 28.99 ms per gap one
-// sub-frame at a time, 23.87 ms in pairs, 22.12 ms in threes; with the later emission and
-// timestamp changes 20.91 ms in threes and 19.82 ms in fours.  64 environments of 346 x 260,
-// K = 16, 32 x 16 tiles: 2.87 ms in pairs, 2.81 ms in threes.  Colour
+// three for 32 x 32 and for 32 x 16 (with a 512-event stage, keeping four CTAs per SM).
+// 96 environments of 640 x 480, K = 32, 64 x 16 tiles: 28.99 ms per gap one sub-frame at a
+// time, 23.87 ms in pairs, 22.12 ms in threes; with the later emission and timestamp
+// changes 20.91 ms in threes and 19.82 ms in fours.  64 environments of 346 x 260, K = 16,
+// 32 x 16 tiles: 2.87 ms in pairs, 2.81 ms in threes.  Colour
 // (three channels' state in registers) runs one sub-frame per pass: 64 environments of
 // 346 x 260, 64 x 16 tiles, 8.20 ms per gap against 8.88 in pairs and 9.13 in threes.
-template <int TX, int TY, bool NOISE, int NC>
+template <int TX, int TY, int NC>
 __host__ __device__ constexpr int step_pass() {
-  return NC == 3 ? 1 : ((TX == 64 && TY == 16) ? 4 : ((TX == 32 && (TY == 32 || (TY == 16 && !NOISE))) ? 3 : 2));
+  return NC == 3 ? 1 : ((TX == 64 && TY == 16) ? 4 : ((TX == 32 && (TY == 32 || TY == 16)) ? 3 : 2));
 }
 
 // Threads of one step CTA for a tile shape: one target per thread for 32 x 16 and 64 x 16,
@@ -289,7 +252,7 @@ struct StepSmem {
 // resident threads and some spills than with fewer and none (measured on 64 environments of
 // 346 x 260: 64 x 16 tiles at 2048 threads 8.15 ms per gap, 32 x 16 at 1536 threads 8.63 ms;
 // before the CTA size followed the tile, six CTAs of 32 x 8 beat four, five tied).
-template <int TX, int TY, bool NOISE, int NC>
+template <int TX, int TY, int NC>
 __host__ __device__ constexpr int step_min_blocks() {
   constexpr int nth = step_threads<TX, TY>(), nt = TX * TY / nth;
   return (nt == 1 && nth >= 512 ? 2048
@@ -305,7 +268,6 @@ struct TileStats {
   unsigned holes_ab;     // target-sub-frames without a source of A | without one of B << 16
   unsigned holes_both;   // ... without either
   unsigned pol;          // staged events copied out since the last fold: ON | OFF << 16
-  unsigned noise;        // noise events staged in this sub-frame
   unsigned long long tot[kStatOverLimit];
 };
 
@@ -317,8 +279,7 @@ __device__ __forceinline__ void fold_stats(TileStats &st) {
   st.tot[kStatHolesBoth] += st.holes_both;
   st.tot[kStatEventsOn] += st.pol & 0xFFFFu;
   st.tot[kStatEventsOff] += st.pol >> 16;
-  st.tot[kStatNoise] += st.noise;
-  st.holes_ab = st.holes_both = st.pol = st.noise = 0;
+  st.holes_ab = st.holes_both = st.pol = 0;
 }
 
 // A record written to global memory without the stage (the stage was full) counts at once.
@@ -359,7 +320,7 @@ __device__ __forceinline__ void flush_stage(const StepSmem<TX, TY, NP> &S, unsig
 
 // Stages the records of the warp's lanes that have emit set (the warp is converged): one
 // shared-memory reservation per warp; past the stage's capacity, one global reservation.
-template <int TX, int TY, int NP, bool NOISE_EVENTS = true>
+template <int TX, int TY, int NP>
 __device__ __forceinline__ void stage_warp(StepSmem<TX, TY, NP> &S, unsigned *s_n,
                                            TileStats &st, bool stats, const StepArgs &a,
                                            bool emit, const ulonglong2 &rec, unsigned lanes_below,
@@ -370,7 +331,6 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY, NP> &S, unsigned *s_
   unsigned base = 0;
   unsigned long long gb = 0;
   if (lane == 0) {
-    if (NOISE_EVENTS && stats) atomicAdd(&st.noise, cnt);
     base = atomicAdd(s_n, cnt);
     if (base + cnt > static_cast<unsigned>(step_stage<TX, TY, NP>()))
       gb = atomicAdd(a.ev_count, static_cast<unsigned long long>(
@@ -390,16 +350,15 @@ __device__ __forceinline__ void stage_warp(StepSmem<TX, TY, NP> &S, unsigned *s_
   }
 }
 
-// All K sub-frames of one target tile (the body of step_kernel).  NOISE compiles the sensor
-// noise of Sec. 3.4 in (environments with it off skip it at run time); NC = 3 runs the event
+// All K sub-frames of one target tile (the body of step_kernel).  NC = 3 runs the event
 // model on the R, G and B planes (Sec. 3.2), NC = 1 on the one log-intensity plane.
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
+template <int TX, int TY, bool TRACE, bool PACKED, int NC, bool STATS>
 __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   constexpr int NTH = step_threads<TX, TY>();
   constexpr int NT = TX * TY / NTH;        // targets per thread
   constexpr int NW = NTH / 32;
   constexpr int ROWS = NTH / TX;           // tile rows covered by one pass of the block
-  constexpr int NP = step_pass<TX, TY, NOISE, NC>();  // sub-frames per pass
+  constexpr int NP = step_pass<TX, TY, NC>();  // sub-frames per pass
   constexpr unsigned NSTAGE = step_stage<TX, TY, NP>();
   static_assert(TX % 32 == 0 && NTH % TX == 0 && NT * NTH == TX * TY, "tile shape");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -474,7 +433,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     s_over = 0;
   }
   if (tid < kStatOverLimit) tstat.tot[tid] = 0;
-  if (tid == 0) tstat.holes_ab = tstat.holes_both = tstat.pol = tstat.noise = 0;
+  if (tid == 0) tstat.holes_ab = tstat.holes_both = tstat.pol = 0;
   // z-buffers start empty; afterwards each thread clears its own slots once it has read them
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
@@ -532,22 +491,6 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   const int dr = static_cast<int>(a.dt % K);  // remainders stay below K <= 4096
   int64_t tq = 0;
   int trem = 0;
-  // noise: this gap's counter and the hot pixels among this thread's targets (bit j NC + c)
-  const bool noisy = NOISE && E.noise != 0;
-  const unsigned gap = noisy ? a.gap_in[tl.env] : 0u;
-  unsigned hot = 0;
-  if (noisy && E.hot_hz > 0.0f) {
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {  // counters use the sensor pixel index (inside the margin)
-      const unsigned pix = static_cast<unsigned>((ty0 + ROWS * j - E.margin) * (W - 2 * E.margin) +
-                                                 (tx - E.margin));
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-        if (act[j] && fires(philox4x32_10(make_uint4(pix, 0xFFFFFFFFu, 0u, 2u + 4u * c), E.key0,
-                                          E.key1).x, E.hot_fraction))
-          hot |= 1u << (j * NC + c);
-    }
-  }
 
   // Sub-frames are processed in passes of NP (i0 .. i0 + ns - 1; the last pass may hold
   // fewer): one source list serves them all, each listed source is read once and splat at
@@ -754,7 +697,6 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
     const int i = i0 + u;
     const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
     const float g = __fsub_rn(1.0f, f);
-    const int64_t tim1 = T0 + tq;  // t_{i-1}
     tq += dq;
     trem += dr;
     if (trem >= K) {
@@ -854,7 +796,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
                          (static_cast<unsigned>(tl.env) & 0xFFFFu) |
                          (static_cast<unsigned>(static_cast<uint16_t>(static_cast<int16_t>(pol * (1 + c)))) << 16))
                      << 32);
-            stage_warp<TX, TY, NP, false>(S, &s_n, tstat, stats, a, emit, rec, lanes_below, lane);
+            stage_warp<TX, TY, NP>(S, &s_n, tstat, stats, a, emit, rec, lanes_below, lane);
           }
         } else {
         // Otherwise item c of the warp (pixels in lane order, k ascending) is computed by lane
@@ -957,37 +899,6 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
           __syncwarp();  // the next chunk reuses this warp's refractory scratch
         }
         }  // crossings spread over the lanes
-        if (noisy) {  // leak, shot and hot-pixel events of this target and channel (Sec. 3.4)
-          const int64_t d = ti - tim1;
-          const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
-          const int ex = tx - E.margin, ey = ty - E.margin;  // sensor coordinates
-          const unsigned npix = static_cast<unsigned>(ey * (W - 2 * E.margin) + ex);
-          const unsigned cw = 4u * c;                        // the channel's streams
-          bool fl = false, fs = false, fh = false;
-          if (act[j]) {
-            const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), cw), E.key0, E.key1);
-            fl = E.leak_hz > 0.0f && fires(r.x, __fmul_rn(E.leak_hz, dts));
-            if (E.shot_hz > 0.0f && has) {
-              float ib = __fdiv_rn(__fsub_rn(L, E.noise_lo), __fsub_rn(E.noise_hi, E.noise_lo));
-              ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
-              fs = fires(r.y, __fmul_rn(__fmul_rn(E.shot_hz, dts), __fsub_rn(1.0f, ib)));
-            }
-            fh = ((hot >> (j * NC + c)) & 1u) && fires(r.z, __fmul_rn(E.hot_hz, dts));
-          }
-          if (__any_sync(kFull, fl || fs || fh)) {
-            uint4 rt = make_uint4(0u, 0u, 0u, 0u);
-            if (fl || fs || fh)
-              rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u + cw), E.key0, E.key1);
-            const int cp = 1 + c;
-            stage_warp(S, &s_n, tstat, stats, a, fl, make_event(noise_time(rt.x, tim1, d), ex, ey, tl.env, cp),
-                       lanes_below, lane);
-            stage_warp(S, &s_n, tstat, stats, a, fs,
-                       make_event(noise_time(rt.y, tim1, d), ex, ey, tl.env, (rt.w & 1u) ? cp : -cp),
-                       lanes_below, lane);
-            stage_warp(S, &s_n, tstat, stats, a, fh, make_event(noise_time(rt.z, tim1, d), ex, ey, tl.env, cp),
-                       lanes_below, lane);
-          }
-        }
         if (has) {
           if (nf > 0.0f) Lref[j][c] = __fadd_rn(Lref[j][c], __fmul_rn(pol > 0 ? nf : -nf, th));
           Lprev[j][c] = L;
@@ -1040,13 +951,13 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 
 // One CTA per resident slot; CTAs take tiles from the list in order (largest K first), the
 // first one by block index, the next ones from a work counter that starts at 0.
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
-__global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY, NOISE, NC>())
+template <int TX, int TY, bool TRACE, bool PACKED, int NC, bool STATS>
+__global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY, NC>())
     step_kernel(const StepArgs a) {
   __shared__ int s_tile;
   int t = blockIdx.x;
   while (t < a.n_tiles) {
-    run_tile<TX, TY, TRACE, PACKED, NOISE, NC, STATS>(a, a.tiles[t]);
+    run_tile<TX, TY, TRACE, PACKED, NC, STATS>(a, a.tiles[t]);
     __syncthreads();  // the tile's shared memory is free again
     if (threadIdx.x == 0) s_tile = static_cast<int>(gridDim.x + atomicAdd(a.work_counter, 1u));
     __syncthreads();
@@ -1056,27 +967,27 @@ __global__ void __launch_bounds__(step_threads<TX, TY>(), step_min_blocks<TX, TY
 
 }  // namespace
 
-template <int TX, int TY, bool TRACE, bool PACKED, bool NOISE, int NC, bool STATS>
+template <int TX, int TY, bool TRACE, bool PACKED, int NC, bool STATS>
 cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStream_t s) {
   // per device (the shared-memory attribute belongs to the device's context): resident CTAs
   // per SM x SMs, looked up at the first launch of this instantiation on that device
   constexpr int kMaxDevices = 64;
   static std::atomic<int> resident_of[kMaxDevices];
-  const int smem = static_cast<int>(sizeof(StepSmem<TX, TY, step_pass<TX, TY, NOISE, NC>()>));
+  const int smem = static_cast<int>(sizeof(StepSmem<TX, TY, step_pass<TX, TY, NC>()>));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   int resident = resident_of[dev].load(std::memory_order_relaxed);
   if (!resident) {
-    if ((e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NOISE, NC, STATS>,
+    if ((e = cudaFuncSetAttribute(step_kernel<TX, TY, TRACE, PACKED, NC, STATS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return e;
     int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NOISE, NC, STATS>, step_threads<TX, TY>(),
+             &per_sm, step_kernel<TX, TY, TRACE, PACKED, NC, STATS>, step_threads<TX, TY>(),
              smem)) != cudaSuccess)
       return e;
     resident = max(1, per_sm) * sms;
@@ -1084,7 +995,7 @@ cudaError_t launch_shape(const StepArgs &a, int n_tiles, int grid_cap, cudaStrea
   }
   int grid = n_tiles;
   if (grid_cap > 0) grid = min(grid, grid_cap * resident);  // persistent: a multiple of the SM slots
-  step_kernel<TX, TY, TRACE, PACKED, NOISE, NC, STATS><<<grid, step_threads<TX, TY>(), smem, s>>>(a);
+  step_kernel<TX, TY, TRACE, PACKED, NC, STATS><<<grid, step_threads<TX, TY>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -4,11 +4,11 @@
 
 namespace evis {
 
-template cudaError_t launch_shape<32, 8, true, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 16, true, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 32, true, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 16, true, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 32, true, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<128, 16, true, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 8, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 16, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, true, true, 3, true>(const StepArgs &, int, int, cudaStream_t);
 
 }  // namespace evis

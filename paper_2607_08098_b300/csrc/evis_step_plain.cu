@@ -3,12 +3,12 @@
 
 namespace evis {
 
-template cudaError_t launch_shape<32, 8, false, true, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 16, false, true, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 32, false, true, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 16, false, true, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 32, false, true, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<128, 16, false, true, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 16, false, false, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 8, false, true, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 16, false, true, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, false, true, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, false, true, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, false, true, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, false, true, 1, false>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, false, false, 1, false>(const StepArgs &, int, int, cudaStream_t);
 
 }  // namespace evis

@@ -4,11 +4,11 @@
 
 namespace evis {
 
-template cudaError_t launch_shape<32, 8, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 16, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 32, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 16, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 32, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<128, 16, false, true, false, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 8, false, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 16, false, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, false, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, false, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, false, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, false, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
 
 }  // namespace evis

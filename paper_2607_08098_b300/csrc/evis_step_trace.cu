@@ -3,11 +3,11 @@
 
 namespace evis {
 
-template cudaError_t launch_shape<32, 8, true, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 16, true, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<32, 32, true, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 16, true, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<64, 32, true, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
-template cudaError_t launch_shape<128, 16, true, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 8, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 16, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<32, 32, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 16, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<64, 32, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
+template cudaError_t launch_shape<128, 16, true, true, 1, true>(const StepArgs &, int, int, cudaStream_t);
 
 }  // namespace evis

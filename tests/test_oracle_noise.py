@@ -153,3 +153,83 @@ def test_leak_fires_in_holes_and_streams_differ_per_env(oracle_mod):
     k0 = set(zip(e0["x"].tolist(), e0["y"].tolist(), e0["t"].tolist()))
     k1 = set(zip(e1["x"].tolist(), e1["y"].tolist(), e1["t"].tolist()))
     assert len(k0 & k1) < 0.05 * min(len(k0), len(k1))
+
+
+def _subframe_of(t, dt, K):
+    """Sub-frame index i (1..K) of event times inside a gap starting at a multiple of dt
+    (dt divisible by K)."""
+    return (t % dt) // (dt // K) + 1
+
+
+def test_competing_sources_fire_at_most_once_with_the_summed_probability(oracle_mod):
+    """Leak, shot and hot noise share one draw per pixel-sub-frame: at most one noise event
+    per pixel and sub-frame, with probability p_leak + p_shot + p_hot, split by source; with
+    the probabilities summing past 1 every pixel-sub-frame fires exactly once."""
+    env = TinyEnv(W=64, H=48, K=8, c_on=0.2, c_off=0.2)
+    n = packed_total([env])
+    L = np.full(n, -5.0, np.float32)          # dark everywhere: normalised intensity 0
+    dt = 8_000_000                             # sub-frames of 1 ms
+    spec = dict(leak_hz=100.0, shot_hz=200.0, hot_hz=300.0, hot_fraction=1.0, lo=-5.0, hi=5.0, seed=3)
+    o = _static_run(oracle_mod, env, spec, [L] * 5, dt)
+    ev = o.events()
+    i = _subframe_of(ev["t"].astype(np.int64), dt, env.K)
+    key = (ev["t"].astype(np.int64) // dt) * 10**6 + (ev["y"].astype(np.int64) * env.W + ev["x"]) * 16 + i
+    assert len(np.unique(key)) == len(ev)                    # one event per pixel-sub-frame
+    trials = env.W * env.H * env.K * 4
+    p_on, p_off = 0.1 + 0.3 + 0.1, 0.1                       # shot splits its 0.2 in halves
+    for cnt, p in (((ev["p"] > 0).sum(), p_on), ((ev["p"] < 0).sum(), p_off)):
+        assert abs(cnt - trials * p) < 5 * np.sqrt(trials * p * (1 - p)), (cnt, trials * p)
+    sat = _static_run(oracle_mod, env, dict(spec, leak_hz=700.0), [L] * 2, dt).events()
+    assert len(sat) == env.W * env.H * env.K
+
+
+def test_shot_noise_follows_the_pixels_interpolated_intensity(oracle_mod):
+    """Keyframe A dark, B bright, no motion: the pixel's log intensity rises linearly over the
+    gap, so the shot probability of sub-frame i is shot_hz dts (1 - i / K), zero at i = K."""
+    env = TinyEnv(W=64, H=64, K=8, c_on=50.0, c_off=50.0)   # thresholds no signal event reaches
+    n = packed_total([env])
+    dark, bright = np.full(n, -5.0, np.float32), np.full(n, 5.0, np.float32)
+    dt = 8_000_000
+    o = _static_run(oracle_mod, env, dict(shot_hz=400.0, lo=-5.0, hi=5.0, seed=21),
+                    [dark, bright, dark, bright, dark, bright, dark], dt)
+    ev = o.events()
+    gap = ev["t"].astype(np.int64) // dt
+    rising = (gap % 2) == 0                                  # gaps dark -> bright
+    i = _subframe_of(ev["t"].astype(np.int64), dt, env.K)
+    per = np.bincount(i[rising], minlength=env.K + 1)[1:]
+    trials = env.W * env.H * 3                               # three rising gaps
+    p = 0.4 * (1.0 - np.arange(1, env.K + 1) / env.K)
+    exp = trials * p
+    assert per[-1] == 0
+    z = (per[:-1] - exp[:-1]) / np.sqrt(exp[:-1] * (1 - p[:-1]))
+    assert np.all(np.abs(z) < 5), (per, exp)
+    per_fall = np.bincount(i[~rising], minlength=env.K + 1)[1:]   # bright -> dark: rising rate
+    assert per_fall[0] < per_fall[-1] and per[0] > per[-1]
+
+
+def test_draw_and_time_words_follow_the_counter_layout(oracle_mod):
+    """The draw of sub-frame i is word (i - 1) mod 4 of Philox4x32-10 at (pixel, gap,
+    floor((i - 1) / 4), 0); a fired leak takes its time from word 0 at (pixel, gap, i, 1):
+    recomputed here from the generator (pinned by its known answers) and the binary32
+    threshold, event by event."""
+    env = TinyEnv(W=16, H=8, K=8, c_on=50.0, c_off=50.0)
+    n = packed_total([env])
+    dt = 8_000_000
+    seed = (5 << 32) | 77
+    o = _static_run(oracle_mod, env, dict(leak_hz=500.0, seed=seed), [np.zeros(n, np.float32)] * 3, dt)
+    got = oracle_mod.sort_events(o.events())
+    k = (77, 5 ^ 0)                                           # (seed low, seed high ^ env)
+    d = dt // env.K
+    thr = np.float32(np.float32(500.0) * np.float32(np.float32(d) * np.float32(1e-9))) * np.float32(2**24)
+    want = []
+    for g in range(2):
+        for pix in range(env.W * env.H):
+            for i in range(1, env.K + 1):
+                u = oracle_mod.philox(1, g, (i - 1) // 4, 0, key=k, base=pix)[0][(i - 1) % 4]
+                if np.float32(int(u) >> 8) < thr:
+                    v = int(oracle_mod.philox(1, g, i, 1, key=k, base=pix)[0][0])
+                    t0 = g * dt + (i - 1) * d
+                    want.append((t0 + (v * d >> 32), pix % env.W, pix // env.W, 0, 1))
+    want = oracle_mod.sort_events(np.array(want, dtype=got.dtype))
+    assert 100 < len(want)
+    np.testing.assert_array_equal(got, want)
