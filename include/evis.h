@@ -241,21 +241,27 @@ evis_status evis_set_state(evis_ctx *ctx, const float *Lref, const int64_t *t_la
                            const int64_t *clocks, const uint32_t *gaps);
 
 /* Sensor non-idealities of one environment (Sec. 3.4).  The paper lists leak events, shot
- * noise and hot pixels without fixing their distributions; this library draws each as at most
- * one event per pixel and sub-frame [t_{i-1}, t_i), d = t_i - t_{i-1} ns, from the counter-
- * based generator Philox4x32-10 (Salmon et al., SC 2011) keyed by (seed low 32 bits, seed
- * high 32 bits ^ environment index), so the events do not depend on the launch shape:
- *   leak: probability leak_hz * d * 1e-9, polarity +1, at every pixel, sample or not;
- *   shot: probability shot_hz * d * 1e-9 * (1 - clamp((L - lo) / (hi - lo), 0, 1)), with L
- *         the sub-frame's blended log intensity (pixels without a sample have none), random
- *         polarity; dark pixels fire most;
- *   hot:  a fixed subset of pixels (each with probability hot_fraction, the same in every
- *         gap) fires with probability hot_hz * d * 1e-9, polarity +1.
- * Counters (pixel index y * W + x, gap g, sub-frame i, stream): draws (p, g, i, 0), times
- * and shot polarity (p, g, i, 1), hot subset (p, 2^32 - 1, 0, 2); a Bernoulli draw with
- * probability q from word u fires when (float)(u >> 8) < q * 2^24 in binary32; an event's
- * time is t_{i-1} + floor(u * d / 2^32).  Noise events pass no refractory filter and leave
- * the reference levels unchanged.  g counts the keyframe gaps the context has processed. */
+ * noise and hot pixels without fixing their distributions; this library treats them as
+ * competing sources of at most one noise event per sensor pixel, channel and sub-frame
+ * [t_{i-1}, t_i), d = t_i - t_{i-1} ns, dts = d * 1e-9 s:
+ *   leak: probability p_leak = leak_hz * dts, polarity +1;
+ *   shot: p_shot = shot_hz * dts * (1 - clamp((L_i - lo) / (hi - lo), 0, 1)) with
+ *         L_i = (1 - f) LA + f LB (f = i / K) the pixel's own log intensity interpolated
+ *         between the gap's two keyframes (dark pixels fire most), random polarity;
+ *   hot:  p_hot = hot_hz * dts on a fixed subset of pixels (each with probability
+ *         hot_fraction, the same in every gap), polarity +1.
+ * One uniform word u decides: with x = (float)(u >> 8), leak if x < p_leak * 2^24, else shot
+ * if x < (p_leak + p_shot) * 2^24, else hot if x < (p_leak + p_shot + p_hot) * 2^24
+ * (binary32, 1 / (hi - lo) rounded once, sums left to right; past a total of 1 the last
+ * sources lose probability).  Words come from the counter-based generator Philox4x32-10
+ * (Salmon et al., SC 2011) keyed by (seed low 32 bits, seed high 32 bits ^ environment index)
+ * at counters (p, g, floor((i - 1) / 4), 4c), word (i - 1) mod 4, with p = y * W + x the
+ * sensor pixel index, g the count of keyframe gaps the environment has processed and c the
+ * channel; a fired event's time is t_{i-1} + floor(v * d / 2^32) with v word 0 at
+ * (p, g, i, 1 + 4c), and a shot event is ON when bit 0 of word 3 there is set; the hot
+ * subset uses word 0 at (p, 2^32 - 1, 0, 2 + 4c) against hot_fraction.  Noise events do not
+ * depend on the launch shape, pass no refractory filter and leave the reference levels
+ * unchanged. */
 typedef struct {
   float leak_hz, shot_hz, hot_hz; /* rates per pixel (1/s), finite and >= 0; all 0 = off */
   float hot_fraction;             /* 0..1 */

@@ -3,11 +3,13 @@
 // event state, so they need only the gap's two prepared keyframes.
 //
 // noise_kernel: one thread per sensor pixel and channel of one environment (grid.y) for all
-// K sub-frames.  Each pixel-sub-frame draws one 32-bit word, four consecutive sub-frames
-// sharing one Philox4x32-10 call; the word picks at most one of the competing sources by
-// cumulative thresholds (leak, then shot, then hot), and a source that fires takes its time
-// (and the shot polarity) from a second call.  A block stages its events in shared memory
-// and reserves their range of the event buffer with one atomic at the end.
+// K sub-frames.  The block first puts each sub-frame's constants (f, the sources' rates times
+// its duration, its start and duration) in shared memory.  Each pixel-sub-frame draws one
+// 32-bit word, four consecutive sub-frames sharing one Philox4x32-10 call; the word picks at
+// most one of the competing sources by cumulative thresholds (leak, then shot, then hot), and
+// a source that fires takes its time (and the shot polarity) from a second call.  A block
+// stages its events in shared memory and reserves their range of the event buffer with one
+// atomic at the end.
 #include "evis_device.cuh"
 #include "evis_internal.h"
 
@@ -52,9 +54,12 @@ __device__ __forceinline__ ulonglong2 make_event(int64_t t, int x, int y, int en
 
 constexpr int kNoiseThreads = 256;
 constexpr int kNoiseStage = 1024;   // events staged per block; more go out one atomic each
+constexpr int kSubChunk = 256;      // sub-frames whose constants a block holds at once (4 | it)
 
 __global__ void __launch_bounds__(kNoiseThreads) noise_kernel(const StepArgs a) {
   __shared__ ulonglong2 s_ev[kNoiseStage];
+  __shared__ float4 s_sf[kSubChunk];     // per sub-frame: f, leak dts, shot dts, hot dts
+  __shared__ longlong2 s_t[kSubChunk];   // per sub-frame: t_{i-1}, d = t_i - t_{i-1}
   __shared__ unsigned s_n, s_on, s_off;
   __shared__ unsigned long long s_base;
   const int env = blockIdx.y, c = blockIdx.z;
@@ -63,7 +68,6 @@ __global__ void __launch_bounds__(kNoiseThreads) noise_kernel(const StepArgs a) 
   const int m = E.margin, SW = E.W - 2 * m, SH = E.H - 2 * m;
   if (static_cast<int64_t>(blockIdx.x) * kNoiseThreads >= static_cast<int64_t>(SW) * SH) return;
   if (threadIdx.x == 0) s_n = s_on = s_off = 0u;
-  __syncthreads();
   const int sp = blockIdx.x * kNoiseThreads + threadIdx.x;   // sensor pixel index sy * SW + sx
   const bool valid = sp < SW * SH;
   const int sy = valid ? sp / SW : 0, sx = valid ? sp - sy * SW : 0;
@@ -74,63 +78,70 @@ __global__ void __launch_bounds__(kNoiseThreads) noise_kernel(const StepArgs a) 
   const unsigned gap = a.gap_in[env];
   const int K = E.K;
   const int64_t T0 = a.clock_in[env];
+  const unsigned k0 = E.key0, k1 = E.key1;
   // the hot subset: fixed per pixel and channel, the same in every gap
   const bool hot = valid && E.hot_hz > 0.0f &&
-                   below(__uint2float_rn(philox4x32_10(make_uint4(npix, 0xFFFFFFFFu, 0u, 2u + cw),
-                                                       E.key0, E.key1).x >> 8),
+                   below(__uint2float_rn(philox4x32_10(make_uint4(npix, 0xFFFFFFFFu, 0u, 2u + cw), k0, k1).x >> 8),
                          E.hot_fraction);
-  const float inv_range = __frcp_rn(__fsub_rn(E.noise_hi, E.noise_lo));
-  // t_i = T0 + floor(i dt / K), stepped with a quotient and a remainder
+  const float lo = E.noise_lo, inv_range = __frcp_rn(__fsub_rn(E.noise_hi, E.noise_lo));
+  // t_i = T0 + floor(i dt / K) = T0 + i q + floor(i r / K) with dt = q K + r (no overflow)
   const int64_t dq = a.dt / K;
-  const int dr = static_cast<int>(a.dt % K);
-  int64_t tq = 0;
-  int trem = 0;
-  uint4 r = make_uint4(0u, 0u, 0u, 0u);
+  const int64_t dr = a.dt % K;
   const unsigned lanes_below = (1u << (threadIdx.x & 31)) - 1u;
-  for (int i = 1; i <= K; ++i) {   // the same K for every thread of the block
-    const int64_t tim1 = T0 + tq;
-    tq += dq;
-    trem += dr;
-    if (trem >= K) {
-      trem -= K;
-      ++tq;
+  for (int c0 = 0; c0 < K; c0 += kSubChunk) {   // sub-frames c0 + 1 .. c0 + nk
+    const int nk = min(kSubChunk, K - c0);
+    __syncthreads();   // the previous chunk's constants are no longer read
+    for (int k = threadIdx.x; k < nk; k += kNoiseThreads) {
+      const int i = c0 + k + 1;
+      const int64_t tim1 = T0 + (i - 1) * dq + ((i - 1) * dr) / K;
+      const int64_t d = T0 + i * dq + (i * dr) / K - tim1;
+      const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
+      s_sf[k] = make_float4(__fdiv_rn(static_cast<float>(i), static_cast<float>(K)), __fmul_rn(E.leak_hz, dts),
+                            __fmul_rn(E.shot_hz, dts), __fmul_rn(E.hot_hz, dts));
+      s_t[k] = make_longlong2(tim1, d);
     }
-    const int64_t d = T0 + tq - tim1;
-    const int w = (i - 1) & 3;
-    if (w == 0) r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i - 1) >> 2, cw), E.key0, E.key1);
-    const unsigned u = w == 0 ? r.x : (w == 1 ? r.y : (w == 2 ? r.z : r.w));
-    // probabilities of this sub-frame: leak, shot (darker fires more), hot
-    const float dts = __fmul_rn(__ll2float_rn(d), 1e-9f);
-    const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
-    const float L = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, f), la), __fmul_rn(f, lb));
-    float ib = __fmul_rn(__fsub_rn(L, E.noise_lo), inv_range);
-    ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
-    const float s1 = __fmul_rn(E.leak_hz, dts);
-    const float s2 = __fadd_rn(s1, __fmul_rn(__fmul_rn(E.shot_hz, dts), __fsub_rn(1.0f, ib)));
-    const float s3 = hot ? __fadd_rn(s2, __fmul_rn(E.hot_hz, dts)) : s2;
-    const float x24 = __uint2float_rn(u >> 8);
-    const bool fire = valid && below(x24, s3);
-    const unsigned mf = __ballot_sync(kFull, fire);
-    if (mf == 0) continue;   // by far the common case
-    ulonglong2 rec = make_ulonglong2(0ull, 0ull);
-    if (fire) {
-      const bool leak = below(x24, s1), shot = !leak && below(x24, s2);
-      const uint4 rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u + cw), E.key0, E.key1);
-      const int p = (shot && !(rt.w & 1u)) ? -(1 + c) : 1 + c;
-      rec = make_event(noise_time(rt.x, tim1, d), sx, sy, env, p);
-    }
-    unsigned base = 0;
-    if ((threadIdx.x & 31) == 0) base = atomicAdd(&s_n, static_cast<unsigned>(__popc(mf)));
-    base = __shfl_sync(kFull, base, 0);
-    if (fire) {
-      const unsigned idx = base + static_cast<unsigned>(__popc(mf & lanes_below));
-      if (idx < static_cast<unsigned>(kNoiseStage)) {
-        s_ev[idx] = rec;
-      } else {   // the stage is full: straight to the buffer
-        const unsigned long long gi = atomicAdd(a.ev_count, 1ull);
-        if (gi < a.capacity) a.events[gi] = rec;
+    __syncthreads();
+    for (int k4 = 0; k4 < nk; k4 += 4) {   // one Philox call per four sub-frames
+      const uint4 r = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(c0 + k4) >> 2, cw), k0, k1);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int k = k4 + w;
+        if (k >= nk) break;   // uniform over the block
+        const unsigned u = w == 0 ? r.x : (w == 1 ? r.y : (w == 2 ? r.z : r.w));
+        const float4 q = s_sf[k];   // f, leak dts, shot dts, hot dts
+        const float L = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, q.x), la), __fmul_rn(q.x, lb));
+        float ib = __fmul_rn(__fsub_rn(L, lo), inv_range);
+        ib = ib < 0.0f ? 0.0f : (ib > 1.0f ? 1.0f : ib);
+        const float s1 = q.y;
+        const float s2 = __fadd_rn(s1, __fmul_rn(q.z, __fsub_rn(1.0f, ib)));
+        const float s3 = hot ? __fadd_rn(s2, q.w) : s2;
+        const float x24 = __uint2float_rn(u >> 8);
+        const bool fire = valid && below(x24, s3);
+        const unsigned mf = __ballot_sync(kFull, fire);
+        if (mf == 0) continue;   // by far the common case
+        ulonglong2 rec = make_ulonglong2(0ull, 0ull);
+        if (fire) {
+          const int i = c0 + k + 1;
+          const bool leak = below(x24, s1), shot = !leak && below(x24, s2);
+          const uint4 rt = philox4x32_10(make_uint4(npix, gap, static_cast<unsigned>(i), 1u + cw), k0, k1);
+          const int p = (shot && !(rt.w & 1u)) ? -(1 + c) : 1 + c;
+          const longlong2 tt = s_t[k];
+          rec = make_event(noise_time(rt.x, tt.x, tt.y), sx, sy, env, p);
+        }
+        unsigned base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(&s_n, static_cast<unsigned>(__popc(mf)));
+        base = __shfl_sync(kFull, base, 0);
+        if (fire) {
+          const unsigned idx = base + static_cast<unsigned>(__popc(mf & lanes_below));
+          if (idx < static_cast<unsigned>(kNoiseStage)) {
+            s_ev[idx] = rec;
+          } else {   // the stage is full: straight to the buffer
+            const unsigned long long gi = atomicAdd(a.ev_count, 1ull);
+            if (gi < a.capacity) a.events[gi] = rec;
+          }
+          if (a.stats) atomicAdd(static_cast<long long>(rec.y) < 0 ? &s_off : &s_on, 1u);
+        }
       }
-      if (a.stats) atomicAdd(static_cast<long long>(rec.y) < 0 ? &s_off : &s_on, 1u);
     }
   }
   __syncthreads();
