@@ -721,7 +721,72 @@ def config3_leg(ev, args):
             "batched_over_per_env": vals["batched_step"] / vals["per_env_contexts"],
             "graph_over_per_env": vals["batched_graph_autotuned"] / vals["per_env_contexts"],
             "events_last_step": n_events, "event_buffer_overflow": n_events > sum(cap_env),
-            "autotuned_tile_shapes": classes, "autotune_best_ms": best}
+            "autotuned_tile_shapes": classes, "autotune_best_ms": best,
+            "graph_on_config1": graph_small_leg(ev)}
+
+
+def graph_small_leg(ev, reps=200):
+    """The graph form on the smallest workload, config 1 (one 128x128 environment, K=8,
+    131 k pixel-substeps per gap, a few microseconds of kernel work).  `reps` consecutive gaps
+    of the same keyframe pair (identical device work on both paths): through evis_step
+    (caller's buffers kept) and through evis_replay of a captured graph whose input buffers
+    already hold the keyframe (where a renderer would write it).
+    CUDA events around each whole run of gaps, so the time includes the device idling while
+    the host launches, and the host's wall clock; per gap.  Then the host's own cost per call,
+    issued while the stream is held by a spin kernel.  At this size a gap is bound by the step
+    kernel's latency (its passes' dependent phases in 32 CTAs), not by launches."""
+    import time
+    import torch
+    import scenes
+    w = scenes.config1()
+    dev = upload_keyframes(w, 11, "I")
+    stream = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(stream):
+        def run(name, one_gap):
+            for k in range(1, 11):
+                one_gap(k)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            a.record(stream)
+            for j in range(reps):
+                one_gap(1 + j % 10)
+            b.record(stream)
+            b.synchronize()
+            wall = time.perf_counter() - t0
+            # the host's own cost per call: the calls are issued while the stream is held by
+            # a spin kernel, so none of them waits for the device
+            torch.cuda._sleep(int(1e9))
+            t1 = time.perf_counter()
+            for j in range(reps):
+                one_gap(1 + j % 10)
+            host = time.perf_counter() - t1
+            torch.cuda.synchronize()
+            out[name] = {"device_us_per_gap": a.elapsed_time(b) * 1e3 / reps,
+                         "wall_us_per_gap": wall * 1e6 / reps,
+                         "host_us_per_call": host * 1e6 / reps}
+
+        cap = (2 * reps + 12) * 131072
+        step_ctx = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM | ev.KEEP_INPUTS, capacity=cap,
+                              stream=stream)
+        step_ctx.step(*dev[0], w.dt_ns)
+        run("evis_step", lambda k: step_ctx.step(*dev[1], w.dt_ns))
+        step_ctx.close()
+        graph = ev.Context(w.envs, eps=1e-4, flags=ev.IN_LUM, capacity=cap, stream=stream)
+        graph.step(*dev[0], w.dt_ns)
+        graph.step(*dev[1], w.dt_ns)
+        graph.capture(w.dt_ns)
+        graph.write_inputs(*dev[1])
+        run("evis_replay", lambda k: graph.replay())
+        graph.close()
+    del dev
+    out["workload"] = ("config 1: one env at 128x128, K=8, 131,072 pixel-substeps per gap, "
+                       "linear inputs, the same keyframe pair every gap")
+    out["gaps"] = reps
+    out["replay_speedup_device"] = out["evis_step"]["device_us_per_gap"] / out["evis_replay"]["device_us_per_gap"]
+    out["replay_host_saving"] = out["evis_step"]["host_us_per_call"] / out["evis_replay"]["host_us_per_call"]
+    return out
 
 
 def envs64_arm(args, world, rank, local):
