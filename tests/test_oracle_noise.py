@@ -82,20 +82,25 @@ def test_leak_rate_times_and_isolation(oracle_mod):
 
 
 def test_shot_noise_follows_darkness(oracle_mod):
-    env = TinyEnv(W=64, H=32, K=8, c_on=0.2, c_off=0.2)
+    """Only dark pixels fire, with random polarity; a pixel darker than `lo` fires at the
+    same rate as one at `lo` (the normalised intensity clamps at 0)."""
+    env = TinyEnv(W=64, H=48, K=8, c_on=0.2, c_off=0.2)
     n = packed_total([env])
     L = np.zeros(n, np.float32)
-    L[: env.W * env.H // 2] = -5.0      # top half dark (normalised intensity 0)
-    L[env.W * env.H // 2:] = 5.0        # bottom half bright (normalised intensity 1)
+    band = env.W * env.H // 3
+    L[:band] = -10.0                    # top third darker than lo
+    L[band:2 * band] = -5.0             # middle third at lo (normalised intensity 0)
+    L[2 * band:env.W * env.H] = 5.0     # bottom third bright (normalised intensity 1)
     o = _static_run(oracle_mod, env, dict(shot_hz=20.0, lo=-5.0, hi=5.0, seed=7), [L] * 4, 10_000_000)
     ev = o.events()
     assert len(ev) > 50
-    assert np.all(ev["y"] < env.H // 2)                     # only the dark half fires
+    assert np.all(ev["y"] < 2 * env.H // 3)                 # only the dark two thirds fire
     pos = (ev["p"] > 0).mean()
     assert abs(pos - 0.5) < 5 * np.sqrt(0.25 / len(ev))      # random polarity
-    trials = env.W * env.H // 2 * env.K * 3
+    trials = band * env.K * 3
     p = 20.0 * 10_000_000 / env.K * 1e-9
-    assert abs(len(ev) - trials * p) < 5 * np.sqrt(trials * p)
+    for rows in (ev["y"] < env.H // 3, (ev["y"] >= env.H // 3) & (ev["y"] < 2 * env.H // 3)):
+        assert abs(rows.sum() - trials * p) < 5 * np.sqrt(trials * p), (rows.sum(), trials * p)
 
 
 def test_hot_pixels_are_a_fixed_subset(oracle_mod):
