@@ -828,6 +828,31 @@ def test_extreme_shapes_and_long_k(ev, oracle_mod, tile):
     assert evs["x"].max() >= 65000 and evs["y"].max() >= 65000
 
 
+def test_noise_with_long_k(ev, oracle_mod):
+    """Sensor noise over K = 700, 257 and 300 sub-frames: the noise kernel's per-sub-frame
+    constants come in chunks of 256, and the last block of four sub-frames is partial."""
+    rng = np.random.default_rng(43)
+    envs = [TinyEnv(W=1, H=1, K=700, c_on=0.05, c_off=0.05),
+            TinyEnv(W=4, H=3, K=257, c_on=0.05, c_off=0.05, refractory_ns=30_000),
+            TinyEnv(W=300, H=5, K=300, c_on=0.2, c_off=0.2)]
+    n = packed_total(envs)
+
+    class KF:
+        pass
+
+    kfs = []
+    for _ in range(3):
+        k = KF()
+        k.mv = rng.uniform(-2.5, 2.5, size=(n, 2)).astype(np.float32)
+        k.Z = rng.uniform(1, 5, size=n).astype(np.float32)
+        k.L = rng.normal(0, 1, size=n).astype(np.float32)
+        kfs.append(k)
+    noise = [dict(leak_hz=200.0, shot_hz=400.0, hot_hz=900.0, hot_fraction=0.2, lo=-2.0, hi=2.0,
+                  seed=77 + i) for i in range(3)]
+    evs = run_both(ev, oracle_mod, envs, kfs, 16_666_667, noise=noise, capacity=1 << 22)
+    assert len(evs) > 1000
+
+
 @pytest.mark.parametrize("tile", [(32, 16), (64, 16), (32, 8)])
 def test_crossing_limit_is_reported(ev, oracle_mod, tile):
     """Pixel-sub-frames whose Eq. 4 count n exceeds the per-pixel emission limit (4096):

@@ -81,3 +81,28 @@ def test_voxel_grid_of_a_synthesis_step(ev, oracle_mod, scenes_mod):
     _, want = oracle_mod.voxel_grid(recs, segs, bins=128)
     np.testing.assert_array_equal(g1.cpu().numpy(), want)
     ctx.close()
+
+
+def test_voxel_grid_many_environments(ev, oracle_mod):
+    """100 environments (more than the record passes stage in shared memory, so their
+    descriptors are read from global memory), sizes from 1x1 to 40x33, ragged row segments."""
+    rng = np.random.default_rng(11)
+    segs = [(int(rng.integers(1, 41)), int(rng.integers(1, 34)), int(t0), int(t0) + int(rng.integers(1000, 10**8)))
+            for t0 in rng.integers(0, 10**9, 100)]
+    rec = _records(rng, 300_000, segs)
+    _, want = oracle_mod.voxel_grid(rec, segs, bins=16)
+    d = torch.from_numpy(rec.view(np.int64).reshape(-1)).cuda()
+    got = ev.voxel_grid(d.data_ptr(), None, rec.size, segs, 16).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+
+
+def test_voxel_grid_without_records(ev, oracle_mod):
+    """No records (max_events = 0, or a device count of 0): every plane is empty, so the
+    grid is all zeros."""
+    segs = [(64, 48, 0, 1_000_000), (37, 23, 5, 99)]
+    d = torch.zeros(2 * 16, dtype=torch.int64, device="cuda")
+    g0 = ev.voxel_grid(d.data_ptr(), None, 0, segs, 7)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    g1 = ev.voxel_grid(d.data_ptr(), cnt.data_ptr(), 16, segs, 7)
+    assert g0.numel() == 2 * 7 * (64 * 48 + 37 * 23)
+    assert not torch.any(g0) and not torch.any(g1)
