@@ -366,7 +366,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   __shared__ unsigned s_n, s_flush, s_nitems[2], s_novf[2], s_nfull[2], s_p1[2], s_arrive;
   __shared__ unsigned long long s_base;
   __shared__ TileStats tstat;  // this tile's statistics
-  __shared__ float s_fs[2][NP], s_gs[2][NP];  // the pass's fractions (passes of up to three)
+  __shared__ float s_fs[2][NP], s_gs[2][NP];  // the pass's fractions f and 1 - f
   __shared__ int s_nc[2], s_over, s_ovf_full[2];
 
   const DevEnv E = a.envs[tl.env];
@@ -499,9 +499,11 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
   for (int i0 = 1; i0 <= K; i0 += NP) {
     const int ns = min(NP, K - i0 + 1);
     // The pass's fractions f and 1 - f (past ns: the last sub-frame's again, which extends
-    // no bound): for passes of up to three in shared memory (double-buffered by pass
-    // parity), which frees registers through the splat (64 x 346x260, 32 x 16 tiles: 2.82 ->
-    // 2.76 ms); for passes of four in registers (96 x 640x480, 64 x 16: 19.80 against 19.96).
+    // no bound), in shared memory (double-buffered by pass parity) for phase 3 of every
+    // pass, which then divides no more (2.76 -> 2.74 ms on 64 x 346x260).  The splat reads
+    // them there for passes of up to three, which frees registers through it (64 x 346x260,
+    // 32 x 16 tiles: 2.82 -> 2.76 ms), and from registers for passes of four (96 x 640x480,
+    // 64 x 16: 19.80 against 19.96).
     const int par = ((i0 - 1) / NP) & 1;
     constexpr bool kSharedF = NP <= 3;
     float fs[NP], gs[NP];
@@ -510,7 +512,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
       fs[u] = __fdiv_rn(static_cast<float>(min(i0 + u, K)), static_cast<float>(K));
       gs[u] = __fsub_rn(1.0f, fs[u]);
     }
-    if (kSharedF && tid < NP) {
+    if (tid < NP) {
 #pragma unroll
       for (int u = 0; u < NP; ++u)
         if (u == tid) {
@@ -695,8 +697,7 @@ __device__ __forceinline__ void run_tile(const StepArgs &a, const Tile tl) {
 #pragma unroll 1
     for (int u = 0; u < ns; ++u) {
     const int i = i0 + u;
-    const float f = __fdiv_rn(static_cast<float>(i), static_cast<float>(K));
-    const float g = __fsub_rn(1.0f, f);
+    const float f = s_fs[par][u], g = s_gs[par][u];   // i / K and 1 - i / K
     tq += dq;
     trem += dr;
     if (trem >= K) {

@@ -1,5 +1,5 @@
-// Explicit instantiations of the synthesis kernel: colour events (three channels, sensor
-// noise compiled in), every tile shape.
+// Explicit instantiations of the synthesis kernel: colour events (three channels, with the
+// statistics code), every tile shape.
 #include "evis_step.cuh"
 
 namespace evis {

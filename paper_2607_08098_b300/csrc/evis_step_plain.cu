@@ -1,4 +1,5 @@
-// Explicit instantiations of the synthesis kernel: production variants without sensor noise, every tile shape, and the unpacked 64x16 variant of the allocation-free entry point.
+// Explicit instantiations of the synthesis kernel: production variants without the statistics
+// code, every tile shape, and the unpacked 64x16 variant of the allocation-free entry point.
 #include "evis_step.cuh"
 
 namespace evis {

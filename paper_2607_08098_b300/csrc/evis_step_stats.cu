@@ -1,5 +1,5 @@
-// Explicit instantiations of the synthesis kernel: production variants without sensor noise that
-// collect the statistics of EVIS_STATS, every tile shape.
+// Explicit instantiations of the synthesis kernel: production variants that collect the
+// statistics of EVIS_STATS, every tile shape.
 #include "evis_step.cuh"
 
 namespace evis {

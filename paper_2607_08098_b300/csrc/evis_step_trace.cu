@@ -1,4 +1,5 @@
-// Explicit instantiations of the synthesis kernel: debug-trace variants (sensor noise compiled in), every tile shape.
+// Explicit instantiations of the synthesis kernel: debug-trace variants (with the statistics
+// code), every tile shape.
 #include "evis_step.cuh"
 
 namespace evis {
