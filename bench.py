@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--hs-envs", type=int, default=1024,
                     help="environments of the high-speed workload (640x480, K=32)")
     ap.add_argument("--envs", type=int, default=64, help="environments of the 346x260 workload")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--tile", default=None,
                     help="WxH: fixed tile shape instead of the autotuner's (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -348,7 +348,9 @@ def e2e_leg(ev, w, dev, n_steps, capacity, flags_host):
     """Host buffers in, events out, through the public API: pinned host keyframes copied by
     evis_step_host, every gap's events copied to pinned host memory by
     evis_read_events_async (while the next gap runs), all inside the timed region.  The
-    copy of a gap completes before the next one starts, so one destination buffer serves."""
+    copy of a gap completes before the next one starts, so one destination buffer serves.
+    Six gaps by default: with two, filling and draining the pipeline (the first gap's input
+    copy and compute, the last gap's read-back) was a third of the time."""
     import torch
     n = n_steps
     need = sum(t.numel() * 4 for t in dev[0]) * (n + 1) + capacity * 16
