@@ -491,7 +491,9 @@ __global__ void __launch_bounds__(kVoxThreads) voxel_region(const VoxelEnvDev *_
       }
     } else {
       const int64_t plane_px = q.plane_px, base = q.base;
-      if (q.nx == kSeg && (base & 3) == 0 && (plane_px & 3) == 0) {
+      // 16-byte stores need every plane's row start on a 16-byte boundary (the grid itself
+      // need only be 4-byte aligned)
+      if (q.nx == kSeg && (reinterpret_cast<uintptr_t>(grid + base) & 15) == 0 && (plane_px & 3) == 0) {
         // four pixels per thread: eight threads per plane row, 32 planes per pass of the block
         const int px = (tid & 7) * 4;
         for (int pl = tid >> 3; pl < q.np; pl += kVoxThreads / 8) {

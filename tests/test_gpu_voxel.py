@@ -106,3 +106,26 @@ def test_voxel_grid_without_records(ev, oracle_mod):
     g1 = ev.voxel_grid(d.data_ptr(), cnt.data_ptr(), 16, segs, 7)
     assert g0.numel() == 2 * 7 * (64 * 48 + 37 * 23)
     assert not torch.any(g0) and not torch.any(g1)
+
+
+def test_voxel_grid_into_a_grid_not_on_a_16_byte_boundary(ev, oracle_mod):
+    """A grid pointer that is 4-byte but not 16-byte aligned (allowed by the header) takes the
+    one-pixel-per-lane stores and gives the same grid."""
+    import ctypes
+    rng = np.random.default_rng(21)
+    segs = [(64, 48, 1_000, 500_001_000), (640, 2, 0, 123_456_789)]
+    bins = 8
+    rec = _records(rng, 100_000, segs)
+    _, want = oracle_mod.voxel_grid(rec, segs, bins=bins)
+    d = torch.from_numpy(rec.view(np.int64).reshape(-1)).cuda()
+    n_vox = sum(2 * bins * W * H for W, H, _, _ in segs)
+    out = torch.zeros(n_vox + 4, dtype=torch.float32, device="cuda")
+    wsb = ev.voxel_workspace_size(segs, bins, rec.size)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    arr = ev._voxel_envs(segs)
+    st = ev.lib().evis_voxel_grid(d.data_ptr(), None, rec.size, ctypes.addressof(arr), len(segs), bins,
+                                  ws.data_ptr(), wsb, out.data_ptr() + 4, None)
+    assert st == ev.OK
+    got = out[1:1 + n_vox].cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert out[0].item() == 0.0 and not torch.any(out[1 + n_vox:])
