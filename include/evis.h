@@ -320,7 +320,7 @@ evis_status evis_voxel_workspace_size(const evis_voxel_env *envs, int32_t n_envs
  * max_events when count is NULL.  grid is a device float array, per environment in order
  * [2][bins][height][width].  workspace is device memory of evis_voxel_workspace_size(...,
  * max_events, ...) bytes (its contents need not be initialised).  events and workspace must
- * be 16-byte aligned, grid 4-byte aligned.  Asynchronous on stream; EVIS_ERR_INVALID_ARG
+ * be 16-byte aligned, count 8-byte and grid 4-byte aligned.  Asynchronous on stream; EVIS_ERR_INVALID_ARG
  * (evis_last_error(NULL) says why) before any work for a bad argument. */
 evis_status evis_voxel_grid(const evis_event *events, const uint64_t *count, int64_t max_events,
                             const evis_voxel_env *envs, int32_t n_envs, int32_t bins,

@@ -608,8 +608,8 @@ extern "C" evis_status evis_voxel_grid(const evis_event *events, const uint64_t 
   if (max_events > 0 && !events) return reject("events is null");
   if (!workspace || !grid) return reject("null workspace or grid");
   if (reinterpret_cast<uintptr_t>(events) % 16 || reinterpret_cast<uintptr_t>(workspace) % 16 ||
-      reinterpret_cast<uintptr_t>(grid) % 4)
-    return reject("events and workspace need 16-byte alignment, grid 4-byte");
+      reinterpret_cast<uintptr_t>(grid) % 4 || reinterpret_cast<uintptr_t>(count) % 8)
+    return reject("events and workspace need 16-byte alignment, count 8-byte, grid 4-byte");
   const Layout L = layout(n_envs, bins, R, max_events);
   if (workspace_bytes < static_cast<int64_t>(L.total))
     return reject("workspace smaller than evis_voxel_workspace_size");

@@ -117,6 +117,21 @@ def test_voxel_arguments_checked_without_a_gpu(evis, seg, bins):
         evis.voxel_workspace_size([seg], bins)
 
 
+def test_voxel_grid_rejects_misaligned_pointers_without_a_gpu(evis):
+    """Alignment is checked on the host before any CUDA call (the pointers here are never
+    dereferenced): events and workspace 16 bytes, count 8, grid 4."""
+    import ctypes
+    segs = [(8, 8, 0, 1000)]
+    arr = evis._voxel_envs(segs)
+    L = evis.lib()
+    ok = dict(events=0x10000, count=0x20000, ws=0x30000, grid=0x40000)
+    for key, bad in (("events", 0x10008), ("count", 0x20004), ("ws", 0x30008), ("grid", 0x40002)):
+        p = dict(ok, **{key: bad})
+        st = L.evis_voxel_grid(p["events"], p["count"], 10, ctypes.addressof(arr), 1, 4, p["ws"],
+                               1 << 30, p["grid"], None)
+        assert st == evis.ERR_INVALID_ARG, key
+
+
 def test_voxel_workspace_size(evis):
     """Two uint64 per region (a row segment of 32 pixels across 256 planes), one uint32 entry
     per record, two once the planes of an environment span two groups (bins > 128)."""
