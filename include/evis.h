@@ -145,7 +145,8 @@ evis_status evis_create(const evis_env_desc *envs, int32_t n_envs, const evis_co
  * their events (Sec. 3.2 Eq. 4, Sec. 3.4) to the device buffer; sub-frame i of environment
  * e is at t = T_e + (i * dt_ns) / K_e, T_e being the previous keyframe's time.
  * Asynchronous; inputs may be reused once the stream has passed this call, except under
- * EVIS_KEEP_INPUTS.  0 < dt_ns <= 2^40. */
+ * EVIS_KEEP_INPUTS.  0 < dt_ns <= 2^40.  frames and depth must be 4-byte aligned, mv 8-byte
+ * (it is read as float pairs); EVIS_ERR_INVALID_ARG otherwise. */
 evis_status evis_step(evis_ctx *ctx, const float *frames, const float *mv, const float *depth,
                       int64_t dt_ns);
 
@@ -320,8 +321,9 @@ evis_status evis_voxel_workspace_size(const evis_voxel_env *envs, int32_t n_envs
  * max_events when count is NULL.  grid is a device float array, per environment in order
  * [2][bins][height][width].  workspace is device memory of evis_voxel_workspace_size(...,
  * max_events, ...) bytes (its contents need not be initialised).  events and workspace must
- * be 16-byte aligned, count 8-byte and grid 4-byte aligned.  Asynchronous on stream; EVIS_ERR_INVALID_ARG
- * (evis_last_error(NULL) says why) before any work for a bad argument. */
+ * be 16-byte aligned, count 8-byte and grid 4-byte aligned.  Asynchronous on stream;
+ * EVIS_ERR_INVALID_ARG (evis_last_error(NULL) says why) before any work for a bad
+ * argument. */
 evis_status evis_voxel_grid(const evis_event *events, const uint64_t *count, int64_t max_events,
                             const evis_voxel_env *envs, int32_t n_envs, int32_t bins,
                             void *workspace, int64_t workspace_bytes, float *grid,
@@ -333,7 +335,8 @@ evis_status evis_voxel_grid(const evis_event *events, const uint64_t *count, int
  * source index, all ones = no source) and the blended log-intensity (Lint[(i-1) * H*W + p],
  * NaN where the pixel got no sample).  keys / Lint are device arrays of
  * sum_e K_e * 2 * H_e * W_e uint64 and sum_e K_e * H_e * W_e floats.  With a margin, only
- * the sensor's entries are written; the margin's are left as they were. */
+ * the sensor's entries are written; the margin's are left as they were.  keys must be
+ * 8-byte aligned, Lint 4-byte, the inputs as for evis_step. */
 evis_status evis_step_trace(evis_ctx *ctx, const float *frames, const float *mv,
                             const float *depth, int64_t dt_ns, uint64_t *keys, float *Lint);
 
@@ -362,7 +365,8 @@ evis_status evis_get_tile_shapes(evis_ctx *ctx, int32_t *tile_w, int32_t *tile_h
  * warm-up, and keeps the fastest shape per class.  Nothing is consumed: the per-pixel
  * state and the event buffer's count are restored, so the caller then steps with the same
  * B as usual.  *best_ms (optional) receives the sum over classes of the best times.
- * EVIS_ERR_STATE before the first keyframe.  Synchronises; invalidates captured graphs. */
+ * Alignment as for evis_step.  EVIS_ERR_STATE before the first keyframe.  Synchronises;
+ * invalidates captured graphs. */
 evis_status evis_autotune(evis_ctx *ctx, const float *frames, const float *mv,
                           const float *depth, int64_t dt_ns, int32_t reps, float *best_ms);
 
@@ -400,7 +404,9 @@ evis_status evis_replay(evis_ctx *ctx);
  * vectors, depth, start-of-gap reference levels Lref0) and C [n_envs]; counts is
  * [2][H][W] per environment at offset 2 * pix_off.  The workspace (device, at least
  * evis_soft_workspace_size bytes) keeps what the backward needs; the forward is
- * deterministic.  Asynchronous on stream. */
+ * deterministic.  Motion vectors (and, in the backward, their gradients) must be 8-byte
+ * aligned, the other arrays 4-byte, the workspace 16-byte; EVIS_ERR_INVALID_ARG otherwise.
+ * Asynchronous on stream. */
 evis_status evis_soft_workspace_size(const evis_env_desc *envs, int32_t n_envs, int64_t *bytes);
 evis_status evis_soft_forward(const evis_env_desc *envs, int32_t n_envs, float tau, float delta,
                               const float *L_A, const float *L_B, const float *mv_A,
@@ -444,7 +450,9 @@ evis_status evis_profile_read(evis_ctx *ctx, float *ms, int32_t cap, int32_t *n_
  * Sub-frame i is at t_a_ns + (i * dt_ns) / K.  The results equal those of evis_step.
  * flags may hold EVIS_MODE_B_PRIMARY and EVIS_TIE_INDEX only.
  *
- * Invalid arguments return EVIS_ERR_INVALID_ARG before any work.
+ * Invalid arguments return EVIS_ERR_INVALID_ARG before any work, among them misaligned
+ * buffers: the float arrays need 4-byte alignment, mv_A, mv_B, t_last and count 8-byte,
+ * events 16-byte.
  *
  * Limits: width, height <= 4096 and width * height <= 1048576, set by a static scratch
  * array of about 1.3 MB that every GPU loading the library holds until the process exits

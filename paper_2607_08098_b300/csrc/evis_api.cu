@@ -336,6 +336,8 @@ evis::StepArgs step_args(const evis_ctx *c, const KeyframeB &B, int64_t dt) {
 evis_status do_step(evis_ctx *c, const float *frames, const float *mv, const float *depth,
                     int64_t dt, uint64_t *tr_keys, float *tr_L) {
   if (!frames || !mv || !depth) return fail(c, EVIS_ERR_INVALID_ARG, "null input pointer");
+  if (!evis::aligned(frames, 4) || !evis::aligned(mv, 8) || !evis::aligned(depth, 4))
+    return fail(c, EVIS_ERR_INVALID_ARG, "frames and depth need 4-byte alignment, mv 8-byte");
   if (dt <= 0 || dt > kMaxDt) return fail(c, EVIS_ERR_INVALID_ARG, "dt_ns must be in 1..2^40");
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
@@ -520,6 +522,8 @@ evis_status evis_step_trace(evis_ctx *c, const float *frames, const float *mv,
                             const float *depth, int64_t dt_ns, uint64_t *keys, float *Lint) {
   if (!c) return EVIS_ERR_INVALID_ARG;
   if (!keys || !Lint) return fail(c, EVIS_ERR_INVALID_ARG, "null trace buffer");
+  if (!evis::aligned(keys, 8) || !evis::aligned(Lint, 4))
+    return fail(c, EVIS_ERR_INVALID_ARG, "trace buffers need 8-byte (keys) and 4-byte alignment");
   drop_graphs(c);
   return do_step(c, frames, mv, depth, dt_ns, keys, Lint);
 }
@@ -900,7 +904,8 @@ evis_status evis_get_tile_shapes(evis_ctx *c, int32_t *tile_w, int32_t *tile_h) 
 evis_status evis_autotune(evis_ctx *c, const float *frames, const float *mv, const float *depth,
                           int64_t dt_ns, int32_t reps, float *best_ms) {
   if (!c) return EVIS_ERR_INVALID_ARG;
-  if (!frames || !mv || !depth || reps < 1 || reps > 100 || dt_ns <= 0 || dt_ns > kMaxDt)
+  if (!frames || !mv || !depth || reps < 1 || reps > 100 || dt_ns <= 0 || dt_ns > kMaxDt ||
+      !evis::aligned(frames, 4) || !evis::aligned(mv, 8) || !evis::aligned(depth, 4))
     return fail(c, EVIS_ERR_INVALID_ARG, "bad autotune arguments");
   if (!c->have_A) return fail(c, EVIS_ERR_STATE, "autotune needs a retained keyframe (step once first)");
   cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -148,6 +148,11 @@ bool tile_shape_supported(int tile_w, int tile_h);
 // planes), a.clock_in, a.gap_in, a.dt, a.nc, a.plane and writes a.events, a.ev_count and,
 // with a.stats, a.env_stats.  max_px: the largest sensor (pixels) of those environments.
 cudaError_t launch_noise(const StepArgs &a, int n_envs, int max_px, cudaStream_t s);
+// Host-side check that a device pointer is a multiple of align bytes (kernels read motion
+// vectors as float2, event records as 16-byte pairs); null counts as aligned.
+inline bool aligned(const void *p, size_t align) {
+  return reinterpret_cast<uintptr_t>(p) % align == 0;
+}
 // Error text reported by evis_last_error(NULL) for calls made without a context.
 void set_detached_error(const std::string &msg);
 cudaError_t launch_log(const float *in, int64_t n, uint32_t mode, float eps, float *out,

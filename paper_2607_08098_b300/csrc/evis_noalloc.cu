@@ -111,6 +111,11 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
     return reject("only EVIS_MODE_B_PRIMARY and EVIS_TIE_INDEX are accepted (inputs are log-intensity)");
   if (!L_A || !mv_A || !Z_A || !L_B || !mv_B || !Z_B || !Lref || !count)
     return reject("null buffer");  // count: two 64-bit words (events, pixels over the limit)
+  if (!evis::aligned(L_A, 4) || !evis::aligned(Z_A, 4) || !evis::aligned(L_B, 4) ||
+      !evis::aligned(Z_B, 4) || !evis::aligned(Lref, 4) || !evis::aligned(mv_A, 8) ||
+      !evis::aligned(mv_B, 8) || !evis::aligned(t_last, 8) || !evis::aligned(count, 8) ||
+      !evis::aligned(events, 16))
+    return reject("misaligned buffer: floats 4 bytes, mv, t_last and count 8, events 16");
   if (d.refractory_ns > 0 && !t_last) return reject("t_last is required with a refractory period");
   if (dt_ns <= 0 || dt_ns > (int64_t(1) << 40)) return reject("dt_ns must be in 1..2^40");
   if (capacity < 0 || capacity > (int64_t(1) << 40) || (capacity > 0 && !events))

@@ -425,6 +425,11 @@ evis_status evis_soft_forward(const evis_env_desc *envs, int32_t n_envs, float t
   if (!(tau > 0.0f) || !(delta >= 0.0f) || !LA || !LB || !mvA || !mvB || !ZA || !ZB || !Lref0 ||
       !C || !counts)
     return EVIS_ERR_INVALID_ARG;
+  if (!evis::aligned(mvA, 8) || !evis::aligned(mvB, 8) || !evis::aligned(LA, 4) ||
+      !evis::aligned(LB, 4) || !evis::aligned(ZA, 4) || !evis::aligned(ZB, 4) ||
+      !evis::aligned(Lref0, 4) || !evis::aligned(C, 4) || !evis::aligned(counts, 4) ||
+      !evis::aligned(workspace, 16))
+    return EVIS_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SoftArgs a{};
   int max_hw = 0;
@@ -456,6 +461,12 @@ evis_status evis_soft_backward(const evis_env_desc *envs, int32_t n_envs, float 
                                int64_t workspace_bytes, evis_stream_t stream) {
   if (!(tau > 0.0f) || !(delta >= 0.0f) || !LA || !LB || !mvA || !mvB || !ZA || !ZB || !C ||
       !gcounts || !dLA || !dLB || !dmvA || !dmvB || !dC)
+    return EVIS_ERR_INVALID_ARG;
+  if (!evis::aligned(mvA, 8) || !evis::aligned(mvB, 8) || !evis::aligned(dmvA, 8) ||
+      !evis::aligned(dmvB, 8) || !evis::aligned(LA, 4) || !evis::aligned(LB, 4) ||
+      !evis::aligned(ZA, 4) || !evis::aligned(ZB, 4) || !evis::aligned(C, 4) ||
+      !evis::aligned(gcounts, 4) || !evis::aligned(dLA, 4) || !evis::aligned(dLB, 4) ||
+      !evis::aligned(dC, 4) || !evis::aligned(workspace, 16))
     return EVIS_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   SoftArgs a{};

@@ -132,6 +132,29 @@ def test_voxel_grid_rejects_misaligned_pointers_without_a_gpu(evis):
         assert st == evis.ERR_INVALID_ARG, key
 
 
+def test_misaligned_inputs_rejected_without_a_gpu(evis):
+    """Motion vectors are read as float pairs and event records as 16-byte pairs: the
+    allocation-free step and the soft surrogate reject misaligned device pointers on the host,
+    before any CUDA call (the fake addresses here are never dereferenced)."""
+    import ctypes
+    L = evis.lib()
+    env = evis.EnvDesc(16, 8, 4, 0.2, 0.2, 0, None, None, 0, 0)
+    b = 0x100000
+    na = dict(L_A=b, mv_A=b, Z_A=b, L_B=b, mv_B=b, Z_B=b, Lref=b, t_last=b, events=b, count=b)
+    for key, off in (("mv_A", 4), ("mv_B", 4), ("L_A", 2), ("t_last", 4), ("count", 4), ("events", 8)):
+        p = dict(na, **{key: b + off})
+        st = L.evis_step_noalloc(ctypes.byref(env), 0, p["L_A"], p["mv_A"], p["Z_A"], p["L_B"],
+                                 p["mv_B"], p["Z_B"], p["Lref"], p["t_last"], 0, 1000, p["events"],
+                                 p["count"], 10, None)
+        assert st == evis.ERR_INVALID_ARG, key
+    sf = dict(LA=b, LB=b, mvA=b, mvB=b, ZA=b, ZB=b, Lref0=b, C=b, counts=b, ws=b)
+    for key, off in (("mvA", 4), ("mvB", 4), ("ZB", 2), ("ws", 8)):
+        p = dict(sf, **{key: b + off})
+        st = L.evis_soft_forward(ctypes.byref(env), 1, 0.02, 1e-3, p["LA"], p["LB"], p["mvA"], p["mvB"],
+                                 p["ZA"], p["ZB"], p["Lref0"], p["C"], p["counts"], p["ws"], 1 << 30, None)
+        assert st == evis.ERR_INVALID_ARG, key
+
+
 def test_voxel_workspace_size(evis):
     """Two uint64 per region (a row segment of 32 pixels across 256 planes), one uint32 entry
     per record, two once the planes of an environment span two groups (bins > 128)."""

@@ -220,6 +220,24 @@ def test_statistics_count_sources_that_cannot_splat(ev, scenes_mod):
     ctx.close()
 
 
+def test_misaligned_motion_vectors_are_rejected(ev, scenes_mod):
+    """mv is read as float pairs: a pointer 4 bytes off an 8-byte boundary returns
+    ERR_INVALID_ARG before any work, and the context steps on with aligned inputs."""
+    rng = np.random.default_rng(6)
+    envs = [TinyEnv(W=40, H=30, K=2)]
+    n = packed_total(envs)
+    L = _dev(rng.normal(0, 1, n).astype(np.float32))
+    mv = torch.zeros(2 * n + 1, dtype=torch.float32, device="cuda")
+    Z = _dev(rng.uniform(1, 5, n).astype(np.float32))
+    ctx = ev.Context(envs, flags=ev.IN_LOG, capacity=1 << 16)
+    ctx.step(L, mv[:2 * n], Z, 1_000_000)
+    st = ev.lib().evis_step(ctx.handle, L.data_ptr(), mv.data_ptr() + 4, Z.data_ptr(), 1_000_000)
+    assert st == ev.ERR_INVALID_ARG
+    ctx.step(L, mv[:2 * n], Z, 1_000_000)
+    assert ctx.stats()["gaps"] == 1
+    ctx.close()
+
+
 def test_wild_motion_overflows_candidate_lists(ev, oracle_mod):
     """Motion of up to +-300 px in every row segment: each tile's list of candidate source
     segments overflows and the kernel scans its whole source region instead."""
