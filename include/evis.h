@@ -289,7 +289,7 @@ evis_status evis_set_defocus(evis_ctx *ctx, const float *sigma_px);
 
 /* The defocus of one image alone: in is [height][width] luminance (mode EVIS_IN_LUM) or
  * [height][width][3] linear RGB (EVIS_IN_RGB); out is the blurred luminance [height][width].
- * Device pointers; asynchronous on stream; sizes as for an environment. */
+ * Device pointers (4-byte aligned); asynchronous on stream; sizes as for an environment. */
 evis_status evis_defocus(const float *in, int32_t width, int32_t height, uint32_t mode,
                          float sigma_px, float *out, evis_stream_t stream);
 
@@ -342,7 +342,7 @@ evis_status evis_step_trace(evis_ctx *ctx, const float *frames, const float *mv,
 
 /* Log-intensity of n samples (Sec. 3.2, Eq. 3): mode EVIS_IN_LUM reads n floats, EVIS_IN_RGB
  * n RGB triplets; out[i] = log(I + eps) (non-positive arguments clamp to the smallest
- * normal float).  Device pointers, enqueued on stream. */
+ * normal float).  Device pointers (4-byte aligned), enqueued on stream. */
 evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float eps, float *out,
                                evis_stream_t stream);
 

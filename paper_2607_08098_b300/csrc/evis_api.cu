@@ -744,7 +744,7 @@ evis_status evis_set_state(evis_ctx *c, const float *Lref, const int64_t *t_last
 evis_status evis_log_intensity(const float *in, int64_t n, uint32_t mode, float eps, float *out,
                                evis_stream_t stream) {
   if (n < 0 || (n > 0 && (!in || !out)) || (mode != EVIS_IN_LUM && mode != EVIS_IN_RGB) ||
-      !std::isfinite(eps) || eps < 0.0f)
+      !std::isfinite(eps) || eps < 0.0f || !evis::aligned(in, 4) || !evis::aligned(out, 4))
     return EVIS_ERR_INVALID_ARG;
   cudaError_t e = evis::launch_log(in, n, mode, eps, out, reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? EVIS_OK : EVIS_ERR_CUDA;
@@ -771,7 +771,7 @@ evis_status evis_defocus(const float *in, int32_t width, int32_t height, uint32_
                          float sigma_px, float *out, evis_stream_t stream) {
   if (!in || !out || width < 1 || height < 1 || width > 65535 || height > 65535 ||
       int64_t(width) * height > (int64_t(1) << 24) || (mode != EVIS_IN_LUM && mode != EVIS_IN_RGB) ||
-      !defocus_sigma_ok(sigma_px))
+      !defocus_sigma_ok(sigma_px) || !evis::aligned(in, 4) || !evis::aligned(out, 4))
     return EVIS_ERR_INVALID_ARG;
   evis::BlurArgs ba{};
   ba.W = width;
