@@ -118,7 +118,8 @@ typedef struct {
                           * y - margin).  0 <= 2 * margin < min(width, height); 0 = none.
                           * Per-pixel arrays (state, threshold maps) stay rendered-frame sized. */
   const float *c_on_map; /* optional device [H*W] per-pixel thresholds (Eq. 8); both or */
-  const float *c_off_map;/* neither; caller-owned, read at every step, must outlive ctx */
+  const float *c_off_map;/* neither, 4-byte aligned; caller-owned, read at every step, must
+                          * outlive ctx */
   int64_t refractory_ns; /* 0 = off (Sec. 3.4) */
   int64_t t0_ns;         /* time of the first keyframe */
 } evis_env_desc;

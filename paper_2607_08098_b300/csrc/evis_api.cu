@@ -137,6 +137,8 @@ std::string validate(const evis_env_desc *envs, int32_t n, const evis_config *cf
     if (!finite_pos(d.c_on) || !finite_pos(d.c_off)) return p + "thresholds must be finite and > 0";
     if ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))
       return p + "give both threshold maps or neither";
+    if (!evis::aligned(d.c_on_map, 4) || !evis::aligned(d.c_off_map, 4))
+      return p + "threshold maps need 4-byte alignment";
     if (d.refractory_ns < 0) return p + "refractory_ns must be >= 0";
     if (d.margin < 0 || 2 * int64_t(d.margin) >= d.width || 2 * int64_t(d.margin) >= d.height)
       return p + "margin must satisfy 0 <= 2 * margin < min(width, height)";

@@ -104,6 +104,8 @@ extern "C" evis_status evis_step_noalloc(const evis_env_desc *env, uint32_t flag
   if (!finite_pos(d.c_on) || !finite_pos(d.c_off)) return reject("thresholds must be finite and > 0");
   if ((d.c_on_map == nullptr) != (d.c_off_map == nullptr))
     return reject("give both threshold maps or neither");
+  if (!evis::aligned(d.c_on_map, 4) || !evis::aligned(d.c_off_map, 4))
+    return reject("threshold maps need 4-byte alignment");
   if (d.refractory_ns < 0) return reject("refractory_ns must be >= 0");
   if (d.margin < 0 || 2 * int64_t(d.margin) >= d.width || 2 * int64_t(d.margin) >= d.height)
     return reject("margin must satisfy 0 <= 2 * margin < min(width, height)");

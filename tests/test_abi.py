@@ -57,7 +57,8 @@ def _desc(ev, **kw):
     dict(width=0), dict(height=70000), dict(width=8192, height=4096), dict(K=0), dict(K=5000),
     dict(c_on=0.0), dict(c_off=-1.0), dict(c_on=float("nan")), dict(c_off=float("inf")),
     dict(refractory_ns=-1), dict(c_on_map=1234), dict(margin=-1), dict(margin=16),
-    dict(width=8, margin=4),
+    dict(width=8, margin=4), dict(c_on_map=0x100002, c_off_map=0x200000),
+    dict(c_on_map=0x100000, c_off_map=0x200001),
 ])
 def test_create_rejects_bad_descriptors_before_cuda(evis, bad):
     L = evis.lib()
