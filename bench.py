@@ -344,28 +344,42 @@ def host_mem_available():
     return None
 
 
-def e2e_leg(ev, w, dev, n_steps, capacity, flags_host):
+def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1):
     """Host buffers in, events out, through the public API: pinned host keyframes copied by
     evis_step_host, every gap's events copied to pinned host memory by
     evis_read_events_async (while the next gap runs), all inside the timed region.  The
     copy of a gap completes before the next one starts, so one destination buffer serves.
     Six gaps by default: with two, filling and draining the pipeline (the first gap's input
-    copy and compute, the last gap's read-back) was a third of the time."""
+    copy and compute, the last gap's read-back) was a third of the time.  Each rank pins at
+    most 0.6 of the host's available memory divided by the number of ranks (so the ranks of
+    one host never pin more than 0.6 of it between them) and the ranks agree on the number
+    of gaps, or on skipping; under several ranks the figures are whole-job (the slowest
+    rank's time, work and bytes summed)."""
     import torch
-    n = n_steps
-    need = sum(t.numel() * 4 for t in dev[0]) * (n + 1) + capacity * 16
+    kf = sum(t.numel() * 4 for t in dev[0])
+    out_bytes = capacity * 16
     avail = host_mem_available()
-    if avail is not None and need > 0.6 * avail:
-        return {"skipped": f"needs {need / 2**30:.0f} GiB of pinned host memory, "
-                           f"{avail / 2**30:.0f} GiB available"}
+    n = n_steps
+    if avail is not None:
+        n = min(n, int((0.6 * avail / world - out_bytes) // kf) - 1)
+    n = max(n, 0)
+    if dist:
+        t = torch.tensor([n], device="cuda", dtype=torch.int64)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        n = int(t.item())
+    if n < 1:
+        return {"skipped": f"two keyframes ({2 * kf / 2**30:.0f} GiB) and the event buffer "
+                           f"({out_bytes / 2**30:.0f} GiB) of pinned host memory per rank do not "
+                           f"fit 0.6 of the {(avail or 0) / 2**30:.0f} GiB available over {world} ranks"}
     host = [tuple(t.cpu().pin_memory() for t in dev[k]) for k in range(n + 1)]
     out = torch.empty(capacity * 16, dtype=torch.uint8).pin_memory()
-    h2d = sum(t.numel() * 4 for t in host[0])
     cnt = ctypes.c_int64()
     L = ev.lib()
     ctx = ev.Context(w.envs, eps=1e-4, flags=flags_host, capacity=capacity)
     ctx.step_host(*host[0], w.dt_ns)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     d2h = 0
     t0 = time.perf_counter()
     for k in range(1, n + 1):
@@ -376,11 +390,14 @@ def e2e_leg(ev, w, dev, n_steps, capacity, flags_host):
         d2h += cnt.value * 16 + 16
     ctx.read_wait()
     torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
+    ms = (time.perf_counter() - t0) * 1e3
     ctx.close()
     del host, out
-    return {"value": w.pixel_substeps * n / sec / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h // n, "steps": n,
+    units = w.pixel_substeps * n
+    if dist:
+        ms, units, d2h = reduce_over_ranks(ms, units, d2h, "cuda")
+    return {"value": units / (ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": kf * world,
+            "d2h_bytes_per_step": int(d2h) // n, "steps": n,
             "path": "evis_step_host (pinned host keyframe -> device) + evis_read_events_async "
                     "(every event -> pinned host, copied while the next gap runs), host wall "
                     "clock over the steps"}
@@ -569,7 +586,9 @@ def headline_arm(args, world, rank, local):
     torch.cuda.empty_cache()
     e2e = None
     if args.e2e_steps > 0:
-        e2e = e2e_leg(ev, w, dev, args.e2e_steps, r["capacity"], ev.IN_LOG)
+        # the read-back empties the buffer every gap: room for the largest gap seen, and more
+        cap_e2e = min(r["capacity"], int(1.3 * max(r["events"])) + 4096)
+        e2e = e2e_leg(ev, w, dev, args.e2e_steps, cap_e2e, ev.IN_LOG, dist, world)
     cpu = cpu_par = parity = None
     if world == 1 and not args.no_cpu_baseline:
         n = len(w.envs)

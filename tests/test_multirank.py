@@ -46,3 +46,29 @@ def test_two_rank_sharding_and_reduction():
         assert not set(a) & set(b)              # disjoint scenes per rank
     assert t0 == t1 == 11.0                     # slowest rank's time
     assert u0 == u1 == 3000 and e0 == e1 == 14  # work summed over ranks
+
+
+def test_e2e_leg_stays_inside_its_share_of_host_memory(monkeypatch):
+    """The end-to-end leg pins at most 0.6 of the host's available memory divided by the
+    ranks: when two keyframes and the event buffer do not fit that share it reports why and
+    pins nothing (no CUDA call is made on that path)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    gib = 1 << 30
+    monkeypatch.setattr(bench, "host_mem_available", lambda: 100 * gib)
+
+    class Plane:                      # the leg reads only the element count of a keyframe
+        def __init__(self, n):
+            self.n = n
+
+        def numel(self):
+            return self.n
+
+    kf = (Plane(gib // 4), Plane(2 * gib // 4), Plane(2 * gib // 4))   # 5 GiB of float32
+    dev = [kf] * 7
+    capacity = 10 * gib // 16                                       # a 10 GiB event buffer
+    out = bench.e2e_leg(None, None, dev, 6, capacity, 0, dist=None, world=8)   # 7.5 GiB share
+    assert "skipped" in out
+    out = bench.e2e_leg(None, None, dev, 6, capacity, 0, dist=None, world=4)   # 15 GiB share: 0 gaps
+    assert "skipped" in out
