@@ -246,13 +246,15 @@ def roofline_block(envs, n_events_per_step, syn_ms, prep_ms, shapes, tuned_ms, w
 # device-timed keyframe gaps
 # ------------------------------------------------------------------------------------------
 
-def upload_keyframes(w, n_kf, frame_key):
-    """Renders keyframes 0..n_kf-1 (host) and keeps them on the device: (frames, mv, depth)."""
+def upload_keyframes(w, n_kf, frame_key, world=1):
+    """Renders keyframes 0..n_kf-1 (host) and keeps them on the device: (frames, mv, depth).
+    Under several ranks on one host each renders with its share of the host's cores."""
     import scenes
     import torch
+    threads = max(1, (os.cpu_count() or 1) // max(world, 1))
     dev = []
     for k in range(n_kf):
-        kf = scenes.render(w.envs, k, want=(frame_key, "mv", "Z"))
+        kf = scenes.render(w.envs, k, want=(frame_key, "mv", "Z"), threads=threads)
         dev.append(tuple(torch.from_numpy(np.ascontiguousarray(a).reshape(-1)).cuda()
                          for a in (getattr(kf, frame_key), kf.mv, kf.Z)))
         del kf
@@ -565,7 +567,7 @@ def headline_arm(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = highspeed_workload(args.hs_envs, rank)
     n_kf = max(args.warmup + args.steps + 1, 4)
-    dev = upload_keyframes(w, n_kf, "L")
+    dev = upload_keyframes(w, n_kf, "L", world)
     flags = ev.IN_LOG | ev.KEEP_INPUTS
     clocks = ClockSampler(local)            # sampled from the autotuner and warm-up on
     r = timed_gaps(ev, w, dev, flags, args.steps, args.warmup, dist=dist, tile=args.tile)
@@ -624,7 +626,7 @@ def config2_leg(ev, args, world=1, rank=0, dist=None):
     import torch
     w = config2_workload(args.envs, rank)
     steps = args.steps
-    dev = upload_keyframes(w, args.warmup + steps + 1, "I")
+    dev = upload_keyframes(w, args.warmup + steps + 1, "I", world)
     clocks = ClockSampler(torch.cuda.current_device())
     r = timed_gaps(ev, w, dev, ev.IN_LUM | ev.KEEP_INPUTS, steps, args.warmup, dist=dist,
                    reps_autotune=2, tile=args.tile)
