@@ -4,8 +4,8 @@
 Headline workload (default): the high-speed batch, the largest configuration that fits one
 GPU.  1024 environments at 640x480, K = 32 sub-frames per keyframe gap (8 ms), C = 0.15, five
 depth layers of seeded textured disks moving up to 40 px per keyframe (about 10 % of the
-target-sub-frames are disocclusion holes of one warp direction), fp32 log-intensity inputs,
-no refractory period.  Synthetic scenes, no dataset.
+target-sub-frames have a disocclusion hole in one warp direction or the other; the line's
+`holes` key measures it), fp32 log-intensity inputs, no refractory period.  Synthetic scenes, no dataset.
 
 One step = one keyframe gap of every environment: the input-preparation kernel (motion
 bounds, per-source packs) and the synthesis kernel (bidirectional splat, z-buffer, blend,
@@ -92,7 +92,7 @@ def highspeed_workload(n_envs, rank=0):
 def highspeed_config(w, n_envs):
     e = w.envs[0]
     return {"workload": f"high-speed batch: {n_envs} envs at {e.W}x{e.H}, K={e.K}, C={e.c_on}, "
-                        "5 depth layers, flows up to 40 px per keyframe (~10 % holes), "
+                        "5 depth layers, flows up to 40 px per keyframe (~10 % of target-sub-frames with a hole in one direction), "
                         "log-intensity inputs, no refractory period",
             "envs": n_envs, "width": e.W, "height": e.H, "K": e.K, "C": e.c_on,
             "refractory_ns": 0, "dt_ns": w.dt_ns, "input": "log intensity, fp32",
@@ -346,6 +346,27 @@ def host_mem_available():
     return None
 
 
+def hole_fraction_leg(ev, w, dev, n_sample=16, gaps=2):
+    """Disocclusion holes of the workload (Sec. 3.3, the blend's hole filling): the first
+    n_sample environments over `gaps` keyframe gaps in a context with EVIS_STATS, as fractions
+    of their target-sub-frames with no source of A, of B, of both, and of at least one."""
+    import torch
+    n_px = sum(e.H * e.W for e in w.envs[:n_sample])   # equal sizes: no packing pads between
+    ctx = ev.Context(w.envs[:n_sample], flags=ev.IN_LOG | ev.KEEP_INPUTS | ev.STATS,
+                     capacity=1 << 27)
+    for k in range(gaps + 1):
+        L, mv, Z = dev[k]
+        ctx.step(L[:n_px], mv[:2 * n_px], Z[:n_px], w.dt_ns)
+    st = ctx.env_stats()
+    ctx.close()
+    torch.cuda.synchronize()
+    tot = float(st["target_subframes"].sum())
+    a, b, both = (float(st[f].sum()) for f in ("holes_a", "holes_b", "holes_both"))
+    return {"sample": f"environments 0-{n_sample - 1}, {gaps} keyframe gaps",
+            "target_subframes": int(tot), "no_source_of_A": a / tot, "no_source_of_B": b / tot,
+            "no_source_of_either": both / tot, "at_least_one_direction": (a + b - both) / tot}
+
+
 def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1):
     """Host buffers in, events out, through the public API: pinned host keyframes copied by
     evis_step_host, every gap's events copied to pinned host memory by
@@ -583,6 +604,7 @@ def headline_arm(args, world, rank, local):
                           r["shapes"], r["tuned_ms"], "highspeed_1024x640x480_K32"
                           if args.hs_envs == 1024 else f"highspeed_{args.hs_envs}x640x480_K32",
                           clk, sms)
+    holes = hole_fraction_leg(ev, w, dev) if rank == 0 else None
     keep = max(4, args.e2e_steps + 1)
     del dev[keep:]                          # the legs below need the first keyframes only
     torch.cuda.empty_cache()
@@ -611,7 +633,7 @@ def headline_arm(args, world, rank, local):
             "events_per_step": n_events / args.steps / max(world, 1), "step_ms": r["step_ms"],
             "wall_s": r["wall_s"], "roofline": roof, "cpu_baseline": cpu,
             "cpu_baseline_parallel": cpu_par, "parity": parity, "e2e": e2e,
-            "gpu_launches": 2 * args.steps, "clocks": clk,
+            "gpu_launches": 2 * args.steps, "clocks": clk, "holes": holes,
             "parallelism": f"env shards x{world}, no collective on the data path"}
     if world == 1 and not args.no_extras:
         line["config2"] = config2_leg(ev, args)

@@ -281,7 +281,8 @@ def config4(n_envs: int = 1024, W: int = 640, H: int = 480, first_env: int = 0) 
     """High-speed: 640x480, K=32, flows up to 40 px/frame, five depth layers, C=0.15.
 
     Disks of radius 0.2-0.4 x 480 moving up to 40 px/frame leave about 10 % of the
-    pixel-substeps without a source in one warp direction (disocclusion holes); textures are
+    pixel-substeps without a source in one warp direction or the other (5-8 % in each,
+    measured on environments 0, 511 and 1023: disocclusion holes); textures are
     smoother (64 px cells, sigma 0.3) so that the output stays event-dense but bounded
     (about 0.11 events per pixel-substep).  ``first_env`` shifts the seeds (environment e
     uses seed index first_env + e)."""
