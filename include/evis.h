@@ -208,9 +208,9 @@ evis_status evis_get_state(evis_ctx *ctx, float *Lref, int64_t *t_last, int64_t 
 evis_status evis_get_stats(evis_ctx *ctx, uint64_t *keyframes, uint64_t *gaps,
                            uint64_t *invalid_sources);
 
-/* Per-environment statistics since creation (the survey's counters: event count, ON/OFF
- * split, hole fraction per warp direction; Sec. 3.3 fills the holes of one direction from
- * the other).  A target-sub-frame is one sensor pixel at one sub-frame i = 1..K. */
+/* Per-environment statistics since creation (event count, ON/OFF split, hole fraction per
+ * warp direction; Sec. 3.3 fills the holes of one direction from the other).  A
+ * target-sub-frame is one sensor pixel at one sub-frame i = 1..K. */
 typedef struct {
   uint64_t target_subframes; /* sensor pixels x K x keyframe gaps synthesised */
   uint64_t holes_a;          /* target-sub-frames that no source of A (forward warp) reached */

@@ -1,6 +1,6 @@
 """Pins of the oracle's soft event-count surrogate (CPU, binary64).
 
-The surrogate is this build's own definition (the paper has no backward): frozen discrete
+The surrogate is defined here (the paper has no backward pass): frozen discrete
 decisions, a normalised bilinear splat over the winning surface, and sigmoid counts.  Its
 analytic gradient is checked against central finite differences with the decisions frozen,
 and the zero-motion case against its closed form."""
