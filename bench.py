@@ -61,6 +61,9 @@ def parse():
                     help="environments of the high-speed workload (640x480, K=32)")
     ap.add_argument("--envs", type=int, default=64, help="environments of the 346x260 workload")
     ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-slices", type=int, default=4,
+                    help="contexts (one stream each) the end-to-end leg splits the "
+                         "environments into")
     ap.add_argument("--tile", default=None,
                     help="WxH: fixed tile shape instead of the autotuner's (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -367,20 +370,81 @@ def hole_fraction_leg(ev, w, dev, n_sample=16, gaps=2):
             "no_source_of_either": both / tot, "at_least_one_direction": (a + b - both) / tot}
 
 
-def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1):
+def link_rates(nbytes=1 << 30, reps=3):
+    """Host<->device copy rates of this GPU's link with pinned host memory (GB/s, best of
+    reps): host to device alone, device to host alone, and both at once on two streams
+    (their sum)."""
+    import torch
+    d0 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d1 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h0 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h1 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    s0, s1 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def best(fn):
+        t = float("inf")
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            t = min(t, time.perf_counter() - t0)
+        return t
+
+    def both():
+        with torch.cuda.stream(s0):
+            d0.copy_(h0, non_blocking=True)
+        with torch.cuda.stream(s1):
+            h1.copy_(d1, non_blocking=True)
+
+    out = {"h2d_gbs": nbytes / best(lambda: d0.copy_(h0, non_blocking=True)) / 1e9,
+           "d2h_gbs": nbytes / best(lambda: h1.copy_(d1, non_blocking=True)) / 1e9,
+           "both_gbs": 2 * nbytes / best(both) / 1e9}
+    del d0, d1, h0, h1
+    torch.cuda.empty_cache()
+    return out
+
+
+def link_floor_ms(h2d_bytes, d2h_bytes, rates):
+    """Least time the link needs for one step's copies: each direction at most at its own
+    rate, both together at most at their summed rate."""
+    return 1e3 * max(h2d_bytes / (rates["h2d_gbs"] * 1e9), d2h_bytes / (rates["d2h_gbs"] * 1e9),
+                     (h2d_bytes + d2h_bytes) / (rates["both_gbs"] * 1e9))
+
+
+def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1, shapes=None,
+            slices=4):
     """Host buffers in, events out, through the public API: pinned host keyframes copied by
     evis_step_host, every gap's events copied to pinned host memory by
-    evis_read_events_async (while the next gap runs), all inside the timed region.  The
-    copy of a gap completes before the next one starts, so one destination buffer serves.
+    evis_read_events_async, all inside the timed region.
+
+    The environments are split into `slices` contexts, each on its own stream with its own
+    event buffers.  A context's synthesis launch is persistent (one wave of resident CTAs),
+    so the slices' launches take the GPU in turn.  As soon as a slice is done, the read-back
+    of its events starts and its next gap is enqueued: both copies run while the later
+    slices compute, and the next gap's launch is ready when they finish.  In one context the
+    whole gap's read-back waited for its last tile, and the next keyframe's copy for the
+    read-back.  The copy of a slice's gap completes before that slice's next read-back
+    starts, so one destination buffer per slice serves.
+
     Six gaps by default: with two, filling and draining the pipeline (the first gap's input
     copy and compute, the last gap's read-back) was a third of the time.  Each rank pins at
     most 0.6 of the host's available memory divided by the number of ranks (so the ranks of
     one host never pin more than 0.6 of it between them) and the ranks agree on the number
     of gaps, or on skipping; under several ranks the figures are whole-job (the slowest
-    rank's time, work and bytes summed)."""
+    rank's time, work and bytes summed).  The contexts take the tile shapes of the timed
+    leg (per resolution class); the host link's copy rates, measured beside it, give the
+    least time per step that the step's copies need."""
     import torch
     kf = sum(t.numel() * 4 for t in dev[0])
-    out_bytes = capacity * 16
+    n_env = len(w.envs) if w is not None else 1
+    S = max(1, min(slices, n_env))
+    cut = [n_env * q // S for q in range(S + 1)]
+    # each slice's buffer: its share of the whole launch's capacity, with a margin for an
+    # uneven split of the events
+    margin = 1.2 if S > 1 else 1.0
+    cap = [int(capacity * (cut[q + 1] - cut[q]) / n_env * margin) + 4096 for q in range(S)]
+    out_bytes = sum(cap) * 16
     avail = host_mem_available()
     n = n_steps
     if avail is not None:
@@ -391,39 +455,71 @@ def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1):
         dist.all_reduce(t, op=dist.ReduceOp.MIN)
         n = int(t.item())
     if n < 1:
-        return {"skipped": f"two keyframes ({2 * kf / 2**30:.0f} GiB) and the event buffer "
+        return {"skipped": f"two keyframes ({2 * kf / 2**30:.0f} GiB) and the event buffers "
                            f"({out_bytes / 2**30:.0f} GiB) of pinned host memory per rank do not "
                            f"fit 0.6 of the {(avail or 0) / 2**30:.0f} GiB available over {world} ranks"}
+    px = np.cumsum([0] + [e.W * e.H for e in w.envs])
+    total = int(px[-1])
     host = [tuple(t.cpu().pin_memory() for t in dev[k]) for k in range(n + 1)]
-    out = torch.empty(capacity * 16, dtype=torch.uint8).pin_memory()
+
+    def part(k, q):   # slice q of keyframe k: views of the packed host planes
+        lo, hi = int(px[cut[q]]), int(px[cut[q + 1]])
+        return tuple(t[lo * (t.numel() // total):hi * (t.numel() // total)] for t in host[k])
+
+    outs = [torch.empty(c * 16, dtype=torch.uint8).pin_memory() for c in cap]
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    ctxs = [ev.Context(w.envs[cut[q]:cut[q + 1]], eps=1e-4, flags=flags_host, capacity=cap[q],
+                       stream=streams[q]) for q in range(S)]
     cnt = ctypes.c_int64()
     L = ev.lib()
-    ctx = ev.Context(w.envs, eps=1e-4, flags=flags_host, capacity=capacity)
-    ctx.step_host(*host[0], w.dt_ns)
+    for q, ctx in enumerate(ctxs):
+        if shapes:
+            ctx.set_env_tile_shapes([tuple(int(v) for v in shapes[f"{e.W}x{e.H}"].split("x"))
+                                     for e in w.envs[cut[q]:cut[q + 1]]])
+        ctx.step_host(*part(0, q), w.dt_ns)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     d2h = 0
     t0 = time.perf_counter()
+    for q, ctx in enumerate(ctxs):
+        ctx.step_host(*part(1, q), w.dt_ns)
     for k in range(1, n + 1):
-        ctx.step_host(*host[k], w.dt_ns)
-        st = L.evis_read_events_async(ctx.handle, out.data_ptr(), capacity, ctypes.byref(cnt))
-        if st != ev.OK:
-            raise RuntimeError(f"event read-back: {ev.status_string(st)}")
-        d2h += cnt.value * 16 + 16
-    ctx.read_wait()
+        for q, ctx in enumerate(ctxs):
+            # slice q's gap k is done: its read-back starts, and its next gap is enqueued
+            # (the input copy then runs while the other slices compute)
+            st = L.evis_read_events_async(ctx.handle, outs[q].data_ptr(), cap[q], ctypes.byref(cnt))
+            if st != ev.OK:
+                raise RuntimeError(f"event read-back: {ev.status_string(st)}")
+            d2h += cnt.value * 16 + 16
+            if k < n:
+                ctx.step_host(*part(k + 1, q), w.dt_ns)
+    for ctx in ctxs:
+        ctx.read_wait()
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3
-    ctx.close()
-    del host, out
+    for ctx in ctxs:
+        ctx.close()
+    del host, outs
+    torch.cuda.empty_cache()
+    rates = link_rates()
+    floor = link_floor_ms(kf, d2h / n, rates)
     units = w.pixel_substeps * n
+    ms_rank = ms
     if dist:
         ms, units, d2h = reduce_over_ranks(ms, units, d2h, "cuda")
     return {"value": units / (ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": kf * world,
-            "d2h_bytes_per_step": int(d2h) // n, "steps": n,
-            "path": "evis_step_host (pinned host keyframe -> device) + evis_read_events_async "
-                    "(every event -> pinned host, copied while the next gap runs), host wall "
-                    "clock over the steps"}
+            "d2h_bytes_per_step": int(d2h) // n, "steps": n, "slices": S,
+            "link": dict({k: round(v, 2) for k, v in rates.items()},
+                         floor_ms_per_step=round(floor, 2), ms_per_step=round(ms_rank / n, 2),
+                         frac=round(floor / (ms_rank / n), 3),
+                         note="this rank's link, measured after the leg with 1 GiB pinned "
+                              "copies; floor = the step's copies alone at those rates"),
+            "path": f"{S} contexts over consecutive environment slices, one stream each: "
+                    "evis_step_host (pinned host keyframe -> device) + evis_read_events_async "
+                    "(every event -> pinned host, copied while the later slices and the next "
+                    "gap run); each slice's next gap enqueued as soon as its gap is done; host "
+                    "wall clock over the steps"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -612,7 +708,8 @@ def headline_arm(args, world, rank, local):
     if args.e2e_steps > 0:
         # the read-back empties the buffer every gap: room for the largest gap seen, and more
         cap_e2e = min(r["capacity"], int(1.3 * max(r["events"])) + 4096)
-        e2e = e2e_leg(ev, w, dev, args.e2e_steps, cap_e2e, ev.IN_LOG, dist, world)
+        e2e = e2e_leg(ev, w, dev, args.e2e_steps, cap_e2e, ev.IN_LOG, dist, world, r["shapes"],
+                      args.e2e_slices)
     cpu = cpu_par = parity = None
     if world == 1 and not args.no_cpu_baseline:
         n = len(w.envs)

@@ -78,3 +78,60 @@ def test_pipelined_readback_overflow(ev, scenes_mod):
     c.step(*dev[2], w.dt_ns)
     assert c.event_count() > cap   # counted from zero in the other buffer, beyond capacity again
     c.close()
+
+
+def test_slices_on_their_own_streams_match_one_context(ev, scenes_mod):
+    """Consecutive environment slices in separate contexts, each on its own stream, fed from
+    host buffers; as soon as a slice's gap is done its read-back starts and its next gap is
+    enqueued, while the other slices compute.  Every gap's records are those of one context
+    over all environments (with the slice's environment indices)."""
+    import ctypes
+    w, dev = _gaps(scenes_mod, 5)
+    cap = 1 << 22
+    a = ev.Context(w.envs, flags=ev.IN_LOG, capacity=cap)
+    want = []
+    for d in dev:
+        a.step(*d, w.dt_ns)
+        want.append(np.sort(a.read_events()))
+    a.close()
+    assert sum(len(x) for x in want) > 100_000
+    host = [tuple(t.cpu().pin_memory() for t in d) for d in dev]
+    px = [int(v) for v in np.cumsum([0] + [e.W * e.H for e in w.envs])]
+    cut = [0, 1, 3, 4]  # uneven slices: 1, 2 and 1 environments
+    S = len(cut) - 1
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    ctxs = [ev.Context(w.envs[cut[q]:cut[q + 1]], flags=ev.IN_LOG, capacity=cap, stream=streams[q])
+            for q in range(S)]
+    bufs = [[torch.empty(cap * 16, dtype=torch.uint8).pin_memory() for _ in range(2)]
+            for _ in range(S)]
+    counts = [[0] * len(dev) for _ in range(S)]
+    got = [[] for _ in dev]
+    n = ctypes.c_int64()
+
+    def part(k, q):
+        lo, hi = px[cut[q]], px[cut[q + 1]]
+        return tuple(t[lo * (t.numel() // px[-1]):hi * (t.numel() // px[-1])] for t in host[k])
+
+    def collect(q, k):  # slice q's copy of gap k is complete
+        r = bufs[q][k % 2].numpy().view(ev.EVENT_DTYPE)[:counts[q][k]].copy()
+        r["env"] += cut[q]
+        got[k].append(r)
+
+    for q, c in enumerate(ctxs):
+        c.step_host(*part(0, q), w.dt_ns)
+    for k in range(len(dev)):
+        for q, c in enumerate(ctxs):
+            assert ev.lib().evis_read_events_async(c.handle, bufs[q][k % 2].data_ptr(), cap,
+                                                   ctypes.byref(n)) == ev.OK
+            counts[q][k] = n.value
+            if k > 0:
+                collect(q, k - 1)
+            if k + 1 < len(dev):
+                c.step_host(*part(k + 1, q), w.dt_ns)
+    for q, c in enumerate(ctxs):
+        c.read_wait()
+        collect(q, len(dev) - 1)
+    for k in range(len(dev)):
+        np.testing.assert_array_equal(np.sort(np.concatenate(got[k])), want[k])
+    for c in ctxs:
+        c.close()

@@ -72,3 +72,16 @@ def test_e2e_leg_stays_inside_its_share_of_host_memory(monkeypatch):
     assert "skipped" in out
     out = bench.e2e_leg(None, None, dev, 6, capacity, 0, dist=None, world=4)   # 15 GiB share: 0 gaps
     assert "skipped" in out
+
+
+def test_link_floor_takes_the_slowest_bound():
+    """The end-to-end leg's link floor: each direction at its own rate, both together at
+    their summed rate (5 GB up and 15 GB down at 50 / 50 / 75 GB/s: the way down alone,
+    0.3 s; 15 GB each way: the shared rate, 0.4 s)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    r = {"h2d_gbs": 50.0, "d2h_gbs": 50.0, "both_gbs": 75.0}
+    assert abs(bench.link_floor_ms(5e9, 15e9, r) - 300.0) < 1e-9
+    assert abs(bench.link_floor_ms(15e9, 15e9, r) - 400.0) < 1e-9
+    assert abs(bench.link_floor_ms(0, 0, r)) == 0.0
