@@ -441,9 +441,14 @@ def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1, shape
     S = max(1, min(slices, n_env))
     cut = [n_env * q // S for q in range(S + 1)]
     # each slice's buffer: its share of the whole launch's capacity, with a margin for an
-    # uneven split of the events
-    margin = 1.2 if S > 1 else 1.0
-    cap = [int(capacity * (cut[q + 1] - cut[q]) / n_env * margin) + 4096 for q in range(S)]
+    # uneven split of the events that grows as the slice holds fewer environments (their
+    # event counts differ from scene to scene), and never more than the whole capacity
+    def slice_cap(m):
+        if S == 1:
+            return capacity
+        return min(capacity, int(capacity * m / n_env * (1.2 + 2.0 / m ** 0.5)) + 4096)
+
+    cap = [slice_cap(cut[q + 1] - cut[q]) for q in range(S)]
     out_bytes = sum(cap) * 16
     avail = host_mem_available()
     n = n_steps
