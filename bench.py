@@ -755,6 +755,11 @@ def config2_leg(ev, args, world=1, rank=0, dist=None):
     r = timed_gaps(ev, w, dev, ev.IN_LUM | ev.KEEP_INPUTS, steps, args.warmup, dist=dist,
                    reps_autotune=2, tile=args.tile)
     clk = clocks.stop()
+    e2e = None
+    if args.e2e_steps > 0:  # the same sliced host pipeline as the headline's
+        cap_e2e = min(r["capacity"], int(1.3 * max(r["events"])) + 4096)
+        e2e = e2e_leg(ev, w, dev, args.e2e_steps, cap_e2e, ev.IN_LUM, dist, world, r["shapes"],
+                      args.e2e_slices)
     del dev
     torch.cuda.empty_cache()
     total_ms = float(sum(r["step_ms"]))
@@ -766,7 +771,7 @@ def config2_leg(ev, args, world=1, rank=0, dist=None):
            "roofline": roofline_block(w.envs, sum(r["events"]) / steps, r["syn_ms"], r["prep_ms"],
                                       r["shapes"], r["tuned_ms"], f"config2_{args.envs}x346x260_K16",
                                       clk, sms),
-           "clocks": clk}
+           "clocks": clk, "e2e": e2e}
     return out
 
 
