@@ -412,6 +412,32 @@ def link_floor_ms(h2d_bytes, d2h_bytes, rates):
                      (h2d_bytes + d2h_bytes) / (rates["both_gbs"] * 1e9))
 
 
+def slice_plan(n_env, slices, capacity):
+    """Consecutive environment slices for the end-to-end leg: the cut points (slice q holds
+    environments cut[q] .. cut[q+1]-1) and each slice's event capacity.  A slice's buffer is
+    its share of the whole launch's capacity with a margin for an uneven split of the events,
+    growing as the slice holds fewer environments (their counts differ from scene to scene),
+    and never more than the whole capacity."""
+    S = max(1, min(slices, n_env))
+    cut = [n_env * q // S for q in range(S + 1)]
+    if S == 1:
+        return cut, [capacity]
+    caps = []
+    for q in range(S):
+        m = cut[q + 1] - cut[q]
+        caps.append(min(capacity, int(capacity * m / n_env * (1.2 + 2.0 / m ** 0.5)) + 4096))
+    return cut, caps
+
+
+def slice_planes(planes, px, lo_env, hi_env):
+    """Views of packed per-pixel planes (each a flat array of total pixels x its per-pixel
+    width, px the pixel prefix sums over environments) restricted to environments
+    lo_env .. hi_env-1."""
+    total = int(px[-1])
+    lo, hi = int(px[lo_env]), int(px[hi_env])
+    return tuple(t[lo * (t.numel() // total):hi * (t.numel() // total)] for t in planes)
+
+
 def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1, shapes=None,
             slices=4):
     """Host buffers in, events out, through the public API: pinned host keyframes copied by
@@ -438,17 +464,8 @@ def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1, shape
     import torch
     kf = sum(t.numel() * 4 for t in dev[0])
     n_env = len(w.envs) if w is not None else 1
-    S = max(1, min(slices, n_env))
-    cut = [n_env * q // S for q in range(S + 1)]
-    # each slice's buffer: its share of the whole launch's capacity, with a margin for an
-    # uneven split of the events that grows as the slice holds fewer environments (their
-    # event counts differ from scene to scene), and never more than the whole capacity
-    def slice_cap(m):
-        if S == 1:
-            return capacity
-        return min(capacity, int(capacity * m / n_env * (1.2 + 2.0 / m ** 0.5)) + 4096)
-
-    cap = [slice_cap(cut[q + 1] - cut[q]) for q in range(S)]
+    cut, cap = slice_plan(n_env, slices, capacity)
+    S = len(cap)
     out_bytes = sum(cap) * 16
     avail = host_mem_available()
     n = n_steps
@@ -464,12 +481,10 @@ def e2e_leg(ev, w, dev, n_steps, capacity, flags_host, dist=None, world=1, shape
                            f"({out_bytes / 2**30:.0f} GiB) of pinned host memory per rank do not "
                            f"fit 0.6 of the {(avail or 0) / 2**30:.0f} GiB available over {world} ranks"}
     px = np.cumsum([0] + [e.W * e.H for e in w.envs])
-    total = int(px[-1])
     host = [tuple(t.cpu().pin_memory() for t in dev[k]) for k in range(n + 1)]
 
     def part(k, q):   # slice q of keyframe k: views of the packed host planes
-        lo, hi = int(px[cut[q]]), int(px[cut[q + 1]])
-        return tuple(t[lo * (t.numel() // total):hi * (t.numel() // total)] for t in host[k])
+        return slice_planes(host[k], px, cut[q], cut[q + 1])
 
     outs = [torch.empty(c * 16, dtype=torch.uint8).pin_memory() for c in cap]
     streams = [torch.cuda.Stream() for _ in range(S)]

@@ -85,3 +85,29 @@ def test_link_floor_takes_the_slowest_bound():
     assert abs(bench.link_floor_ms(5e9, 15e9, r) - 300.0) < 1e-9
     assert abs(bench.link_floor_ms(15e9, 15e9, r) - 400.0) < 1e-9
     assert abs(bench.link_floor_ms(0, 0, r)) == 0.0
+
+
+def test_e2e_slices_cover_every_environment_once():
+    """The end-to-end leg's slices: consecutive, covering every environment once, each
+    buffer at least its share of the capacity (with a margin that grows as slices shrink) and
+    at most the whole; the planes' views of a slice hold exactly its environments' pixels."""
+    import sys
+    import numpy as np
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    for n_env, S in ((1024, 4), (16, 4), (3, 4), (1, 4), (7, 1)):
+        cut, caps = bench.slice_plan(n_env, S, 1_000_000)
+        assert cut[0] == 0 and cut[-1] == n_env and len(caps) == len(cut) - 1 == min(S, n_env)
+        assert all(cut[q] < cut[q + 1] for q in range(len(caps)))
+        for q, c in enumerate(caps):
+            share = 1_000_000 * (cut[q + 1] - cut[q]) / n_env
+            assert (c >= 1.2 * share or c == 1_000_000) and c <= 1_000_000
+    # three environments of 2, 3 and 4 pixels; planes of 1 and 2 values per pixel
+    px = np.cumsum([0, 2, 3, 4])
+    L = torch.arange(9, dtype=torch.float32)
+    mv = torch.arange(18, dtype=torch.float32)
+    a, b = bench.slice_planes((L, mv), px, 1, 3)
+    assert a.tolist() == [2, 3, 4, 5, 6, 7, 8] and b.tolist() == list(range(4, 18))
+    a, b = bench.slice_planes((L, mv), px, 0, 1)
+    assert a.tolist() == [0, 1] and b.tolist() == [0, 1, 2, 3]
