@@ -158,7 +158,10 @@ evis_status evis_step_host(evis_ctx *ctx, const float *frames, const float *mv,
                            const float *depth, int64_t dt_ns);
 
 /* Synchronises the stream, copies the buffered events (in no particular order) to dst
- * (host or device, up to cap events), empties the buffer and clears latched errors.
+ * (host or device, up to cap events), empties the buffer and clears latched errors.  The
+ * reads (this one, evis_read_events_async and evis_event_count) wait for the context's own
+ * stream only: their copies run on it, so work of other contexts on other streams, blocking
+ * or not, keeps running.
  * *n_out = number of events produced since the last read.  Returns EVIS_ERR_RANGE when
  * some pixel-sub-frame since the last read exceeded the crossing limit (see the
  * conventions above; the events are delivered as usual), else EVIS_ERR_OVERFLOW when the

@@ -556,18 +556,29 @@ static evis_status read_status(const evis_ctx *c, const unsigned long long cnt[2
   return (produced > c->cfg.event_capacity || produced > cap) ? EVIS_ERR_OVERFLOW : EVIS_OK;
 }
 
+// The two counter words, copied on the context's own stream once it is idle.  A copy on the
+// legacy default stream would also wait for every blocking stream of the device, such as
+// other contexts' steps, and so serialise contexts that overlap on their own streams.
+static cudaError_t read_counter(evis_ctx *c, unsigned long long cnt[2]) {
+  cudaError_t e = cudaMemcpyAsync(cnt, c->d_count, 2 * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e;
+}
+
 evis_status evis_read_events(evis_ctx *c, evis_event *dst, int64_t cap, int64_t *n_out) {
   if (!c || !n_out || cap < 0 || (cap > 0 && !dst)) return EVIS_ERR_INVALID_ARG;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "read sync");
   unsigned long long cnt[2] = {0, 0};
-  if ((e = cudaMemcpy(cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return cuda_fail(c, e, "read count");
+  if ((e = read_counter(c, cnt)) != cudaSuccess) return cuda_fail(c, e, "read count");
   const int64_t produced = static_cast<int64_t>(cnt[0]);
   const int64_t n = std::min<int64_t>(produced, std::min<int64_t>(c->cfg.event_capacity, cap));
-  if (n > 0 && (e = cudaMemcpy(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault)) != cudaSuccess)
+  if (n > 0 && (e = cudaMemcpyAsync(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault,
+                                    c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "copy events");
-  if ((e = cudaMemset(c->d_count, 0, 2 * sizeof(unsigned long long))) != cudaSuccess)
+  if ((e = cudaMemsetAsync(c->d_count, 0, 2 * sizeof(unsigned long long), c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "reset count");
   *n_out = produced;
   return read_status(c, cnt, cap);
@@ -598,8 +609,7 @@ evis_status evis_read_events_async(evis_ctx *c, evis_event *dst, int64_t cap, in
     c->copy_pending = false;
   }
   unsigned long long cnt[2] = {0, 0};
-  if ((e = cudaMemcpy(cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return cuda_fail(c, e, "read count");
+  if ((e = read_counter(c, cnt)) != cudaSuccess) return cuda_fail(c, e, "read count");
   const int64_t produced = static_cast<int64_t>(cnt[0]);
   const int64_t n = std::min<int64_t>(produced, std::min<int64_t>(c->cfg.event_capacity, cap));
   if (n > 0 && (e = cudaMemcpyAsync(dst, c->d_events, sizeof(evis_event) * n, cudaMemcpyDefault,
@@ -634,8 +644,7 @@ evis_status evis_event_count(evis_ctx *c, int64_t *n_out) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "count sync");
   unsigned long long cnt[2] = {0, 0};
-  if ((e = cudaMemcpy(cnt, c->d_count, sizeof cnt, cudaMemcpyDeviceToHost)) != cudaSuccess)
-    return cuda_fail(c, e, "read count");
+  if ((e = read_counter(c, cnt)) != cudaSuccess) return cuda_fail(c, e, "read count");
   *n_out = static_cast<int64_t>(cnt[0]);
   return read_status(c, cnt, INT64_MAX);
 }

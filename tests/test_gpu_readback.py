@@ -135,3 +135,40 @@ def test_slices_on_their_own_streams_match_one_context(ev, scenes_mod):
         np.testing.assert_array_equal(np.sort(np.concatenate(got[k])), want[k])
     for c in ctxs:
         c.close()
+
+
+def test_reads_do_not_wait_for_other_contexts_streams(ev, scenes_mod):
+    """A context's reads copy its counter on its own stream: reading an idle context returns
+    while another context's gaps still run on a blocking stream of the same device (a copy on
+    the legacy default stream would wait for them)."""
+    rt = pytest.importorskip("cuda.bindings.runtime")
+    w = scenes_mod.config4(n_envs=16)
+    kfs = [scenes_mod.render(w.envs, k, want=("L", "mv", "Z")) for k in range(6)]
+    dev = [tuple(torch.from_numpy(np.ascontiguousarray(getattr(kf, a)).reshape(-1)).cuda()
+                 for a in ("L", "mv", "Z")) for kf in kfs]
+    handles = []
+    for _ in range(2):
+        err, s = rt.cudaStreamCreateWithFlags(0)   # blocking streams
+        assert int(err) == 0
+        handles.append(s)
+    sa, sb = (torch.cuda.ExternalStream(int(s)) for s in handles)
+    a = ev.Context(w.envs, flags=ev.IN_LOG | ev.KEEP_INPUTS, capacity=1 << 25, stream=sa)
+    b = ev.Context(w.envs[:1], flags=ev.IN_LOG | ev.KEEP_INPUTS, capacity=1 << 20, stream=sb)
+    first = tuple(t[:w.envs[0].W * w.envs[0].H * (t.numel() // sum(e.W * e.H for e in w.envs))]
+                  for t in dev[0])
+    b.step(*first, w.dt_ns)
+    a.step(*dev[0], w.dt_ns)
+    a.step(*dev[1], w.dt_ns)                     # every allocation made, nothing pending
+    a.event_count()
+    b.event_count()
+    torch.cuda.synchronize()
+    for d in dev[2:]:                            # several gaps queued on a's stream
+        a.step(*d, w.dt_ns)
+    assert b.event_count() == 0                  # b's own counter, read while a runs
+    busy = int(rt.cudaStreamQuery(handles[0])[0]) != 0
+    torch.cuda.synchronize()
+    a.close()
+    b.close()
+    for s in handles:
+        rt.cudaStreamDestroy(s)
+    assert busy, "the read waited for another context's stream"
