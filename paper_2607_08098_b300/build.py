@@ -12,6 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libevis.so")
+MANIFEST = LIB + ".sources"   # the translation units of the last link, one name per line
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no fused multiply-add contraction anywhere; every float operation of the
@@ -40,9 +41,19 @@ def _newest(paths) -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
+def _manifest() -> str:
+    return "".join(os.path.basename(s) + "\n" for s in sources())
+
+
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    """The library is out of date when a source or header is newer, or when the set of
+    translation units differs from the one it was linked from (a unit added or removed: a
+    removed one's kernels would otherwise stay in a library newer than every source)."""
+    if not os.path.exists(LIB) or not os.path.exists(MANIFEST):
         return True
+    with open(MANIFEST) as f:
+        if f.read() != _manifest():
+            return True
     return _newest(sources() + _headers()) > os.path.getmtime(LIB)
 
 
@@ -80,6 +91,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
+    with open(MANIFEST + ".tmp", "w") as f:
+        f.write(_manifest())
+    os.replace(MANIFEST + ".tmp", MANIFEST)
     return LIB
 
 

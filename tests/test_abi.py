@@ -181,3 +181,20 @@ def test_pipelined_readback_rejects_a_null_context_without_a_gpu(evis):
     n = ctypes.c_int64()
     assert L.evis_read_events_async(None, None, 0, ctypes.byref(n)) == evis.ERR_INVALID_ARG
     assert L.evis_read_wait(None) == evis.ERR_INVALID_ARG
+
+
+def test_build_relinks_when_the_units_change(evis, monkeypatch, tmp_path):
+    """The library counts as out of date when a translation unit is added or removed since
+    its link, even when it is newer than every source (a removed unit's kernels must not
+    stay in it)."""
+    from paper_2607_08098_b300 import build
+    assert not build._stale()                       # just built by the fixture
+    real = build.sources()
+    extra = tmp_path / "evis_extra.cu"
+    extra.write_text("")
+    monkeypatch.setattr(build, "sources", lambda: sorted(real + [str(extra)]))
+    assert build._stale()                           # a unit added
+    monkeypatch.setattr(build, "sources", lambda: real[:-1])
+    assert build._stale()                           # a unit removed
+    monkeypatch.setattr(build, "sources", lambda: real)
+    assert not build._stale()
